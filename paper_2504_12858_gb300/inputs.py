@@ -1,0 +1,210 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module holds input generation only: seed positions, orientations, thermal
+fields and parameter sets.  It contains none of the particle method's arithmetic
+(no growth law, no advance, no spawning, no contact search), so that both
+implementations can be fed identical inputs without sharing method code.
+
+Workloads (sizes and parameters follow the paper's benchmark families; every
+random draw comes from numpy's PCG64 with the stated seed):
+
+* ``single_grain``  - one grain at the centre of a 200 um cube, uniform
+  undercooling, v = A dT^2 (the octahedron check of Sec. 2.1.2 / Fig. 1).
+* ``columnar_slab`` - 50 seeds on the bottom face of a 1 mm x 1 mm x 50 um slab,
+  frozen-temperature field T = T_L + G z - Tdot t (competitive columnar growth,
+  the situation of Sec. 3.3 / 3.4).
+* ``weld_fixture``  - a 4 x 2 x 1 mm plate (half domain, y >= 0 from the weld
+  centre line), Rosenthal moving point source tabulated on a 512 x 256 x 128
+  FP32 grid in the frame of the source, 1e4 Voronoi seeds with random
+  orientations, each seeded as an octahedral shell (the laser-welding
+  application of Sec. 4.2, with an analytic field standing in for the CFD).
+* ``cet_runs``      - per-run parameters of an ensemble of cubes with columnar
+  bottom seeds and bulk nucleation sites (Sec. 3.5 family).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def shoemake_quaternions(n: int, g: np.random.Generator) -> np.ndarray:
+    """Uniformly distributed unit quaternions (w, x, y, z).
+
+    K. Shoemake, "Uniform random rotations", Graphics Gems III (1992): with
+    u1, u2, u3 ~ U[0, 1), q = (sqrt(1-u1) sin 2pi u2, sqrt(1-u1) cos 2pi u2,
+    sqrt(u1) sin 2pi u3, sqrt(u1) cos 2pi u3).
+    """
+    u = g.random((n, 3))
+    a = np.sqrt(1.0 - u[:, 0])
+    b = np.sqrt(u[:, 0])
+    t1 = 2.0 * math.pi * u[:, 1]
+    t2 = 2.0 * math.pi * u[:, 2]
+    q = np.stack([b * np.cos(t2), a * np.sin(t1), a * np.cos(t1), b * np.sin(t2)], axis=1)
+    return np.ascontiguousarray(q)
+
+
+def euler_zxz_to_quaternion(psi_deg: float, theta_deg: float, phi_deg: float) -> np.ndarray:
+    """Bunge (Z-X-Z) Euler angles in degrees -> unit quaternion (w, x, y, z).
+
+    The paper quotes orientations as Euler angles (psi, theta, phi) without a
+    convention; the Z-X-Z (Bunge) convention is the one taken here.
+    """
+    def qz(a):
+        return np.array([math.cos(a / 2), 0.0, 0.0, math.sin(a / 2)])
+
+    def qx(a):
+        return np.array([math.cos(a / 2), math.sin(a / 2), 0.0, 0.0])
+
+    def mul(p, q):
+        w1, x1, y1, z1 = p
+        w2, x2, y2, z2 = q
+        return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
+                         w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                         w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
+                         w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+    r = math.radians
+    return mul(mul(qz(r(psi_deg)), qx(r(theta_deg))), qz(r(phi_deg)))
+
+
+def truncated_normal(n: int, mean: float, sigma: float, lo: float, hi: float,
+                     g: np.random.Generator) -> np.ndarray:
+    """Normal(mean, sigma) draws restricted to [lo, hi] by rejection and redraw."""
+    out = np.empty(n)
+    filled = 0
+    while filled < n:
+        d = g.normal(mean, sigma, size=max(16, 2 * (n - filled)))
+        d = d[(d >= lo) & (d <= hi)]
+        take = min(d.size, n - filled)
+        out[filled:filled + take] = d[:take]
+        filled += take
+    return out
+
+
+@dataclass
+class Workload:
+    """Parameters of one simulation, in SI units."""
+    name: str
+    lo: tuple
+    hi: tuple
+    h: float
+    dt: float
+    a: tuple
+    b: tuple
+    T_L: float
+    steps: int
+    seeds: np.ndarray = None          # (n, 3) nucleus positions
+    quats: np.ndarray = None          # (n, 4)
+    analytic: dict = None             # T0, G, xref, Tdot
+    grid: dict = None                 # T (nz, ny, nx) float32, origin, spacing, vel
+    shell_n0: int = 0                 # > 0: seed each grain as a shell of n0 lattice shells
+    nuclei: dict = None               # pos (m,3), dTn (m,), quat (m,4)
+    extra: dict = field(default_factory=dict)
+
+
+def single_grain(seed: int = 1, steps: int = 400, dT: float = 5.0) -> Workload:
+    """One grain, uniform undercooling dT, A = 1e-5 m/s/K^2, h = 2 um, dt = 2 ms."""
+    g = rng(seed)
+    q = shoemake_quaternions(1, g)
+    T_L = 1000.0
+    return Workload(
+        name="single_grain", lo=(0.0, 0.0, 0.0), hi=(200e-6, 200e-6, 200e-6), h=2e-6,
+        dt=2e-3, a=(1e-5,), b=(2.0,), T_L=T_L, steps=steps,
+        seeds=np.array([[100e-6, 100e-6, 100e-6]]), quats=q,
+        analytic=dict(T0=T_L - dT, G=(0.0, 0.0, 0.0), xref=(0.0, 0.0, 0.0), Tdot=0.0))
+
+
+def columnar_slab(seed: int = 2, n_seeds: int = 50, size_xy: float = 1e-3,
+                  height: float = 50e-6, steps: int = 600) -> Workload:
+    """Seeds on z = 0, T = T_L + G z - Tdot t with G = 1e4 K/m, Tdot = 10 K/s."""
+    g = rng(seed)
+    xy = g.random((n_seeds, 2)) * size_xy
+    seeds = np.concatenate([xy, np.zeros((n_seeds, 1))], axis=1)
+    q = shoemake_quaternions(n_seeds, g)
+    T_L = 1000.0
+    return Workload(
+        name="columnar_slab", lo=(0.0, 0.0, 0.0), hi=(size_xy, size_xy, height), h=2e-6,
+        dt=1e-3, a=(1e-5,), b=(2.0,), T_L=T_L, steps=steps, seeds=seeds, quats=q,
+        analytic=dict(T0=T_L, G=(0.0, 0.0, 1e4), xref=(0.0, 0.0, 0.0), Tdot=-10.0))
+
+
+def rosenthal_table(shape=(128, 256, 512), extent=(4e-3, 2e-3, 1e-3), q=1000.0, k=30.0,
+                    alpha=6e-6, V=1.0 / 60.0, T0=300.0, T_cap=3134.0, x_src=3e-3):
+    """Thick-plate moving point source (Rosenthal) tabulated in the source frame.
+
+    T = T0 + q / (2 pi k R) exp(-V (xi + R) / (2 alpha)), xi = x - x_src along the
+    travel direction, R the distance to the source at the top surface
+    (z = extent_z, y = 0).  Capped at T_cap (boiling point of 316L, Table S8)
+    near the source.  Nodes are at origin + i * spacing, i = 0..n-1 (x fastest).
+    Returns (T[nz, ny, nx] float32, origin, spacing).
+    """
+    nz, ny, nx = shape
+    Lx, Ly, Lz = extent
+    sp = (Lx / (nx - 1), Ly / (ny - 1), Lz / (nz - 1))
+    x = np.arange(nx) * sp[0]
+    y = np.arange(ny) * sp[1]
+    z = np.arange(nz) * sp[2]
+    X = x[None, None, :] - x_src
+    Y = y[None, :, None]
+    Zd = (Lz - z)[:, None, None]
+    R = np.sqrt(X * X + Y * Y + Zd * Zd)
+    R = np.maximum(R, 1e-9)
+    T = T0 + q / (2.0 * math.pi * k * R) * np.exp(-V * (X + R) / (2.0 * alpha))
+    T = np.minimum(T, T_cap).astype(np.float32)
+    return np.ascontiguousarray(T), (0.0, 0.0, 0.0), sp
+
+
+def weld_fixture(seed: int = 3, n_grains: int = 10000, shell_n0: int = 50,
+                 steps: int = 2000, grid_shape=(128, 256, 512)) -> Workload:
+    """Rosenthal plate with 1e4 grains, each seeded as an octahedral shell.
+
+    A = 3e-6 m/s/K^3 (v = A dT^3), h = 2 um, dt = 0.1 ms, T_L = 1780 K; the
+    1 kW, 1 m/min source moves along +x (the table is sampled in its frame, so
+    the particle position is shifted by -V t before the lookup).
+    """
+    g = rng(seed)
+    ext = (4e-3, 2e-3, 1e-3)
+    seeds = g.random((n_grains, 3)) * np.array(ext)
+    q = shoemake_quaternions(n_grains, g)
+    V = 1.0 / 60.0
+    T, origin, sp = rosenthal_table(shape=grid_shape, extent=ext, V=V)
+    return Workload(
+        name="weld_fixture", lo=(0.0, 0.0, 0.0), hi=ext, h=2e-6, dt=1e-4, a=(3e-6,), b=(3.0,),
+        T_L=1780.0, steps=steps, seeds=seeds, quats=q,
+        grid=dict(T=T, origin=origin, spacing=sp, vel=(V, 0.0, 0.0)), shell_n0=shell_n0)
+
+
+def cet_runs(n_runs: int = 256, base_seed: int = 1000):
+    """Per-run parameters of the CET ensemble (Sec. 3.5 family).
+
+    Run r (seed base_seed + r): cube edge L ~ U[0.5, 2] mm, bottom seeds at
+    50 / mm^2 with dT_n = 0, bulk nucleation sites Poisson with density 1e11 m^-3
+    and dT_n ~ N(5, 1) truncated to >= 0, G ~ U[100, 1e4] K/m along +z,
+    Tdot ~ U[0.5, 20] K/s (cooling), A = 1e-5, n = 2, h = 2 um, dt = 1 ms.
+    """
+    runs = []
+    for r in range(n_runs):
+        g = rng(base_seed + r)
+        L = g.uniform(0.5e-3, 2e-3)
+        nb = max(1, g.poisson(50.0 * (L * 1e3) ** 2))
+        bottom = np.concatenate([g.random((nb, 2)) * L, np.zeros((nb, 1))], axis=1)
+        qb = shoemake_quaternions(nb, g)
+        nv = g.poisson(1e11 * L ** 3)
+        bulk = g.random((nv, 3)) * L
+        dTn = truncated_normal(nv, 5.0, 1.0, 0.0, np.inf, g)
+        qv = shoemake_quaternions(nv, g)
+        G = g.uniform(100.0, 1e4)
+        Tdot = g.uniform(0.5, 20.0)
+        T_L = 1000.0
+        runs.append(Workload(
+            name=f"cet_run_{r}", lo=(0.0, 0.0, 0.0), hi=(L, L, L), h=2e-6, dt=1e-3,
+            a=(1e-5,), b=(2.0,), T_L=T_L, steps=1000, seeds=bottom, quats=qb,
+            analytic=dict(T0=T_L, G=(0.0, 0.0, G), xref=(0.0, 0.0, 0.0), Tdot=-Tdot),
+            nuclei=dict(pos=bulk, dTn=dTn, quat=qv)))
+    return runs
