@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Throughput of the grain-envelope particle step on GB300.
+
+Workload (largest configuration, one GPU): a 4 x 2 x 1 mm plate with a 1 kW,
+1 m/min Rosenthal moving point source tabulated on a 512 x 256 x 128 binary32
+grid (sampled trilinearly in the source frame), 1e4 grains at uniform random
+seeds with uniform random orientations, each seeded as an octahedral envelope
+of 50 lattice shells (about 1e8 particles), v = 3e-6 dT^3, h = 2 um, dt = 0.1 ms.
+A step is one pass of the whole hot path (hash + sort, contact, thermal sample,
+growth law, advance, spawn/claim, clip, compaction, nucleation check) over all
+particles.  Metric: particle-steps/s = ACTIVE particles at the start of each
+timed step, summed, divided by the device time of the timed steps.
+
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(weak scaling, no collective in the data path); the timed region is bracketed by
+barriers and the maximum time over ranks is used.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the first grains of the fixture) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD_NAME = ("weld_fixture: 4x2x1 mm plate, Rosenthal 1 kW 1 m/min on a 512x256x128 FP32 "
+                 "grid, 1e4 grains seeded as 50-shell octahedral envelopes (~1e8 particles), "
+                 "v = 3e-6 dT^3, h = 2 um, dt = 0.1 ms")
+METRIC = "particle-steps/s"
+
+
+# ----------------------------------------------------------------------------------
+# distributed plumbing (host logic, tested on CPU with gloo)
+# ----------------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_timing(local_ms: float, local_units: float, world: int):
+    """Max of the timed region over ranks and the sum of the work of all ranks."""
+    if world <= 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        smax = max(r["smax"] for r in rows)
+        load = [r for r in rows if r["sm"] > 0.3 * smax] or rows
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": smax,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------------
+# workload construction
+# ----------------------------------------------------------------------------------
+def fixture(n_grains: int, n0: int):
+    from paper_2504_12858_gb300 import inputs
+    return inputs.weld_fixture(n_grains=n_grains, shell_n0=n0)
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_sources_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2504_12858_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per unit of `kernel` from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("sources_digest") != kernel_sources_digest():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes_per_unit"])
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------------
+def oracle_sample(n_grains_sample: int, n0: int):
+    import oracle
+    w = fixture(10000, n0)
+    o = oracle.Oracle(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L)
+    g = w.grid
+    o.set_thermal_grid(g["T"], g["origin"], g["spacing"], g["vel"])
+    o.add_grains(w.seeds[:n_grains_sample], w.quats[:n_grains_sample], nucleate=False)
+    o.seed_shell(np.arange(n_grains_sample), n0)
+    return o
+
+
+def time_oracle(o, steps: int):
+    before = o.stats()["particle_steps"]
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return (o.stats()["particle_steps"] - before) / dt, dt
+
+
+def cpu_baseline(n_grains_sample=100, n0=50, steps=2):
+    o = oracle_sample(n_grains_sample, n0)
+    o.step(1)  # warm the allocator
+    rate, dt = time_oracle(o, steps)
+    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": (f"first {n_grains_sample} of the 1e4 grains of the same workload "
+                       f"(~{o.n_particles:.2e} particles), {steps} steps after 1 untimed step, "
+                       f"{dt:.1f} s of single-threaded FP64 work")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    o = oracle_sample(args.ref_grains, args.n0)
+    o.step(args.warmup)
+    rate, dt = time_oracle(o, args.steps)
+    cb = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+          "sample": (f"first {args.ref_grains} of the 1e4 grains of the same workload, "
+                     f"{args.steps} timed steps after {args.warmup} warm-up steps")}
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample_grains": args.ref_grains},
+            "cpu_baseline": cb,
+            "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------
+def run_native(args, rank, world, local_rank):
+    import torch
+    from paper_2504_12858_gb300 import native
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    native.load()
+    w = fixture(args.grains, args.n0)
+    per_grain = 4 * (args.n0 + 1) ** 2 + 2
+    n0_est = args.grains * per_grain
+    total_steps = args.warmup + args.steps + args.e2e_steps
+    # the envelopes grow by about 4 % per step; every crossing records a reached site
+    capacity = int(args.capacity or min((1 << 30) - 1, int(n0_est * 1.05 ** total_steps * 1.3)
+                                        + 1000000))
+    reached = int(args.reached or min((1 << 32) - 2, int(n0_est * (1.2 + 0.9 * total_steps))))
+    sim = native.Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=capacity,
+                     reached_capacity=reached, claim_buckets=args.claim_buckets,
+                     max_grains=args.grains + 16, grid_nodes=int(np.prod(w.grid["T"].shape)),
+                     device=dev)
+    g = w.grid
+    sim.gp_set_thermal_grid(g["T"], g["origin"], g["spacing"], g["vel"])
+    sim.gp_add_grains(w.seeds, w.quats, nucleate=False)
+    sim.gp_seed_shell(np.arange(args.grains), args.n0)
+    n_start = sim.gp_stats()["n_live"]
+    stream = sim.stream
+
+    sim.gp_step(args.warmup)
+    torch.cuda.synchronize(dev)
+    st0 = sim.gp_stats()
+    sim.gp_profile(True)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.gp_step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ms_local = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    st1 = sim.gp_stats()
+    prof = sim.gp_profile_read()
+    sim.gp_profile(False)
+    units_local = float(st1["particle_steps"] - st0["particle_steps"])
+    ms, units = reduce_timing(ms_local, units_local, world)
+    value = units / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: the thermal table is copied
+    # from pinned host memory every step (as a coupled thermal solver would supply
+    # it) and the step statistics are read back to the host every step
+    Th = torch.from_numpy(np.ascontiguousarray(g["T"])).pin_memory()
+    Th_np = Th.numpy()
+    e2e_units = 0.0
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t0 = time.perf_counter()
+    sa = sim.gp_stats()
+    for _ in range(args.e2e_steps):
+        sim.gp_set_thermal_grid(Th_np, g["origin"], g["spacing"], g["vel"])
+        sim.gp_step(1)
+        sim.gp_stats()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    sb = sim.gp_stats()
+    e2e_units = float(sb["particle_steps"] - sa["particle_steps"])
+    e2e_ms, e2e_units = reduce_timing(e2e_s * 1e3, e2e_units, world)
+    e2e_value = e2e_units / (e2e_ms / 1e3)
+
+    if rank != 0:
+        sim.close()
+        return 0
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    peak, peak_kind = measured_peak()
+    dom = max(prof, key=lambda k: k["total_ms"]) if prof else None
+    roof = None
+    if dom:
+        achieved = dom["units"] * dom["bytes_per_unit"] / (dom["total_ms"] / 1e3) / 1e9
+        per_launch_units = dom["units"] / max(dom["launches"], 1)
+        tb = ncu_traffic(dom["name"])
+        roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": None if tb is None else tb * per_launch_units,
+                "algorithmic_bytes_per_launch": dom["bytes_per_unit"] * per_launch_units,
+                "avg_launch_ms": dom["total_ms"] / max(dom["launches"], 1)}
+    launches = sum(k["launches"] for k in prof)
+    kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
+                           "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in prof),
+                                                               1e-9), 4)} for k in prof}
+    cb = cpu_baseline(args.cpu_grains, args.n0, 2) if (world == 1 and not args.no_cpu) else None
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "grains": args.grains, "shell_n0": args.n0,
+                       "particles_at_start": n_start,
+                       "active_at_timed_start": st0["n_active"],
+                       "live_at_end": st1["n_live"], "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (particle store > 1.5 GB)"},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cb,
+            "e2e": {"value": e2e_value, "unit": METRIC, "steps": args.e2e_steps,
+                    "h2d_bytes_per_step": int(Th.numel() * 4),
+                    "d2h_bytes_per_step": 160},
+            "clocks": clk, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--grains", type=int, default=10000)
+    ap.add_argument("--n0", type=int, default=50)
+    ap.add_argument("--capacity", type=int, default=0)
+    ap.add_argument("--reached", type=int, default=0)
+    ap.add_argument("--claim-buckets", type=int, default=1 << 24)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-grains", type=int, default=100)
+    ap.add_argument("--ref-grains", type=int, default=40)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "native" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_native(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,272 @@
+/*
+ * gp.h - C ABI of the GB300 (sm_103a) grain-envelope particle library.
+ *
+ * The library implements the per-timestep update of the particle-based grain
+ * envelope tracking method of Mosbah et al., "A particle-based approach for the
+ * prediction of grain microstructures in solidification processes"
+ * (arXiv 2504.12858), Sec. 2.1 and 2.3:
+ *   nucleation activation (Sec. 2.1.1), growth of tracking points along the
+ *   rotated <100> directions with a power-law tip velocity (Sec. 2.1.2, Eq. 1 and
+ *   Eq. 2), generation of outer tracking points every lambda_0 (Sec. 2.1.2,
+ *   Fig. 2), impingement of grains by a cell-list contact search (Sec. 2.1.2 and
+ *   Sec. 2.3) and grain-id voxelisation by nearest tracking information
+ *   (Sec. 2.3).
+ *
+ * Conventions for every call:
+ *  - Units are SI.  Scalars and host arrays at the boundary are double precision;
+ *    the device state is binary32.
+ *  - Every call returns a gp_status.  On failure gp_last_error(ctx) returns a
+ *    message.  A status other than GP_OK from gp_step leaves the context in an
+ *    error state: only gp_stats, gp_last_error and gp_destroy remain valid.
+ *  - Host input arrays are read during the call and not retained: the caller
+ *    keeps ownership.  Output arrays are caller-allocated.
+ *  - A context is bound to the CUDA device current at gp_create and to one CUDA
+ *    stream; all its work is ordered on that stream.  A context is not
+ *    thread-safe.  Calls that return data to host memory synchronise the stream.
+ *  - Lattice sites are integer coordinates in the crystal frame of a grain,
+ *    relative to its nucleus, |s_a| <= 4095 (gp_create rejects domains whose
+ *    diagonal exceeds 4000 lattice spacings).
+ *  - Directions k = 0..5 are +x, -x, +y, -y, +z, -z of the crystal frame.
+ *  - Particle states: 0 ACTIVE, 1 FROZEN (stopped by another grain), 2 REMOVED.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GP_OK = 0,
+  GP_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, bad value)  */
+  GP_ERR_CAPACITY = 2,  /* a particle, site, grain or nucleus capacity exceeded  */
+  GP_ERR_HASH_FULL = 3, /* the lattice-site claim table is full                  */
+  GP_ERR_CUDA = 4,      /* a CUDA runtime call failed                            */
+  GP_ERR_STATE = 5,     /* call not valid in the current state                   */
+  GP_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up                    */
+} gp_status;
+
+typedef struct gp_ctx gp_ctx;
+
+/* Axis-aligned simulation box [lo, hi] (m).  Particles leaving it are removed. */
+typedef struct {
+  double lo[3], hi[3];
+} gp_domain;
+
+/* Tip-velocity law v(dT) for dT = T_L - T > 0, zero otherwise.
+ * nterms = 1: v = a[0] dT^b[0]                       (Eq. 1)
+ * nterms = 2: v = a[0] dT^b[0] + a[1] dT^b[1]        (Eq. 2)
+ * T_liquidus is T_L of the alloy at its nominal composition (Sec. 2.1.2). */
+typedef struct {
+  int32_t nterms;
+  double a[2], b[2];
+  double T_liquidus;
+} gp_growth_law;
+
+/* Imposed temperature T(x, t) = T0 + G . (x - x_ref) + Tdot t
+ * (frozen-temperature approximation, Sec. 3.3 / 3.4). */
+typedef struct {
+  double T0, G[3], x_ref[3], Tdot;
+} gp_thermal_analytic;
+
+/* Imposed temperature tabulated on a node-centred grid that moves with velocity
+ * frame_vel: node (i,j,k) sits at origin + frame_vel t + (i,j,k) * spacing; T is
+ * n[0]*n[1]*n[2] binary32 values, x fastest.  Sampled trilinearly after clamping
+ * to the table (this replaces the cellPointFace interpolation of Sec. 2.3).
+ * flags & GP_DEVICE_PTR: T is a device pointer (copied device-to-device),
+ * otherwise a host pointer.  Each n[a] >= 2. */
+typedef struct {
+  const float* T;
+  int32_t n[3];
+  double origin[3], spacing[3], frame_vel[3];
+  int32_t flags;
+} gp_thermal_grid;
+
+/* Voxel grid for gp_grain_map: voxel centres origin + (i + 1/2) spacing. */
+typedef struct {
+  double origin[3], spacing[3];
+  int32_t n[3];
+} gp_voxel_grid;
+
+/* Capacities and memory.  Zero fields take defaults (given per field).  If arena
+ * is non-NULL it must be device memory of arena_bytes >= gp_arena_bytes(...),
+ * 256-byte aligned; the library then allocates no device memory of its own and
+ * the caller keeps the arena alive until gp_destroy.  If arena is NULL the
+ * library allocates (and frees) its memory with cudaMalloc. */
+typedef struct {
+  int64_t capacity;         /* live (ACTIVE + FROZEN) particles; required > 0     */
+  int64_t reached_capacity; /* reached lattice sites; default 2 * capacity        */
+  int64_t claim_buckets;    /* 8^3-site blocks of the claim table (power of two);
+                               default from capacity                              */
+  int32_t max_grains;       /* default 1 << 20                                    */
+  int32_t max_nuclei;       /* pending nucleation sites; default 4096             */
+  int64_t grid_nodes;       /* thermal-grid nodes reserved in the arena; default 0 */
+  void* arena;
+  size_t arena_bytes;
+} gp_memory;
+
+typedef struct {
+  int64_t step;           /* timesteps taken (t = step * dt)                      */
+  int64_t n_live;         /* ACTIVE + FROZEN particles                            */
+  int64_t n_active;
+  int64_t n_frozen;
+  int64_t n_grains;
+  int64_t n_reached;      /* reached lattice sites recorded                        */
+  int64_t particle_steps; /* sum over steps of the ACTIVE particles at step start  */
+  int64_t n_frozen_new;   /* particles frozen by contact (cumulative)              */
+  int64_t n_spawned;      /* new particles from outer directions (cumulative)      */
+  int64_t n_claims_lost;  /* spawn candidates refused by the claim rule            */
+  int64_t n_clipped;      /* particles removed at the domain boundary              */
+  int64_t n_clamped;      /* advances capped at one lattice spacing per step       */
+  int64_t n_nucleated;
+  int64_t n_claim_blocks; /* occupied claim-table blocks                           */
+  int64_t error_flags;    /* sticky device error bits (0 when healthy)             */
+  int64_t reserved[5];
+} gp_stats_t;
+
+/* Per-kernel timing collected with CUDA events when profiling is enabled. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+  double units;           /* items processed (particles, keys, voxels) summed     */
+  double bytes_per_unit;  /* algorithmic DRAM bytes per item                      */
+} gp_kernel_prof;
+
+#define GP_DEVICE_PTR 1
+
+/* ---- context ------------------------------------------------------------------ */
+
+/* Device bytes gp_create needs for this domain, spacing h and capacities. */
+gp_status gp_arena_bytes(const gp_domain* domain, double h, const gp_memory* mem,
+                         size_t* out_bytes);
+
+/* Creates a simulation with lattice spacing h = lambda_0 (Sec. 2.1.2; also the
+ * contact radius; the spatial hash uses cells of edge h (1 + 2^-9)) and
+ * timestep dt.  Returns GP_ERR_ARG if the domain spans more than 4000 lattice
+ * spacings along its diagonal or more than 2^32 hash cells.
+ * cuda_stream is a cudaStream_t (NULL: the legacy default stream). */
+gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growth_law* law,
+                    const gp_memory* mem, void* cuda_stream, gp_ctx** out);
+
+gp_status gp_destroy(gp_ctx* ctx);
+
+const char* gp_last_error(const gp_ctx* ctx);
+
+/* ---- set-up ------------------------------------------------------------------ */
+
+/* Adds n grains with nuclei at pos3 (n x 3) and crystal->lab orientations given
+ * as unit quaternions quat4 (n x 4, w x y z; normalised here).  If nucleate != 0
+ * each grain starts with its six tracking points at the nucleus (Sec. 2.1.2,
+ * Fig. 2 Step 0).  *out_first_id (optional) receives the id of the first grain;
+ * ids are consecutive. */
+gp_status gp_add_grains(gp_ctx* ctx, int64_t n, const double* pos3, const double* quat4,
+                        int32_t nucleate, int32_t* out_first_id);
+
+/* Seeds each listed grain with the envelope a nucleus reaches after n0 complete
+ * lattice shells in a uniform melt: one ACTIVE particle per site t with
+ * |t|_1 = n0 + 1, placed at the site reached from the lowest axis a with
+ * t_a != 0, heading to t, with progress ell0 in [0,1).  Sites with |s|_1 = n0
+ * are recorded as reached; they and the targets are claimed.  Particles outside
+ * the domain are not seeded. */
+gp_status gp_seed_shell(gp_ctx* ctx, int64_t n, const int32_t* grains, int32_t n0,
+                        double ell0);
+
+gp_status gp_set_thermal_analytic(gp_ctx* ctx, const gp_thermal_analytic* th);
+gp_status gp_set_thermal_grid(gp_ctx* ctx, const gp_thermal_grid* th);
+
+/* Registers n pending nucleation sites (Sec. 2.1.1): position pos3 (n x 3),
+ * nucleation undercooling dTn (n) and orientation quat4 (n x 4).  A site becomes
+ * a grain at the end of the first step after which its undercooling is >= dTn,
+ * unless a reached site of an existing grain lies within h of it.  Grain ids of
+ * sites activating in the same step follow registration order. */
+gp_status gp_nucleation_sites(gp_ctx* ctx, int64_t n, const double* pos3, const double* dTn,
+                              const double* quat4);
+
+/* ---- time stepping ----------------------------------------------------------- */
+
+/* Advances nsteps timesteps.  Each step: spatial hash of all live particles,
+ * contact freeze, thermal sample and growth law at (x_n, t_n), explicit Euler
+ * advance capped at one lattice spacing, spawning of outer points at reached
+ * sites with the once-per-site claim rule, domain clip, nucleation at t_{n+1}. */
+gp_status gp_step(gp_ctx* ctx, int32_t nsteps);
+
+/* Grain id of every voxel centre: the grain of the nearest reached lattice site
+ * closer than h (ties: smaller grain id), else -1 (Sec. 2.3 Voronoi
+ * interpolation).  out has n[0]*n[1]*n[2] int32 values, x fastest; it is a device
+ * pointer if flags & GP_DEVICE_PTR, else host memory. */
+gp_status gp_grain_map(gp_ctx* ctx, const gp_voxel_grid* grid, int32_t* out, int32_t flags);
+
+/* ---- state access -------------------------------------------------------------- */
+
+gp_status gp_stats(gp_ctx* ctx, gp_stats_t* out);
+
+/* Copies up to cap live particles to host arrays (any may be NULL): grain,
+ * site3 (cap x 3), dir, ell, state, x3 (cap x 3, binary32 positions).  *n_out
+ * receives the number of live particles.  Order is the library's store order. */
+gp_status gp_get_particles(gp_ctx* ctx, int64_t cap, int32_t* grain, int32_t* site3,
+                           int8_t* dir, float* ell, uint8_t* state, float* x3,
+                           int64_t* n_out);
+
+/* Replaces the particle set with n particles given on the host and sets the step
+ * counter (state import, e.g. from a checkpoint). */
+gp_status gp_load_particles(gp_ctx* ctx, int64_t n, const int32_t* grain,
+                            const int32_t* site3, const int8_t* dir, const float* ell,
+                            const uint8_t* state, int64_t step);
+
+/* Marks n lattice sites (grain, site3) as reached (reached != 0) and/or claimed
+ * (claimed != 0). */
+gp_status gp_add_sites(gp_ctx* ctx, int64_t n, const int32_t* grain, const int32_t* site3,
+                       int32_t reached, int32_t claimed);
+
+/* Copies up to cap reached sites (grain, site3) to the host; *n_out = count. */
+gp_status gp_get_reached(gp_ctx* ctx, int64_t cap, int32_t* grain, int32_t* site3,
+                         int64_t* n_out);
+
+/* Enables (1) / disables (0) per-kernel CUDA-event timing and resets it. */
+gp_status gp_profile(gp_ctx* ctx, int32_t enable);
+/* Copies up to max entries of per-kernel timing; *n_out = number of kernels. */
+gp_status gp_profile_read(gp_ctx* ctx, int32_t max, gp_kernel_prof* out, int32_t* n_out);
+
+/* ---- stand-alone steps on caller device buffers ------------------------------ */
+
+/* Device workspace bytes for gp_hash_build / gp_contact on n points. */
+gp_status gp_hash_workspace_bytes(int64_t n, const gp_domain* domain, double h,
+                                  size_t* out_bytes);
+
+/* Spatial hash (Sec. 2.3 point partitioning): for n binary32 points x3 (device,
+ * n x 3), cell key = (cz*ny + cy)*nx + cx with c_a = clamp(floor((x_a - lo_a) *
+ * inv), 0, n_a - 1), lo_a = (float)domain.lo[a], cell edge e = h (1 + 2^-9),
+ * inv = (float)(1/e), n_a = max(1, ceil((hi_a - lo_a)/e)), in binary32 without
+ * contraction.  The edge margin makes any two points closer than h fall in
+ * neighbouring cells despite binary32 rounding (up to 4096 cells per axis).
+ * Writes the keys sorted stably (keys_sorted, n), the point ids in that order
+ * (ids_sorted, n), the occupied cells (cell_keys) and the index of their first
+ * point (cell_start); *n_cells (host) receives the number of occupied cells
+ * (cell_keys and cell_start need n entries).  All arrays are device memory; the
+ * call synchronises the stream to return *n_cells. */
+gp_status gp_hash_build(const float* x3, int64_t n, const gp_domain* domain, double h,
+                        uint32_t* keys_sorted, int32_t* ids_sorted, uint32_t* cell_keys,
+                        int32_t* cell_start, int64_t* n_cells, void* workspace,
+                        size_t workspace_bytes, void* cuda_stream);
+
+/* Contact search (Sec. 2.1.2 impingement): freeze[i] = 1 iff state[i] == 0
+ * (ACTIVE) and a point j with state[j] != 2 and grain[j] != grain[i] satisfies
+ * ((dx*dx + dy*dy) + dz*dz) < hf*hf in binary32, hf = (float)h, d = x_i - x_j.
+ * If pairs != NULL, the unordered pairs (i < j) of non-removed points of
+ * different grains within that distance are written (2 int32 each, up to
+ * pair_cap, in no particular order) and *n_pairs (host) receives their total
+ * count.  Device arrays; synchronises the stream when pairs != NULL. */
+gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state, int64_t n,
+                     const gp_domain* domain, double h, uint8_t* freeze, int32_t* pairs,
+                     int64_t pair_cap, int64_t* n_pairs, void* workspace,
+                     size_t workspace_bytes, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GP_H */

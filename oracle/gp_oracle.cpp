@@ -40,6 +40,9 @@ namespace {
 
 enum State : int { ACTIVE = 0, FROZEN = 1, REMOVED = 2 };
 
+// progress tolerance of the reached-target test (reading r6)
+constexpr double kReachTol = 1.0 / 1048576.0;
+
 inline int axis_of(int k) { return k >> 1; }
 inline int sign_of(int k) { return (k & 1) ? -1 : +1; }
 
@@ -204,11 +207,13 @@ struct Sim {
     return true;
   }
 
-  // Cell list in FP64 (cell edge = contact radius = h, reading r7).  Returns the
-  // cell index triple, clamped to the domain grid.
+  // Cell list in FP64.  The cell edge is the contact radius h enlarged by 2^-9
+  // (reading r3), so two points closer than h always lie in neighbouring cells.
+  // Returns the cell index triple, clamped to the domain grid.
+  double cell_edge() const { return h * (1.0 + 1.0 / 512.0); }
   void cell_of(const double x[3], int c[3], const int n[3]) const {
     for (int a_ = 0; a_ < 3; ++a_) {
-      int v = (int)std::floor((x[a_] - lo[a_]) / h);
+      int v = (int)std::floor((x[a_] - lo[a_]) / cell_edge());
       if (v < 0) v = 0;
       if (v > n[a_] - 1) v = n[a_] - 1;
       c[a_] = v;
@@ -216,7 +221,7 @@ struct Sim {
   }
   void ncells(int n[3]) const {
     for (int a_ = 0; a_ < 3; ++a_) {
-      int v = (int)std::ceil((hi[a_] - lo[a_]) / h);
+      int v = (int)std::ceil((hi[a_] - lo[a_]) / cell_edge());
       n[a_] = v < 1 ? 1 : v;
     }
   }
@@ -326,7 +331,10 @@ struct Sim {
     // (3)-(5) thermal sample at (x_n, t_n), growth law, explicit Euler advance of
     // the progress ell (reading r2).  Reading r6: the progress made in one step is
     // capped at one lattice spacing, so a particle reaches at most one site per
-    // step; the excess over the reached site is carried into its children.
+    // step; the excess over the reached site is carried into its children.  The
+    // target counts as reached once the progress is within 2^-20 of a full
+    // spacing, so that a step commensurate with h (v dt = h/4, say) spawns on the
+    // same step whatever the rounding of the accumulated progress.
     std::vector<uint8_t> cross(N, 0);
     std::vector<double> carry(N, 0.0);
     int64_t active_at_start = 0;
@@ -347,9 +355,9 @@ struct Sim {
         ++st.n_clamped;
       }
       double e = p.ell + dl;
-      if (e >= 1.0) {
+      if (e >= 1.0 - kReachTol) {
         cross[i] = 1;
-        carry[i] = e - 1.0;
+        carry[i] = e > 1.0 ? e - 1.0 : 0.0;
       } else {
         p.ell = e;
       }
@@ -467,7 +475,7 @@ struct Sim {
                    const int n[3], const std::vector<std::array<double, 3>>& RP) const {
     double rc2 = h * h;
     int c[3];
-    for (int a_ = 0; a_ < 3; ++a_) c[a_] = (int)std::floor((p[a_] - lo[a_]) / h);
+    for (int a_ = 0; a_ < 3; ++a_) c[a_] = (int)std::floor((p[a_] - lo[a_]) / cell_edge());
     double best = rc2;
     int32_t bg = -1;
     for (int dz = -1; dz <= 1; ++dz)
@@ -495,10 +503,12 @@ struct Sim {
 };
 
 // ---------- binary32 predicates for the stand-alone hash / contact functions ----
-// Cell key (reading r3): with lo_f = (float)lo, inv = (float)(1/h) and
-// n_a = max(1, ceil((hi-lo)/h)), the cell index along an axis is
-// clamp(floor((x - lo_f) * inv), 0, n_a - 1) evaluated in binary32, and the key is
-// the linear index (cz * ny + cy) * nx + cx.
+// Cell key (reading r3): with cell edge e = h (1 + 2^-9), lo_f = (float)lo,
+// inv = (float)(1/e) and n_a = max(1, ceil((hi-lo)/e)), the cell index along an
+// axis is clamp(floor((x - lo_f) * inv), 0, n_a - 1) evaluated in binary32, and
+// the key is the linear index (cz * ny + cy) * nx + cx.  The 2^-9 margin exceeds
+// the binary32 rounding of the cell coordinate for up to 4096 cells per axis, so
+// any two points closer than h fall in neighbouring cells.
 struct F32Grid {
   float lo[3];
   float inv;
@@ -506,12 +516,13 @@ struct F32Grid {
 };
 F32Grid make_f32grid(const double lo[3], const double hi[3], double h) {
   F32Grid g;
+  const double e = h * (1.0 + 1.0 / 512.0);
   for (int a = 0; a < 3; ++a) {
     g.lo[a] = (float)lo[a];
-    int v = (int)std::ceil((hi[a] - lo[a]) / h);
+    int v = (int)std::ceil((hi[a] - lo[a]) / e);
     g.n[a] = v < 1 ? 1 : v;
   }
-  g.inv = (float)(1.0 / h);
+  g.inv = (float)(1.0 / e);
   return g;
 }
 inline int f32cell(float x, float lo, float inv, int n) {

@@ -1,0 +1,1133 @@
+// C ABI of the grain-envelope particle library: context, memory, time loop.
+// The declarations and the contract of every entry point are in include/gp.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gp.h"
+#include "gp_kernels.cuh"
+
+using namespace gp;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// cell edge: contact radius h enlarged by 2^-9 so that binary32 rounding of the
+// cell coordinate can never separate two points closer than h by more than one
+// cell (up to 4096 cells per axis)
+inline double cell_edge(double h) { return h * (1.0 + 1.0 / 512.0); }
+
+struct Layout {
+  int nc[3];
+  uint64_t ncells;
+  int nbits;
+  int64_t cap, rcap, buckets;
+  int max_grains, max_nuclei;
+  int64_t grid_nodes;
+  // offsets into the arena
+  size_t rec0, rec1, pos4, keys0, keys1, vals0, vals1, sstatus, hist, tickets, estatus, cells,
+      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, dstats, grid, total;
+};
+
+bool cells_of(const gp_domain* d, double h, int nc[3], uint64_t* ncells) {
+  const double e = cell_edge(h);
+  uint64_t tot = 1;
+  for (int a = 0; a < 3; ++a) {
+    double ext = d->hi[a] - d->lo[a];
+    if (!(ext >= 0) || !std::isfinite(ext)) return false;
+    double v = std::ceil(ext / e);
+    if (v > 4096.0) return false;
+    nc[a] = v < 1 ? 1 : (int)v;
+    tot *= (uint64_t)nc[a];
+  }
+  *ncells = tot;
+  return tot < (1ull << 32);
+}
+
+int64_t pow2_at_least(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, std::string* why) {
+  if (!d || !m || !(h > 0)) {
+    *why = "domain, memory and h > 0 are required";
+    return false;
+  }
+  if (!cells_of(d, h, L->nc, &L->ncells)) {
+    *why = "domain too large for the spatial hash (more than 4096 cells per axis or 2^32 cells)";
+    return false;
+  }
+  double diag = 0;
+  for (int a = 0; a < 3; ++a) diag += (d->hi[a] - d->lo[a]) * (d->hi[a] - d->lo[a]);
+  if (std::sqrt(diag) / h > 4000.0) {
+    *why = "domain diagonal exceeds 4000 lattice spacings";
+    return false;
+  }
+  if (m->capacity <= 0 || m->capacity >= (1ll << 30)) {
+    *why = "capacity must be in [1, 2^30)";
+    return false;
+  }
+  L->cap = m->capacity;
+  L->rcap = m->reached_capacity > 0 ? m->reached_capacity : 2 * m->capacity;
+  if (L->rcap >= (1ll << 32) - 1) L->rcap = (1ll << 32) - 2;
+  int64_t b = m->claim_buckets > 0 ? m->claim_buckets : std::max<int64_t>(4096, m->capacity / 16);
+  L->buckets = pow2_at_least(b);
+  if (L->buckets > (1ll << 31)) {
+    *why = "claim_buckets too large";
+    return false;
+  }
+  L->max_grains = m->max_grains > 0 ? m->max_grains : (1 << 20);
+  if (L->max_grains > (1 << 24)) {
+    *why = "max_grains must be <= 2^24";
+    return false;
+  }
+  L->max_nuclei = m->max_nuclei > 0 ? m->max_nuclei : 4096;
+  L->grid_nodes = m->grid_nodes > 0 ? m->grid_nodes : 0;
+  uint64_t nm1 = L->ncells - 1;
+  L->nbits = 0;
+  while (nm1) {
+    ++L->nbits;
+    nm1 >>= 1;
+  }
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  const size_t cap = (size_t)L->cap;
+  L->rec0 = take(16 * cap);
+  L->rec1 = take(16 * cap);
+  L->pos4 = take(16 * cap);
+  L->keys0 = take(4 * cap + 16);
+  L->keys1 = take(4 * cap + 16);
+  L->vals0 = take(4 * cap + 16);
+  L->vals1 = take(4 * cap + 16);
+  L->sstatus = take(4 * radix_status_words(L->cap));
+  L->hist = take(4 * 4 * 256);
+  L->tickets = take(4 * 8);
+  L->estatus = take(8 * (size_t)std::max<int64_t>(1, emit_tiles(L->cap)));
+  L->cells = take(8 * (size_t)L->ncells);
+  L->rkey = take(8 * (size_t)L->rcap);
+  L->rnext = take(4 * (size_t)L->rcap);
+  L->rhead = take(4 * (size_t)L->ncells);
+  L->ckeys = take(8 * (size_t)L->buckets);
+  L->cdata = take(4 * kBrickWords * (size_t)L->buckets);
+  L->gtab = take(64 * (size_t)L->max_grains);
+  L->npos = take(16 * (size_t)L->max_nuclei);
+  L->ngrain = take(64 * (size_t)L->max_nuclei);
+  L->nstate = take(4 * (size_t)L->max_nuclei);
+  L->dstats = take(sizeof(DevStats));
+  L->grid = take(4 * (size_t)L->grid_nodes);
+  L->total = o;
+  return true;
+}
+
+// rotation (crystal -> lab) of a unit quaternion (w, x, y, z)
+void quat_rot(const double* qin, double R[9]) {
+  double n = std::sqrt(qin[0] * qin[0] + qin[1] * qin[1] + qin[2] * qin[2] + qin[3] * qin[3]);
+  double w = qin[0] / n, x = qin[1] / n, y = qin[2] / n, z = qin[3] / n;
+  R[0] = 1 - 2 * (y * y + z * z);
+  R[1] = 2 * (x * y - w * z);
+  R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);
+  R[4] = 1 - 2 * (x * x + z * z);
+  R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);
+  R[7] = 2 * (y * z + w * x);
+  R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// grain table entry: c, then the rows of h R
+void grain_entry(const double* pos, const double* q, double h, float4 out[4]) {
+  double R[9];
+  quat_rot(q, R);
+  out[0] = make_float4((float)pos[0], (float)pos[1], (float)pos[2], 0.f);
+  for (int r = 0; r < 3; ++r)
+    out[1 + r] = make_float4((float)(h * R[3 * r]), (float)(h * R[3 * r + 1]),
+                             (float)(h * R[3 * r + 2]), 0.f);
+}
+
+const char* kKernelNames[K_COUNT] = {"hist",      "onesweep", "keys", "build",
+                                     "advance",   "emit",     "nucleate", "grain_map",
+                                     "seed",      "contact",  "cells",    "finalize"};
+// algorithmic DRAM bytes per processed item:
+//   hist      read key (4)
+//   onesweep  read key + value, write key + value (16)
+//   keys      read record (16), write key + value (8)
+//   build     read value + key (8), gather record (16), write record (16), write
+//             position + grain (16)
+//   advance   read record (16) + own position (16), write record (16); neighbour
+//             positions are re-reads of the same cells (cache)
+//   emit      read record (16), write record (16) + key + value (8) per output
+const double kKernelBytes[K_COUNT] = {4, 16, 24, 56, 48, 40, 0, 0, 0, 0, 0, 0};
+
+struct Prof : ProfHook {
+  cudaStream_t st = nullptr;
+  bool on = false;
+  struct Ev {
+    cudaEvent_t a, b;
+    int kid;
+    double units;
+  };
+  std::vector<Ev> pending;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[K_COUNT] = {};
+  double ms[K_COUNT] = {};
+  double units[K_COUNT] = {};
+  cudaEvent_t cur = nullptr;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int kid) override {
+    (void)kid;
+    if (!on) return;
+    cur = get();
+    cudaEventRecord(cur, st);
+  }
+  void end(int kid, double u) override {
+    if (!on || !cur) return;
+    cudaEvent_t e = get();
+    cudaEventRecord(e, st);
+    pending.push_back({cur, e, kid, u});
+    cur = nullptr;
+    if (pending.size() > 4096) flush();
+  }
+  void flush() {
+    if (pending.empty()) return;
+    cudaStreamSynchronize(st);
+    for (auto& p : pending) {
+      float t = 0;
+      cudaEventElapsedTime(&t, p.a, p.b);
+      launches[p.kid] += 1;
+      ms[p.kid] += t;
+      units[p.kid] += p.units;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    flush();
+    for (int i = 0; i < K_COUNT; ++i) {
+      launches[i] = 0;
+      ms[i] = 0;
+      units[i] = 0;
+    }
+  }
+  ~Prof() override {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace
+
+struct gp_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own = false;
+  char* base = nullptr;
+  Layout L{};
+  double lo[3], hi[3], h = 0, dt = 0;
+  gp_growth_law law{};
+  Params P{};
+  // thermal
+  int thermal = 0;
+  double T0 = 0, Tdot = 0;
+  double gorigin[3] = {0, 0, 0}, gvel[3] = {0, 0, 0};
+  float* grid_own = nullptr;  // cudaMalloc'ed grid when the arena has none
+  size_t grid_own_bytes = 0;
+  // device views
+  int4* rec[2] = {nullptr, nullptr};
+  int cur = 0;  // rec[cur] is the (unsorted) store
+  float4* pos4 = nullptr;
+  SortBufs sb{};
+  unsigned long long* cells = nullptr;
+  uint32_t stamp = 0;
+  Claims C{};
+  Reached R{};
+  float4* gtab = nullptr;
+  float4* npos = nullptr;
+  float4* ngrain = nullptr;
+  int* nstate = nullptr;
+  DevStats* dst = nullptr;
+  DevStats* hst = nullptr;  // pinned mirror
+  unsigned long long* estatus = nullptr;
+  uint32_t* eticket = nullptr;
+  // host mirrors
+  int64_t n_live = 0, n_grains = 0, step = 0;
+  int n_nuclei = 0;
+  bool keys_valid = false;
+  bool broken = false;
+  std::string err;
+  Prof prof;
+  int sms = 152;
+};
+
+namespace {
+
+gp_status fail(gp_ctx* c, gp_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+gp_status cuda_check(gp_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return GP_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (c) {
+    c->err = m;
+    c->broken = true;
+  }
+  return GP_ERR_CUDA;
+}
+
+#define GP_CUDA(c, call)                                  \
+  do {                                                    \
+    gp_status _s = cuda_check((c), (call), #call);        \
+    if (_s != GP_OK) return _s;                           \
+  } while (0)
+
+template <class T>
+T* at(gp_ctx* c, size_t off) {
+  return reinterpret_cast<T*>(c->base + off);
+}
+
+void refresh_params(gp_ctx* c) {
+  Params& P = c->P;
+  for (int a = 0; a < 3; ++a) {
+    P.lo[a] = (float)c->lo[a];
+    P.hi[a] = (float)c->hi[a];
+    P.nc[a] = c->L.nc[a];
+  }
+  P.inv_c = (float)(1.0 / cell_edge(c->h));
+  float hf = (float)c->h;
+  P.rc2 = hf * hf;
+  P.dt_over_h = (float)(c->dt / c->h);
+  P.nterms = c->law.nterms;
+  for (int i = 0; i < 2; ++i) {
+    P.a[i] = (float)c->law.a[i];
+    P.b[i] = (float)c->law.b[i];
+    double bi = c->law.b[i];
+    P.bint[i] = (bi == std::floor(bi) && bi >= 1.0 && bi <= 8.0) ? (int)bi : -1;
+  }
+  P.TL = (float)c->law.T_liquidus;
+  P.gtab = c->gtab;
+}
+
+StepArgs step_args(const gp_ctx* c, int64_t n) {
+  StepArgs S{};
+  const double t = (double)n * c->dt;
+  if (c->thermal == 1) S.dT_base = (float)(c->law.T_liquidus - c->T0 - c->Tdot * t);
+  for (int a = 0; a < 3; ++a) S.gshift[a] = (float)(c->gorigin[a] + c->gvel[a] * t);
+  S.parity = (int)(n & 1);
+  return S;
+}
+
+gp_status sync_stats(gp_ctx* c) {
+  GP_CUDA(c, cudaMemcpyAsync(c->hst, c->dst, sizeof(DevStats), cudaMemcpyDeviceToHost, c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  uint32_t e = c->hst->err | *((volatile uint32_t*)&c->hst->err);
+  c->n_live = (int64_t)c->hst->n_live;
+  c->n_grains = (int64_t)c->hst->n_grains;
+  if (e) {
+    c->broken = true;
+    if (e & ERR_CAPACITY) return fail(c, GP_ERR_CAPACITY, "particle capacity exceeded");
+    if (e & ERR_REACHED_CAP) return fail(c, GP_ERR_CAPACITY, "reached-site capacity exceeded");
+    if (e & ERR_GRAINS) return fail(c, GP_ERR_CAPACITY, "grain capacity exceeded");
+    if (e & ERR_HASH_FULL) return fail(c, GP_ERR_HASH_FULL, "claim table full");
+    if (e & ERR_TIMEOUT) return fail(c, GP_ERR_TIMEOUT, "bounded device wait gave up");
+    if (e & ERR_CELL_OVERFLOW) return fail(c, GP_ERR_CAPACITY, "more than 65535 particles in a cell");
+    if (e & ERR_SITE_RANGE) return fail(c, GP_ERR_ARG, "lattice site outside [-4095, 4095]");
+    return fail(c, GP_ERR_STATE, "device error");
+  }
+  return GP_OK;
+}
+
+// writes the host mirrors of n_live / n_grains into the device counters
+gp_status push_counts(gp_ctx* c) {
+  c->hst->n_live = (unsigned long long)c->n_live;
+  c->hst->n_grains = (unsigned long long)c->n_grains;
+  GP_CUDA(c, cudaMemcpyAsync(&c->dst->n_live, &c->hst->n_live, sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaMemcpyAsync(&c->dst->n_grains, &c->hst->n_grains, sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  return GP_OK;
+}
+
+gp_status check_ctx(gp_ctx* c) {
+  if (!c) return GP_ERR_ARG;
+  if (c->broken) return fail(c, GP_ERR_STATE, "context is in an error state: " + c->err);
+  GP_CUDA(c, cudaSetDevice(c->device));
+  return GP_OK;
+}
+
+// L1 sphere |t|_1 = m of the integer lattice, as short4 offsets
+std::vector<short4> l1_sphere(int m) {
+  std::vector<short4> v;
+  if (m == 0) {
+    v.push_back(make_short4(0, 0, 0, 0));
+    return v;
+  }
+  for (int x = -m; x <= m; ++x)
+    for (int y = -(m - std::abs(x)); y <= m - std::abs(x); ++y) {
+      int rz = m - std::abs(x) - std::abs(y);
+      v.push_back(make_short4((short)x, (short)y, (short)rz, 0));
+      if (rz) v.push_back(make_short4((short)x, (short)y, (short)-rz, 0));
+    }
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_arena_bytes(const gp_domain* domain, double h, const gp_memory* mem,
+                         size_t* out_bytes) {
+  if (!out_bytes) return GP_ERR_ARG;
+  Layout L{};
+  std::string why;
+  if (!make_layout(domain, h, mem, &L, &why)) return GP_ERR_ARG;
+  *out_bytes = L.total;
+  return GP_OK;
+}
+
+gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growth_law* law,
+                    const gp_memory* mem, void* cuda_stream, gp_ctx** out) {
+  if (!out || !domain || !law || !mem) return GP_ERR_ARG;
+  *out = nullptr;
+  if (!(dt > 0) || law->nterms < 1 || law->nterms > 2) return GP_ERR_ARG;
+  for (int i = 0; i < law->nterms; ++i)
+    if (!std::isfinite(law->a[i]) || !std::isfinite(law->b[i]) || law->b[i] < 0) return GP_ERR_ARG;
+  gp_ctx* c = new gp_ctx();
+  std::string why;
+  if (!make_layout(domain, h, mem, &c->L, &why)) {
+    delete c;
+    return GP_ERR_ARG;
+  }
+  cudaGetDevice(&c->device);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->st = (cudaStream_t)cuda_stream;
+  for (int a = 0; a < 3; ++a) {
+    c->lo[a] = domain->lo[a];
+    c->hi[a] = domain->hi[a];
+  }
+  c->h = h;
+  c->dt = dt;
+  c->law = *law;
+  if (c->law.nterms == 1) {
+    c->law.a[1] = 0;
+    c->law.b[1] = 0;
+  }
+  if (mem->arena) {
+    if (mem->arena_bytes < c->L.total || ((uintptr_t)mem->arena & (kAlign - 1))) {
+      delete c;
+      return GP_ERR_ARG;
+    }
+    c->base = (char*)mem->arena;
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, c->L.total);
+    if (e != cudaSuccess) {
+      delete c;
+      return e == cudaErrorMemoryAllocation ? GP_ERR_CAPACITY : GP_ERR_CUDA;
+    }
+    c->base = (char*)p;
+    c->own = true;
+  }
+  if (cudaMallocHost((void**)&c->hst, sizeof(DevStats)) != cudaSuccess) {
+    if (c->own) cudaFree(c->base);
+    delete c;
+    return GP_ERR_CUDA;
+  }
+  std::memset(c->hst, 0, sizeof(DevStats));
+  const Layout& L = c->L;
+  c->rec[0] = at<int4>(c, L.rec0);
+  c->rec[1] = at<int4>(c, L.rec1);
+  c->pos4 = at<float4>(c, L.pos4);
+  c->sb.keys[0] = at<uint32_t>(c, L.keys0);
+  c->sb.keys[1] = at<uint32_t>(c, L.keys1);
+  c->sb.vals[0] = at<uint32_t>(c, L.vals0);
+  c->sb.vals[1] = at<uint32_t>(c, L.vals1);
+  c->sb.status = at<uint32_t>(c, L.sstatus);
+  c->sb.hist = at<uint32_t>(c, L.hist);
+  c->sb.ticket = at<uint32_t>(c, L.tickets);
+  c->sb.max_n = L.cap;
+  c->sb.sms = c->sms;
+  c->sb.prof = &c->prof;
+  c->prof.st = c->st;
+  c->eticket = at<uint32_t>(c, L.tickets) + 4;
+  c->estatus = at<unsigned long long>(c, L.estatus);
+  c->cells = at<unsigned long long>(c, L.cells);
+  c->dst = at<DevStats>(c, L.dstats);
+  c->sb.err = &c->dst->err;
+  c->R.key = at<unsigned long long>(c, L.rkey);
+  c->R.next = at<uint32_t>(c, L.rnext);
+  c->R.head = at<uint32_t>(c, L.rhead);
+  c->R.count = &c->dst->reached;
+  c->R.cap = (unsigned long long)L.rcap;
+  c->R.err = &c->dst->err;
+  c->C.keys = at<unsigned long long>(c, L.ckeys);
+  c->C.data = at<uint32_t>(c, L.cdata);
+  c->C.mask = (uint32_t)(L.buckets - 1);
+  c->C.used = &c->dst->claim_used;
+  c->C.err = &c->dst->err;
+  c->gtab = at<float4>(c, L.gtab);
+  c->npos = at<float4>(c, L.npos);
+  c->ngrain = at<float4>(c, L.ngrain);
+  c->nstate = at<int>(c, L.nstate);
+  refresh_params(c);
+  cudaStream_t s = c->st;
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMemsetAsync(c->cells, 0, 8 * L.ncells, s);
+  e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.ncells, s);
+  e = e ? e : cudaMemsetAsync(c->C.keys, 0, 8 * (size_t)L.buckets, s);
+  e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.buckets, s);
+  e = e ? e : cudaMemsetAsync(c->dst, 0, sizeof(DevStats), s);
+  e = e ? e : cudaMemsetAsync(c->gtab, 0, 64 * (size_t)L.max_grains, s);
+  e = e ? e : cudaMemsetAsync(c->nstate, 0, 4 * (size_t)L.max_nuclei, s);
+  e = e ? e : cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    gp_destroy(c);
+    return GP_ERR_CUDA;
+  }
+  *out = c;
+  return GP_OK;
+}
+
+gp_status gp_destroy(gp_ctx* c) {
+  if (!c) return GP_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  c->prof.pending.clear();
+  if (c->own && c->base) cudaFree(c->base);
+  if (c->grid_own) cudaFree(c->grid_own);
+  if (c->hst) cudaFreeHost(c->hst);
+  delete c;
+  return GP_OK;
+}
+
+const char* gp_last_error(const gp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+gp_status gp_add_grains(gp_ctx* c, int64_t n, const double* pos3, const double* quat4,
+                        int32_t nucleate, int32_t* out_first_id) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!pos3 || !quat4))) return fail(c, GP_ERR_ARG, "bad arguments");
+  if (c->n_grains + n > c->L.max_grains) return fail(c, GP_ERR_CAPACITY, "grain capacity");
+  if (nucleate && c->n_live + 6 * n > c->L.cap) return fail(c, GP_ERR_CAPACITY, "particle capacity");
+  for (int64_t i = 0; i < n; ++i) {
+    const double* q = quat4 + 4 * i;
+    double nq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (!(nq > 0) || !std::isfinite(nq)) return fail(c, GP_ERR_ARG, "quaternion is zero or not finite");
+    for (int a = 0; a < 3; ++a)
+      if (!(pos3[3 * i + a] >= c->lo[a] && pos3[3 * i + a] <= c->hi[a]))
+        return fail(c, GP_ERR_ARG, "nucleus outside the domain");
+  }
+  if (out_first_id) *out_first_id = (int32_t)c->n_grains;
+  if (n == 0) return GP_OK;
+  std::vector<float4> G(4 * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) grain_entry(pos3 + 3 * i, quat4 + 4 * i, c->h, &G[4 * i]);
+  GP_CUDA(c, cudaMemcpyAsync(c->gtab + 4 * c->n_grains, G.data(), sizeof(float4) * G.size(),
+                             cudaMemcpyHostToDevice, c->st));
+  const int64_t g0 = c->n_grains;
+  c->n_grains += n;
+  if (nucleate) {
+    // six nucleation particles per grain, staged through the sorted-record buffer
+    // (idle between steps)
+    std::vector<int4> recs(6 * (size_t)n);
+    std::vector<int4> nuc(n), tgt(6 * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+      const int g = (int)(g0 + i);
+      nuc[i] = make_int4(g, 0, 0, 0);
+      for (int k = 0; k < 6; ++k) {
+        Rec r{};
+        r.grain = g;
+        r.dir = k;
+        r.state = ST_ACTIVE;
+        recs[6 * i + k] = rec_pack(r);
+        int t[3] = {0, 0, 0};
+        t[k >> 1] = (k & 1) ? -1 : 1;
+        tgt[6 * i + k] = make_int4(g, t[0], t[1], t[2]);
+      }
+    }
+    int4* stg = c->rec[c->cur ^ 1];
+    GP_CUDA(c, cudaMemcpyAsync(stg, recs.data(), sizeof(int4) * recs.size(),
+                               cudaMemcpyHostToDevice, c->st));
+    launch_append(stg, (int64_t)recs.size(), c->rec[c->cur], c->n_live, c->st);
+    // nucleus site: reached + claimed; first targets: claimed.  Site lists are
+    // staged through the position buffer in chunks of its capacity.
+    int4* sstg = reinterpret_cast<int4*>(c->pos4);
+    const int64_t chunk = c->L.cap;
+    for (int pass = 0; pass < 2; ++pass) {
+      const std::vector<int4>& v = pass == 0 ? nuc : tgt;
+      for (int64_t b = 0; b < (int64_t)v.size(); b += chunk) {
+        const int64_t m = std::min<int64_t>(chunk, (int64_t)v.size() - b);
+        GP_CUDA(c, cudaMemcpyAsync(sstg, v.data() + b, sizeof(int4) * m, cudaMemcpyHostToDevice,
+                                   c->st));
+        launch_mark_sites(c->P, sstg, m, pass == 0 ? 1 : 0, 1, c->C, c->R, c->st);
+        GP_CUDA(c, cudaStreamSynchronize(c->st));
+      }
+    }
+    c->n_live += 6 * n;
+    c->keys_valid = false;
+  }
+  GP_CUDA(c, cudaGetLastError());
+  s = push_counts(c);
+  if (s) return s;
+  return sync_stats(c);
+}
+
+gp_status gp_seed_shell(gp_ctx* c, int64_t n, const int32_t* grains, int32_t n0, double ell0) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (n < 0 || (n > 0 && !grains) || n0 < 0 || n0 > 2000 || !(ell0 >= 0 && ell0 < 1))
+    return fail(c, GP_ERR_ARG, "bad arguments");
+  for (int64_t i = 0; i < n; ++i)
+    if (grains[i] < 0 || grains[i] >= c->n_grains) return fail(c, GP_ERR_ARG, "unknown grain");
+  if (n == 0) return GP_OK;
+  std::vector<short4> toff = l1_sphere(n0 + 1), soff = l1_sphere(n0);
+  // staging: grains + offsets in the key/value buffers (idle between steps)
+  size_t need = 4 * (size_t)n + 8 * (toff.size() + soff.size()) + 1024;
+  if (need > 16 * (size_t)c->L.cap) return fail(c, GP_ERR_CAPACITY, "staging too small for shell list");
+  char* stg = reinterpret_cast<char*>(c->pos4);
+  int32_t* dg = reinterpret_cast<int32_t*>(stg);
+  short4* dt = reinterpret_cast<short4*>(stg + align_up(4 * (size_t)n));
+  short4* ds = dt + toff.size();
+  GP_CUDA(c, cudaMemcpyAsync(dg, grains, 4 * (size_t)n, cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaMemcpyAsync(dt, toff.data(), 8 * toff.size(), cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaMemcpyAsync(ds, soff.data(), 8 * soff.size(), cudaMemcpyHostToDevice, c->st));
+  s = push_counts(c);
+  if (s) return s;
+  launch_seed_shell(c->P, dg, n, dt, (int64_t)toff.size(), (float)ell0, c->rec[c->cur], c->L.cap,
+                    &c->dst->n_live, c->C, &c->dst->err, c->st);
+  launch_seed_shell_sites(c->P, dg, n, ds, (int64_t)soff.size(), c->C, c->R, c->st);
+  GP_CUDA(c, cudaGetLastError());
+  c->keys_valid = false;
+  return sync_stats(c);
+}
+
+gp_status gp_set_thermal_analytic(gp_ctx* c, const gp_thermal_analytic* th) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (!th) return fail(c, GP_ERR_ARG, "null field");
+  c->thermal = 1;
+  c->T0 = th->T0;
+  c->Tdot = th->Tdot;
+  c->P.thermal = 1;
+  for (int a = 0; a < 3; ++a) {
+    c->P.G[a] = (float)th->G[a];
+    c->P.xref[a] = (float)th->x_ref[a];
+  }
+  return GP_OK;
+}
+
+gp_status gp_set_thermal_grid(gp_ctx* c, const gp_thermal_grid* th) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (!th || !th->T) return fail(c, GP_ERR_ARG, "null grid");
+  for (int a = 0; a < 3; ++a)
+    if (th->n[a] < 2 || !(th->spacing[a] > 0)) return fail(c, GP_ERR_ARG, "grid needs n >= 2 and spacing > 0");
+  const size_t nodes = (size_t)th->n[0] * th->n[1] * th->n[2];
+  float* dstp = nullptr;
+  if ((int64_t)nodes <= c->L.grid_nodes) {
+    dstp = at<float>(c, c->L.grid);
+  } else if (c->own) {
+    if (c->grid_own_bytes < 4 * nodes) {
+      if (c->grid_own) cudaFree(c->grid_own);
+      c->grid_own = nullptr;
+      c->grid_own_bytes = 0;
+      GP_CUDA(c, cudaMalloc((void**)&c->grid_own, 4 * nodes));
+      c->grid_own_bytes = 4 * nodes;
+    }
+    dstp = c->grid_own;
+  } else {
+    return fail(c, GP_ERR_CAPACITY, "thermal grid larger than gp_memory.grid_nodes");
+  }
+  GP_CUDA(c, cudaMemcpyAsync(dstp, th->T, 4 * nodes,
+                             (th->flags & GP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyHostToDevice,
+                             c->st));
+  c->thermal = 2;
+  c->P.thermal = 2;
+  c->P.grid = dstp;
+  for (int a = 0; a < 3; ++a) {
+    c->P.gn[a] = th->n[a];
+    c->P.ginv[a] = (float)(1.0 / th->spacing[a]);
+    c->gorigin[a] = th->origin[a];
+    c->gvel[a] = th->frame_vel[a];
+  }
+  return GP_OK;
+}
+
+gp_status gp_nucleation_sites(gp_ctx* c, int64_t n, const double* pos3, const double* dTn,
+                              const double* quat4) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!pos3 || !dTn || !quat4))) return fail(c, GP_ERR_ARG, "bad arguments");
+  if (c->n_nuclei + n > c->L.max_nuclei) return fail(c, GP_ERR_CAPACITY, "nucleus capacity");
+  if (n == 0) return GP_OK;
+  std::vector<float4> P(n), G(4 * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    P[i] = make_float4((float)pos3[3 * i], (float)pos3[3 * i + 1], (float)pos3[3 * i + 2],
+                       (float)dTn[i]);
+    grain_entry(pos3 + 3 * i, quat4 + 4 * i, c->h, &G[4 * i]);
+  }
+  GP_CUDA(c, cudaMemcpyAsync(c->npos + c->n_nuclei, P.data(), sizeof(float4) * n,
+                             cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaMemcpyAsync(c->ngrain + 4 * (size_t)c->n_nuclei, G.data(),
+                             sizeof(float4) * G.size(), cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  c->n_nuclei += (int)n;
+  return GP_OK;
+}
+
+gp_status gp_step(gp_ctx* c, int32_t nsteps) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (nsteps < 0) return fail(c, GP_ERR_ARG, "nsteps < 0");
+  if (c->thermal == 0 && c->n_live > 0)
+    return fail(c, GP_ERR_STATE, "no thermal field set");
+  for (int it = 0; it < nsteps; ++it) {
+    const int64_t n = c->n_live;
+    const StepArgs S = step_args(c, c->step);
+    GP_CUDA(c, cudaMemsetAsync(&c->dst->n_out, 0, sizeof(unsigned long long), c->st));
+    GP_CUDA(c, cudaMemsetAsync(&c->dst->n_frozen, 0, sizeof(unsigned long long), c->st));
+    if (n > 0) {
+      if (!c->keys_valid) {
+        c->prof.begin(K_KEYS);
+        launch_keys(c->P, c->rec[c->cur], n, c->sb.keys[0], c->sb.vals[0], c->st);
+        c->prof.end(K_KEYS, (double)n);
+        c->keys_valid = true;
+      }
+      const int w = radix_sort(c->sb, n, c->L.nbits, c->st);
+      if (++c->stamp > 0xffffu) {
+        GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 8 * c->L.ncells, c->st));
+        c->stamp = 1;
+      }
+      int4* sorted = c->rec[c->cur ^ 1];
+      c->prof.begin(K_BUILD);
+      launch_build(c->P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4, c->cells,
+                   c->stamp, n, &c->dst->err, c->st);
+      c->prof.end(K_BUILD, (double)n);
+      c->prof.begin(K_ADVANCE);
+      launch_advance(c->P, S, sorted, c->pos4, c->cells, c->stamp, n, c->C, c->dst, c->st);
+      c->prof.end(K_ADVANCE, (double)n);
+      c->prof.begin(K_EMIT);
+      launch_emit(c->P, S, sorted, n, c->rec[c->cur], c->sb.keys[0], c->sb.vals[0], c->L.cap,
+                  c->C, c->R, c->estatus, c->eticket, c->dst, c->st);
+      c->prof.end(K_EMIT, (double)n);
+    }
+    const int64_t pending = c->n_nuclei - (int64_t)c->hst->nucleated;
+    if (pending > 0) {
+      const StepArgs S1 = step_args(c, c->step + 1);
+      c->prof.begin(K_NUCLEATE);
+      launch_nucleate(c->P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
+                      c->L.max_grains, c->rec[c->cur], c->sb.keys[0], c->sb.vals[0], c->L.cap,
+                      c->C, c->R, c->dst, c->st);
+      c->prof.end(K_NUCLEATE, 1.0);
+    } else {
+      c->prof.begin(K_FINALIZE);
+      launch_finalize(c->dst, c->L.cap, c->st);
+      c->prof.end(K_FINALIZE, 1.0);
+    }
+    GP_CUDA(c, cudaGetLastError());
+    ++c->step;
+    c->keys_valid = true;
+    s = sync_stats(c);
+    if (s) return s;
+  }
+  return GP_OK;
+}
+
+gp_status gp_stats(gp_ctx* c, gp_stats_t* o) {
+  if (!c || !o) return GP_ERR_ARG;
+  cudaSetDevice(c->device);
+  std::memset(o, 0, sizeof(*o));
+  if (cudaMemcpyAsync(c->hst, c->dst, sizeof(DevStats), cudaMemcpyDeviceToHost, c->st) ==
+      cudaSuccess)
+    cudaStreamSynchronize(c->st);
+  const DevStats& d = *c->hst;
+  o->step = c->step;
+  o->n_live = (int64_t)d.n_live;
+  o->n_frozen = (int64_t)d.n_frozen;
+  o->n_active = o->n_live - o->n_frozen;
+  o->n_grains = (int64_t)d.n_grains;
+  o->n_reached = (int64_t)std::min<unsigned long long>(d.reached, (unsigned long long)c->L.rcap);
+  o->particle_steps = (int64_t)d.particle_steps;
+  o->n_frozen_new = (int64_t)d.frozen_new;
+  o->n_spawned = (int64_t)d.spawned;
+  o->n_claims_lost = (int64_t)d.claims_lost;
+  o->n_clipped = (int64_t)d.clipped;
+  o->n_clamped = (int64_t)d.clamped;
+  o->n_nucleated = (int64_t)d.nucleated;
+  o->n_claim_blocks = (int64_t)d.claim_used;
+  o->error_flags = (int64_t)d.err;
+  return GP_OK;
+}
+
+gp_status gp_get_particles(gp_ctx* c, int64_t cap, int32_t* grain, int32_t* site3, int8_t* dir,
+                           float* ell, uint8_t* state, float* x3, int64_t* n_out) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (cap < 0) return fail(c, GP_ERR_ARG, "cap < 0");
+  const int64_t n = c->n_live;
+  if (n_out) *n_out = n;
+  const int64_t m = std::min(n, cap);
+  if (m == 0) return GP_OK;
+  std::vector<int4> recs(m);
+  GP_CUDA(c, cudaMemcpyAsync(recs.data(), c->rec[c->cur], sizeof(int4) * m,
+                             cudaMemcpyDeviceToHost, c->st));
+  if (x3) {
+    float* dx = reinterpret_cast<float*>(c->pos4);
+    launch_positions(c->P, c->rec[c->cur], m, dx, c->st);
+    GP_CUDA(c, cudaMemcpyAsync(x3, dx, sizeof(float) * 3 * m, cudaMemcpyDeviceToHost, c->st));
+  }
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  for (int64_t i = 0; i < m; ++i) {
+    Rec r = rec_unpack(recs[i]);
+    if (grain) grain[i] = r.grain;
+    if (site3) {
+      site3[3 * i] = r.sx;
+      site3[3 * i + 1] = r.sy;
+      site3[3 * i + 2] = r.sz;
+    }
+    if (dir) dir[i] = (int8_t)r.dir;
+    if (ell) ell[i] = r.ell;
+    if (state) state[i] = (uint8_t)r.state;
+  }
+  return GP_OK;
+}
+
+gp_status gp_load_particles(gp_ctx* c, int64_t n, const int32_t* grain, const int32_t* site3,
+                            const int8_t* dir, const float* ell, const uint8_t* state,
+                            int64_t step) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (n < 0 || n > c->L.cap) return fail(c, GP_ERR_CAPACITY, "n exceeds capacity");
+  if (n > 0 && (!grain || !site3 || !dir || !ell || !state)) return fail(c, GP_ERR_ARG, "null array");
+  std::vector<int4> recs(n);
+  for (int64_t i = 0; i < n; ++i) {
+    if (grain[i] < 0 || grain[i] >= c->n_grains || dir[i] < 0 || dir[i] > 5 || state[i] > 1 ||
+        !(ell[i] >= 0.f && ell[i] < 1.f))
+      return fail(c, GP_ERR_ARG, "invalid particle");
+    for (int a = 0; a < 3; ++a)
+      if (site3[3 * i + a] < -kSiteMax || site3[3 * i + a] > kSiteMax)
+        return fail(c, GP_ERR_ARG, "site out of range");
+    Rec r{};
+    r.grain = grain[i];
+    r.sx = site3[3 * i];
+    r.sy = site3[3 * i + 1];
+    r.sz = site3[3 * i + 2];
+    r.dir = dir[i];
+    r.state = state[i];
+    r.ell = ell[i];
+    recs[i] = rec_pack(r);
+  }
+  if (n > 0)
+    GP_CUDA(c, cudaMemcpyAsync(c->rec[c->cur], recs.data(), sizeof(int4) * n,
+                               cudaMemcpyHostToDevice, c->st));
+  c->n_live = n;
+  c->step = step;
+  c->keys_valid = false;
+  return push_counts(c);
+}
+
+gp_status gp_add_sites(gp_ctx* c, int64_t n, const int32_t* grain, const int32_t* site3,
+                       int32_t reached, int32_t claimed) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!grain || !site3))) return fail(c, GP_ERR_ARG, "bad arguments");
+  const int64_t chunk = c->L.cap;  // int4 entries that fit in the position buffer
+  std::vector<int4> v;
+  for (int64_t b = 0; b < n; b += chunk) {
+    const int64_t m = std::min(chunk, n - b);
+    v.resize(m);
+    for (int64_t i = 0; i < m; ++i) {
+      const int64_t j = b + i;
+      if (grain[j] < 0 || grain[j] >= c->n_grains) return fail(c, GP_ERR_ARG, "unknown grain");
+      v[i] = make_int4(grain[j], site3[3 * j], site3[3 * j + 1], site3[3 * j + 2]);
+    }
+    int4* stg = reinterpret_cast<int4*>(c->pos4);
+    GP_CUDA(c, cudaMemcpyAsync(stg, v.data(), sizeof(int4) * m, cudaMemcpyHostToDevice, c->st));
+    launch_mark_sites(c->P, stg, m, reached ? 1 : 0, claimed ? 1 : 0, c->C, c->R, c->st);
+    GP_CUDA(c, cudaStreamSynchronize(c->st));
+  }
+  GP_CUDA(c, cudaGetLastError());
+  return sync_stats(c);
+}
+
+gp_status gp_get_reached(gp_ctx* c, int64_t cap, int32_t* grain, int32_t* site3, int64_t* n_out) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  s = sync_stats(c);
+  if (s) return s;
+  const int64_t n = (int64_t)std::min<unsigned long long>(c->hst->reached, c->L.rcap);
+  if (n_out) *n_out = n;
+  const int64_t m = std::min(n, cap);
+  if (m <= 0) return GP_OK;
+  std::vector<unsigned long long> k(m);
+  GP_CUDA(c, cudaMemcpy(k.data(), c->R.key, 8 * m, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < m; ++i) {
+    int g, x, y, z;
+    unpack_site(k[i], g, x, y, z);
+    if (grain) grain[i] = g;
+    if (site3) {
+      site3[3 * i] = x;
+      site3[3 * i + 1] = y;
+      site3[3 * i + 2] = z;
+    }
+  }
+  return GP_OK;
+}
+
+gp_status gp_grain_map(gp_ctx* c, const gp_voxel_grid* g, int32_t* out, int32_t flags) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (!g || !out) return fail(c, GP_ERR_ARG, "null argument");
+  for (int a = 0; a < 3; ++a)
+    if (g->n[a] < 0) return fail(c, GP_ERR_ARG, "negative voxel count");
+  const int64_t nv = (int64_t)g->n[0] * g->n[1] * g->n[2];
+  if (nv == 0) return GP_OK;
+  const int nvox[3] = {g->n[0], g->n[1], g->n[2]};
+  c->prof.begin(K_GRAIN_MAP);
+  if (flags & GP_DEVICE_PTR) {
+    launch_grain_map(c->P, c->R, g->origin, g->spacing, nvox, out, 0, nv, c->st);
+  } else {
+    int32_t* stg = reinterpret_cast<int32_t*>(c->pos4);
+    const int64_t chunk = 4 * c->L.cap;
+    for (int64_t v0 = 0; v0 < nv; v0 += chunk) {
+      const int64_t m = std::min(chunk, nv - v0);
+      launch_grain_map(c->P, c->R, g->origin, g->spacing, nvox, stg, v0, m, c->st);
+      GP_CUDA(c, cudaMemcpyAsync(out + v0, stg, 4 * m, cudaMemcpyDeviceToHost, c->st));
+      GP_CUDA(c, cudaStreamSynchronize(c->st));
+    }
+  }
+  c->prof.end(K_GRAIN_MAP, (double)nv);
+  GP_CUDA(c, cudaGetLastError());
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  return GP_OK;
+}
+
+gp_status gp_profile(gp_ctx* c, int32_t enable) {
+  if (!c) return GP_ERR_ARG;
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return GP_OK;
+}
+
+gp_status gp_profile_read(gp_ctx* c, int32_t max, gp_kernel_prof* out, int32_t* n_out) {
+  if (!c) return GP_ERR_ARG;
+  c->prof.flush();
+  int k = 0;
+  for (int i = 0; i < K_COUNT; ++i) {
+    if (c->prof.launches[i] == 0) continue;
+    if (out && k < max) {
+      std::memset(&out[k], 0, sizeof(gp_kernel_prof));
+      std::snprintf(out[k].name, sizeof(out[k].name), "%s", kKernelNames[i]);
+      out[k].launches = c->prof.launches[i];
+      out[k].total_ms = c->prof.ms[i];
+      out[k].units = c->prof.units[i];
+      out[k].bytes_per_unit = kKernelBytes[i];
+    }
+    ++k;
+  }
+  if (n_out) *n_out = k;
+  return GP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// stand-alone hash / contact
+// ---------------------------------------------------------------------------------
+namespace {
+struct SaLayout {
+  size_t keys0, keys1, vals0, vals1, status, hist, tickets, err, flags, ofs, bsum, ncell, pos4,
+      sstate, cells, total;
+};
+bool sa_layout(int64_t n, uint64_t ncells, SaLayout* L) {
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t a = o;
+    o = align_up(o + b);
+    return a;
+  };
+  const size_t m = (size_t)std::max<int64_t>(n, 1);
+  L->keys0 = take(4 * m + 16);
+  L->keys1 = take(4 * m + 16);
+  L->vals0 = take(4 * m + 16);
+  L->vals1 = take(4 * m + 16);
+  L->status = take(4 * radix_status_words(n));
+  L->hist = take(4 * 4 * 256);
+  L->tickets = take(64);
+  L->err = take(64);
+  L->flags = take(4 * m);
+  L->ofs = take(4 * m);
+  L->bsum = take(4 * ((m + 255) / 256) + 16);
+  L->ncell = take(64);
+  L->pos4 = take(16 * m);
+  L->sstate = take(m);
+  L->cells = take(8 * (size_t)ncells);
+  L->total = o;
+  return true;
+}
+Params sa_params(const gp_domain* d, double h, const int nc[3]) {
+  Params P{};
+  for (int a = 0; a < 3; ++a) {
+    P.lo[a] = (float)d->lo[a];
+    P.hi[a] = (float)d->hi[a];
+    P.nc[a] = nc[a];
+  }
+  P.inv_c = (float)(1.0 / cell_edge(h));
+  float hf = (float)h;
+  P.rc2 = hf * hf;
+  return P;
+}
+}  // namespace
+
+gp_status gp_hash_workspace_bytes(int64_t n, const gp_domain* domain, double h,
+                                  size_t* out_bytes) {
+  if (!domain || !out_bytes || n < 0 || !(h > 0) || n >= (1ll << 30)) return GP_ERR_ARG;
+  int nc[3];
+  uint64_t ncells;
+  if (!cells_of(domain, h, nc, &ncells)) return GP_ERR_ARG;
+  SaLayout L;
+  sa_layout(n, ncells, &L);
+  *out_bytes = L.total;
+  return GP_OK;
+}
+
+static gp_status sa_sort(const float* x3, const uint8_t* state, int64_t n, const gp_domain* domain,
+                         double h, void* ws, size_t wsb, cudaStream_t st, SaLayout* L,
+                         Params* P, uint64_t* ncells, int* w, SortBufs* sb) {
+  int nc[3];
+  if (!cells_of(domain, h, nc, ncells)) return GP_ERR_ARG;
+  sa_layout(n, *ncells, L);
+  if (!ws || wsb < L->total || ((uintptr_t)ws & (kAlign - 1))) return GP_ERR_ARG;
+  char* b = (char*)ws;
+  *P = sa_params(domain, h, nc);
+  sb->keys[0] = (uint32_t*)(b + L->keys0);
+  sb->keys[1] = (uint32_t*)(b + L->keys1);
+  sb->vals[0] = (uint32_t*)(b + L->vals0);
+  sb->vals[1] = (uint32_t*)(b + L->vals1);
+  sb->status = (uint32_t*)(b + L->status);
+  sb->hist = (uint32_t*)(b + L->hist);
+  sb->ticket = (uint32_t*)(b + L->tickets);
+  sb->err = (uint32_t*)(b + L->err);
+  sb->max_n = n;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  sb->sms = 152;
+  cudaDeviceGetAttribute(&sb->sms, cudaDevAttrMultiProcessorCount, dev);
+  sb->prof = nullptr;
+  if (cudaMemsetAsync(sb->err, 0, 64, st) != cudaSuccess) return GP_ERR_CUDA;
+  launch_keys_pos(*P, x3, state, n, sb->keys[0], sb->vals[0], st);
+  uint64_t nm1 = *ncells - 1;
+  int nbits = 0;
+  while (nm1) {
+    ++nbits;
+    nm1 >>= 1;
+  }
+  if (state) nbits = 32;  // removed points carry key 0xffffffff and sort last
+  *w = radix_sort(*sb, n, nbits, st);
+  return GP_OK;
+}
+
+gp_status gp_hash_build(const float* x3, int64_t n, const gp_domain* domain, double h,
+                        uint32_t* keys_sorted, int32_t* ids_sorted, uint32_t* cell_keys,
+                        int32_t* cell_start, int64_t* n_cells, void* workspace,
+                        size_t workspace_bytes, void* cuda_stream) {
+  if (!domain || n < 0 || n >= (1ll << 30) || !(h > 0)) return GP_ERR_ARG;
+  if (n > 0 && (!x3 || !keys_sorted || !ids_sorted || !cell_keys || !cell_start))
+    return GP_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (n == 0) {
+    if (n_cells) *n_cells = 0;
+    return GP_OK;
+  }
+  SaLayout L;
+  Params P;
+  uint64_t ncells;
+  int w;
+  SortBufs sb{};
+  gp_status s = sa_sort(x3, nullptr, n, domain, h, workspace, workspace_bytes, st, &L, &P,
+                        &ncells, &w, &sb);
+  if (s) return s;
+  char* b = (char*)workspace;
+  if (cudaMemcpyAsync(keys_sorted, sb.keys[w], 4 * n, cudaMemcpyDeviceToDevice, st) ||
+      cudaMemcpyAsync(ids_sorted, sb.vals[w], 4 * n, cudaMemcpyDeviceToDevice, st) ||
+      cudaMemsetAsync(b + L.ncell, 0, 8, st))
+    return GP_ERR_CUDA;
+  launch_cells(sb.keys[w], n, (uint32_t)ncells, (uint32_t*)(b + L.flags), (uint32_t*)(b + L.ofs),
+               (uint32_t*)(b + L.bsum), cell_keys, cell_start,
+               (unsigned long long*)(b + L.ncell), st);
+  unsigned long long nc = 0;
+  uint32_t err = 0;
+  if (cudaMemcpyAsync(&nc, b + L.ncell, 8, cudaMemcpyDeviceToHost, st) ||
+      cudaMemcpyAsync(&err, sb.err, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st) ||
+      cudaGetLastError())
+    return GP_ERR_CUDA;
+  if (err) return GP_ERR_TIMEOUT;
+  if (n_cells) *n_cells = (int64_t)nc;
+  return GP_OK;
+}
+
+gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state, int64_t n,
+                     const gp_domain* domain, double h, uint8_t* freeze, int32_t* pairs,
+                     int64_t pair_cap, int64_t* n_pairs, void* workspace, size_t workspace_bytes,
+                     void* cuda_stream) {
+  if (!domain || n < 0 || n >= (1ll << 30) || !(h > 0) || pair_cap < 0) return GP_ERR_ARG;
+  if (n > 0 && (!x3 || !grain || !state)) return GP_ERR_ARG;
+  if (pairs && !n_pairs) return GP_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (n == 0) {
+    if (n_pairs) *n_pairs = 0;
+    return GP_OK;
+  }
+  SaLayout L;
+  Params P;
+  uint64_t ncells;
+  int w;
+  SortBufs sb{};
+  gp_status s = sa_sort(x3, state, n, domain, h, workspace, workspace_bytes, st, &L, &P, &ncells,
+                        &w, &sb);
+  if (s) return s;
+  char* b = (char*)workspace;
+  if (cudaMemsetAsync(b + L.cells, 0, 8 * ncells, st) || cudaMemsetAsync(b + L.ncell, 0, 8, st))
+    return GP_ERR_CUDA;
+  if (freeze && cudaMemsetAsync(freeze, 0, n, st)) return GP_ERR_CUDA;
+  launch_build_sa(P, x3, grain, state, sb.keys[w], sb.vals[w], n, (float4*)(b + L.pos4),
+                  (uint8_t*)(b + L.sstate), (unsigned long long*)(b + L.cells), sb.err, st);
+  launch_contact_sa(P, (const float4*)(b + L.pos4), (const uint8_t*)(b + L.sstate), sb.vals[w],
+                    (const unsigned long long*)(b + L.cells), n, freeze, pairs, pair_cap,
+                    (unsigned long long*)(b + L.ncell), st);
+  unsigned long long np = 0;
+  uint32_t err = 0;
+  if (cudaMemcpyAsync(&np, b + L.ncell, 8, cudaMemcpyDeviceToHost, st) ||
+      cudaMemcpyAsync(&err, sb.err, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st) ||
+      cudaGetLastError())
+    return GP_ERR_CUDA;
+  if (err) return GP_ERR_TIMEOUT;
+  if (n_pairs) *n_pairs = (int64_t)np;
+  return GP_OK;
+}
+
+}  // extern "C"

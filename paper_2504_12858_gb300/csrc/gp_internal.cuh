@@ -1,0 +1,414 @@
+// Internal device-side definitions of the grain-envelope particle library.
+//
+// Device state is binary32.  Notation follows Sec. 2.1.2 of the paper: a
+// particle of grain g at lattice site s (crystal frame, relative to the nucleus
+// c_g) moving in direction k with progress ell sits at
+//     x = c_g + h R_g s + ell * sigma_k * h R_g e_{a_k}
+// where a_k = k >> 1 is the axis and sigma_k = +1 for even k, -1 for odd k.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gp {
+
+// ---------------------------------------------------------------------------------
+// constants
+// ---------------------------------------------------------------------------------
+enum : int { ST_ACTIVE = 0, ST_FROZEN = 1, ST_REMOVED = 2 };
+
+// sticky device error bits (reported in gp_stats_t.error_flags)
+enum : uint32_t {
+  ERR_CAPACITY = 1u,      // particle store full
+  ERR_HASH_FULL = 2u,     // claim table probe limit / load exceeded
+  ERR_TIMEOUT = 4u,       // a bounded look-back wait gave up
+  ERR_REACHED_CAP = 8u,   // reached-site list full
+  ERR_CELL_OVERFLOW = 16u,// more than 65535 particles in one hash cell
+  ERR_GRAINS = 32u,       // grain table full
+  ERR_SITE_RANGE = 64u,   // lattice site outside [-4095, 4095]
+};
+
+constexpr int kSiteMax = 4095;
+constexpr int kClaimProbeLimit = 4096;
+constexpr uint32_t kSpinLimit = 1u << 22;  // polls (~seconds) before a look-back wait gives up
+constexpr int kBrickWords = 128;           // 8^3 sites, one byte each, 4 per word
+
+// ---------------------------------------------------------------------------------
+// particle record: 16 bytes, loaded and stored as one int4
+//   x: grain id
+//   y: sx (int16, low half) | sy (int16, high half)
+//   z: sz (int16, bits 0..15) | dir (bits 16..18) | state (bits 20..21) |
+//      crossing flag (bit 24: the particle reached its target this step)
+//   w: ell (binary32 bits)
+// ---------------------------------------------------------------------------------
+struct Rec {
+  int grain;
+  int sx, sy, sz;
+  int dir;
+  int state;
+  int cross;
+  float ell;
+};
+
+__host__ __device__ inline int4 rec_pack(const Rec& r) {
+  int4 v;
+  v.x = r.grain;
+  v.y = (int)((uint32_t)(uint16_t)(int16_t)r.sx | ((uint32_t)(uint16_t)(int16_t)r.sy << 16));
+  v.z = (int)((uint32_t)(uint16_t)(int16_t)r.sz | ((uint32_t)(r.dir & 7) << 16) |
+              ((uint32_t)(r.state & 3) << 20) | ((uint32_t)(r.cross & 1) << 24));
+#ifdef __CUDA_ARCH__
+  v.w = __float_as_int(r.ell);
+#else
+  union { float f; int i; } u;
+  u.f = r.ell;
+  v.w = u.i;
+#endif
+  return v;
+}
+
+__host__ __device__ inline Rec rec_unpack(int4 v) {
+  Rec r;
+  r.grain = v.x;
+  r.sx = (int16_t)(uint16_t)((uint32_t)v.y & 0xFFFFu);
+  r.sy = (int16_t)(uint16_t)((uint32_t)v.y >> 16);
+  r.sz = (int16_t)(uint16_t)((uint32_t)v.z & 0xFFFFu);
+  r.dir = ((uint32_t)v.z >> 16) & 7;
+  r.state = ((uint32_t)v.z >> 20) & 3;
+  r.cross = ((uint32_t)v.z >> 24) & 1;
+#ifdef __CUDA_ARCH__
+  r.ell = __int_as_float(v.w);
+#else
+  union { float f; int i; } u;
+  u.i = v.w;
+  r.ell = u.f;
+#endif
+  return r;
+}
+
+// ---------------------------------------------------------------------------------
+// simulation constants (passed by value to every kernel)
+// ---------------------------------------------------------------------------------
+struct Params {
+  float lo[3], hi[3];
+  float inv_c;       // (float)(1/h): cell index scale
+  int nc[3];         // hash cells per axis
+  float rc2;         // contact radius squared, hf * hf with hf = (float)h
+  float dt_over_h;   // (float)(dt / h)
+  int nterms;
+  float a[2], b[2];
+  int bint[2];       // b as a small integer exponent (1..8), else -1 (powf)
+  float TL;
+  int thermal;       // 0 none, 1 analytic, 2 grid
+  float G[3], xref[3];
+  const float* grid;
+  int gn[3];
+  float ginv[3];     // 1 / spacing
+  const float4* gtab;// grain table: 4 float4 per grain (c, rows of h R)
+};
+
+// per-step thermal constants (computed on the host in double, rounded once)
+struct StepArgs {
+  float dT_base;     // analytic: T_L - T0 - Tdot t
+  float gshift[3];   // grid: origin + frame_vel t
+  int parity;        // step & 1: which claimant bits of a site byte are live
+};
+
+// ---------------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void grain_load(const float4* gtab, int g, float4& c, float4& r0,
+                                           float4& r1, float4& r2) {
+  const float4* p = gtab + 4 * (size_t)g;
+  c = __ldg(p);
+  r0 = __ldg(p + 1);
+  r1 = __ldg(p + 2);
+  r2 = __ldg(p + 3);
+}
+
+// x = c + hR s, evaluated with explicit fused multiply-adds so every kernel that
+// needs a position obtains the same binary32 value.
+__device__ __forceinline__ float3 site_pos_g(float4 c, float4 r0, float4 r1, float4 r2, int sx,
+                                             int sy, int sz) {
+  float fx = (float)sx, fy = (float)sy, fz = (float)sz;
+  float3 p;
+  p.x = __fmaf_rn(r0.z, fz, __fmaf_rn(r0.y, fy, __fmaf_rn(r0.x, fx, c.x)));
+  p.y = __fmaf_rn(r1.z, fz, __fmaf_rn(r1.y, fy, __fmaf_rn(r1.x, fx, c.y)));
+  p.z = __fmaf_rn(r2.z, fz, __fmaf_rn(r2.y, fy, __fmaf_rn(r2.x, fx, c.z)));
+  return p;
+}
+
+__device__ __forceinline__ float3 add_dir(float3 p, float4 r0, float4 r1, float4 r2, int dir,
+                                          float ell) {
+  int a = dir >> 1;
+  float sl = (dir & 1) ? -ell : ell;
+  float cx = a == 0 ? r0.x : (a == 1 ? r0.y : r0.z);
+  float cy = a == 0 ? r1.x : (a == 1 ? r1.y : r1.z);
+  float cz = a == 0 ? r2.x : (a == 1 ? r2.y : r2.z);
+  p.x = __fmaf_rn(sl, cx, p.x);
+  p.y = __fmaf_rn(sl, cy, p.y);
+  p.z = __fmaf_rn(sl, cz, p.z);
+  return p;
+}
+
+__device__ __forceinline__ float3 part_pos(const float4* gtab, int g, int sx, int sy, int sz,
+                                           int dir, float ell) {
+  float4 c, r0, r1, r2;
+  grain_load(gtab, g, c, r0, r1, r2);
+  return add_dir(site_pos_g(c, r0, r1, r2, sx, sy, sz), r0, r1, r2, dir, ell);
+}
+
+__device__ __forceinline__ int cell1(float x, float lo, float inv, int n) {
+  float u = __fmul_rn(__fsub_rn(x, lo), inv);
+  int c = __float2int_rd(u);
+  return min(max(c, 0), n - 1);
+}
+
+__device__ __forceinline__ uint32_t cell_key(const Params& P, float3 p, int& cx, int& cy,
+                                             int& cz) {
+  cx = cell1(p.x, P.lo[0], P.inv_c, P.nc[0]);
+  cy = cell1(p.y, P.lo[1], P.inv_c, P.nc[1]);
+  cz = cell1(p.z, P.lo[2], P.inv_c, P.nc[2]);
+  return (uint32_t)(((uint64_t)cz * P.nc[1] + cy) * P.nc[0] + cx);
+}
+
+__device__ __forceinline__ bool inside(const Params& P, float3 p) {
+  return p.x >= P.lo[0] && p.x <= P.hi[0] && p.y >= P.lo[1] && p.y <= P.hi[1] &&
+         p.z >= P.lo[2] && p.z <= P.hi[2];
+}
+
+// squared distance with every product and sum rounded separately (no contraction)
+__device__ __forceinline__ float dist2_rn(float3 a, float3 b) {
+  float dx = __fsub_rn(a.x, b.x);
+  float dy = __fsub_rn(a.y, b.y);
+  float dz = __fsub_rn(a.z, b.z);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// outer direction at site s (increases |s|_1): s_a == 0 or sign(s_a) == sigma
+__device__ __forceinline__ bool is_outer(int sx, int sy, int sz, int k) {
+  int a = k >> 1;
+  int sa = a == 0 ? sx : (a == 1 ? sy : sz);
+  return sa == 0 || ((sa > 0) == ((k & 1) == 0));
+}
+
+__device__ __forceinline__ void step_site(int& sx, int& sy, int& sz, int k) {
+  int d = (k & 1) ? -1 : 1;
+  if ((k >> 1) == 0) sx += d;
+  else if ((k >> 1) == 1) sy += d;
+  else sz += d;
+}
+
+// ---------------------------------------------------------------------------------
+// thermal field and growth law
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float grid_T(const Params& P, const StepArgs& S, float3 p) {
+  float u[3] = {__fmul_rn(__fsub_rn(p.x, S.gshift[0]), P.ginv[0]),
+                __fmul_rn(__fsub_rn(p.y, S.gshift[1]), P.ginv[1]),
+                __fmul_rn(__fsub_rn(p.z, S.gshift[2]), P.ginv[2])};
+  int i0[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float um = (float)(P.gn[a] - 1);
+    float v = fminf(fmaxf(u[a], 0.f), um);
+    int i = min(__float2int_rd(v), P.gn[a] - 2);
+    i0[a] = i;
+    f[a] = v - (float)i;
+  }
+  const int nx = P.gn[0];
+  const size_t plane = (size_t)P.gn[0] * P.gn[1];
+  const float* b = P.grid + (size_t)i0[2] * plane + (size_t)i0[1] * nx + i0[0];
+  float t000 = __ldg(b), t100 = __ldg(b + 1);
+  float t010 = __ldg(b + nx), t110 = __ldg(b + nx + 1);
+  float t001 = __ldg(b + plane), t101 = __ldg(b + plane + 1);
+  float t011 = __ldg(b + plane + nx), t111 = __ldg(b + plane + nx + 1);
+  float c00 = __fmaf_rn(f[0], t100 - t000, t000);
+  float c10 = __fmaf_rn(f[0], t110 - t010, t010);
+  float c01 = __fmaf_rn(f[0], t101 - t001, t001);
+  float c11 = __fmaf_rn(f[0], t111 - t011, t011);
+  float e0 = __fmaf_rn(f[1], c10 - c00, c00);
+  float e1 = __fmaf_rn(f[1], c11 - c01, c01);
+  return __fmaf_rn(f[2], e1 - e0, e0);
+}
+
+__device__ __forceinline__ float undercooling(const Params& P, const StepArgs& S, float3 p) {
+  if (P.thermal == 1) {
+    float g = __fmul_rn(P.G[0], __fsub_rn(p.x, P.xref[0]));
+    g = __fmaf_rn(P.G[1], __fsub_rn(p.y, P.xref[1]), g);
+    g = __fmaf_rn(P.G[2], __fsub_rn(p.z, P.xref[2]), g);
+    return S.dT_base - g;
+  }
+  if (P.thermal == 2) return P.TL - grid_T(P, S, p);
+  return 0.f;
+}
+
+__device__ __forceinline__ float ipow(float x, int n) {
+  float r = x;
+  for (int i = 1; i < n; ++i) r *= x;
+  return r;
+}
+
+// Eq. (1) / Eq. (2); zero velocity without undercooling
+__device__ __forceinline__ float growth_v(const Params& P, float dT) {
+  if (!(dT > 0.f)) return 0.f;
+  float v = 0.f;
+  for (int i = 0; i < P.nterms; ++i) {
+    float pw = P.bint[i] > 0 ? ipow(dT, P.bint[i]) : powf(dT, P.b[i]);
+    v = __fmaf_rn(P.a[i], pw, v);
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------------
+// lattice-site claim table: open addressing over 8^3-site blocks of a grain; each
+// block holds one byte per site: bit 7 = claimed, bits 0..2 = claimant axes of an
+// even step, bits 3..5 = claimant axes of an odd step.
+// ---------------------------------------------------------------------------------
+struct Claims {
+  unsigned long long* keys;   // 0 = empty
+  uint32_t* data;             // kBrickWords words per bucket
+  uint32_t mask;              // buckets - 1
+  unsigned long long* used;   // occupied buckets
+  uint32_t* err;
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z ^= z >> 33;
+  z *= 0xff51afd7ed558ccdull;
+  z ^= z >> 33;
+  z *= 0xc4ceb9fe1a85ec53ull;
+  z ^= z >> 33;
+  return z;
+}
+
+// word holding the byte of site t of grain g; nullptr if absent (insert == false)
+// or if the table is full.
+__device__ inline uint32_t* claim_word(const Claims& C, int g, int tx, int ty, int tz,
+                                       bool insert, int& shift) {
+  if (tx < -kSiteMax || tx > kSiteMax || ty < -kSiteMax || ty > kSiteMax || tz < -kSiteMax ||
+      tz > kSiteMax) {
+    atomicOr(C.err, ERR_SITE_RANGE);
+    return nullptr;
+  }
+  unsigned long long key = ((unsigned long long)(g + 1) << 30) |
+                           ((unsigned long long)((tx >> 3) + 512) << 20) |
+                           ((unsigned long long)((ty >> 3) + 512) << 10) |
+                           (unsigned long long)((tz >> 3) + 512);
+  int local = (((tz & 7) << 3) | (ty & 7)) << 3 | (tx & 7);
+  shift = (local & 3) << 3;
+  uint32_t b = (uint32_t)mix64(key) & C.mask;
+  for (int i = 0; i < kClaimProbeLimit; ++i) {
+    unsigned long long k = *((volatile unsigned long long*)(C.keys + b));
+    if (k == key) return C.data + (size_t)b * kBrickWords + (local >> 2);
+    if (k == 0ull) {
+      if (!insert) return nullptr;
+      unsigned long long old = atomicCAS(C.keys + b, 0ull, key);
+      if (old == 0ull) {
+        atomicAdd(C.used, 1ull);
+        return C.data + (size_t)b * kBrickWords + (local >> 2);
+      }
+      if (old == key) return C.data + (size_t)b * kBrickWords + (local >> 2);
+    }
+    b = (b + 1) & C.mask;
+  }
+  atomicOr(C.err, ERR_HASH_FULL);
+  return nullptr;
+}
+
+// ---------------------------------------------------------------------------------
+// reached lattice sites: append-only list, linked per hash cell for range queries
+// ---------------------------------------------------------------------------------
+struct Reached {
+  unsigned long long* key;  // packed (grain, site)
+  uint32_t* next;           // next entry in the same cell, 0xFFFFFFFF ends
+  uint32_t* head;           // per hash cell
+  unsigned long long* count;
+  unsigned long long cap;
+  uint32_t* err;
+};
+
+__host__ __device__ __forceinline__ unsigned long long pack_site(int g, int sx, int sy, int sz) {
+  return ((unsigned long long)(uint32_t)g << 39) |
+         ((unsigned long long)(uint32_t)(sx + 4096) << 26) |
+         ((unsigned long long)(uint32_t)(sy + 4096) << 13) | (unsigned long long)(uint32_t)(sz + 4096);
+}
+__host__ __device__ __forceinline__ void unpack_site(unsigned long long k, int& g, int& sx, int& sy,
+                                                     int& sz) {
+  g = (int)(k >> 39);
+  sx = (int)((k >> 26) & 8191) - 4096;
+  sy = (int)((k >> 13) & 8191) - 4096;
+  sz = (int)(k & 8191) - 4096;
+}
+
+// ---------------------------------------------------------------------------------
+// device counters
+// ---------------------------------------------------------------------------------
+struct DevStats {
+  unsigned long long particle_steps;
+  unsigned long long frozen_new;
+  unsigned long long spawned;
+  unsigned long long claims_lost;
+  unsigned long long clipped;
+  unsigned long long clamped;
+  unsigned long long nucleated;
+  unsigned long long n_out;        // particles written by the last emit
+  unsigned long long n_frozen;     // FROZEN among them
+  unsigned long long n_grains;
+  unsigned long long reached;      // reached-site count (== Reached::count target)
+  unsigned long long claim_used;   // occupied claim buckets
+  unsigned long long n_live;       // after nucleation
+  uint32_t err;
+  uint32_t pad;
+  unsigned long long scratch[3];
+};
+
+// warp-aggregated 64-bit counter increment
+__device__ __forceinline__ void warp_add(unsigned long long* ctr, unsigned int v) {
+  unsigned int m = __activemask();
+  unsigned int s = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(m, s, o);
+  // all active lanes hold the sum only if m is full; fall back to per-lane atomics
+  if (m == 0xffffffffu) {
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+  } else if (v) {
+    atomicAdd(ctr, (unsigned long long)v);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------
+// kernel ids for the optional CUDA-event timing
+enum KernelId : int {
+  K_HIST = 0, K_ONESWEEP, K_KEYS, K_BUILD, K_ADVANCE, K_EMIT, K_NUCLEATE, K_GRAIN_MAP,
+  K_SEED, K_CONTACT, K_CELLS, K_FINALIZE, K_COUNT
+};
+
+struct ProfHook {
+  virtual void begin(int kid) = 0;
+  virtual void end(int kid, double units) = 0;
+  virtual ~ProfHook() {}
+};
+
+struct SortBufs {
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* status;          // look-back words: max_tiles * 256
+  uint32_t* hist;            // 4 passes * 256
+  uint32_t* ticket;          // 4 counters
+  uint32_t* err;
+  int64_t max_n;
+  int sms;
+  ProfHook* prof;
+};
+
+// radix sort of (keys[0], vals[0]) over the low nbits of the keys; returns the
+// buffer index (0 or 1) holding the sorted result.
+int radix_sort(const SortBufs& B, int64_t n, int nbits, cudaStream_t st);
+size_t radix_status_words(int64_t n);
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 15;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+}  // namespace gp

@@ -1,0 +1,51 @@
+// Host launchers of the step kernels (defined in gp_kernels.cu).
+#pragma once
+
+#include "gp_internal.cuh"
+
+namespace gp {
+
+void launch_keys(const Params& P, const int4* rec, int64_t n, uint32_t* keys, uint32_t* vals,
+                 cudaStream_t st);
+void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals, const int4* rin,
+                  int4* rout, float4* pos4, unsigned long long* tab, uint32_t stamp, int64_t n,
+                  uint32_t* err, cudaStream_t st);
+void launch_advance(const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
+                    const unsigned long long* tab, uint32_t stamp, int64_t n, const Claims& C,
+                    DevStats* dst, cudaStream_t st);
+int64_t emit_tiles(int64_t n);
+void launch_emit(const Params& P, const StepArgs& S, const int4* rs, int64_t n, int4* rout,
+                 uint32_t* keys, uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
+                 unsigned long long* status, uint32_t* ticket, DevStats* dst, cudaStream_t st);
+void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
+                     int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
+                     uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,
+                     cudaStream_t st);
+void launch_finalize(DevStats* dst, int64_t cap, cudaStream_t st);
+void launch_append(const int4* src, int64_t m, int4* rout, int64_t base, cudaStream_t st);
+void launch_mark_sites(const Params& P, const int4* sites, int64_t m, int reached, int claimed,
+                       const Claims& C, const Reached& R, cudaStream_t st);
+void launch_seed_shell(const Params& P, const int32_t* grains, int64_t ng, const short4* toff,
+                       int64_t nt, float ell0, int4* rout, int64_t cap,
+                       unsigned long long* counter, const Claims& C, uint32_t* err,
+                       cudaStream_t st);
+void launch_seed_shell_sites(const Params& P, const int32_t* grains, int64_t ng,
+                             const short4* soff, int64_t ns, const Claims& C, const Reached& R,
+                             cudaStream_t st);
+void launch_positions(const Params& P, const int4* rec, int64_t n, float* x3, cudaStream_t st);
+void launch_grain_map(const Params& P, const Reached& R, const double o[3], const double s[3],
+                      const int nvox[3], int32_t* out, int64_t v0, int64_t nv, cudaStream_t st);
+void launch_keys_pos(const Params& P, const float* x3, const uint8_t* state, int64_t n,
+                     uint32_t* keys, uint32_t* vals, cudaStream_t st);
+void launch_cells(const uint32_t* skeys, int64_t n, uint32_t nvalid_key, uint32_t* flags,
+                  uint32_t* ofs, uint32_t* bsum, uint32_t* cell_keys, int32_t* cell_start,
+                  unsigned long long* ncell, cudaStream_t st);
+void launch_build_sa(const Params& P, const float* x3, const int32_t* grain, const uint8_t* state,
+                     const uint32_t* skeys, const uint32_t* svals, int64_t n, float4* pos4,
+                     uint8_t* sstate, unsigned long long* tab, uint32_t* err, cudaStream_t st);
+void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstate,
+                       const uint32_t* ids, const unsigned long long* tab, int64_t n,
+                       uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
+                       unsigned long long* npairs, cudaStream_t st);
+
+}  // namespace gp

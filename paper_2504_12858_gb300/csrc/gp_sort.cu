@@ -1,0 +1,225 @@
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.
+//
+// One histogram kernel reads the keys once and counts every digit of every
+// pass.  Each pass is then a single kernel ("onesweep", after Adinets & Merrill,
+// "Onesweep: a faster least significant digit radix sort for GPUs", 2022):
+// a CTA ranks a tile of 3840 keys in shared memory (warp-level match ranking,
+// stable in input order), obtains the global offset of each digit for its tile by
+// decoupled look-back over the per-tile digit counts of the preceding tiles, and
+// scatters the tile through a shared-memory staging buffer so that equal digits
+// leave as contiguous runs.  Tiles are numbered by an atomic ticket, so a CTA
+// only ever waits for tiles whose CTAs are already resident; every wait is
+// bounded and reports ERR_TIMEOUT instead of spinning forever.
+#include "gp_internal.cuh"
+
+namespace gp {
+
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+__global__ void __launch_bounds__(256) k_hist(const uint32_t* __restrict__ keys, int64_t n,
+                                              int npass, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[4 * 256];
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n4 = n >> 2;
+  const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    uint4 v = __ldg(k4 + i);
+    uint32_t kk[4] = {v.x, v.y, v.z, v.w};
+    const uint32_t m = __activemask();
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      for (int p = 0; p < npass; ++p) {
+        // nearly sorted keys share digits across a warp: one shared atomic per
+        // distinct digit instead of one per lane
+        const uint32_t d = (kk[q] >> (8 * p)) & 255u;
+        const uint32_t peers = __match_any_sync(m, d);
+        if (lane == __ffs(peers) - 1) atomicAdd(&sh[p * 256 + d], (uint32_t)__popc(peers));
+      }
+  }
+  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t k = keys[i];
+    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// exclusive scan of 256 values held one per thread (blockDim.x == 256)
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < 8 ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < 8) s_warp[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t base = warp ? s_warp[warp - 1] : 0;
+  uint32_t r = base + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
+    uint32_t* status, uint32_t* ticket, uint32_t* err) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t s_whist[W][256];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_start[256];  // tile-local start of each digit
+  __shared__ uint32_t s_gofs[256];   // global position of tile-local index 0 of each digit
+  __shared__ uint32_t s_tmp[8];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+  for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t base = (int64_t)tile * kSortTile;
+
+  uint32_t k[kSortItems], v[kSortItems], rk[kSortItems];
+  int dg[kSortItems];
+  const int64_t wbase = base + (int64_t)warp * kSortItems * 32;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    int64_t idx = wbase + r * 32 + lane;
+    bool ok = idx < n;
+    k[r] = ok ? kin[idx] : 0xffffffffu;
+    v[r] = ok ? vin[idx] : 0u;
+    dg[r] = ok ? (int)((k[r] >> shift) & 255u) : 256;
+  }
+  const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int d = dg[r];
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0;
+    if (d < 256) before = s_whist[warp][d];
+    rk[r] = before + __popc(peers & lt_mask);
+    __syncwarp();
+    if (d < 256 && lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // per digit (one thread each): warp-exclusive offsets and the tile count
+  const int d = tid;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    uint32_t c = s_whist[w][d];
+    s_whist[w][d] = cnt;
+    cnt += c;
+  }
+  const uint32_t start = block_excl_scan_256(cnt, s_tmp);
+  s_start[d] = start;
+
+  // global digit base: exclusive scan of the whole-array histogram
+  const uint32_t dbase = block_excl_scan_256(hist[d], s_tmp);
+
+  // decoupled look-back over preceding tiles, digit d
+  uint32_t* my = status + (size_t)tile * 256 + d;
+  uint32_t excl = 0;
+  if (tile == 0) {
+    atomicExch(my, kFlagInc | cnt);
+  } else {
+    atomicExch(my, kFlagAgg | cnt);
+    int64_t pred = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (pred >= 0) {
+      uint32_t s = *((volatile uint32_t*)(status + (size_t)pred * 256 + d));
+      uint32_t flag = s & ~kValMask;
+      if (flag == 0u) {
+        if (++spins > kSpinLimit) {
+          atomicOr(err, ERR_TIMEOUT);
+          break;
+        }
+        continue;
+      }
+      excl += s & kValMask;
+      if (flag == kFlagInc) break;
+      --pred;
+    }
+    atomicExch(my, kFlagInc | ((excl + cnt) & kValMask));
+  }
+  s_gofs[d] = dbase + excl - start;  // wraps modulo 2^32; the sum below is exact
+  __syncthreads();
+
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    if (dg[r] < 256) {
+      uint32_t lp = s_start[dg[r]] + s_whist[warp][dg[r]] + rk[r];
+      s_keys[lp] = k[r];
+      s_vals[lp] = v[r];
+    }
+  }
+  __syncthreads();
+  const int64_t rem = n - base;
+  const int tn = rem < kSortTile ? (int)rem : kSortTile;
+  for (int i = tid; i < tn; i += kSortThreads) {
+    uint32_t key = s_keys[i];
+    uint32_t g = s_gofs[(key >> shift) & 255u] + (uint32_t)i;
+    if ((int64_t)g < n) {
+      kout[g] = key;
+      vout[g] = s_vals[i];
+    } else {
+      atomicOr(err, ERR_TIMEOUT);
+    }
+  }
+}
+
+}  // namespace
+
+size_t radix_status_words(int64_t n) {
+  int64_t tiles = (n + kSortTile - 1) / kSortTile;
+  return (size_t)(tiles < 1 ? 1 : tiles) * 256;
+}
+
+int radix_sort(const SortBufs& B, int64_t n, int nbits, cudaStream_t st) {
+  if (n <= 1 || nbits <= 0) return 0;
+  const int npass = (nbits + 7) / 8;
+  const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+  cudaMemsetAsync(B.hist, 0, sizeof(uint32_t) * 256 * npass, st);
+  cudaMemsetAsync(B.ticket, 0, sizeof(uint32_t) * 4, st);
+  int hblocks = (int)((n / 4 + 255) / 256);
+  if (hblocks > B.sms * 8) hblocks = B.sms * 8;
+  if (hblocks < 1) hblocks = 1;
+  if (B.prof) B.prof->begin(K_HIST);
+  k_hist<<<hblocks, 256, 0, st>>>(B.keys[0], n, npass, B.hist);
+  if (B.prof) B.prof->end(K_HIST, (double)n);
+  int cur = 0;
+  for (int p = 0; p < npass; ++p) {
+    cudaMemsetAsync(B.status, 0, sizeof(uint32_t) * 256 * (size_t)tiles, st);
+    if (B.prof) B.prof->begin(K_ONESWEEP);
+    k_onesweep<<<(unsigned)tiles, kSortThreads, 0, st>>>(
+        B.keys[cur], B.vals[cur], B.keys[cur ^ 1], B.vals[cur ^ 1], n, 8 * p, B.hist + 256 * p,
+        B.status, B.ticket + p, B.err);
+    if (B.prof) B.prof->end(K_ONESWEEP, (double)n);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+}  // namespace gp

@@ -1,0 +1,52 @@
+"""Test helpers: set up the same workload on the oracle and on the CUDA library."""
+import numpy as np
+
+import oracle
+from paper_2504_12858_gb300 import inputs
+
+
+def oracle_from(w: inputs.Workload, nucleate=True):
+    o = oracle.Oracle(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L)
+    if w.analytic:
+        o.set_thermal_analytic(w.analytic["T0"], w.analytic["G"], w.analytic["xref"],
+                               w.analytic["Tdot"])
+    if w.grid:
+        o.set_thermal_grid(w.grid["T"], w.grid["origin"], w.grid["spacing"], w.grid["vel"])
+    if w.seeds is not None and len(w.seeds):
+        o.add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0)
+        if w.shell_n0:
+            o.seed_shell(np.arange(len(w.seeds)), w.shell_n0)
+    if w.nuclei:
+        o.nucleation_sites(w.nuclei["pos"], w.nuclei["dTn"], w.nuclei["quat"])
+    return o
+
+
+def sim_from(w: inputs.Workload, capacity, nucleate=True, **kw):
+    from paper_2504_12858_gb300.native import Sim
+    grid_nodes = int(np.prod(w.grid["T"].shape)) if w.grid else 0
+    s = Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=capacity, grid_nodes=grid_nodes,
+            max_grains=max(16, 2 * (len(w.seeds) if w.seeds is not None else 0) +
+                           (len(w.nuclei["pos"]) if w.nuclei else 0)), **kw)
+    if w.analytic:
+        s.gp_set_thermal_analytic(w.analytic["T0"], w.analytic["G"], w.analytic["xref"],
+                                  w.analytic["Tdot"])
+    if w.grid:
+        s.gp_set_thermal_grid(w.grid["T"], w.grid["origin"], w.grid["spacing"], w.grid["vel"])
+    if w.seeds is not None and len(w.seeds):
+        s.gp_add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0)
+        if w.shell_n0:
+            s.gp_seed_shell(np.arange(len(w.seeds)), w.shell_n0)
+    if w.nuclei:
+        s.gp_nucleation_sites(w.nuclei["pos"], w.nuclei["dTn"], w.nuclei["quat"])
+    return s
+
+
+def canon(p):
+    """Particles sorted by (grain, site, dir): a canonical order for set comparison."""
+    key = np.lexsort((p["dir"], p["site"][:, 2], p["site"][:, 1], p["site"][:, 0], p["grain"]))
+    return {k: v[key] for k, v in p.items()}
+
+
+def keyset(p):
+    return {(int(g), int(a), int(b), int(c), int(d)) for g, (a, b, c), d in
+            zip(p["grain"], p["site"], p["dir"])}

@@ -330,7 +330,8 @@ def test_hash_f32_properties(n):
     if n > 10:
         x[:10] = x[10:20]         # duplicates exercise stability
     ks, ids, ck, cs = oracle.hash_build_f32(x, lo, hi, h)
-    nx = [max(1, math.ceil((hi[a] - lo[a]) / h)) for a in range(3)]
+    e = h * (1 + 1 / 512)
+    nx = [max(1, math.ceil((hi[a] - lo[a]) / e)) for a in range(3)]
     assert sorted(ids.tolist()) == list(range(n))
     assert np.all(np.diff(ks.astype(np.int64)) >= 0)
     same = np.diff(ks.astype(np.int64)) == 0
@@ -342,7 +343,7 @@ def test_hash_f32_properties(n):
     cy = (keys // nx[0]) % nx[1]
     cz = keys // (nx[0] * nx[1])
     cell = np.stack([cx, cy, cz], 1).astype(np.float64)
-    u = (x.astype(np.float64) - lo) / h
+    u = (x.astype(np.float64) - lo) / e
     assert (u >= cell - 1e-4).all() and (u < cell + 1 + 1e-4).all()
     # cell starts
     assert len(ck) == len(np.unique(ks))
@@ -445,3 +446,16 @@ def test_grain_map_equals_bruteforce_and_octahedron():
     m = int(math.floor(40 * v * dt / h))
     assert (mp[r <= m - 1.0] == 0).all()
     assert (mp[r >= m + 2.0] == -1).all()
+
+
+def test_commensurate_step_spawns_on_schedule():
+    # v dt = h / 4 exactly (the 200 um single-grain configuration): the target is
+    # reached every fourth step, so after 4k steps exactly the k-ball of sites is
+    # reached, whatever the rounding of the accumulated progress.
+    o = _uniform_sim(5.0, half=100e-6)          # A = 1e-5, dT = 5 K, dt = 2 ms, h = 2 um
+    for k in range(1, 16):
+        o.step(4)
+        g, _ = o.reached()
+        assert len(g) == (2 * k + 1) * (2 * k * k + 2 * k + 3) // 3
+        assert o.n_particles == 4 * (k + 1) ** 2 + 2
+        assert np.all(o.particles()["ell"] < 1e-9)
