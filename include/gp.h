@@ -265,6 +265,34 @@ gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state
                      int64_t pair_cap, int64_t* n_pairs, void* workspace,
                      size_t workspace_bytes, void* cuda_stream);
 
+/* ---- stand-alone hash without allocation ------------------------------------- */
+
+/* Largest point count gp_hash_build_static accepts. */
+#define GP_STATIC_SCRATCH_MAX_POINTS 262144
+
+/* The spatial hash of gp_hash_build (same keys, order, cells and arguments, with
+ * x3, keys_sorted, ids_sorted, cell_keys and cell_start in device memory), for
+ * callers that can neither pass a workspace nor let the library allocate one:
+ * for example a solver embedded in a host code whose device memory is owned and
+ * budgeted by that code's own allocator, or a caller that must not pay the
+ * device synchronisation of cudaMalloc.  The paper has no counterpart of this
+ * call; it exists for such callers only.
+ * Scratch comes from one static device array of the library (about 6.5 MB),
+ * which every GPU that loads the library keeps until the process exits.  The
+ * call allocates no device memory.
+ *  - n > GP_STATIC_SCRATCH_MAX_POINTS returns GP_ERR_CAPACITY (nothing runs).
+ *  - All calls on a device share the array and find what the previous call left
+ *    there; the call clears the counters that must start at zero.  Calls whose
+ *    device work can overlap (other streams, unordered host threads) race on the
+ *    array and must be ordered by the caller.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current and caches it; make that first call before any stream
+ *    capture on the device.
+ * Synchronises cuda_stream to return *n_cells. */
+gp_status gp_hash_build_static(const float* x3, int64_t n, const gp_domain* domain, double h,
+                               uint32_t* keys_sorted, int32_t* ids_sorted, uint32_t* cell_keys,
+                               int32_t* cell_start, int64_t* n_cells, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

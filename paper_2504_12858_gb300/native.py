@@ -95,7 +95,10 @@ SIGNATURES = {
                                 C.POINTER(C.c_int64), _P, C.c_size_t, _P]),
     "gp_contact": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(gp_domain), C.c_double, _P, _P,
                              C.c_int64, C.POINTER(C.c_int64), _P, C.c_size_t, _P]),
+    "gp_hash_build_static": (C.c_int, [_P, C.c_int64, C.POINTER(gp_domain), C.c_double, _P, _P,
+                                       _P, _P, C.POINTER(C.c_int64), _P]),
 }
+GP_STATIC_SCRATCH_MAX_POINTS = 262144
 
 _lib = None
 
