@@ -131,9 +131,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------
 # workload construction
 # ----------------------------------------------------------------------------------
-def fixture(n_grains: int, n0: int):
+def fixture(n_grains: int, n0: int, plate_mm=(4.0, 2.0, 1.0)):
     from paper_2504_12858_gb300 import inputs
-    return inputs.weld_fixture(n_grains=n_grains, shell_n0=n0)
+    return inputs.weld_fixture(n_grains=n_grains, shell_n0=n0,
+                               extent=tuple(v * 1e-3 for v in plate_mm))
 
 
 def measured_peak():
@@ -229,7 +230,7 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     native.load()
-    w = fixture(args.grains, args.n0)
+    w = fixture(args.grains, args.n0, args.plate)
     per_grain = 4 * (args.n0 + 1) ** 2 + 2
     n0_est = args.grains * per_grain
     total_steps = args.warmup + args.steps + args.e2e_steps
@@ -237,8 +238,11 @@ def run_native(args, rank, world, local_rank):
     capacity = int(args.capacity or min((1 << 30) - 1, int(n0_est * 1.05 ** total_steps * 1.3)
                                         + 1000000))
     reached = int(args.reached or min((1 << 32) - 2, int(n0_est * (1.2 + 0.9 * total_steps))))
+    # claim blocks: an envelope growing from 50 to 70 lattice shells touches about
+    # 1200 blocks of 8^3 sites (plus reservations lost to insertion races)
+    blocks = args.claim_blocks or args.grains * 2000
     sim = native.Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=capacity,
-                     reached_capacity=reached, claim_buckets=args.claim_buckets,
+                     reached_capacity=reached, claim_blocks=blocks,
                      max_grains=args.grains + 16, grid_nodes=int(np.prod(w.grid["T"].shape)),
                      device=dev)
     g = w.grid
@@ -320,9 +324,11 @@ def run_native(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "grains": args.grains, "shell_n0": args.n0,
+                       "plate_mm": list(args.plate),
                        "particles_at_start": n_start,
                        "active_at_timed_start": st0["n_active"],
                        "live_at_end": st1["n_live"], "parallelism": f"replicas x{world}",
+                       "claim_blocks_used": round(st1["n_claim_blocks"] / blocks, 3),
                        "l2": "inputs larger than L2 (particle store > 1.5 GB)"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cb,
             "e2e": {"value": e2e_value, "unit": METRIC, "steps": args.e2e_steps,
@@ -344,7 +350,10 @@ def main():
     ap.add_argument("--n0", type=int, default=50)
     ap.add_argument("--capacity", type=int, default=0)
     ap.add_argument("--reached", type=int, default=0)
-    ap.add_argument("--claim-buckets", type=int, default=1 << 24)
+    ap.add_argument("--claim-blocks", type=int, default=0)
+    ap.add_argument("--plate", type=float, nargs=3, default=(4.0, 2.0, 1.0),
+                    help="plate size in mm (smaller plates with proportionally fewer grains "
+                         "keep the grain density; used for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-grains", type=int, default=100)
     ap.add_argument("--ref-grains", type=int, default=40)

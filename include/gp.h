@@ -99,8 +99,9 @@ typedef struct {
 typedef struct {
   int64_t capacity;         /* live (ACTIVE + FROZEN) particles; required > 0     */
   int64_t reached_capacity; /* reached lattice sites; default 2 * capacity        */
-  int64_t claim_buckets;    /* 8^3-site blocks of the claim table (power of two);
-                               default from capacity                              */
+  int64_t claim_blocks;     /* 8^3-site blocks of lattice-site claims (512 bytes
+                               each, allocated on first claim); default
+                               capacity / 32                                      */
   int32_t max_grains;       /* default 1 << 20                                    */
   int32_t max_nuclei;       /* pending nucleation sites; default 4096             */
   int64_t grid_nodes;       /* thermal-grid nodes reserved in the arena; default 0 */
@@ -122,7 +123,7 @@ typedef struct {
   int64_t n_clipped;      /* particles removed at the domain boundary              */
   int64_t n_clamped;      /* advances capped at one lattice spacing per step       */
   int64_t n_nucleated;
-  int64_t n_claim_blocks; /* occupied claim-table blocks                           */
+  int64_t n_claim_blocks; /* claim blocks in use (at most gp_memory.claim_blocks)   */
   int64_t error_flags;    /* sticky device error bits (0 when healthy)             */
   int64_t reserved[5];
 } gp_stats_t;

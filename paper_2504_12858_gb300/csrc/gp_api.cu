@@ -25,12 +25,14 @@ inline double cell_edge(double h) { return h * (1.0 + 1.0 / 512.0); }
 struct Layout {
   int nc[3];
   uint64_t ncells;
+  int nsx;        // cell-table segments per x row
+  uint64_t nseg;  // cell-table entries
   int nbits;
-  int64_t cap, rcap, buckets;
+  int64_t cap, rcap, blocks, buckets;
   int max_grains, max_nuclei;
   int64_t grid_nodes;
   // offsets into the arena
-  size_t rec0, rec1, pos4, keys0, keys1, vals0, vals1, sstatus, hist, tickets, estatus, cells,
+  size_t rec0, rec1, pos4, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
       rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, dstats, grid, total;
 };
 
@@ -77,10 +79,10 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
   L->cap = m->capacity;
   L->rcap = m->reached_capacity > 0 ? m->reached_capacity : 2 * m->capacity;
   if (L->rcap >= (1ll << 32) - 1) L->rcap = (1ll << 32) - 2;
-  int64_t b = m->claim_buckets > 0 ? m->claim_buckets : std::max<int64_t>(4096, m->capacity / 16);
-  L->buckets = pow2_at_least(b);
-  if (L->buckets > (1ll << 31)) {
-    *why = "claim_buckets too large";
+  L->blocks = m->claim_blocks > 0 ? m->claim_blocks : std::max<int64_t>(4096, m->capacity / 32);
+  L->buckets = pow2_at_least(2 * L->blocks);
+  if (L->buckets > (1ll << 31) || L->blocks >= (1ll << 32) - 1) {
+    *why = "claim_blocks too large";
     return false;
   }
   L->max_grains = m->max_grains > 0 ? m->max_grains : (1 << 20);
@@ -90,6 +92,8 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
   }
   L->max_nuclei = m->max_nuclei > 0 ? m->max_nuclei : 4096;
   L->grid_nodes = m->grid_nodes > 0 ? m->grid_nodes : 0;
+  L->nsx = (L->nc[0] + kSegCells - 1) / kSegCells;
+  L->nseg = (uint64_t)L->nsx * L->nc[1] * L->nc[2];
   uint64_t nm1 = L->ncells - 1;
   L->nbits = 0;
   while (nm1) {
@@ -113,13 +117,12 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
   L->sstatus = take(4 * radix_status_words(L->cap));
   L->hist = take(4 * 4 * 256);
   L->tickets = take(4 * 8);
-  L->estatus = take(8 * (size_t)std::max<int64_t>(1, emit_tiles(L->cap)));
-  L->cells = take(8 * (size_t)L->ncells);
+  L->cells = take(16 * (size_t)L->nseg);
   L->rkey = take(8 * (size_t)L->rcap);
   L->rnext = take(4 * (size_t)L->rcap);
   L->rhead = take(4 * (size_t)L->ncells);
-  L->ckeys = take(8 * (size_t)L->buckets);
-  L->cdata = take(4 * kBrickWords * (size_t)L->buckets);
+  L->ckeys = take(16 * (size_t)L->buckets);
+  L->cdata = take(4 * kBrickWords * (size_t)L->blocks);
   L->gtab = take(64 * (size_t)L->max_grains);
   L->npos = take(16 * (size_t)L->max_nuclei);
   L->ngrain = take(64 * (size_t)L->max_nuclei);
@@ -260,7 +263,7 @@ struct gp_ctx {
   int cur = 0;  // rec[cur] is the (unsorted) store
   float4* pos4 = nullptr;
   SortBufs sb{};
-  unsigned long long* cells = nullptr;
+  uint4* cells = nullptr;
   uint32_t stamp = 0;
   Claims C{};
   Reached R{};
@@ -270,8 +273,6 @@ struct gp_ctx {
   int* nstate = nullptr;
   DevStats* dst = nullptr;
   DevStats* hst = nullptr;  // pinned mirror
-  unsigned long long* estatus = nullptr;
-  uint32_t* eticket = nullptr;
   // host mirrors
   int64_t n_live = 0, n_grains = 0, step = 0;
   int n_nuclei = 0;
@@ -317,6 +318,7 @@ void refresh_params(gp_ctx* c) {
     P.hi[a] = (float)c->hi[a];
     P.nc[a] = c->L.nc[a];
   }
+  P.nsx = c->L.nsx;
   P.inv_c = (float)(1.0 / cell_edge(c->h));
   float hf = (float)c->h;
   P.rc2 = hf * hf;
@@ -352,7 +354,7 @@ gp_status sync_stats(gp_ctx* c) {
     if (e & ERR_CAPACITY) return fail(c, GP_ERR_CAPACITY, "particle capacity exceeded");
     if (e & ERR_REACHED_CAP) return fail(c, GP_ERR_CAPACITY, "reached-site capacity exceeded");
     if (e & ERR_GRAINS) return fail(c, GP_ERR_CAPACITY, "grain capacity exceeded");
-    if (e & ERR_HASH_FULL) return fail(c, GP_ERR_HASH_FULL, "claim table full");
+    if (e & ERR_HASH_FULL) return fail(c, GP_ERR_HASH_FULL, "claim table full (raise claim_blocks)");
     if (e & ERR_TIMEOUT) return fail(c, GP_ERR_TIMEOUT, "bounded device wait gave up");
     if (e & ERR_CELL_OVERFLOW) return fail(c, GP_ERR_CAPACITY, "more than 65535 particles in a cell");
     if (e & ERR_SITE_RANGE) return fail(c, GP_ERR_ARG, "lattice site outside [-4095, 4095]");
@@ -474,9 +476,7 @@ gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growt
   c->sb.sms = c->sms;
   c->sb.prof = &c->prof;
   c->prof.st = c->st;
-  c->eticket = at<uint32_t>(c, L.tickets) + 4;
-  c->estatus = at<unsigned long long>(c, L.estatus);
-  c->cells = at<unsigned long long>(c, L.cells);
+  c->cells = at<uint4>(c, L.cells);
   c->dst = at<DevStats>(c, L.dstats);
   c->sb.err = &c->dst->err;
   c->R.key = at<unsigned long long>(c, L.rkey);
@@ -485,9 +485,10 @@ gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growt
   c->R.count = &c->dst->reached;
   c->R.cap = (unsigned long long)L.rcap;
   c->R.err = &c->dst->err;
-  c->C.keys = at<unsigned long long>(c, L.ckeys);
+  c->C.bucket = at<ulonglong2>(c, L.ckeys);
   c->C.data = at<uint32_t>(c, L.cdata);
   c->C.mask = (uint32_t)(L.buckets - 1);
+  c->C.pool_cap = (uint32_t)L.blocks;
   c->C.used = &c->dst->claim_used;
   c->C.err = &c->dst->err;
   c->gtab = at<float4>(c, L.gtab);
@@ -497,10 +498,10 @@ gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growt
   refresh_params(c);
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
-  e = e ? e : cudaMemsetAsync(c->cells, 0, 8 * L.ncells, s);
+  e = e ? e : cudaMemsetAsync(c->cells, 0, 16 * L.nseg, s);
   e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.ncells, s);
-  e = e ? e : cudaMemsetAsync(c->C.keys, 0, 8 * (size_t)L.buckets, s);
-  e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.buckets, s);
+  e = e ? e : cudaMemsetAsync(c->C.bucket, 0, 16 * (size_t)L.buckets, s);
+  e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.blocks, s);
   e = e ? e : cudaMemsetAsync(c->dst, 0, sizeof(DevStats), s);
   e = e ? e : cudaMemsetAsync(c->gtab, 0, 64 * (size_t)L.max_grains, s);
   e = e ? e : cudaMemsetAsync(c->nstate, 0, 4 * (size_t)L.max_nuclei, s);
@@ -721,7 +722,7 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       }
       const int w = radix_sort(c->sb, n, c->L.nbits, c->st);
       if (++c->stamp > 0xffffu) {
-        GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 8 * c->L.ncells, c->st));
+        GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
         c->stamp = 1;
       }
       int4* sorted = c->rec[c->cur ^ 1];
@@ -730,16 +731,18 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                    c->stamp, n, &c->dst->err, c->st);
       c->prof.end(K_BUILD, (double)n);
       c->prof.begin(K_ADVANCE);
-      launch_advance(c->P, S, sorted, c->pos4, c->cells, c->stamp, n, c->C, c->dst, c->st);
+      launch_advance(c->P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->C,
+                     c->dst, c->st);
       c->prof.end(K_ADVANCE, (double)n);
       c->prof.begin(K_EMIT);
       launch_emit(c->P, S, sorted, n, c->rec[c->cur], c->sb.keys[0], c->sb.vals[0], c->L.cap,
-                  c->C, c->R, c->estatus, c->eticket, c->dst, c->st);
+                  c->C, c->R, c->dst, c->st);
       c->prof.end(K_EMIT, (double)n);
     }
     const int64_t pending = c->n_nuclei - (int64_t)c->hst->nucleated;
     if (pending > 0) {
       const StepArgs S1 = step_args(c, c->step + 1);
+      launch_link_reached(c->P, c->R, &c->dst->linked, c->sms, c->st);
       c->prof.begin(K_NUCLEATE);
       launch_nucleate(c->P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
                       c->L.max_grains, c->rec[c->cur], c->sb.keys[0], c->sb.vals[0], c->L.cap,
@@ -909,6 +912,7 @@ gp_status gp_grain_map(gp_ctx* c, const gp_voxel_grid* g, int32_t* out, int32_t 
   const int64_t nv = (int64_t)g->n[0] * g->n[1] * g->n[2];
   if (nv == 0) return GP_OK;
   const int nvox[3] = {g->n[0], g->n[1], g->n[2]};
+  launch_link_reached(c->P, c->R, &c->dst->linked, c->sms, c->st);
   c->prof.begin(K_GRAIN_MAP);
   if (flags & GP_DEVICE_PTR) {
     launch_grain_map(c->P, c->R, g->origin, g->spacing, nvox, out, 0, nv, c->st);
@@ -963,7 +967,10 @@ struct SaLayout {
   size_t keys0, keys1, vals0, vals1, status, hist, tickets, err, flags, ofs, bsum, ncell, pos4,
       sstate, cells, total;
 };
-bool sa_layout(int64_t n, uint64_t ncells, SaLayout* L) {
+uint64_t sa_segments(const int nc[3]) {
+  return (uint64_t)((nc[0] + kSegCells - 1) / kSegCells) * nc[1] * nc[2];
+}
+bool sa_layout(int64_t n, uint64_t nseg, SaLayout* L) {
   size_t o = 0;
   auto take = [&](size_t b) {
     size_t a = o;
@@ -985,7 +992,7 @@ bool sa_layout(int64_t n, uint64_t ncells, SaLayout* L) {
   L->ncell = take(64);
   L->pos4 = take(16 * m);
   L->sstate = take(m);
-  L->cells = take(8 * (size_t)ncells);
+  L->cells = take(16 * (size_t)nseg);
   L->total = o;
   return true;
 }
@@ -996,6 +1003,7 @@ Params sa_params(const gp_domain* d, double h, const int nc[3]) {
     P.hi[a] = (float)d->hi[a];
     P.nc[a] = nc[a];
   }
+  P.nsx = (nc[0] + kSegCells - 1) / kSegCells;
   P.inv_c = (float)(1.0 / cell_edge(h));
   float hf = (float)h;
   P.rc2 = hf * hf;
@@ -1010,7 +1018,7 @@ gp_status gp_hash_workspace_bytes(int64_t n, const gp_domain* domain, double h,
   uint64_t ncells;
   if (!cells_of(domain, h, nc, &ncells)) return GP_ERR_ARG;
   SaLayout L;
-  sa_layout(n, ncells, &L);
+  sa_layout(n, sa_segments(nc), &L);
   *out_bytes = L.total;
   return GP_OK;
 }
@@ -1020,7 +1028,7 @@ static gp_status sa_sort(const float* x3, const uint8_t* state, int64_t n, const
                          Params* P, uint64_t* ncells, int* w, SortBufs* sb) {
   int nc[3];
   if (!cells_of(domain, h, nc, ncells)) return GP_ERR_ARG;
-  sa_layout(n, *ncells, L);
+  sa_layout(n, sa_segments(nc), L);
   if (!ws || wsb < L->total || ((uintptr_t)ws & (kAlign - 1))) return GP_ERR_ARG;
   char* b = (char*)ws;
   *P = sa_params(domain, h, nc);
@@ -1111,14 +1119,15 @@ gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state
                         &w, &sb);
   if (s) return s;
   char* b = (char*)workspace;
-  if (cudaMemsetAsync(b + L.cells, 0, 8 * ncells, st) || cudaMemsetAsync(b + L.ncell, 0, 8, st))
+  if (cudaMemsetAsync(b + L.cells, 0, 16 * sa_segments(P.nc), st) ||
+      cudaMemsetAsync(b + L.ncell, 0, 8, st))
     return GP_ERR_CUDA;
   if (freeze && cudaMemsetAsync(freeze, 0, n, st)) return GP_ERR_CUDA;
   launch_build_sa(P, x3, grain, state, sb.keys[w], sb.vals[w], n, (float4*)(b + L.pos4),
-                  (uint8_t*)(b + L.sstate), (unsigned long long*)(b + L.cells), sb.err, st);
+                  (uint8_t*)(b + L.sstate), (uint4*)(b + L.cells), sb.err, st);
   launch_contact_sa(P, (const float4*)(b + L.pos4), (const uint8_t*)(b + L.sstate), sb.vals[w],
-                    (const unsigned long long*)(b + L.cells), n, freeze, pairs, pair_cap,
-                    (unsigned long long*)(b + L.ncell), st);
+                    sb.keys[w], (const uint4*)(b + L.cells), n, freeze, pairs,
+                    pair_cap, (unsigned long long*)(b + L.ncell), st);
   unsigned long long np = 0;
   uint32_t err = 0;
   if (cudaMemcpyAsync(&np, b + L.ncell, 8, cudaMemcpyDeviceToHost, st) ||

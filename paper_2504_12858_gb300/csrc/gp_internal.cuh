@@ -32,6 +32,8 @@ constexpr int kSiteMax = 4095;
 constexpr int kClaimProbeLimit = 4096;
 constexpr uint32_t kSpinLimit = 1u << 22;  // polls (~seconds) before a look-back wait gives up
 constexpr int kBrickWords = 128;           // 8^3 sites, one byte each, 4 per word
+constexpr int kSegShift = 4;               // the cell table has one entry per 16 cells of a row
+constexpr int kSegCells = 1 << kSegShift;
 
 // ---------------------------------------------------------------------------------
 // particle record: 16 bytes, loaded and stored as one int4
@@ -90,8 +92,9 @@ __host__ __device__ inline Rec rec_unpack(int4 v) {
 // ---------------------------------------------------------------------------------
 struct Params {
   float lo[3], hi[3];
-  float inv_c;       // (float)(1/h): cell index scale
+  float inv_c;       // (float)(1/edge): cell index scale
   int nc[3];         // hash cells per axis
+  int nsx;           // segments of kSegCells cells per x row of the hash grid
   float rc2;         // contact radius squared, hf * hf with hf = (float)h
   float dt_over_h;   // (float)(dt / h)
   int nterms;
@@ -264,13 +267,25 @@ __device__ __forceinline__ float growth_v(const Params& P, float dT) {
 // block holds one byte per site: bit 7 = claimed, bits 0..2 = claimant axes of an
 // even step, bits 3..5 = claimant axes of an odd step.
 // ---------------------------------------------------------------------------------
+// The blocks live in a dense pool, handed out in order of first claim (so blocks
+// claimed by nearby particles sit close together in memory); an open-addressing
+// hash maps each block key to its pool slot.  A bucket is {key, slot + 1}: the
+// thread whose compare-and-swap puts the key into an empty bucket reserves the
+// pool slot and publishes it in the second word; until then the bucket is
+// "pending" (key set, slot word 0).  Claims are made by whole warps together
+// (warp_claim_word): each warp first inserts and publishes everything it
+// inserts, and only then waits, with a bound, for slots other warps are
+// publishing, so no wait can close a cycle.
 struct Claims {
-  unsigned long long* keys;   // 0 = empty
-  uint32_t* data;             // kBrickWords words per bucket
+  ulonglong2* bucket;         // {block key, pool slot + 1}; {0, 0} = empty
+  uint32_t* data;             // pool: kBrickWords words per block
   uint32_t mask;              // buckets - 1
-  unsigned long long* used;   // occupied buckets
+  uint32_t pool_cap;          // blocks in the pool
+  unsigned long long* used;   // pool blocks handed out
   uint32_t* err;
 };
+
+constexpr unsigned long long kSlotFull = ~0ull;  // published when the pool is full
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   z ^= z >> 33;
@@ -281,38 +296,130 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z;
 }
 
-// word holding the byte of site t of grain g; nullptr if absent (insert == false)
-// or if the table is full.
-__device__ inline uint32_t* claim_word(const Claims& C, int g, int tx, int ty, int tz,
-                                       bool insert, int& shift) {
-  if (tx < -kSiteMax || tx > kSiteMax || ty < -kSiteMax || ty > kSiteMax || tz < -kSiteMax ||
-      tz > kSiteMax) {
-    atomicOr(C.err, ERR_SITE_RANGE);
-    return nullptr;
-  }
-  unsigned long long key = ((unsigned long long)(g + 1) << 30) |
-                           ((unsigned long long)((tx >> 3) + 512) << 20) |
-                           ((unsigned long long)((ty >> 3) + 512) << 10) |
-                           (unsigned long long)((tz >> 3) + 512);
-  int local = (((tz & 7) << 3) | (ty & 7)) << 3 | (tx & 7);
-  shift = (local & 3) << 3;
+__device__ __forceinline__ unsigned long long block_key(int g, int bx, int by, int bz) {
+  return ((unsigned long long)(g + 1) << 30) | ((unsigned long long)(bx + 512) << 20) |
+         ((unsigned long long)(by + 512) << 10) | (unsigned long long)(bz + 512);
+}
+
+__device__ __forceinline__ int64_t slot_of(unsigned long long v) {
+  return v == kSlotFull ? -1 : (int64_t)(v - 1);
+}
+
+// Looks up (and with insert, inserts) block `key` without waiting.  Returns its
+// pool slot; -1 if absent (insert == false) or if the table or pool is full;
+// -2 - b if bucket b holds the key but another thread has not yet published the
+// slot.  Linear probing from a mixed hash of the full key: a home bucket with
+// spatial locality (grain offset + Morton code of the block) clusters the
+// occupied buckets into long runs and multiplies the probe lengths by two orders
+// of magnitude at the loads used here.
+__device__ inline int64_t claim_probe(const Claims& C, unsigned long long key, bool insert) {
   uint32_t b = (uint32_t)mix64(key) & C.mask;
   for (int i = 0; i < kClaimProbeLimit; ++i) {
-    unsigned long long k = *((volatile unsigned long long*)(C.keys + b));
-    if (k == key) return C.data + (size_t)b * kBrickWords + (local >> 2);
+    volatile unsigned long long* kv = &C.bucket[b].x;
+    volatile unsigned long long* sv = &C.bucket[b].y;
+    unsigned long long k = *kv;
     if (k == 0ull) {
-      if (!insert) return nullptr;
-      unsigned long long old = atomicCAS(C.keys + b, 0ull, key);
-      if (old == 0ull) {
-        atomicAdd(C.used, 1ull);
-        return C.data + (size_t)b * kBrickWords + (local >> 2);
+      if (!insert) return -1;
+      k = atomicCAS(&C.bucket[b].x, 0ull, key);
+      if (k == 0ull) {
+        const unsigned long long s = atomicAdd(C.used, 1ull);
+        if (s >= C.pool_cap) {
+          atomicOr(C.err, ERR_HASH_FULL);
+          atomicExch(&C.bucket[b].y, kSlotFull);
+          return -1;
+        }
+        atomicExch(&C.bucket[b].y, s + 1ull);
+        return (int64_t)s;
       }
-      if (old == key) return C.data + (size_t)b * kBrickWords + (local >> 2);
+    }
+    if (k == key) {
+      const unsigned long long v = *sv;
+      return v ? slot_of(v) : -2 - (int64_t)b;
     }
     b = (b + 1) & C.mask;
   }
   atomicOr(C.err, ERR_HASH_FULL);
-  return nullptr;
+  return -1;
+}
+
+// bounded wait for the slot of bucket b
+__device__ inline int64_t claim_wait(const Claims& C, uint32_t b) {
+  volatile unsigned long long* sv = &C.bucket[b].y;
+  for (uint32_t spins = 0; spins < kSpinLimit; ++spins) {
+    const unsigned long long v = *sv;
+    if (v) return slot_of(v);
+  }
+  atomicOr(C.err, ERR_TIMEOUT);
+  return -1;
+}
+
+// The targets of one particle are the neighbours of one site, so they nearly
+// always share its 8^3 block: the block lookup is remembered between calls.
+struct BlockCache {
+  int bx = 0x7fffffff, by = 0, bz = 0;
+  int64_t b = -1;
+};
+
+__device__ __forceinline__ bool site_in_range(int tx, int ty, int tz) {
+  return tx >= -kSiteMax && tx <= kSiteMax && ty >= -kSiteMax && ty <= kSiteMax &&
+         tz >= -kSiteMax && tz <= kSiteMax;
+}
+
+__device__ __forceinline__ uint32_t* block_word(const Claims& C, int64_t slot, int tx, int ty,
+                                                int tz, int& shift) {
+  const int local = (((tz & 7) << 3) | (ty & 7)) << 3 | (tx & 7);
+  shift = (local & 3) << 3;
+  return C.data + (size_t)slot * kBrickWords + (local >> 2);
+}
+
+// Word holding the claim byte of site t of grain g (shift: its bit offset) for
+// every lane with `have`; nullptr for the others, or if the block is absent / the
+// table is full.  Must be called by all 32 lanes of the warp together (converged,
+// none exited).  Lanes asking for the same block share one probe; inserts made by
+// the warp are published before any lane waits for another warp's insert.
+__device__ inline uint32_t* warp_claim_word(const Claims& C, bool have, int g, int tx, int ty,
+                                            int tz, bool insert, int& shift, BlockCache& bc) {
+  const int lane = threadIdx.x & 31;
+  if (have && !site_in_range(tx, ty, tz)) {
+    atomicOr(C.err, ERR_SITE_RANGE);
+    have = false;
+  }
+  const int bx = tx >> 3, by = ty >> 3, bz = tz >> 3;
+  const bool cached = have && bx == bc.bx && by == bc.by && bz == bc.bz &&
+                      (bc.b >= 0 || !insert);
+  const bool need = have && !cached;
+  const unsigned long long key = need ? block_key(g, bx, by, bz) : 0ull;
+  const uint32_t peers = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(peers) - 1;
+  long long r = -1;
+  if (need && lane == leader) r = claim_probe(C, key, insert);
+  __syncwarp();
+  if (need && lane == leader && r <= -2) r = claim_wait(C, (uint32_t)(-2 - r));
+  r = __shfl_sync(0xffffffffu, r, leader);
+  if (need) {
+    bc.bx = bx;
+    bc.by = by;
+    bc.bz = bz;
+    bc.b = r;
+  }
+  if (!have || bc.b < 0) return nullptr;
+  return block_word(C, bc.b, tx, ty, tz, shift);
+}
+
+// Lookup only, by one thread (no waiting; for use after the inserting kernel).
+__device__ inline uint32_t* claim_lookup(const Claims& C, int g, int tx, int ty, int tz,
+                                         int& shift, BlockCache& bc) {
+  if (!site_in_range(tx, ty, tz)) return nullptr;
+  const int bx = tx >> 3, by = ty >> 3, bz = tz >> 3;
+  if (bx != bc.bx || by != bc.by || bz != bc.bz) {
+    const int64_t r = claim_probe(C, block_key(g, bx, by, bz), false);
+    bc.bx = bx;
+    bc.by = by;
+    bc.bz = bz;
+    bc.b = r < 0 ? -1 : r;
+  }
+  if (bc.b < 0) return nullptr;
+  return block_word(C, bc.b, tx, ty, tz, shift);
 }
 
 // ---------------------------------------------------------------------------------
@@ -359,7 +466,8 @@ struct DevStats {
   unsigned long long n_live;       // after nucleation
   uint32_t err;
   uint32_t pad;
-  unsigned long long scratch[3];
+  unsigned long long linked;       // reached sites linked into the per-cell lists
+  unsigned long long scratch[2];
 };
 
 // warp-aggregated 64-bit counter increment

@@ -5,12 +5,12 @@
 //               kernel writes them otherwise)
 //   radix sort  (key, store index), gp_sort.cu
 //   k_build     gather the store into cell order, positions + grain as float4,
-//               dense cell table (start, count) stamped with the build number
+//               segment table of the cell runs, stamped with the build number
 //   k_advance   contact freeze over the 27 neighbour cells, thermal sample,
 //               growth law, explicit Euler advance, spawn claims
 //   k_emit      claim resolution, reached sites, domain clip, compaction of the
-//               surviving particles and their children (single-pass scan with
-//               decoupled look-back), next-step cell keys
+//               surviving particles and their children (block scan + one atomic
+//               reservation per CTA), next-step cell keys
 //   k_nucleate  nucleation activation at t_{n+1}
 // plus seeding, state decode, grain-id voxelisation and the stand-alone
 // hash / contact entry points.
@@ -20,47 +20,145 @@ namespace gp {
 
 namespace {
 
-constexpr unsigned long long kF64Agg = 1ull << 62;
-constexpr unsigned long long kF64Inc = 2ull << 62;
-constexpr unsigned long long kV64Mask = (1ull << 62) - 1;
 constexpr uint32_t kNoEntry = 0xffffffffu;
 
 // ---------------------------------------------------------------------------------
 // shared helpers
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long cell_entry(uint32_t stamp, uint32_t cnt,
-                                                         uint32_t start) {
-  return ((unsigned long long)stamp << 48) | ((unsigned long long)cnt << 32) | start;
+// Cell table.  The sorted particles of each run of kSegCells = 16 cells along x of
+// one row of the hash grid ("segment") are contiguous.  The table holds one
+// 16-byte entry per segment:
+//   x: sorted index of the segment's first particle
+//   y: build stamp (high 16 bits) | particle count of the segment (low 16 bits)
+//   z, w: particle count of each of the 16 cells, 4 bits each (cell 0 in the low
+//         nibble of z), saturated at 15
+// An entry whose stamp is not the current build's is an empty segment.  A query
+// turns the 3 cells x-1..x+1 of a neighbour row into a candidate range directly
+// from the nibble counts; when a count is saturated it scans the segment's keys.
+__device__ __forceinline__ uint32_t seg_of(const Params& P, uint32_t key, uint32_t& xcell) {
+  const uint32_t row = key / (uint32_t)P.nc[0];
+  xcell = key - row * (uint32_t)P.nc[0];
+  return row * (uint32_t)P.nsx + (xcell >> kSegShift);
 }
 
-// [start, end) of the sorted particles in cells x0..x1 of one row; false if empty
-__device__ __forceinline__ bool row_range(const unsigned long long* __restrict__ tab,
-                                          uint32_t stamp, size_t rowbase, int x0, int x1,
-                                          uint32_t& start, uint32_t& end) {
-  bool any = false;
-  for (int x = x0; x <= x1; ++x) {
-    unsigned long long e = __ldg(tab + rowbase + x);
-    if ((uint32_t)(e >> 48) != stamp) continue;
-    uint32_t s = (uint32_t)e;
-    uint32_t c = (uint32_t)(e >> 32) & 0xffffu;
-    if (!any) start = s;
-    end = s + c;
-    any = true;
+// Writes the entry of the segment that starts at sorted index j (if one does).
+__device__ __forceinline__ void seg_build(const Params& P, const uint32_t* __restrict__ skeys,
+                                          int64_t j, int64_t n, uint32_t key,
+                                          uint4* __restrict__ tab, uint32_t stamp,
+                                          uint32_t* err) {
+  uint32_t x0;
+  const uint32_t sg = seg_of(P, key, x0);
+  if (j > 0) {
+    uint32_t xp;
+    if (seg_of(P, __ldg(skeys + j - 1), xp) == sg) return;
   }
-  return any;
+  const uint32_t nvalid = (uint32_t)((uint64_t)P.nc[0] * P.nc[1] * P.nc[2]);
+  unsigned long long nib = 0;
+  uint32_t c = 0;
+  uint32_t k = key;
+  while (true) {
+    uint32_t x;
+    seg_of(P, k, x);
+    const int sh = 4 * (int)(x & (kSegCells - 1));
+    if (((nib >> sh) & 15ull) < 15ull) nib += 1ull << sh;
+    if (++c == 0xffffu) {
+      atomicOr(err, ERR_CELL_OVERFLOW);
+      break;
+    }
+    if (j + c >= n) break;
+    k = __ldg(skeys + j + c);
+    uint32_t xk;
+    if (k >= nvalid || seg_of(P, k, xk) != sg) break;
+  }
+  tab[sg] = make_uint4((uint32_t)j, (stamp << 16) | c, (uint32_t)nib, (uint32_t)(nib >> 32));
 }
 
-__device__ __forceinline__ void reached_append(const Reached& R, const Params& P, int g, int sx,
-                                               int sy, int sz, float3 sp) {
+// sum of the 4-bit counts of cells 0..p-1 (p <= 16)
+__device__ __forceinline__ uint32_t nib_prefix(unsigned long long nib, int p) {
+  const unsigned long long m = p >= 16 ? nib : (nib & ((1ull << (4 * p)) - 1ull));
+  const unsigned long long b = (m & 0x0f0f0f0f0f0f0f0full) + ((m >> 4) & 0x0f0f0f0f0f0f0f0full);
+  return (uint32_t)((b * 0x0101010101010101ull) >> 56);
+}
+
+// Finds the sorted particles i of another grain than g strictly closer than the
+// contact radius to p, among the particles of the 3x3x3 cells around (cx, cy, cz).
+// PAIRS == false: returns at the first one.  PAIRS == true: visits all of them and
+// appends the pairs (idj, ids[i]) with idj < ids[i] to pairs (up to pair_cap,
+// counted in *npairs).  Returns whether any was found.
+template <bool PAIRS>
+__device__ __forceinline__ bool contact_scan(const Params& P, const uint4* __restrict__ tab,
+                                             uint32_t stamp, const uint32_t* __restrict__ skeys,
+                                             const float4* __restrict__ pos4, int64_t n,
+                                             float3 p, int g, int cx, int cy, int cz,
+                                             const uint32_t* __restrict__ ids = nullptr,
+                                             uint32_t idj = 0, int32_t* pairs = nullptr,
+                                             int64_t pair_cap = 0,
+                                             unsigned long long* npairs = nullptr) {
+  bool hit = false;
+  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nc[0] - 1);
+  const int sa = x0 >> kSegShift, sb = x1 >> kSegShift;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int z = cz + dz;
+    if (z < 0 || z >= P.nc[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = cy + dy;
+      if (y < 0 || y >= P.nc[1]) continue;
+      const uint32_t row = (uint32_t)z * (uint32_t)P.nc[1] + (uint32_t)y;
+      for (int sgi = sa; sgi <= sb; ++sgi) {
+        const uint4 e = __ldg(tab + (size_t)row * P.nsx + sgi);
+        if ((e.y >> 16) != stamp) continue;
+        const int base = sgi << kSegShift;
+        const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
+        const unsigned long long nib = ((unsigned long long)e.w << 32) | e.z;
+        uint32_t i, end;
+        const bool saturated =
+            ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
+        if (!saturated) {
+          i = e.x + nib_prefix(nib, c0);
+          end = e.x + nib_prefix(nib, c1 + 1);
+        } else {
+          // a cell holds 15 or more particles: locate the cells by their keys
+          const uint32_t klo = row * (uint32_t)P.nc[0] + (uint32_t)(base + c0);
+          const uint32_t khi = klo + (uint32_t)(c1 - c0);
+          i = e.x;
+          end = e.x + (e.y & 0xffffu);
+          while (i < end && __ldg(skeys + i) < klo) ++i;
+          uint32_t e2 = i;
+          while (e2 < end && __ldg(skeys + e2) <= khi) ++e2;
+          end = e2;
+        }
+        if ((int64_t)end > n) end = (uint32_t)n;
+        for (; i < end; ++i) {
+          const float4 o = __ldg(pos4 + i);
+          if (__float_as_int(o.w) == g) continue;
+          if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) {
+            if (!PAIRS) return true;
+            hit = true;
+            const uint32_t idi = ids[i];
+            if (idj < idi) {
+              const unsigned long long k = atomicAdd(npairs, 1ull);
+              if ((int64_t)k < pair_cap) {
+                pairs[2 * k] = (int32_t)idj;
+                pairs[2 * k + 1] = (int32_t)idi;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  return hit;
+}
+
+// appends one reached site to the list (linking into the per-cell lists happens
+// lazily, before a query needs it: k_link_reached)
+__device__ __forceinline__ void reached_append(const Reached& R, int g, int sx, int sy, int sz) {
   unsigned long long r = atomicAdd(R.count, 1ull);
   if (r >= R.cap) {
     atomicOr(R.err, ERR_REACHED_CAP);
     return;
   }
-  int cx, cy, cz;
-  uint32_t key = cell_key(P, sp, cx, cy, cz);
   R.key[r] = pack_site(g, sx, sy, sz);
-  R.next[r] = atomicExch(R.head + key, (uint32_t)r);
 }
 
 // nearest reached site strictly closer than sqrt(rc2); ties to the smaller grain.
@@ -134,45 +232,6 @@ __device__ __forceinline__ uint32_t bscan256(uint32_t v, uint32_t* s_warp, uint3
   return r;
 }
 
-// decoupled look-back of a 64-bit tile aggregate (called by warp 0 of the CTA);
-// returns the exclusive prefix of this tile.
-__device__ unsigned long long lookback64(unsigned long long* status, uint32_t tile,
-                                         unsigned long long agg, uint32_t* err) {
-  const int lane = threadIdx.x & 31;
-  if (tile == 0) {
-    if (lane == 0) atomicExch(status, kF64Inc | agg);
-    return 0;
-  }
-  if (lane == 0) atomicExch(status + tile, kF64Agg | agg);
-  unsigned long long excl = 0;
-  long long pred = (long long)tile - 1;
-  uint32_t spins = 0;
-  while (true) {
-    long long idx = pred - lane;
-    unsigned long long s = 2ull << 62;  // before tile 0: an inclusive prefix of 0
-    if (idx >= 0) s = *((volatile unsigned long long*)(status + idx));
-    unsigned long long flag = s & ~kV64Mask;
-    if (__any_sync(0xffffffffu, flag == 0ull)) {
-      if (++spins > kSpinLimit) {
-        if (lane == 0) atomicOr(err, ERR_TIMEOUT);
-        break;
-      }
-      continue;
-    }
-    uint32_t inc = __ballot_sync(0xffffffffu, flag == kF64Inc);
-    unsigned long long v = s & kV64Mask;
-    int first = inc ? __ffs(inc) - 1 : 32;
-    if (lane > first) v = 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    excl += v;
-    if (inc) break;
-    pred -= 32;
-  }
-  if (lane == 0) atomicExch(status + tile, kF64Inc | ((excl + agg) & kV64Mask));
-  return excl;
-}
-
 // ---------------------------------------------------------------------------------
 // k_keys: cell key and identity value of every stored particle
 // ---------------------------------------------------------------------------------
@@ -195,7 +254,7 @@ __global__ void __launch_bounds__(256) k_build(Params P, const uint32_t* __restr
                                                const uint32_t* __restrict__ svals,
                                                const int4* __restrict__ rin,
                                                int4* __restrict__ rout, float4* __restrict__ pos4,
-                                               unsigned long long* __restrict__ tab,
+                                               uint4* __restrict__ tab,
                                                uint32_t stamp, int64_t n, uint32_t ncells,
                                                uint32_t* err) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -211,59 +270,32 @@ __global__ void __launch_bounds__(256) k_build(Params P, const uint32_t* __restr
   Rec r = rec_unpack(rv);
   float3 p = part_pos(P.gtab, r.grain, r.sx, r.sy, r.sz, r.dir, r.ell);
   pos4[j] = make_float4(p.x, p.y, p.z, __int_as_float(r.grain));
-  if (j == 0 || __ldg(skeys + j - 1) != key) {
-    uint32_t c = 1;
-    while (j + c < n && __ldg(skeys + j + c) == key) {
-      if (++c == 0xffffu) {
-        atomicOr(err, ERR_CELL_OVERFLOW);
-        break;
-      }
-    }
-    tab[key] = cell_entry(stamp, c, (uint32_t)j);
-  }
+  seg_build(P, skeys, j, n, key, tab, stamp, err);
 }
 
 // ---------------------------------------------------------------------------------
 // k_advance: contact freeze, growth, advance, spawn claims (sorted store, in place)
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
+__global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
-                                                 const unsigned long long* __restrict__ tab,
+                                                 const uint32_t* __restrict__ skeys,
+                                                 const uint4* __restrict__ tab,
                                                  uint32_t stamp, int64_t n, Claims C,
                                                  DevStats* st) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = false, froze = false, clamped = false;
+  bool crossing = false;
+  int g = 0, sx = 0, sy = 0, sz = 0;
   if (j < n) {
     Rec r = rec_unpack(rs[j]);
     if (r.state == ST_ACTIVE) {
       active = true;
       const float4 q = __ldg(pos4 + j);
       const float3 p = make_float3(q.x, q.y, q.z);
-      const int g = r.grain;
+      g = r.grain;
       int cx, cy, cz;
       cell_key(P, p, cx, cy, cz);
-      const int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nc[0] - 1);
-      bool hit = false;
-      for (int dz = -1; dz <= 1 && !hit; ++dz) {
-        const int z = cz + dz;
-        if (z < 0 || z >= P.nc[2]) continue;
-        for (int dy = -1; dy <= 1 && !hit; ++dy) {
-          const int y = cy + dy;
-          if (y < 0 || y >= P.nc[1]) continue;
-          uint32_t s0, s1;
-          if (!row_range(tab, stamp, ((size_t)z * P.nc[1] + y) * P.nc[0], x0, x1, s0, s1))
-            continue;
-          if ((int64_t)s1 > n) s1 = (uint32_t)n;
-          for (uint32_t i = s0; i < s1; ++i) {
-            const float4 o = __ldg(pos4 + i);
-            if (__float_as_int(o.w) == g) continue;
-            if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) {
-              hit = true;
-              break;
-            }
-          }
-        }
-      }
+      const bool hit = contact_scan<false>(P, tab, stamp, skeys, pos4, n, p, g, cx, cy, cz);
       if (hit) {
         froze = true;
         r.state = ST_FROZEN;
@@ -281,21 +313,29 @@ __global__ void __launch_bounds__(256) k_advance(Params P, StepArgs S, int4* __r
         if (e >= 1.f - 0x1p-20f) {
           r.cross = 1;
           r.ell = fmaxf(__fsub_rn(e, 1.f), 0.f);
-          int sx = r.sx, sy = r.sy, sz = r.sz;
+          crossing = true;
+          sx = r.sx;
+          sy = r.sy;
+          sz = r.sz;
           step_site(sx, sy, sz, r.dir);
-          for (int k = 0; k < 6; ++k) {
-            if (!is_outer(sx, sy, sz, k)) continue;
-            int tx = sx, ty = sy, tz = sz;
-            step_site(tx, ty, tz, k);
-            int sh;
-            uint32_t* w = claim_word(C, g, tx, ty, tz, true, sh);
-            if (w) atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << sh);
-          }
         } else {
           r.ell = e;
         }
       }
       rs[j] = rec_pack(r);
+    }
+  }
+  // spawn claims: every outer direction k' at the reached site s' claims the target
+  // s' + e_k' for this step (claimant bit of its axis).  All lanes take part.
+  {
+    BlockCache bc;
+    for (int k = 0; k < 6; ++k) {
+      const bool have = crossing && is_outer(sx, sy, sz, k);
+      int tx = sx, ty = sy, tz = sz;
+      step_site(tx, ty, tz, k);
+      int sh = 0;
+      uint32_t* w = warp_claim_word(C, have, g, tx, ty, tz, true, sh, bc);
+      if (w) atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << sh);
     }
   }
   warp_add(&st->particle_steps, active ? 1u : 0u);
@@ -304,151 +344,184 @@ __global__ void __launch_bounds__(256) k_advance(Params P, StepArgs S, int4* __r
 }
 
 // ---------------------------------------------------------------------------------
-// k_emit: claim resolution, reached sites, clip, compaction, next keys
+// k_emit: claim resolution, reached sites, clip, compaction, next keys.
+// A CTA handles kEmitTile records (kEmitItems per thread, strided by 256).  Its
+// outputs are placed by a block scan and one atomic reservation per CTA on the
+// output counter, so the store order varies from run to run; every result of the
+// method is independent of that order.
 // ---------------------------------------------------------------------------------
 constexpr int kEmitItems = 4;
 constexpr int kEmitTile = 256 * kEmitItems;
+
+// decides what record j emits: bit 6 = the record itself, bits 0..5 = children in
+// direction k; counts the statistics; appends the reached site of a crossing
+__device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs& S, const Rec& r,
+                                                bool valid, const Claims& C, const Reached& R,
+                                                uint32_t& n_frozen, uint32_t& n_spawn,
+                                                uint32_t& n_lost, uint32_t& n_clip) {
+  const int lane = threadIdx.x & 31;
+  uint32_t mask = 0;
+  const bool crossing = valid && r.state == ST_ACTIVE && r.cross;
+  int sx = r.sx, sy = r.sy, sz = r.sz;
+  if (crossing) step_site(sx, sy, sz, r.dir);
+  // reached site of every crossing particle: one counter update per warp
+  const uint32_t want = __ballot_sync(0xffffffffu, crossing);
+  if (want) {
+    unsigned long long rb = 0;
+    if (lane == __ffs(want) - 1) rb = atomicAdd(R.count, (unsigned long long)__popc(want));
+    rb = __shfl_sync(0xffffffffu, rb, __ffs(want) - 1);
+    if (crossing) {
+      const unsigned long long ri = rb + __popc(want & ((1u << lane) - 1u));
+      if (ri < R.cap) R.key[ri] = pack_site(r.grain, sx, sy, sz);
+      else atomicOr(R.err, ERR_REACHED_CAP);
+    }
+  }
+  if (!valid) return 0;
+  if (r.state == ST_FROZEN) {
+    ++n_frozen;
+    return 1u << 6;
+  }
+  if (r.state != ST_ACTIVE) return 0;
+  float4 gc, r0, r1, r2;
+  grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+  if (!crossing) {
+    const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
+    if (inside(P, p)) return 1u << 6;
+    ++n_clip;
+    return 0;
+  }
+  const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
+  BlockCache bc;
+  for (int k = 0; k < 6; ++k) {
+    if (!is_outer(sx, sy, sz, k)) continue;
+    int tx = sx, ty = sy, tz = sz;
+    step_site(tx, ty, tz, k);
+    int sh;
+    uint32_t* w = claim_lookup(C, r.grain, tx, ty, tz, sh, bc);
+    bool win = false;
+    if (w) {
+      const uint32_t byte = (*((volatile uint32_t*)w) >> sh) & 0xffu;
+      const uint32_t live = (byte >> (3 * S.parity)) & 7u;
+      win = !(byte & 0x80u) && live && (__ffs(live) - 1) == (k >> 1);
+      if (win) atomicOr(w, 0x80u << sh);
+    }
+    if (!win) {
+      ++n_lost;
+      continue;
+    }
+    if (k != r.dir) ++n_spawn;
+    if (inside(P, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
+    else ++n_clip;
+  }
+  return mask;
+}
+
+__device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32_t mask,
+                                           unsigned long long o, int4* __restrict__ rout,
+                                           uint32_t* __restrict__ keys,
+                                           uint32_t* __restrict__ vals, int64_t cap) {
+  float4 gc, r0, r1, r2;
+  grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+  int cx, cy, cz;
+  if (mask & (1u << 6)) {
+    if (o < (unsigned long long)cap) {
+      Rec w = r;
+      w.cross = 0;
+      rout[o] = rec_pack(w);
+      const float3 p =
+          add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
+      keys[o] = cell_key(P, p, cx, cy, cz);
+      vals[o] = (uint32_t)o;
+    }
+    return;
+  }
+  int sx = r.sx, sy = r.sy, sz = r.sz;
+  step_site(sx, sy, sz, r.dir);
+  const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
+  for (int k = 0; k < 6; ++k) {
+    if (!(mask & (1u << k))) continue;
+    if (o < (unsigned long long)cap) {
+      Rec w;
+      w.grain = r.grain;
+      w.sx = sx;
+      w.sy = sy;
+      w.sz = sz;
+      w.dir = k;
+      w.state = ST_ACTIVE;
+      w.cross = 0;
+      w.ell = r.ell;
+      rout[o] = rec_pack(w);
+      keys[o] = cell_key(P, add_dir(sp, r0, r1, r2, k, r.ell), cx, cy, cz);
+      vals[o] = (uint32_t)o;
+    }
+    ++o;
+  }
+}
 
 __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* __restrict__ rs,
                                               int64_t n, int4* __restrict__ rout,
                                               uint32_t* __restrict__ keys,
                                               uint32_t* __restrict__ vals, int64_t cap,
-                                              Claims C, Reached R,
-                                              unsigned long long* status, uint32_t* ticket,
-                                              uint32_t ntiles, DevStats* st) {
+                                              Claims C, Reached R, DevStats* st) {
   __shared__ uint32_t s_warp[8];
-  __shared__ uint32_t s_tile;
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int64_t base = (int64_t)tile * kEmitTile;
-
-  // phase A: decide what every record emits.  mask bit 6 = the record itself,
-  // bits 0..5 = children in direction k.
-  uint32_t mask[kEmitItems];
-  Rec rec[kEmitItems];
+  const int64_t base = (int64_t)blockIdx.x * kEmitTile;
+  uint32_t masks = 0;  // 7 bits per item
   uint32_t n_frozen = 0, n_spawn = 0, n_lost = 0, n_clip = 0;
-#pragma unroll
+#pragma unroll 1
   for (int it = 0; it < kEmitItems; ++it) {
     const int64_t j = base + it * 256 + tid;
-    mask[it] = 0;
-    if (j >= n) continue;
-    Rec r = rec_unpack(__ldg(rs + j));
-    rec[it] = r;
-    if (r.state == ST_FROZEN) {
-      mask[it] = 1u << 6;
-      ++n_frozen;
-      continue;
-    }
-    if (r.state != ST_ACTIVE) continue;
-    float4 gc, r0, r1, r2;
-    grain_load(P.gtab, r.grain, gc, r0, r1, r2);
-    if (!r.cross) {
-      float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
-      if (inside(P, p)) mask[it] = 1u << 6;
-      else ++n_clip;
-      continue;
-    }
-    int sx = r.sx, sy = r.sy, sz = r.sz;
-    step_site(sx, sy, sz, r.dir);
-    const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
-    reached_append(R, P, r.grain, sx, sy, sz, sp);
-    for (int k = 0; k < 6; ++k) {
-      if (!is_outer(sx, sy, sz, k)) continue;
-      int tx = sx, ty = sy, tz = sz;
-      step_site(tx, ty, tz, k);
-      int sh;
-      uint32_t* w = claim_word(C, r.grain, tx, ty, tz, false, sh);
-      bool win = false;
-      if (w) {
-        const uint32_t byte = (*((volatile uint32_t*)w) >> sh) & 0xffu;
-        const uint32_t live = (byte >> (3 * S.parity)) & 7u;
-        win = !(byte & 0x80u) && live && (__ffs(live) - 1) == (k >> 1);
-        if (win) atomicOr(w, 0x80u << sh);
-      }
-      if (!win) {
-        ++n_lost;
-        continue;
-      }
-      if (k != r.dir) ++n_spawn;
-      const float3 cp = add_dir(sp, r0, r1, r2, k, r.ell);
-      if (inside(P, cp)) mask[it] |= 1u << k;
-      else ++n_clip;
-    }
+    const bool valid = j < n;
+    const Rec r = valid ? rec_unpack(__ldg(rs + j)) : Rec{};
+    const uint32_t m = emit_decide(P, S, r, valid, C, R, n_frozen, n_spawn, n_lost, n_clip);
+    masks |= m << (7 * it);
   }
-
-  // phase B: offsets.  Output order within the tile is (item, thread).
-  uint32_t ofs[kEmitItems];
-  uint32_t run = 0;
+  uint32_t cnt = 0;
 #pragma unroll
-  for (int it = 0; it < kEmitItems; ++it) {
-    uint32_t tot;
-    ofs[it] = run + bscan256((uint32_t)__popc(mask[it]), s_warp, tot);
-    run += tot;
-  }
-  if (tid < 32) {
-    unsigned long long excl = lookback64(status, tile, run, st == nullptr ? nullptr : &st->err);
-    if (tid == 0) {
-      s_base = excl;
-      if (tile == ntiles - 1) {
-        st->n_out = excl + run;
-        if (excl + run > (unsigned long long)cap) atomicOr(&st->err, ERR_CAPACITY);
-      }
-    }
-  }
+  for (int it = 0; it < kEmitItems; ++it) cnt += __popc((masks >> (7 * it)) & 0x7fu);
+  uint32_t tot;
+  const uint32_t ofs = bscan256(cnt, s_warp, tot);
+  if (tid == 0) s_base = tot ? atomicAdd(&st->n_out, (unsigned long long)tot) : 0ull;
   __syncthreads();
-  const unsigned long long obase = s_base;
-
-  // phase C: write the records and next-step keys
+  unsigned long long o = s_base + ofs;
+#pragma unroll 1
   for (int it = 0; it < kEmitItems; ++it) {
-    uint32_t m = mask[it];
+    const uint32_t m = (masks >> (7 * it)) & 0x7fu;
     if (!m) continue;
-    unsigned long long o = obase + ofs[it];
-    const Rec r = rec[it];
-    float4 gc, r0, r1, r2;
-    grain_load(P.gtab, r.grain, gc, r0, r1, r2);
-    if (m & (1u << 6)) {
-      if (o < (unsigned long long)cap) {
-        Rec w = r;
-        w.cross = 0;
-        rout[o] = rec_pack(w);
-        float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
-        int cx, cy, cz;
-        keys[o] = cell_key(P, p, cx, cy, cz);
-        vals[o] = (uint32_t)o;
-      }
-      continue;
-    }
-    int sx = r.sx, sy = r.sy, sz = r.sz;
-    step_site(sx, sy, sz, r.dir);
-    const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
-    for (int k = 0; k < 6; ++k) {
-      if (!(m & (1u << k))) continue;
-      if (o < (unsigned long long)cap) {
-        Rec w;
-        w.grain = r.grain;
-        w.sx = sx;
-        w.sy = sy;
-        w.sz = sz;
-        w.dir = k;
-        w.state = ST_ACTIVE;
-        w.cross = 0;
-        w.ell = r.ell;
-        rout[o] = rec_pack(w);
-        float3 p = add_dir(sp, r0, r1, r2, k, r.ell);
-        int cx, cy, cz;
-        keys[o] = cell_key(P, p, cx, cy, cz);
-        vals[o] = (uint32_t)o;
-      }
-      ++o;
-    }
+    const int64_t j = base + it * 256 + tid;
+    const Rec r = rec_unpack(__ldg(rs + j));
+    emit_write(P, r, m, o, rout, keys, vals, cap);
+    o += __popc(m);
   }
   warp_add(&st->n_frozen, n_frozen);
   warp_add(&st->spawned, n_spawn);
   warp_add(&st->claims_lost, n_lost);
   warp_add(&st->clipped, n_clip);
+}
+
+__global__ void k_emit_check(DevStats* st, int64_t cap) {
+  if (st->n_out > (unsigned long long)cap) atomicOr(&st->err, ERR_CAPACITY);
+}
+
+// links the reached sites [linked, count) into the per-cell lists; grid-stride
+__global__ void k_link_reached(Params P, Reached R, const unsigned long long* linked) {
+  const unsigned long long r0 = *linked;
+  const unsigned long long r1 = min(*R.count, R.cap);
+  for (unsigned long long r = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       r < r1; r += (unsigned long long)gridDim.x * blockDim.x) {
+    int g, sx, sy, sz;
+    unpack_site(R.key[r], g, sx, sy, sz);
+    float4 gc, q0, q1, q2;
+    grain_load(P.gtab, g, gc, q0, q1, q2);
+    int cx, cy, cz;
+    const uint32_t key = cell_key(P, site_pos_g(gc, q0, q1, q2, sx, sy, sz), cx, cy, cz);
+    R.next[r] = atomicExch(R.head + key, (uint32_t)r);
+  }
+}
+
+__global__ void k_link_done(Reached R, unsigned long long* linked) {
+  *linked = min(*R.count, R.cap);
 }
 
 // ---------------------------------------------------------------------------------
@@ -480,35 +553,32 @@ __global__ void __launch_bounds__(256) k_nucleate(Params P, StepArgs S1, const f
     const uint32_t cand = (j < m && nstate[j] == 1) ? 1u : 0u;
     uint32_t tot;
     const uint32_t rank = bscan256(cand, s_warp, tot) + s_run;
+    const unsigned long long g = g0 + rank;
+    const bool made = cand && g < (unsigned long long)max_grains;
+    // nucleus site and the six first targets are claimed (all lanes take part)
+    {
+      BlockCache bc;
+      for (int k = -1; k < 6; ++k) {
+        int tx = 0, ty = 0, tz = 0;
+        if (k >= 0) step_site(tx, ty, tz, k);
+        int sh = 0;
+        uint32_t* w = warp_claim_word(C, made, (int)g, tx, ty, tz, true, sh, bc);
+        if (w) atomicOr(w, 0x80u << sh);
+      }
+    }
     if (cand) {
       nstate[j] = 2;
-      const unsigned long long g = g0 + rank;
-      if (g >= (unsigned long long)max_grains) {
+      if (!made) {
         atomicOr(&st->err, ERR_GRAINS);
       } else {
         for (int q = 0; q < 4; ++q) gtab[4 * g + q] = ngrain[4 * j + q];
         const float4 cq = ngrain[4 * j];
         const float3 c = make_float3(cq.x, cq.y, cq.z);
-        // nucleus site reached and claimed; six first targets claimed
-        unsigned long long r = atomicAdd(R.count, 1ull);
-        if (r < R.cap) {
-          int cx, cy, cz;
-          uint32_t key = cell_key(P, c, cx, cy, cz);
-          R.key[r] = pack_site((int)g, 0, 0, 0);
-          R.next[r] = atomicExch(R.head + key, (uint32_t)r);
-        } else {
-          atomicOr(R.err, ERR_REACHED_CAP);
-        }
-        int sh;
-        uint32_t* w = claim_word(C, (int)g, 0, 0, 0, true, sh);
-        if (w) atomicOr(w, 0x80u << sh);
+        // nucleus site reached
+        reached_append(R, (int)g, 0, 0, 0);
         int cx, cy, cz;
         const uint32_t key = cell_key(P, c, cx, cy, cz);
         for (int k = 0; k < 6; ++k) {
-          int tx = 0, ty = 0, tz = 0;
-          step_site(tx, ty, tz, k);
-          w = claim_word(C, (int)g, tx, ty, tz, true, sh);
-          if (w) atomicOr(w, 0x80u << sh);
           const unsigned long long o = nout + 6ull * rank + k;
           if (o < (unsigned long long)cap) {
             Rec rr;
@@ -559,18 +629,15 @@ __global__ void k_append(const int4* __restrict__ src, int64_t m, int4* __restri
 __global__ void k_mark_sites(Params P, const int4* __restrict__ sites, int64_t m, int reached,
                              int claimed, Claims C, Reached R) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  const int4 s = sites[i];
-  if (claimed) {
-    int sh;
-    uint32_t* w = claim_word(C, s.x, s.y, s.z, s.w, true, sh);
+  const bool ok = i < m;
+  const int4 s = ok ? sites[i] : make_int4(0, 0, 0, 0);
+  if (claimed) {  // uniform across the launch
+    BlockCache bc;
+    int sh = 0;
+    uint32_t* w = warp_claim_word(C, ok, s.x, s.y, s.z, s.w, true, sh, bc);
     if (w) atomicOr(w, 0x80u << sh);
   }
-  if (reached) {
-    float4 gc, r0, r1, r2;
-    grain_load(P.gtab, s.x, gc, r0, r1, r2);
-    reached_append(R, P, s.x, s.y, s.z, s.w, site_pos_g(gc, r0, r1, r2, s.y, s.z, s.w));
-  }
+  if (ok && reached) reached_append(R, s.x, s.y, s.z, s.w);
 }
 
 // shell seeding: for every (grain, target offset t with |t|_1 = n0 + 1) one ACTIVE
@@ -580,34 +647,36 @@ __global__ void k_seed_shell(Params P, const int32_t* __restrict__ grains, int64
                              int4* __restrict__ rout, int64_t cap, unsigned long long* counter,
                              Claims C, uint32_t* err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ng * nt) return;
-  const int g = grains[i / nt];
-  const short4 t = toff[i % nt];
+  bool ok = i < ng * nt;
+  const int g = ok ? grains[i / nt] : 0;
+  const short4 t = ok ? toff[i % nt] : make_short4(1, 0, 0, 0);
   int ts[3] = {t.x, t.y, t.z};
   int a = ts[0] != 0 ? 0 : (ts[1] != 0 ? 1 : 2);
   int sg = ts[a] > 0 ? 1 : -1;
   int s[3] = {ts[0], ts[1], ts[2]};
   s[a] -= sg;
   const int dir = 2 * a + (sg > 0 ? 0 : 1);
-  float3 p = part_pos(P.gtab, g, s[0], s[1], s[2], dir, ell0);
-  if (!inside(P, p)) return;
-  unsigned long long o = atomicAdd(counter, 1ull);
-  if (o >= (unsigned long long)cap) {
-    atomicOr(err, ERR_CAPACITY);
-    return;
+  if (ok) ok = inside(P, part_pos(P.gtab, g, s[0], s[1], s[2], dir, ell0));
+  if (ok) {
+    unsigned long long o = atomicAdd(counter, 1ull);
+    if (o >= (unsigned long long)cap) {
+      atomicOr(err, ERR_CAPACITY);
+    } else {
+      Rec r;
+      r.grain = g;
+      r.sx = s[0];
+      r.sy = s[1];
+      r.sz = s[2];
+      r.dir = dir;
+      r.state = ST_ACTIVE;
+      r.cross = 0;
+      r.ell = ell0;
+      rout[o] = rec_pack(r);
+    }
   }
-  Rec r;
-  r.grain = g;
-  r.sx = s[0];
-  r.sy = s[1];
-  r.sz = s[2];
-  r.dir = dir;
-  r.state = ST_ACTIVE;
-  r.cross = 0;
-  r.ell = ell0;
-  rout[o] = rec_pack(r);
-  int sh;
-  uint32_t* w = claim_word(C, g, ts[0], ts[1], ts[2], true, sh);
+  BlockCache bc;
+  int sh = 0;
+  uint32_t* w = warp_claim_word(C, ok, g, ts[0], ts[1], ts[2], true, sh, bc);
   if (w) atomicOr(w, 0x80u << sh);
 }
 
@@ -616,15 +685,14 @@ __global__ void k_seed_shell_sites(Params P, const int32_t* __restrict__ grains,
                                    const short4* __restrict__ soff, int64_t ns, Claims C,
                                    Reached R) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ng * ns) return;
-  const int g = grains[i / ns];
-  const short4 s = soff[i % ns];
-  int sh;
-  uint32_t* w = claim_word(C, g, s.x, s.y, s.z, true, sh);
+  const bool ok = i < ng * ns;
+  const int g = ok ? grains[i / ns] : 0;
+  const short4 s = ok ? soff[i % ns] : make_short4(0, 0, 0, 0);
+  BlockCache bc;
+  int sh = 0;
+  uint32_t* w = warp_claim_word(C, ok, g, s.x, s.y, s.z, true, sh, bc);
   if (w) atomicOr(w, 0x80u << sh);
-  float4 gc, r0, r1, r2;
-  grain_load(P.gtab, g, gc, r0, r1, r2);
-  reached_append(R, P, g, s.x, s.y, s.z, site_pos_g(gc, r0, r1, r2, s.x, s.y, s.z));
+  if (ok) reached_append(R, g, s.x, s.y, s.z);
 }
 
 // ---------------------------------------------------------------------------------
@@ -721,7 +789,8 @@ __global__ void k_cell_write(const uint32_t* __restrict__ keys, const uint32_t* 
 
 __global__ void k_contact_sa(Params P, const float4* __restrict__ pos4,
                              const uint8_t* __restrict__ sstate, const uint32_t* __restrict__ ids,
-                             const unsigned long long* __restrict__ tab, int64_t n,
+                             const uint32_t* __restrict__ skeys,
+                             const uint4* __restrict__ tab, int64_t n,
                              uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
                              unsigned long long* npairs) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -734,44 +803,17 @@ __global__ void k_contact_sa(Params P, const float4* __restrict__ pos4,
   const uint32_t idj = ids[j];
   int cx, cy, cz;
   cell_key(P, p, cx, cy, cz);
-  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nc[0] - 1);
-  bool hit = false;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int z = cz + dz;
-    if (z < 0 || z >= P.nc[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = cy + dy;
-      if (y < 0 || y >= P.nc[1]) continue;
-      uint32_t s0, s1;
-      if (!row_range(tab, 1u, ((size_t)z * P.nc[1] + y) * P.nc[0], x0, x1, s0, s1)) continue;
-      if ((int64_t)s1 > n) s1 = (uint32_t)n;
-      for (uint32_t i = s0; i < s1; ++i) {
-        if (sstate[i] == ST_REMOVED) continue;
-        const float4 o = pos4[i];
-        if (__float_as_int(o.w) == g) continue;
-        if (!(dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2)) continue;
-        hit = true;
-        if (!pairs) break;
-        const uint32_t idi = ids[i];
-        if (idj < idi) {
-          unsigned long long k = atomicAdd(npairs, 1ull);
-          if ((int64_t)k < pair_cap) {
-            pairs[2 * k] = (int32_t)idj;
-            pairs[2 * k + 1] = (int32_t)idi;
-          }
-        }
-      }
-      if (hit && !pairs) break;
-    }
-    if (hit && !pairs) break;
-  }
+  const bool hit =
+      pairs ? contact_scan<true>(P, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz, ids, idj, pairs,
+                                 pair_cap, npairs)
+            : contact_scan<false>(P, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz);
   if (freeze) freeze[idj] = (hit && stj == ST_ACTIVE) ? 1 : 0;
 }
 
 __global__ void k_build_sa(Params P, const float* __restrict__ x3, const int32_t* __restrict__ grain,
                            const uint8_t* __restrict__ state, const uint32_t* __restrict__ skeys,
                            const uint32_t* __restrict__ svals, int64_t n, float4* pos4,
-                           uint8_t* sstate, unsigned long long* tab, uint32_t* err) {
+                           uint8_t* sstate, uint4* tab, uint32_t* err) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const uint32_t id = svals[j];
@@ -783,16 +825,7 @@ __global__ void k_build_sa(Params P, const float* __restrict__ x3, const int32_t
   sstate[j] = state[id];
   const uint32_t key = skeys[j];
   if (key >= (uint32_t)((uint64_t)P.nc[0] * P.nc[1] * P.nc[2])) return;  // removed points
-  if (j == 0 || skeys[j - 1] != key) {
-    uint32_t c = 1;
-    while (j + c < n && skeys[j + c] == key) {
-      if (++c == 0xffffu) {
-        atomicOr(err, ERR_CELL_OVERFLOW);
-        break;
-      }
-    }
-    tab[key] = cell_entry(1u, c, (uint32_t)j);
-  }
+  seg_build(P, skeys, j, n, key, tab, 1u, err);
 }
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -808,7 +841,7 @@ void launch_keys(const Params& P, const int4* rec, int64_t n, uint32_t* keys, ui
 }
 
 void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals, const int4* rin,
-                  int4* rout, float4* pos4, unsigned long long* tab, uint32_t stamp, int64_t n,
+                  int4* rout, float4* pos4, uint4* tab, uint32_t stamp, int64_t n,
                   uint32_t* err, cudaStream_t st) {
   const uint32_t ncells = (uint32_t)((uint64_t)P.nc[0] * P.nc[1] * P.nc[2]);
   if (n > 0)
@@ -817,22 +850,26 @@ void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals,
 }
 
 void launch_advance(const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
-                    const unsigned long long* tab, uint32_t stamp, int64_t n, const Claims& C,
-                    DevStats* dst, cudaStream_t st) {
-  if (n > 0) k_advance<<<blocks(n), 256, 0, st>>>(P, S, rs, pos4, tab, stamp, n, C, dst);
+                    const uint32_t* skeys, const uint4* tab, uint32_t stamp,
+                    int64_t n, const Claims& C, DevStats* dst, cudaStream_t st) {
+  if (n > 0) k_advance<<<blocks(n), 256, 0, st>>>(P, S, rs, pos4, skeys, tab, stamp, n, C, dst);
 }
 
 int64_t emit_tiles(int64_t n) { return (n + kEmitTile - 1) / kEmitTile; }
 
+void launch_link_reached(const Params& P, const Reached& R, unsigned long long* linked, int sms,
+                         cudaStream_t st) {
+  k_link_reached<<<sms * 8, 256, 0, st>>>(P, R, linked);
+  k_link_done<<<1, 1, 0, st>>>(R, linked);
+}
+
 void launch_emit(const Params& P, const StepArgs& S, const int4* rs, int64_t n, int4* rout,
                  uint32_t* keys, uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
-                 unsigned long long* status, uint32_t* ticket, DevStats* dst, cudaStream_t st) {
+                 DevStats* dst, cudaStream_t st) {
   const int64_t nt = emit_tiles(n);
   if (nt == 0) return;
-  cudaMemsetAsync(status, 0, sizeof(unsigned long long) * nt, st);
-  cudaMemsetAsync(ticket, 0, sizeof(uint32_t), st);
-  k_emit<<<(unsigned)nt, 256, 0, st>>>(P, S, rs, n, rout, keys, vals, cap, C, R, status, ticket,
-                                       (uint32_t)nt, dst);
+  k_emit<<<(unsigned)nt, 256, 0, st>>>(P, S, rs, n, rout, keys, vals, cap, C, R, dst);
+  k_emit_check<<<1, 1, 0, st>>>(dst, cap);
 }
 
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
@@ -902,19 +939,19 @@ void launch_cells(const uint32_t* skeys, int64_t n, uint32_t nvalid_key, uint32_
 
 void launch_build_sa(const Params& P, const float* x3, const int32_t* grain, const uint8_t* state,
                      const uint32_t* skeys, const uint32_t* svals, int64_t n, float4* pos4,
-                     uint8_t* sstate, unsigned long long* tab, uint32_t* err, cudaStream_t st) {
+                     uint8_t* sstate, uint4* tab, uint32_t* err, cudaStream_t st) {
   if (n > 0)
     k_build_sa<<<blocks(n), 256, 0, st>>>(P, x3, grain, state, skeys, svals, n, pos4, sstate, tab,
                                           err);
 }
 
 void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstate,
-                       const uint32_t* ids, const unsigned long long* tab, int64_t n,
-                       uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
+                       const uint32_t* ids, const uint32_t* skeys, const uint4* tab,
+                       int64_t n, uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
                        unsigned long long* npairs, cudaStream_t st) {
   if (n > 0)
-    k_contact_sa<<<blocks(n), 256, 0, st>>>(P, pos4, sstate, ids, tab, n, freeze, pairs, pair_cap,
-                                            npairs);
+    k_contact_sa<<<blocks(n), 256, 0, st>>>(P, pos4, sstate, ids, skeys, tab, n, freeze, pairs,
+                                            pair_cap, npairs);
 }
 
 }  // namespace gp

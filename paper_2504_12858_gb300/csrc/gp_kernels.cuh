@@ -8,15 +8,17 @@ namespace gp {
 void launch_keys(const Params& P, const int4* rec, int64_t n, uint32_t* keys, uint32_t* vals,
                  cudaStream_t st);
 void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals, const int4* rin,
-                  int4* rout, float4* pos4, unsigned long long* tab, uint32_t stamp, int64_t n,
+                  int4* rout, float4* pos4, uint4* tab, uint32_t stamp, int64_t n,
                   uint32_t* err, cudaStream_t st);
 void launch_advance(const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
-                    const unsigned long long* tab, uint32_t stamp, int64_t n, const Claims& C,
-                    DevStats* dst, cudaStream_t st);
+                    const uint32_t* skeys, const uint4* tab, uint32_t stamp,
+                    int64_t n, const Claims& C, DevStats* dst, cudaStream_t st);
 int64_t emit_tiles(int64_t n);
+void launch_link_reached(const Params& P, const Reached& R, unsigned long long* linked, int sms,
+                         cudaStream_t st);
 void launch_emit(const Params& P, const StepArgs& S, const int4* rs, int64_t n, int4* rout,
                  uint32_t* keys, uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
-                 unsigned long long* status, uint32_t* ticket, DevStats* dst, cudaStream_t st);
+                 DevStats* dst, cudaStream_t st);
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
                      int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,
@@ -42,10 +44,10 @@ void launch_cells(const uint32_t* skeys, int64_t n, uint32_t nvalid_key, uint32_
                   unsigned long long* ncell, cudaStream_t st);
 void launch_build_sa(const Params& P, const float* x3, const int32_t* grain, const uint8_t* state,
                      const uint32_t* skeys, const uint32_t* svals, int64_t n, float4* pos4,
-                     uint8_t* sstate, unsigned long long* tab, uint32_t* err, cudaStream_t st);
+                     uint8_t* sstate, uint4* tab, uint32_t* err, cudaStream_t st);
 void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstate,
-                       const uint32_t* ids, const unsigned long long* tab, int64_t n,
-                       uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
+                       const uint32_t* ids, const uint32_t* skeys, const uint4* tab,
+                       int64_t n, uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
                        unsigned long long* npairs, cudaStream_t st);
 
 }  // namespace gp

@@ -45,7 +45,7 @@ class gp_voxel_grid(C.Structure):
 
 class gp_memory(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("reached_capacity", C.c_int64),
-                ("claim_buckets", C.c_int64), ("max_grains", C.c_int32),
+                ("claim_blocks", C.c_int64), ("max_grains", C.c_int32),
                 ("max_nuclei", C.c_int32), ("grid_nodes", C.c_int64), ("arena", C.c_void_p),
                 ("arena_bytes", C.c_size_t)]
 
@@ -163,7 +163,7 @@ class Sim:
     """
 
     def __init__(self, lo, hi, h, dt, a, b, T_L, capacity, reached_capacity=0,
-                 claim_buckets=0, max_grains=0, max_nuclei=0, grid_nodes=0, stream=None,
+                 claim_blocks=0, max_grains=0, max_nuclei=0, grid_nodes=0, stream=None,
                  device="cuda"):
         import torch
         self._torch = torch
@@ -174,7 +174,7 @@ class Sim:
         mem = gp_memory()
         mem.capacity = int(capacity)
         mem.reached_capacity = int(reached_capacity)
-        mem.claim_buckets = int(claim_buckets)
+        mem.claim_blocks = int(claim_blocks)
         mem.max_grains = int(max_grains)
         mem.max_nuclei = int(max_nuclei)
         mem.grid_nodes = int(grid_nodes)
