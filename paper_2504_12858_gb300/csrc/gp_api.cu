@@ -32,7 +32,7 @@ struct Layout {
   int max_grains, max_nuclei;
   int64_t grid_nodes;
   // offsets into the arena
-  size_t rec0, rec1, pos4, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
+  size_t rec0, rec1, pos4, sslot, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
       rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, dstats, grid, total;
 };
 
@@ -110,6 +110,7 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
   L->rec0 = take(16 * cap);
   L->rec1 = take(16 * cap);
   L->pos4 = take(16 * cap);
+  L->sslot = take(4 * cap);
   L->keys0 = take(4 * cap + 16);
   L->keys1 = take(4 * cap + 16);
   L->vals0 = take(4 * cap + 16);
@@ -262,6 +263,7 @@ struct gp_ctx {
   int4* rec[2] = {nullptr, nullptr};
   int cur = 0;  // rec[cur] is the (unsorted) store
   float4* pos4 = nullptr;
+  int32_t* site_slot = nullptr;  // claim-block slot of each crossing particle's reached site
   SortBufs sb{};
   uint4* cells = nullptr;
   uint32_t stamp = 0;
@@ -465,6 +467,7 @@ gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growt
   c->rec[0] = at<int4>(c, L.rec0);
   c->rec[1] = at<int4>(c, L.rec1);
   c->pos4 = at<float4>(c, L.pos4);
+  c->site_slot = at<int32_t>(c, L.sslot);
   c->sb.keys[0] = at<uint32_t>(c, L.keys0);
   c->sb.keys[1] = at<uint32_t>(c, L.keys1);
   c->sb.vals[0] = at<uint32_t>(c, L.vals0);
@@ -732,11 +735,11 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       c->prof.end(K_BUILD, (double)n);
       c->prof.begin(K_ADVANCE);
       launch_advance(c->P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->C,
-                     c->dst, c->st);
+                     c->site_slot, c->dst, c->st);
       c->prof.end(K_ADVANCE, (double)n);
       c->prof.begin(K_EMIT);
-      launch_emit(c->P, S, sorted, n, c->rec[c->cur], c->sb.keys[0], c->sb.vals[0], c->L.cap,
-                  c->C, c->R, c->dst, c->st);
+      launch_emit(c->P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
+                  c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->st);
       c->prof.end(K_EMIT, (double)n);
     }
     const int64_t pending = c->n_nuclei - (int64_t)c->hst->nucleated;

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* 
                                                  const uint32_t* __restrict__ skeys,
                                                  const uint4* __restrict__ tab,
                                                  uint32_t stamp, int64_t n, Claims C,
-                                                 DevStats* st) {
+                                                 int32_t* __restrict__ site_slot, DevStats* st) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = false, froze = false, clamped = false;
   bool crossing = false;
@@ -327,16 +327,23 @@ __global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* 
   }
   // spawn claims: every outer direction k' at the reached site s' claims the target
   // s' + e_k' for this step (claimant bit of its axis).  All lanes take part.
-  {
+  // The pool slot of the block holding s' is kept for the resolution in k_emit
+  // (most targets lie in that block).
+  if (__any_sync(0xffffffffu, crossing)) {
     BlockCache bc;
+    int32_t sslot = -1;
     for (int k = 0; k < 6; ++k) {
       const bool have = crossing && is_outer(sx, sy, sz, k);
+      if (!__any_sync(0xffffffffu, have)) continue;  // warp-uniform
       int tx = sx, ty = sy, tz = sz;
       step_site(tx, ty, tz, k);
       int sh = 0;
       uint32_t* w = warp_claim_word(C, have, g, tx, ty, tz, true, sh, bc);
       if (w) atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << sh);
+      if (have && (tx >> 3) == (sx >> 3) && (ty >> 3) == (sy >> 3) && (tz >> 3) == (sz >> 3))
+        sslot = (int32_t)bc.b;
     }
+    if (crossing) site_slot[j] = sslot;
   }
   warp_add(&st->particle_steps, active ? 1u : 0u);
   warp_add(&st->frozen_new, froze ? 1u : 0u);
@@ -356,7 +363,8 @@ constexpr int kEmitTile = 256 * kEmitItems;
 // decides what record j emits: bit 6 = the record itself, bits 0..5 = children in
 // direction k; counts the statistics; appends the reached site of a crossing
 __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs& S, const Rec& r,
-                                                bool valid, const Claims& C, const Reached& R,
+                                                bool valid, int32_t sslot, const Claims& C,
+                                                const Reached& R,
                                                 uint32_t& n_frozen, uint32_t& n_spawn,
                                                 uint32_t& n_lost, uint32_t& n_clip) {
   const int lane = threadIdx.x & 31;
@@ -392,6 +400,12 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
   }
   const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
   BlockCache bc;
+  if (sslot >= 0) {  // block of s', looked up by k_advance
+    bc.bx = sx >> 3;
+    bc.by = sy >> 3;
+    bc.bz = sz >> 3;
+    bc.b = sslot;
+  }
   for (int k = 0; k < 6; ++k) {
     if (!is_outer(sx, sy, sz, k)) continue;
     int tx = sx, ty = sy, tz = sz;
@@ -459,7 +473,8 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
 }
 
 __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* __restrict__ rs,
-                                              int64_t n, int4* __restrict__ rout,
+                                              const int32_t* __restrict__ site_slot, int64_t n,
+                                              int4* __restrict__ rout,
                                               uint32_t* __restrict__ keys,
                                               uint32_t* __restrict__ vals, int64_t cap,
                                               Claims C, Reached R, DevStats* st) {
@@ -474,7 +489,9 @@ __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* 
     const int64_t j = base + it * 256 + tid;
     const bool valid = j < n;
     const Rec r = valid ? rec_unpack(__ldg(rs + j)) : Rec{};
-    const uint32_t m = emit_decide(P, S, r, valid, C, R, n_frozen, n_spawn, n_lost, n_clip);
+    const int32_t sslot = (valid && r.cross && r.state == ST_ACTIVE) ? __ldg(site_slot + j) : -1;
+    const uint32_t m =
+        emit_decide(P, S, r, valid, sslot, C, R, n_frozen, n_spawn, n_lost, n_clip);
     masks |= m << (7 * it);
   }
   uint32_t cnt = 0;
@@ -851,8 +868,11 @@ void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals,
 
 void launch_advance(const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const uint32_t* skeys, const uint4* tab, uint32_t stamp,
-                    int64_t n, const Claims& C, DevStats* dst, cudaStream_t st) {
-  if (n > 0) k_advance<<<blocks(n), 256, 0, st>>>(P, S, rs, pos4, skeys, tab, stamp, n, C, dst);
+                    int64_t n, const Claims& C, int32_t* site_slot, DevStats* dst,
+                    cudaStream_t st) {
+  if (n > 0)
+    k_advance<<<blocks(n), 256, 0, st>>>(P, S, rs, pos4, skeys, tab, stamp, n, C, site_slot,
+                                         dst);
 }
 
 int64_t emit_tiles(int64_t n) { return (n + kEmitTile - 1) / kEmitTile; }
@@ -863,12 +883,12 @@ void launch_link_reached(const Params& P, const Reached& R, unsigned long long* 
   k_link_done<<<1, 1, 0, st>>>(R, linked);
 }
 
-void launch_emit(const Params& P, const StepArgs& S, const int4* rs, int64_t n, int4* rout,
-                 uint32_t* keys, uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
-                 DevStats* dst, cudaStream_t st) {
+void launch_emit(const Params& P, const StepArgs& S, const int4* rs, const int32_t* site_slot,
+                 int64_t n, int4* rout, uint32_t* keys, uint32_t* vals, int64_t cap,
+                 const Claims& C, const Reached& R, DevStats* dst, cudaStream_t st) {
   const int64_t nt = emit_tiles(n);
   if (nt == 0) return;
-  k_emit<<<(unsigned)nt, 256, 0, st>>>(P, S, rs, n, rout, keys, vals, cap, C, R, dst);
+  k_emit<<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout, keys, vals, cap, C, R, dst);
   k_emit_check<<<1, 1, 0, st>>>(dst, cap);
 }
 

@@ -12,13 +12,14 @@ void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals,
                   uint32_t* err, cudaStream_t st);
 void launch_advance(const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const uint32_t* skeys, const uint4* tab, uint32_t stamp,
-                    int64_t n, const Claims& C, DevStats* dst, cudaStream_t st);
+                    int64_t n, const Claims& C, int32_t* site_slot, DevStats* dst,
+                    cudaStream_t st);
 int64_t emit_tiles(int64_t n);
 void launch_link_reached(const Params& P, const Reached& R, unsigned long long* linked, int sms,
                          cudaStream_t st);
-void launch_emit(const Params& P, const StepArgs& S, const int4* rs, int64_t n, int4* rout,
-                 uint32_t* keys, uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
-                 DevStats* dst, cudaStream_t st);
+void launch_emit(const Params& P, const StepArgs& S, const int4* rs, const int32_t* site_slot,
+                 int64_t n, int4* rout, uint32_t* keys, uint32_t* vals, int64_t cap,
+                 const Claims& C, const Reached& R, DevStats* dst, cudaStream_t st);
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
                      int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,

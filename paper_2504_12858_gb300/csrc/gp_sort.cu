@@ -79,7 +79,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* s_
   return r;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     uint32_t* status, uint32_t* ticket, uint32_t* err) {
@@ -99,21 +99,20 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   const uint32_t tile = s_tile;
   const int64_t base = (int64_t)tile * kSortTile;
 
-  uint32_t k[kSortItems], v[kSortItems], rk[kSortItems];
-  int dg[kSortItems];
+  // only keys and ranks live in registers (values are read at the scatter, digits
+  // recomputed), which keeps the kernel at four CTAs per SM
+  uint32_t k[kSortItems], rk[kSortItems];
   const int64_t wbase = base + (int64_t)warp * kSortItems * 32;
+  const int64_t nvalid = n - wbase;  // items of this warp's run that exist
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     int64_t idx = wbase + r * 32 + lane;
-    bool ok = idx < n;
-    k[r] = ok ? kin[idx] : 0xffffffffu;
-    v[r] = ok ? vin[idx] : 0u;
-    dg[r] = ok ? (int)((k[r] >> shift) & 255u) : 256;
+    k[r] = idx < n ? kin[idx] : 0xffffffffu;
   }
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const int d = dg[r];
+    const int d = (r * 32 + lane) < nvalid ? (int)((k[r] >> shift) & 255u) : 256;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
     if (d < 256) before = s_whist[warp][d];
@@ -169,10 +168,12 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    if (dg[r] < 256) {
-      uint32_t lp = s_start[dg[r]] + s_whist[warp][dg[r]] + rk[r];
+    const int64_t idx = wbase + r * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = (k[r] >> shift) & 255u;
+      const uint32_t lp = s_start[d] + s_whist[warp][d] + rk[r];
       s_keys[lp] = k[r];
-      s_vals[lp] = v[r];
+      s_vals[lp] = __ldg(vin + idx);
     }
   }
   __syncthreads();

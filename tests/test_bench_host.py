@@ -1,0 +1,75 @@
+"""Host logic of bench.py on CPU: multi-rank aggregation over gloo (world size 2) and
+the clock-log parser."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, lr = bench.dist_env()
+    assert (r, w, lr) == (rank, world, rank)
+    bench.barrier(world)
+    ms, units = bench.reduce_timing(10.0 + 5.0 * rank, 1000.0 * (rank + 1), world)
+    out[rank] = (ms, units)
+    dist.destroy_process_group()
+
+
+def test_reduce_timing_takes_max_time_and_sums_work_over_ranks():
+    import torch.multiprocessing as mp
+    world = 2
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    for rank in range(world):
+        ms, units = out[rank]
+        assert ms == 15.0            # slowest rank
+        assert units == 3000.0       # all ranks' particle steps
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_timing(3.5, 7.0, 1) == (3.5, 7.0)
+
+
+def test_clock_parser(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "c.csv")
+    with open(c.path, "w") as f:
+        f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 210, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+
+    class _P:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+
+    c.proc = _P()
+    r = c.stop()
+    assert r["sm_max_mhz"] == 2070.0
+    assert r["sm_mhz"] == pytest.approx(2025.0)
+    assert r["reasons"] == ["sw_power_cap"]
