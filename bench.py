@@ -224,6 +224,47 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------
+def adjoint_cost(dev):
+    """Cost of the gradient of the front positions (forward with the adjoint tape +
+    reverse sweep) over the plain forward, on the 32-grain calibration cube
+    (200 steps)."""
+    import torch
+    from paper_2504_12858_gb300 import inputs, native
+    from paper_2504_12858_gb300.adjoint import FrontAdjoint
+    w = inputs.adjoint_cube()
+    an = w.analytic
+
+    def plain():
+        sim = native.Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=400000,
+                         reached_capacity=1600000, max_grains=64, device=dev)
+        sim.gp_set_thermal_analytic(an["T0"], an["G"], an["xref"], an["Tdot"])
+        sim.gp_add_grains(w.seeds, w.quats)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sim.gp_step(w.steps)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        sim.close()
+        return t
+
+    def with_gradient():
+        th = torch.tensor([w.a[0], w.b[0], an["G"][2], -an["Tdot"]], dtype=torch.float64,
+                          requires_grad=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = FrontAdjoint.apply(th, w, 400000)
+        out[1:].sum().backward()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0
+
+    plain()
+    with_gradient()
+    tp = min(plain() for _ in range(3))
+    tg = min(with_gradient() for _ in range(3))
+    return {"case": "adjoint_cube: 200 um cube, 32 grains, 200 steps", "plain_forward_ms": tp * 1e3,
+            "forward_with_tape_plus_backward_ms": tg * 1e3, "cost_ratio": tg / tp}
+
+
 def run_native(args, rank, world, local_rank):
     import torch
     from paper_2504_12858_gb300 import native
@@ -319,6 +360,7 @@ def run_native(args, rank, world, local_rank):
                            "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in prof),
                                                                1e-9), 4)} for k in prof}
     cb = cpu_baseline(args.cpu_grains, args.n0, 2) if (world == 1 and not args.no_cpu) else None
+    adj = adjoint_cost(dev) if not args.no_extras else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -334,7 +376,7 @@ def run_native(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": METRIC, "steps": args.e2e_steps,
                     "h2d_bytes_per_step": int(Th.numel() * 4),
                     "d2h_bytes_per_step": 160},
-            "clocks": clk, "gpu_launches": launches}
+            "clocks": clk, "gpu_launches": launches, "adjoint": adj}
     print(json.dumps(line), flush=True)
     sim.close()
     return 0
@@ -358,6 +400,8 @@ def main():
     ap.add_argument("--cpu-grains", type=int, default=100)
     ap.add_argument("--ref-grains", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint-cost measurement on the calibration cube")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     if world > 1:

@@ -105,6 +105,8 @@ typedef struct {
   int32_t max_grains;       /* default 1 << 20                                    */
   int32_t max_nuclei;       /* pending nucleation sites; default 4096             */
   int64_t grid_nodes;       /* thermal-grid nodes reserved in the arena; default 0 */
+  int64_t tape_steps;       /* steps the adjoint tape holds (capacity particles each,
+                               25 bytes per particle and step); default 0 (none)   */
   void* arena;
   size_t arena_bytes;
 } gp_memory;
@@ -231,6 +233,26 @@ gp_status gp_get_reached(gp_ctx* ctx, int64_t cap, int32_t* grain, int32_t* site
 gp_status gp_profile(gp_ctx* ctx, int32_t enable);
 /* Copies up to max entries of per-kernel timing; *n_out = number of kernels. */
 gp_status gp_profile_read(gp_ctx* ctx, int32_t max, gp_kernel_prof* out, int32_t* n_out);
+
+/* ---- adjoint of the advance ---------------------------------------------------- */
+
+/* Starts recording the adjoint tape: the next steps (at most gp_memory.tape_steps)
+ * store the particle records before the advance, the order of the spatial sort,
+ * the state after the contact search and the parent of every particle of the
+ * following step.  Recording restarts at every call.  Needs an analytic field. */
+gp_status gp_tape_begin(gp_ctx* ctx);
+
+/* Reverse sweep over the taped steps, with the discrete events of the forward run
+ * (contacts, spawns, clips, the one-spacing cap) held fixed.  Each particle's
+ * progress obeys ell' = ell + dl (minus one at a spawn, for every child), with
+ * dl = v(dT(x(ell), t)) dt / h (Eq. 1/2, Sec. 2.1.2), so
+ *   d ell'/d ell = 1 + d dl/d ell   and   d ell'/d theta = d dl/d theta.
+ * seed: dL/d ell of every live particle after the last taped step, in store order
+ * (the order of gp_get_particles), n of them; device pointer if flags &
+ * GP_DEVICE_PTR, else host.  grad[8] receives dL/d(a[0], b[0], a[1], b[1], G[0],
+ * G[1], G[2], Tdot) of the growth law and the analytic field.  The taped steps
+ * must end at the current step. */
+gp_status gp_adjoint(gp_ctx* ctx, const float* seed, int64_t n, int32_t flags, double grad[8]);
 
 /* ---- stand-alone steps on caller device buffers ------------------------------ */
 

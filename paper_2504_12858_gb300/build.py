@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgp.so")
-SOURCES = ["gp_api.cu", "gp_kernels.cu", "gp_sort.cu", "gp_static_scratch.cu"]
+SOURCES = ["gp_api.cu", "gp_kernels.cu", "gp_sort.cu", "gp_adjoint.cu", "gp_static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -31,9 +31,11 @@ struct Layout {
   int64_t cap, rcap, blocks, buckets;
   int max_grains, max_nuclei;
   int64_t grid_nodes;
+  int64_t tape_steps;
   // offsets into the arena
   size_t rec0, rec1, pos4, sslot, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
-      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, dstats, grid, total;
+      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, dstats, grid, tape_rec,
+      tape_vals, tape_state, tape_par, tape_grad, total;
 };
 
 bool cells_of(const gp_domain* d, double h, int nc[3], uint64_t* ncells) {
@@ -92,6 +94,7 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
   }
   L->max_nuclei = m->max_nuclei > 0 ? m->max_nuclei : 4096;
   L->grid_nodes = m->grid_nodes > 0 ? m->grid_nodes : 0;
+  L->tape_steps = m->tape_steps > 0 ? m->tape_steps : 0;
   L->nsx = (L->nc[0] + kSegCells - 1) / kSegCells;
   L->nseg = (uint64_t)L->nsx * L->nc[1] * L->nc[2];
   uint64_t nm1 = L->ncells - 1;
@@ -130,6 +133,12 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
   L->nstate = take(4 * (size_t)L->max_nuclei);
   L->dstats = take(sizeof(DevStats));
   L->grid = take(4 * (size_t)L->grid_nodes);
+  const size_t ts = (size_t)L->tape_steps;
+  L->tape_rec = take(16 * cap * ts);
+  L->tape_vals = take(4 * cap * ts);
+  L->tape_state = take(cap * ts);
+  L->tape_par = take(4 * cap * ts);
+  L->tape_grad = take(8 * 8);
   L->total = o;
   return true;
 }
@@ -280,6 +289,10 @@ struct gp_ctx {
   int n_nuclei = 0;
   bool keys_valid = false;
   bool broken = false;
+  // adjoint tape: taped steps (sorted count n, count after the step m, step index)
+  bool tape_on = false;
+  int64_t tape_pos = 0;
+  std::vector<int64_t> tape_n, tape_m, tape_t;
   std::string err;
   Prof prof;
   int sms = 152;
@@ -714,6 +727,10 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
   for (int it = 0; it < nsteps; ++it) {
     const int64_t n = c->n_live;
     const StepArgs S = step_args(c, c->step);
+    const bool rec = c->tape_on && c->tape_pos < c->L.tape_steps;
+    const size_t tq = (size_t)c->tape_pos, tcap = (size_t)c->L.cap;
+    int32_t* tpar = rec ? at<int32_t>(c, c->L.tape_par) + tq * tcap : nullptr;
+    if (rec) GP_CUDA(c, cudaMemsetAsync(tpar, 0xff, 4 * tcap, c->st));
     GP_CUDA(c, cudaMemsetAsync(&c->dst->n_out, 0, sizeof(unsigned long long), c->st));
     GP_CUDA(c, cudaMemsetAsync(&c->dst->n_frozen, 0, sizeof(unsigned long long), c->st));
     if (n > 0) {
@@ -733,13 +750,20 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       launch_build(c->P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4, c->cells,
                    c->stamp, n, &c->dst->err, c->st);
       c->prof.end(K_BUILD, (double)n);
+      if (rec) {
+        GP_CUDA(c, cudaMemcpyAsync(at<int4>(c, c->L.tape_rec) + tq * tcap, sorted, 16 * n,
+                                   cudaMemcpyDeviceToDevice, c->st));
+        GP_CUDA(c, cudaMemcpyAsync(at<uint32_t>(c, c->L.tape_vals) + tq * tcap, c->sb.vals[w],
+                                   4 * n, cudaMemcpyDeviceToDevice, c->st));
+      }
       c->prof.begin(K_ADVANCE);
       launch_advance(c->P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->C,
                      c->site_slot, c->dst, c->st);
       c->prof.end(K_ADVANCE, (double)n);
+      if (rec) launch_tape_state(sorted, n, at<uint8_t>(c, c->L.tape_state) + tq * tcap, c->st);
       c->prof.begin(K_EMIT);
       launch_emit(c->P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
-                  c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->st);
+                  c->sb.vals[0], c->L.cap, c->C, c->R, tpar, c->dst, c->st);
       c->prof.end(K_EMIT, (double)n);
     }
     const int64_t pending = c->n_nuclei - (int64_t)c->hst->nucleated;
@@ -757,11 +781,67 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       c->prof.end(K_FINALIZE, 1.0);
     }
     GP_CUDA(c, cudaGetLastError());
+    const int64_t stepped = c->step;
     ++c->step;
     c->keys_valid = true;
     s = sync_stats(c);
     if (s) return s;
+    if (rec) {
+      c->tape_n.push_back(n);
+      c->tape_m.push_back(c->n_live);
+      c->tape_t.push_back(stepped);
+      ++c->tape_pos;
+    }
   }
+  return GP_OK;
+}
+
+gp_status gp_tape_begin(gp_ctx* c) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (c->L.tape_steps <= 0) return fail(c, GP_ERR_STATE, "no tape (gp_memory.tape_steps = 0)");
+  if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
+  c->tape_on = true;
+  c->tape_pos = 0;
+  c->tape_n.clear();
+  c->tape_m.clear();
+  c->tape_t.clear();
+  return GP_OK;
+}
+
+gp_status gp_adjoint(gp_ctx* c, const float* seed, int64_t n, int32_t flags, double grad[8]) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (!grad || (n > 0 && !seed)) return fail(c, GP_ERR_ARG, "null argument");
+  if (!c->tape_on || c->tape_pos == 0) return fail(c, GP_ERR_STATE, "nothing taped");
+  if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
+  if (c->tape_t.back() != c->step - 1)
+    return fail(c, GP_ERR_STATE, "the taped steps do not end at the current step");
+  if (n != c->n_live) return fail(c, GP_ERR_ARG, "seed length differs from the live particles");
+  const size_t tcap = (size_t)c->L.cap;
+  float* lam_u = reinterpret_cast<float*>(c->sb.keys[1]);
+  float* lam_s = reinterpret_cast<float*>(c->sb.vals[1]);
+  double* gdev = at<double>(c, c->L.tape_grad);
+  if (n > 0)
+    GP_CUDA(c, cudaMemcpyAsync(lam_u, seed, 4 * n,
+                               (flags & GP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice,
+                               c->st));
+  GP_CUDA(c, cudaMemsetAsync(gdev, 0, 8 * 8, c->st));
+  for (int64_t q = c->tape_pos - 1; q >= 0; --q) {
+    const int64_t nn = c->tape_n[q], m = c->tape_m[q];
+    if (nn > 0) GP_CUDA(c, cudaMemsetAsync(lam_s, 0, 4 * nn, c->st));
+    const StepArgs S = step_args(c, c->tape_t[q]);
+    const float t = (float)((double)c->tape_t[q] * c->dt);
+    launch_adj_step(c->P, S, t, at<int4>(c, c->L.tape_rec) + q * tcap,
+                    at<uint8_t>(c, c->L.tape_state) + q * tcap,
+                    at<int32_t>(c, c->L.tape_par) + q * tcap, lam_u, m, lam_s, gdev, c->st);
+    if (q > 0)
+      launch_adj_unsort(lam_s, at<uint32_t>(c, c->L.tape_vals) + q * tcap, nn, lam_u, c->st);
+  }
+  GP_CUDA(c, cudaGetLastError());
+  GP_CUDA(c, cudaMemcpyAsync(grad, gdev, 8 * 8, cudaMemcpyDeviceToHost, c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
   return GP_OK;
 }
 

@@ -433,7 +433,8 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
 __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32_t mask,
                                            unsigned long long o, int4* __restrict__ rout,
                                            uint32_t* __restrict__ keys,
-                                           uint32_t* __restrict__ vals, int64_t cap) {
+                                           uint32_t* __restrict__ vals, int64_t cap,
+                                           int32_t* __restrict__ parent, int64_t j) {
   float4 gc, r0, r1, r2;
   grain_load(P.gtab, r.grain, gc, r0, r1, r2);
   int cx, cy, cz;
@@ -446,6 +447,7 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
           add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
       keys[o] = cell_key(P, p, cx, cy, cz);
       vals[o] = (uint32_t)o;
+      if (parent) parent[o] = (int32_t)j;
     }
     return;
   }
@@ -467,6 +469,7 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
       rout[o] = rec_pack(w);
       keys[o] = cell_key(P, add_dir(sp, r0, r1, r2, k, r.ell), cx, cy, cz);
       vals[o] = (uint32_t)o;
+      if (parent) parent[o] = (int32_t)j;
     }
     ++o;
   }
@@ -477,7 +480,8 @@ __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* 
                                               int4* __restrict__ rout,
                                               uint32_t* __restrict__ keys,
                                               uint32_t* __restrict__ vals, int64_t cap,
-                                              Claims C, Reached R, DevStats* st) {
+                                              Claims C, Reached R, int32_t* __restrict__ parent,
+                                              DevStats* st) {
   __shared__ uint32_t s_warp[8];
   __shared__ unsigned long long s_base;
   const int tid = threadIdx.x;
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* 
     if (!m) continue;
     const int64_t j = base + it * 256 + tid;
     const Rec r = rec_unpack(__ldg(rs + j));
-    emit_write(P, r, m, o, rout, keys, vals, cap);
+    emit_write(P, r, m, o, rout, keys, vals, cap, parent, j);
     o += __popc(m);
   }
   warp_add(&st->n_frozen, n_frozen);
@@ -885,10 +889,12 @@ void launch_link_reached(const Params& P, const Reached& R, unsigned long long* 
 
 void launch_emit(const Params& P, const StepArgs& S, const int4* rs, const int32_t* site_slot,
                  int64_t n, int4* rout, uint32_t* keys, uint32_t* vals, int64_t cap,
-                 const Claims& C, const Reached& R, DevStats* dst, cudaStream_t st) {
+                 const Claims& C, const Reached& R, int32_t* parent, DevStats* dst,
+                 cudaStream_t st) {
   const int64_t nt = emit_tiles(n);
   if (nt == 0) return;
-  k_emit<<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout, keys, vals, cap, C, R, dst);
+  k_emit<<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout, keys, vals, cap, C, R,
+                                       parent, dst);
   k_emit_check<<<1, 1, 0, st>>>(dst, cap);
 }
 

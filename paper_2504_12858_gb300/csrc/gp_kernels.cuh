@@ -19,7 +19,15 @@ void launch_link_reached(const Params& P, const Reached& R, unsigned long long* 
                          cudaStream_t st);
 void launch_emit(const Params& P, const StepArgs& S, const int4* rs, const int32_t* site_slot,
                  int64_t n, int4* rout, uint32_t* keys, uint32_t* vals, int64_t cap,
-                 const Claims& C, const Reached& R, DevStats* dst, cudaStream_t st);
+                 const Claims& C, const Reached& R, int32_t* parent, DevStats* dst,
+                 cudaStream_t st);
+// adjoint tape and reverse sweep (gp_adjoint.cu)
+void launch_tape_state(const int4* rs, int64_t n, uint8_t* out, cudaStream_t st);
+void launch_adj_step(const Params& P, const StepArgs& S, float t, const int4* rec,
+                     const uint8_t* post, const int32_t* par, const float* lam_u, int64_t m,
+                     float* lam_s, double* grad, cudaStream_t st);
+void launch_adj_unsort(const float* lam_s, const uint32_t* vals, int64_t n, float* lam_u,
+                       cudaStream_t st);
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
                      int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,

@@ -46,7 +46,8 @@ class gp_voxel_grid(C.Structure):
 class gp_memory(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("reached_capacity", C.c_int64),
                 ("claim_blocks", C.c_int64), ("max_grains", C.c_int32),
-                ("max_nuclei", C.c_int32), ("grid_nodes", C.c_int64), ("arena", C.c_void_p),
+                ("max_nuclei", C.c_int32), ("grid_nodes", C.c_int64),
+                ("tape_steps", C.c_int64), ("arena", C.c_void_p),
                 ("arena_bytes", C.c_size_t)]
 
 
@@ -97,6 +98,8 @@ SIGNATURES = {
                              C.c_int64, C.POINTER(C.c_int64), _P, C.c_size_t, _P]),
     "gp_hash_build_static": (C.c_int, [_P, C.c_int64, C.POINTER(gp_domain), C.c_double, _P, _P,
                                        _P, _P, C.POINTER(C.c_int64), _P]),
+    "gp_tape_begin": (C.c_int, [_P]),
+    "gp_adjoint": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.POINTER(C.c_double)]),
 }
 GP_STATIC_SCRATCH_MAX_POINTS = 262144
 
@@ -163,8 +166,8 @@ class Sim:
     """
 
     def __init__(self, lo, hi, h, dt, a, b, T_L, capacity, reached_capacity=0,
-                 claim_blocks=0, max_grains=0, max_nuclei=0, grid_nodes=0, stream=None,
-                 device="cuda"):
+                 claim_blocks=0, max_grains=0, max_nuclei=0, grid_nodes=0, tape_steps=0,
+                 stream=None, device="cuda"):
         import torch
         self._torch = torch
         L = load()
@@ -178,6 +181,7 @@ class Sim:
         mem.max_grains = int(max_grains)
         mem.max_nuclei = int(max_nuclei)
         mem.grid_nodes = int(grid_nodes)
+        mem.tape_steps = int(tape_steps)
         nb = C.c_size_t(0)
         self._check(L.gp_arena_bytes(C.byref(self._dom), self.h, C.byref(mem), C.byref(nb)))
         self.device = torch.device(device)
@@ -320,6 +324,20 @@ class Sim:
         res = np.zeros((int(n[2]), int(n[1]), int(n[0])), np.int32)
         self._check(load().gp_grain_map(self._h, C.byref(g), _ptr(res), 0))
         return res
+
+    def gp_tape_begin(self):
+        self._check(load().gp_tape_begin(self._h))
+
+    def gp_adjoint(self, seed):
+        """seed: dL/d ell of the live particles in store order (numpy float32 or a
+        torch CUDA float32 tensor).  Returns dL/d(a0, b0, a1, b1, Gx, Gy, Gz, Tdot)."""
+        g = (C.c_double * 8)()
+        if hasattr(seed, "data_ptr") and getattr(seed, "is_cuda", False):
+            self._check(load().gp_adjoint(self._h, _dptr(seed), seed.numel(), GP_DEVICE_PTR, g))
+        else:
+            sd = np.ascontiguousarray(seed, np.float32)
+            self._check(load().gp_adjoint(self._h, _ptr(sd), sd.size, 0, g))
+        return np.array(list(g))
 
     def gp_profile(self, enable=True):
         self._check(load().gp_profile(self._h, 1 if enable else 0))

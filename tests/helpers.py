@@ -50,3 +50,31 @@ def canon(p):
 def keyset(p):
     return {(int(g), int(a), int(b), int(c), int(d)) for g, (a, b, c), d in
             zip(p["grain"], p["site"], p["dir"])}
+
+
+def tip_signatures(p, n_grains):
+    """Per grain, the sorted (site, dir, state) tuples of its primary tips, and the
+    identity (grain, site, dir) of the highest particle."""
+    from paper_2504_12858_gb300.adjoint import front_outputs
+    _, _, on_axis, _, ih = front_outputs(p, 1.0, n_grains)
+    sig = [[] for _ in range(n_grains)]
+    for i in map(int, np.nonzero(on_axis)[0]):
+        sig[int(p["grain"][i])].append((tuple(int(v) for v in p["site"][i]), int(p["dir"][i]),
+                                        int(p["state"][i])))
+    top = (int(p["grain"][ih]), tuple(int(v) for v in p["site"][ih]), int(p["dir"][ih]),
+           int(p["state"][ih]))
+    return [tuple(sorted(x)) for x in sig], top
+
+
+def oracle_front_run(theta):
+    """Oracle front outputs (H, F), tip signatures and highest particle of the adjoint
+    case for theta = (A, n, G, Tdot) (runs in a worker process)."""
+    from paper_2504_12858_gb300.adjoint import front_outputs
+    A, n, G, Tdot = theta
+    w = inputs.adjoint_cube(A=A, n=n, G=G, Tdot=Tdot)
+    o = oracle_from(w)
+    o.step(w.steps)
+    p = o.particles()
+    H, F, _, _, _ = front_outputs(p, w.h, len(w.seeds))
+    sig, top = tip_signatures(p, len(w.seeds))
+    return H, F, sig, top
