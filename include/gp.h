@@ -254,6 +254,51 @@ gp_status gp_tape_begin(gp_ctx* ctx);
  * must end at the current step. */
 gp_status gp_adjoint(gp_ctx* ctx, const float* seed, int64_t n, int32_t flags, double grad[8]);
 
+/* ---- batches of independent runs ----------------------------------------------- */
+
+/* A batch context advances nruns (1..256) independent simulations together, for
+ * ensembles of seeds, orientations and thermal histories such as a
+ * columnar-to-equiaxed transition map (Sec. 3.5).  Each run r has its own domain
+ * domains[r], analytic field, grains and nucleation sites; all runs share h, dt,
+ * the growth law and the capacities of mem (the particle, reached-site, claim,
+ * grain and nucleus pools are shared).  A run never sees another run's particles:
+ * the spatial hash, the contact search, the clip and the nucleation test of a
+ * particle use its own run's domain and cells only, so every run evolves exactly
+ * as it would alone in a single-run context (same binary32 arithmetic).  Every
+ * kernel of a step covers all runs in one launch.  The hash tables of all runs
+ * are dense and laid out one after the other: the arena grows by about 1.5 bytes
+ * per hash cell of every run.  The single-run calls (gp_add_grains, gp_step,
+ * gp_stats, gp_get_particles, ...) apply to a batch context too and act on run 0
+ * where they take no run; gp_step advances all runs.  A batch takes analytic
+ * fields only (no gp_set_thermal_grid, gp_seed_shell or adjoint tape). */
+gp_status gp_batch_arena_bytes(int32_t nruns, const gp_domain* domains, double h,
+                               const gp_memory* mem, size_t* out_bytes);
+gp_status gp_batch_create(int32_t nruns, const gp_domain* domains, double h, double dt,
+                          const gp_growth_law* law, const gp_memory* mem, void* cuda_stream,
+                          gp_ctx** out);
+
+/* The calls of the same name without "run_", for run `run` of a context (a
+ * single-run context has run 0 only).  Grain ids are global to the context. */
+gp_status gp_run_set_thermal_analytic(gp_ctx* ctx, int32_t run, const gp_thermal_analytic* th);
+gp_status gp_run_add_grains(gp_ctx* ctx, int32_t run, int64_t n, const double* pos3,
+                            const double* quat4, int32_t nucleate, int32_t* out_first_id);
+/* In a batch context every site reserves its grain id at registration: the sites
+ * of one call get consecutive ids from *out_first_grain on (a single-run context
+ * numbers grains at activation and writes -1). */
+gp_status gp_run_nucleation_sites(gp_ctx* ctx, int32_t run, int64_t n, const double* pos3,
+                                  const double* dTn, const double* quat4,
+                                  int32_t* out_first_grain);
+gp_status gp_run_grain_map(gp_ctx* ctx, int32_t run, const gp_voxel_grid* grid, int32_t* out,
+                           int32_t flags);
+
+/* Live (live[r]) and ACTIVE (active[r]) particles of each of the nruns runs
+ * (host arrays, either may be NULL); nruns must equal the context's run count. */
+gp_status gp_run_counts(gp_ctx* ctx, int32_t nruns, int64_t* live, int64_t* active);
+
+/* Nucleus position (binary32, c3: cap x 3) and run of up to cap grains, by grain
+ * id; *n_out receives the number of grains (including reserved ones). */
+gp_status gp_grain_table(gp_ctx* ctx, int64_t cap, float* c3, int32_t* run, int64_t* n_out);
+
 /* ---- stand-alone steps on caller device buffers ------------------------------ */
 
 /* Device workspace bytes for gp_hash_build / gp_contact on n points. */

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_adj_step(Params P, StepArgs S, float t,
         grain_load(P.gtab, r.grain, gc, r0, r1, r2);
         const float3 x =
             add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
-        const float dT = undercooling(P, S, x);
+        const float dT = undercooling(P, P.geo, S, x, P.geo.dT_base);
         if (dT > 0.f) {
           float v = 0.f, dv = 0.f;  // v(dT) and dv/d dT
           float pw[2] = {0.f, 0.f}, lg = logf(dT);
@@ -62,15 +62,15 @@ __global__ void __launch_bounds__(256) k_adj_step(Params P, StepArgs S, float t,
             const float cxl = sg * (a == 0 ? r0.x : (a == 1 ? r0.y : r0.z));
             const float cyl = sg * (a == 0 ? r1.x : (a == 1 ? r1.y : r1.z));
             const float czl = sg * (a == 0 ? r2.x : (a == 1 ? r2.y : r2.z));
-            const float gdx = P.G[0] * cxl + P.G[1] * cyl + P.G[2] * czl;
+            const float gdx = P.geo.G[0] * cxl + P.geo.G[1] * cyl + P.geo.G[2] * czl;
             dldl = -k * dv * gdx;
             for (int i = 0; i < P.nterms; ++i) {
               g8[2 * i] = lam * k * pw[i];                   // d/d a_i
               g8[2 * i + 1] = lam * k * P.a[i] * pw[i] * lg;  // d/d b_i
             }
-            g8[4] = -lam * k * dv * (x.x - P.xref[0]);       // d/d G
-            g8[5] = -lam * k * dv * (x.y - P.xref[1]);
-            g8[6] = -lam * k * dv * (x.z - P.xref[2]);
+            g8[4] = -lam * k * dv * (x.x - P.geo.xref[0]);       // d/d G
+            g8[5] = -lam * k * dv * (x.y - P.geo.xref[1]);
+            g8[6] = -lam * k * dv * (x.z - P.geo.xref[2]);
             g8[7] = -lam * k * dv * t;                      // d/d Tdot
           }
         }

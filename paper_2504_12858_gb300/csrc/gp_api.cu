@@ -22,20 +22,31 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 // cell (up to 4096 cells per axis)
 inline double cell_edge(double h) { return h * (1.0 + 1.0 / 512.0); }
 
-struct Layout {
+// hash geometry of one run and its place in the context-wide key, cell-table and
+// reached-head ranges
+struct RunLayout {
   int nc[3];
-  uint64_t ncells;
-  int nsx;        // cell-table segments per x row
-  uint64_t nseg;  // cell-table entries
-  int nbits;
-  int64_t cap, rcap, blocks, buckets;
-  int max_grains, max_nuclei;
-  int64_t grid_nodes;
-  int64_t tape_steps;
+  int nsx;
+  uint64_t ncells, nseg, nheads;
+  uint64_t key0, seg0, head0;
+};
+
+struct Layout {
+  bool batch = false;
+  int nruns = 1;
+  int hshift = 0;       // reached-site heads per 2^hshift cells along each axis
+  std::vector<RunLayout> run;
+  uint64_t key_end = 0;  // keys of all runs lie in [0, key_end)
+  uint64_t nseg = 0, nheads = 0;
+  int nbits = 0, key_bytes = 4;
+  int64_t cap = 0, rcap = 0, blocks = 0, buckets = 0;
+  int max_grains = 0, max_nuclei = 0;
+  int64_t grid_nodes = 0;
+  int64_t tape_steps = 0;
   // offsets into the arena
   size_t rec0, rec1, pos4, sslot, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
-      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, dstats, grid, tape_rec,
-      tape_vals, tape_state, tape_par, tape_grad, total;
+      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, dstats, grid, runs,
+      rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, total;
 };
 
 bool cells_of(const gp_domain* d, double h, int nc[3], uint64_t* ncells) {
@@ -59,19 +70,58 @@ int64_t pow2_at_least(int64_t v) {
   return p;
 }
 
-bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, std::string* why) {
-  if (!d || !m || !(h > 0)) {
-    *why = "domain, memory and h > 0 are required";
+int bits_for(uint64_t end) {
+  uint64_t m = end ? end - 1 : 0;
+  int b = 0;
+  while (m) {
+    ++b;
+    m >>= 1;
+  }
+  return b;
+}
+
+bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_memory* m,
+                 Layout* L, std::string* why) {
+  if (!d || !m || !(h > 0) || nruns < 1 || nruns > kMaxRuns || (!batch && nruns != 1)) {
+    *why = "domain, memory, h > 0 and 1..256 runs are required";
     return false;
   }
-  if (!cells_of(d, h, L->nc, &L->ncells)) {
-    *why = "domain too large for the spatial hash (more than 4096 cells per axis or 2^32 cells)";
-    return false;
+  L->batch = batch;
+  L->nruns = nruns;
+  L->hshift = batch ? 1 : 0;
+  L->run.assign(nruns, RunLayout{});
+  uint64_t key = 0, seg = 0, head = 0;
+  for (int r = 0; r < nruns; ++r) {
+    RunLayout& R = L->run[r];
+    if (!cells_of(d + r, h, R.nc, &R.ncells)) {
+      *why = "domain too large for the spatial hash (more than 4096 cells per axis or 2^32 cells)";
+      return false;
+    }
+    double diag = 0;
+    for (int a = 0; a < 3; ++a) diag += (d[r].hi[a] - d[r].lo[a]) * (d[r].hi[a] - d[r].lo[a]);
+    if (std::sqrt(diag) / h > 4000.0) {
+      *why = "domain diagonal exceeds 4000 lattice spacings";
+      return false;
+    }
+    R.nsx = (R.nc[0] + kSegCells - 1) / kSegCells;
+    R.nseg = (uint64_t)R.nsx * R.nc[1] * R.nc[2];
+    const int hm = (1 << L->hshift) - 1;
+    R.nheads = (uint64_t)((R.nc[0] + hm) >> L->hshift) * ((R.nc[1] + hm) >> L->hshift) *
+               ((R.nc[2] + hm) >> L->hshift);
+    R.key0 = key;
+    R.seg0 = seg;
+    R.head0 = head;
+    key += R.ncells;
+    seg += R.nseg;
+    head += R.nheads;
   }
-  double diag = 0;
-  for (int a = 0; a < 3; ++a) diag += (d->hi[a] - d->lo[a]) * (d->hi[a] - d->lo[a]);
-  if (std::sqrt(diag) / h > 4000.0) {
-    *why = "domain diagonal exceeds 4000 lattice spacings";
+  L->key_end = key;
+  L->nseg = seg;
+  L->nheads = head;
+  L->key_bytes = batch ? 8 : 4;
+  L->nbits = bits_for(key);
+  if (L->nbits > 8 * kSortMaxPasses || (!batch && L->nbits > 32)) {
+    *why = "too many hash cells over all runs";
     return false;
   }
   if (m->capacity <= 0 || m->capacity >= (1ll << 30)) {
@@ -88,20 +138,16 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
     return false;
   }
   L->max_grains = m->max_grains > 0 ? m->max_grains : (1 << 20);
-  if (L->max_grains > (1 << 24)) {
+  if (L->max_grains > (1 << kRunShift)) {
     *why = "max_grains must be <= 2^24";
     return false;
   }
   L->max_nuclei = m->max_nuclei > 0 ? m->max_nuclei : 4096;
   L->grid_nodes = m->grid_nodes > 0 ? m->grid_nodes : 0;
   L->tape_steps = m->tape_steps > 0 ? m->tape_steps : 0;
-  L->nsx = (L->nc[0] + kSegCells - 1) / kSegCells;
-  L->nseg = (uint64_t)L->nsx * L->nc[1] * L->nc[2];
-  uint64_t nm1 = L->ncells - 1;
-  L->nbits = 0;
-  while (nm1) {
-    ++L->nbits;
-    nm1 >>= 1;
+  if (batch && (L->grid_nodes || L->tape_steps)) {
+    *why = "a batch of runs takes analytic fields only and no adjoint tape";
+    return false;
   }
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -110,29 +156,34 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
     return at;
   };
   const size_t cap = (size_t)L->cap;
+  const size_t kb = (size_t)L->key_bytes;
   L->rec0 = take(16 * cap);
   L->rec1 = take(16 * cap);
   L->pos4 = take(16 * cap);
   L->sslot = take(4 * cap);
-  L->keys0 = take(4 * cap + 16);
-  L->keys1 = take(4 * cap + 16);
+  L->keys0 = take(kb * cap + 16);
+  L->keys1 = take(kb * cap + 16);
   L->vals0 = take(4 * cap + 16);
   L->vals1 = take(4 * cap + 16);
   L->sstatus = take(4 * radix_status_words(L->cap));
-  L->hist = take(4 * 4 * 256);
+  L->hist = take(4 * kSortMaxPasses * 256);
   L->tickets = take(4 * 8);
   L->cells = take(16 * (size_t)L->nseg);
   L->rkey = take(8 * (size_t)L->rcap);
   L->rnext = take(4 * (size_t)L->rcap);
-  L->rhead = take(4 * (size_t)L->ncells);
+  L->rhead = take(4 * (size_t)L->nheads);
   L->ckeys = take(16 * (size_t)L->buckets);
   L->cdata = take(4 * kBrickWords * (size_t)L->blocks);
   L->gtab = take(64 * (size_t)L->max_grains);
   L->npos = take(16 * (size_t)L->max_nuclei);
   L->ngrain = take(64 * (size_t)L->max_nuclei);
   L->nstate = take(4 * (size_t)L->max_nuclei);
+  L->nmeta = take(8 * (size_t)L->max_nuclei);
   L->dstats = take(sizeof(DevStats));
   L->grid = take(4 * (size_t)L->grid_nodes);
+  L->runs = take(sizeof(Geo) * (size_t)nruns);
+  L->rtherm = take(16 * (size_t)nruns);
+  L->rcount = take(16 * (size_t)nruns);
   const size_t ts = (size_t)L->tape_steps;
   L->tape_rec = take(16 * cap * ts);
   L->tape_vals = take(4 * cap * ts);
@@ -141,6 +192,14 @@ bool make_layout(const gp_domain* d, double h, const gp_memory* m, Layout* L, st
   L->tape_grad = take(8 * 8);
   L->total = o;
   return true;
+}
+
+// T_L - T0 - Tdot t_n of an analytic field with a = T_L - T0 (every product and
+// difference rounded once, as the device-side batch computation does)
+float dT_base_at(double a, double Tdot, int64_t n, double dt) {
+  volatile double t = (double)n * dt;
+  volatile double q = Tdot * t;
+  return (float)(a - q);
 }
 
 // rotation (crystal -> lab) of a unit quaternion (w, x, y, z)
@@ -158,11 +217,13 @@ void quat_rot(const double* qin, double R[9]) {
   R[8] = 1 - 2 * (x * x + y * y);
 }
 
-// grain table entry: c, then the rows of h R
-void grain_entry(const double* pos, const double* q, double h, float4 out[4]) {
+// grain table entry: c (with the run id in w), then the rows of h R
+void grain_entry(const double* pos, const double* q, double h, int run, float4 out[4]) {
   double R[9];
   quat_rot(q, R);
-  out[0] = make_float4((float)pos[0], (float)pos[1], (float)pos[2], 0.f);
+  float w;
+  std::memcpy(&w, &run, sizeof(w));
+  out[0] = make_float4((float)pos[0], (float)pos[1], (float)pos[2], w);
   for (int r = 0; r < 3; ++r)
     out[1 + r] = make_float4((float)(h * R[3 * r]), (float)(h * R[3 * r + 1]),
                              (float)(h * R[3 * r + 2]), 0.f);
@@ -259,12 +320,15 @@ struct gp_ctx {
   bool own = false;
   char* base = nullptr;
   Layout L{};
-  double lo[3], hi[3], h = 0, dt = 0;
+  bool batch = false;                // several independent runs (gp_batch_create)
+  std::vector<gp_domain> dom;        // per run
+  double h = 0, dt = 0;
   gp_growth_law law{};
   Params P{};
   // thermal
-  int thermal = 0;
-  double T0 = 0, Tdot = 0;
+  int thermal = 0;                   // 1 analytic (every run), 2 grid (single run)
+  std::vector<double> T0, Tdot;      // analytic field per run
+  std::vector<char> thermal_set;     // per run
   double gorigin[3] = {0, 0, 0}, gvel[3] = {0, 0, 0};
   float* grid_own = nullptr;  // cudaMalloc'ed grid when the arena has none
   size_t grid_own_bytes = 0;
@@ -282,6 +346,11 @@ struct gp_ctx {
   float4* npos = nullptr;
   float4* ngrain = nullptr;
   int* nstate = nullptr;
+  int2* nmeta = nullptr;             // batch: reserved grain and run of each nucleation site
+  Geo* runs = nullptr;               // batch: per-run geometry table
+  double2* rtherm = nullptr;         // batch: (T_L - T0, Tdot) per run
+  unsigned long long* rcount = nullptr;
+  std::vector<Geo> geo;              // host copy of the per-run geometry
   DevStats* dst = nullptr;
   DevStats* hst = nullptr;  // pinned mirror
   // host mirrors
@@ -328,12 +397,23 @@ T* at(gp_ctx* c, size_t off) {
 
 void refresh_params(gp_ctx* c) {
   Params& P = c->P;
-  for (int a = 0; a < 3; ++a) {
-    P.lo[a] = (float)c->lo[a];
-    P.hi[a] = (float)c->hi[a];
-    P.nc[a] = c->L.nc[a];
+  c->geo.assign(c->L.nruns, Geo{});
+  for (int r = 0; r < c->L.nruns; ++r) {
+    Geo& g = c->geo[r];
+    const RunLayout& R = c->L.run[r];
+    for (int a = 0; a < 3; ++a) {
+      g.lo[a] = (float)c->dom[r].lo[a];
+      g.hi[a] = (float)c->dom[r].hi[a];
+      g.nc[a] = R.nc[a];
+    }
+    g.nsx = R.nsx;
+    g.key0 = R.key0;
+    g.seg0 = R.seg0;
+    g.head0 = R.head0;
   }
-  P.nsx = c->L.nsx;
+  P.geo = c->geo[0];
+  P.runs = c->batch ? c->runs : nullptr;
+  P.hshift = c->L.hshift;
   P.inv_c = (float)(1.0 / cell_edge(c->h));
   float hf = (float)c->h;
   P.rc2 = hf * hf;
@@ -352,10 +432,21 @@ void refresh_params(gp_ctx* c) {
 StepArgs step_args(const gp_ctx* c, int64_t n) {
   StepArgs S{};
   const double t = (double)n * c->dt;
-  if (c->thermal == 1) S.dT_base = (float)(c->law.T_liquidus - c->T0 - c->Tdot * t);
   for (int a = 0; a < 3; ++a) S.gshift[a] = (float)(c->gorigin[a] + c->gvel[a] * t);
   S.parity = (int)(n & 1);
   return S;
+}
+
+// kernel constants for step n of a single-run context (analytic field at t_n and
+// t_{n+1}); a batch computes its runs' values on the device (launch_run_step)
+Params step_params(const gp_ctx* c, int64_t n) {
+  Params P = c->P;
+  if (!c->batch && c->thermal == 1) {
+    const double a = c->law.T_liquidus - c->T0[0];
+    P.geo.dT_base = dT_base_at(a, c->Tdot[0], n, c->dt);
+    P.geo.dT_base1 = dT_base_at(a, c->Tdot[0], n + 1, c->dt);
+  }
+  return P;
 }
 
 gp_status sync_stats(gp_ctx* c) {
@@ -413,40 +504,28 @@ std::vector<short4> l1_sphere(int m) {
   return v;
 }
 
-}  // namespace
-
-extern "C" {
-
-gp_status gp_arena_bytes(const gp_domain* domain, double h, const gp_memory* mem,
-                         size_t* out_bytes) {
-  if (!out_bytes) return GP_ERR_ARG;
-  Layout L{};
-  std::string why;
-  if (!make_layout(domain, h, mem, &L, &why)) return GP_ERR_ARG;
-  *out_bytes = L.total;
-  return GP_OK;
-}
-
-gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growth_law* law,
-                    const gp_memory* mem, void* cuda_stream, gp_ctx** out) {
-  if (!out || !domain || !law || !mem) return GP_ERR_ARG;
+gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, double dt,
+                     const gp_growth_law* law, const gp_memory* mem, void* cuda_stream,
+                     gp_ctx** out) {
+  if (!out || !domains || !law || !mem) return GP_ERR_ARG;
   *out = nullptr;
   if (!(dt > 0) || law->nterms < 1 || law->nterms > 2) return GP_ERR_ARG;
   for (int i = 0; i < law->nterms; ++i)
     if (!std::isfinite(law->a[i]) || !std::isfinite(law->b[i]) || law->b[i] < 0) return GP_ERR_ARG;
   gp_ctx* c = new gp_ctx();
   std::string why;
-  if (!make_layout(domain, h, mem, &c->L, &why)) {
+  if (!make_layout(domains, nruns, batch, h, mem, &c->L, &why)) {
     delete c;
     return GP_ERR_ARG;
   }
+  c->batch = batch;
   cudaGetDevice(&c->device);
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   c->st = (cudaStream_t)cuda_stream;
-  for (int a = 0; a < 3; ++a) {
-    c->lo[a] = domain->lo[a];
-    c->hi[a] = domain->hi[a];
-  }
+  c->dom.assign(domains, domains + nruns);
+  c->T0.assign(nruns, 0.0);
+  c->Tdot.assign(nruns, 0.0);
+  c->thermal_set.assign(nruns, 0);
   c->h = h;
   c->dt = dt;
   c->law = *law;
@@ -481,8 +560,8 @@ gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growt
   c->rec[1] = at<int4>(c, L.rec1);
   c->pos4 = at<float4>(c, L.pos4);
   c->site_slot = at<int32_t>(c, L.sslot);
-  c->sb.keys[0] = at<uint32_t>(c, L.keys0);
-  c->sb.keys[1] = at<uint32_t>(c, L.keys1);
+  c->sb.keys[0] = c->base + L.keys0;
+  c->sb.keys[1] = c->base + L.keys1;
   c->sb.vals[0] = at<uint32_t>(c, L.vals0);
   c->sb.vals[1] = at<uint32_t>(c, L.vals1);
   c->sb.status = at<uint32_t>(c, L.sstatus);
@@ -511,16 +590,23 @@ gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growt
   c->npos = at<float4>(c, L.npos);
   c->ngrain = at<float4>(c, L.ngrain);
   c->nstate = at<int>(c, L.nstate);
+  c->nmeta = at<int2>(c, L.nmeta);
+  c->runs = at<Geo>(c, L.runs);
+  c->rtherm = at<double2>(c, L.rtherm);
+  c->rcount = at<unsigned long long>(c, L.rcount);
   refresh_params(c);
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemsetAsync(c->cells, 0, 16 * L.nseg, s);
-  e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.ncells, s);
+  e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.nheads, s);
   e = e ? e : cudaMemsetAsync(c->C.bucket, 0, 16 * (size_t)L.buckets, s);
   e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.blocks, s);
   e = e ? e : cudaMemsetAsync(c->dst, 0, sizeof(DevStats), s);
   e = e ? e : cudaMemsetAsync(c->gtab, 0, 64 * (size_t)L.max_grains, s);
   e = e ? e : cudaMemsetAsync(c->nstate, 0, 4 * (size_t)L.max_nuclei, s);
+  e = e ? e : cudaMemsetAsync(c->rtherm, 0, 16 * (size_t)L.nruns, s);
+  e = e ? e : cudaMemcpyAsync(c->runs, c->geo.data(), sizeof(Geo) * c->geo.size(),
+                              cudaMemcpyHostToDevice, s);
   e = e ? e : cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     gp_destroy(c);
@@ -528,6 +614,41 @@ gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growt
   }
   *out = c;
   return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_arena_bytes(const gp_domain* domain, double h, const gp_memory* mem,
+                         size_t* out_bytes) {
+  if (!out_bytes) return GP_ERR_ARG;
+  Layout L{};
+  std::string why;
+  if (!make_layout(domain, 1, false, h, mem, &L, &why)) return GP_ERR_ARG;
+  *out_bytes = L.total;
+  return GP_OK;
+}
+
+gp_status gp_batch_arena_bytes(int32_t nruns, const gp_domain* domains, double h,
+                               const gp_memory* mem, size_t* out_bytes) {
+  if (!out_bytes) return GP_ERR_ARG;
+  Layout L{};
+  std::string why;
+  if (!make_layout(domains, nruns, true, h, mem, &L, &why)) return GP_ERR_ARG;
+  *out_bytes = L.total;
+  return GP_OK;
+}
+
+gp_status gp_create(const gp_domain* domain, double h, double dt, const gp_growth_law* law,
+                    const gp_memory* mem, void* cuda_stream, gp_ctx** out) {
+  return create_ctx(domain, 1, false, h, dt, law, mem, cuda_stream, out);
+}
+
+gp_status gp_batch_create(int32_t nruns, const gp_domain* domains, double h, double dt,
+                          const gp_growth_law* law, const gp_memory* mem, void* cuda_stream,
+                          gp_ctx** out) {
+  return create_ctx(domains, nruns, true, h, dt, law, mem, cuda_stream, out);
 }
 
 gp_status gp_destroy(gp_ctx* c) {
@@ -547,8 +668,14 @@ const char* gp_last_error(const gp_ctx* c) { return c ? c->err.c_str() : "null c
 
 gp_status gp_add_grains(gp_ctx* c, int64_t n, const double* pos3, const double* quat4,
                         int32_t nucleate, int32_t* out_first_id) {
+  return gp_run_add_grains(c, 0, n, pos3, quat4, nucleate, out_first_id);
+}
+
+gp_status gp_run_add_grains(gp_ctx* c, int32_t run, int64_t n, const double* pos3,
+                            const double* quat4, int32_t nucleate, int32_t* out_first_id) {
   gp_status s = check_ctx(c);
   if (s) return s;
+  if (run < 0 || run >= c->L.nruns) return fail(c, GP_ERR_ARG, "no such run");
   if (n < 0 || (n > 0 && (!pos3 || !quat4))) return fail(c, GP_ERR_ARG, "bad arguments");
   if (c->n_grains + n > c->L.max_grains) return fail(c, GP_ERR_CAPACITY, "grain capacity");
   if (nucleate && c->n_live + 6 * n > c->L.cap) return fail(c, GP_ERR_CAPACITY, "particle capacity");
@@ -557,13 +684,14 @@ gp_status gp_add_grains(gp_ctx* c, int64_t n, const double* pos3, const double* 
     double nq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     if (!(nq > 0) || !std::isfinite(nq)) return fail(c, GP_ERR_ARG, "quaternion is zero or not finite");
     for (int a = 0; a < 3; ++a)
-      if (!(pos3[3 * i + a] >= c->lo[a] && pos3[3 * i + a] <= c->hi[a]))
+      if (!(pos3[3 * i + a] >= c->dom[run].lo[a] && pos3[3 * i + a] <= c->dom[run].hi[a]))
         return fail(c, GP_ERR_ARG, "nucleus outside the domain");
   }
   if (out_first_id) *out_first_id = (int32_t)c->n_grains;
   if (n == 0) return GP_OK;
   std::vector<float4> G(4 * (size_t)n);
-  for (int64_t i = 0; i < n; ++i) grain_entry(pos3 + 3 * i, quat4 + 4 * i, c->h, &G[4 * i]);
+  for (int64_t i = 0; i < n; ++i)
+    grain_entry(pos3 + 3 * i, quat4 + 4 * i, c->h, run, &G[4 * i]);
   GP_CUDA(c, cudaMemcpyAsync(c->gtab + 4 * c->n_grains, G.data(), sizeof(float4) * G.size(),
                              cudaMemcpyHostToDevice, c->st));
   const int64_t g0 = c->n_grains;
@@ -617,6 +745,7 @@ gp_status gp_add_grains(gp_ctx* c, int64_t n, const double* pos3, const double* 
 gp_status gp_seed_shell(gp_ctx* c, int64_t n, const int32_t* grains, int32_t n0, double ell0) {
   gp_status s = check_ctx(c);
   if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "shell seeding is for single-run contexts");
   if (n < 0 || (n > 0 && !grains) || n0 < 0 || n0 > 2000 || !(ell0 >= 0 && ell0 < 1))
     return fail(c, GP_ERR_ARG, "bad arguments");
   for (int64_t i = 0; i < n; ++i)
@@ -644,23 +773,43 @@ gp_status gp_seed_shell(gp_ctx* c, int64_t n, const int32_t* grains, int32_t n0,
 }
 
 gp_status gp_set_thermal_analytic(gp_ctx* c, const gp_thermal_analytic* th) {
+  return gp_run_set_thermal_analytic(c, 0, th);
+}
+
+gp_status gp_run_set_thermal_analytic(gp_ctx* c, int32_t run, const gp_thermal_analytic* th) {
   gp_status s = check_ctx(c);
   if (s) return s;
+  if (run < 0 || run >= c->L.nruns) return fail(c, GP_ERR_ARG, "no such run");
   if (!th) return fail(c, GP_ERR_ARG, "null field");
   c->thermal = 1;
-  c->T0 = th->T0;
-  c->Tdot = th->Tdot;
   c->P.thermal = 1;
+  c->T0[run] = th->T0;
+  c->Tdot[run] = th->Tdot;
+  c->thermal_set[run] = 1;
+  Geo& g = c->geo[run];
   for (int a = 0; a < 3; ++a) {
-    c->P.G[a] = (float)th->G[a];
-    c->P.xref[a] = (float)th->x_ref[a];
+    g.G[a] = (float)th->G[a];
+    g.xref[a] = (float)th->x_ref[a];
   }
+  if (!c->batch) {
+    for (int a = 0; a < 3; ++a) {
+      c->P.geo.G[a] = g.G[a];
+      c->P.geo.xref[a] = g.xref[a];
+    }
+    return GP_OK;
+  }
+  const double2 th2 = make_double2(c->law.T_liquidus - th->T0, th->Tdot);
+  GP_CUDA(c, cudaMemcpyAsync(c->runs + run, &g, sizeof(Geo), cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaMemcpyAsync(c->rtherm + run, &th2, sizeof(double2), cudaMemcpyHostToDevice,
+                             c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
   return GP_OK;
 }
 
 gp_status gp_set_thermal_grid(gp_ctx* c, const gp_thermal_grid* th) {
   gp_status s = check_ctx(c);
   if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "a batch of runs takes analytic fields only");
   if (!th || !th->T) return fail(c, GP_ERR_ARG, "null grid");
   for (int a = 0; a < 3; ++a)
     if (th->n[a] < 2 || !(th->spacing[a] > 0)) return fail(c, GP_ERR_ARG, "grid needs n >= 2 and spacing > 0");
@@ -698,35 +847,66 @@ gp_status gp_set_thermal_grid(gp_ctx* c, const gp_thermal_grid* th) {
 
 gp_status gp_nucleation_sites(gp_ctx* c, int64_t n, const double* pos3, const double* dTn,
                               const double* quat4) {
+  return gp_run_nucleation_sites(c, 0, n, pos3, dTn, quat4, nullptr);
+}
+
+gp_status gp_run_nucleation_sites(gp_ctx* c, int32_t run, int64_t n, const double* pos3,
+                                  const double* dTn, const double* quat4,
+                                  int32_t* out_first_grain) {
   gp_status s = check_ctx(c);
   if (s) return s;
+  if (run < 0 || run >= c->L.nruns) return fail(c, GP_ERR_ARG, "no such run");
   if (n < 0 || (n > 0 && (!pos3 || !dTn || !quat4))) return fail(c, GP_ERR_ARG, "bad arguments");
   if (c->n_nuclei + n > c->L.max_nuclei) return fail(c, GP_ERR_CAPACITY, "nucleus capacity");
+  if (c->batch && c->n_grains + n > c->L.max_grains)
+    return fail(c, GP_ERR_CAPACITY, "grain capacity");
+  if (out_first_grain) *out_first_grain = c->batch ? (int32_t)c->n_grains : -1;
   if (n == 0) return GP_OK;
   std::vector<float4> P(n), G(4 * (size_t)n);
   for (int64_t i = 0; i < n; ++i) {
     P[i] = make_float4((float)pos3[3 * i], (float)pos3[3 * i + 1], (float)pos3[3 * i + 2],
                        (float)dTn[i]);
-    grain_entry(pos3 + 3 * i, quat4 + 4 * i, c->h, &G[4 * i]);
+    grain_entry(pos3 + 3 * i, quat4 + 4 * i, c->h, run, &G[4 * i]);
   }
   GP_CUDA(c, cudaMemcpyAsync(c->npos + c->n_nuclei, P.data(), sizeof(float4) * n,
                              cudaMemcpyHostToDevice, c->st));
-  GP_CUDA(c, cudaMemcpyAsync(c->ngrain + 4 * (size_t)c->n_nuclei, G.data(),
-                             sizeof(float4) * G.size(), cudaMemcpyHostToDevice, c->st));
-  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  if (!c->batch) {
+    // grain ids are given at activation, in registration order
+    GP_CUDA(c, cudaMemcpyAsync(c->ngrain + 4 * (size_t)c->n_nuclei, G.data(),
+                               sizeof(float4) * G.size(), cudaMemcpyHostToDevice, c->st));
+    GP_CUDA(c, cudaStreamSynchronize(c->st));
+    c->n_nuclei += (int)n;
+    return GP_OK;
+  }
+  // batch: every site reserves its grain id now, so that runs never wait on one
+  // another's activations
+  std::vector<int2> M(n);
+  for (int64_t i = 0; i < n; ++i) M[i] = make_int2((int)(c->n_grains + i), run);
+  GP_CUDA(c, cudaMemcpyAsync(c->gtab + 4 * c->n_grains, G.data(), sizeof(float4) * G.size(),
+                             cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaMemcpyAsync(c->nmeta + c->n_nuclei, M.data(), sizeof(int2) * n,
+                             cudaMemcpyHostToDevice, c->st));
   c->n_nuclei += (int)n;
-  return GP_OK;
+  c->n_grains += n;
+  return push_counts(c);
 }
 
 gp_status gp_step(gp_ctx* c, int32_t nsteps) {
   gp_status s = check_ctx(c);
   if (s) return s;
   if (nsteps < 0) return fail(c, GP_ERR_ARG, "nsteps < 0");
-  if (c->thermal == 0 && c->n_live > 0)
+  if (c->batch) {
+    for (int r = 0; r < c->L.nruns; ++r)
+      if (!c->thermal_set[r]) return fail(c, GP_ERR_STATE, "a run has no thermal field");
+  } else if (c->thermal == 0 && c->n_live > 0) {
     return fail(c, GP_ERR_STATE, "no thermal field set");
+  }
+  const bool batch = c->batch;
   for (int it = 0; it < nsteps; ++it) {
     const int64_t n = c->n_live;
     const StepArgs S = step_args(c, c->step);
+    const Params P = step_params(c, c->step);
+    if (batch) launch_run_step(c->runs, c->rtherm, c->L.nruns, c->step, c->dt, c->st);
     const bool rec = c->tape_on && c->tape_pos < c->L.tape_steps;
     const size_t tq = (size_t)c->tape_pos, tcap = (size_t)c->L.cap;
     int32_t* tpar = rec ? at<int32_t>(c, c->L.tape_par) + tq * tcap : nullptr;
@@ -736,19 +916,21 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
     if (n > 0) {
       if (!c->keys_valid) {
         c->prof.begin(K_KEYS);
-        launch_keys(c->P, c->rec[c->cur], n, c->sb.keys[0], c->sb.vals[0], c->st);
+        launch_keys(batch, P, c->rec[c->cur], n, c->sb.keys[0], c->sb.vals[0], c->st);
         c->prof.end(K_KEYS, (double)n);
         c->keys_valid = true;
       }
-      const int w = radix_sort(c->sb, n, c->L.nbits, c->st);
+      const int w = batch ? radix_sort<uint64_t>(c->sb, n, c->L.nbits, c->st)
+                          : radix_sort<uint32_t>(c->sb, n, c->L.nbits, c->st);
+      if (w < 0) return fail(c, GP_ERR_STATE, "cell keys wider than the sort supports");
       if (++c->stamp > 0xffffu) {
         GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
         c->stamp = 1;
       }
       int4* sorted = c->rec[c->cur ^ 1];
       c->prof.begin(K_BUILD);
-      launch_build(c->P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4, c->cells,
-                   c->stamp, n, &c->dst->err, c->st);
+      launch_build(batch, P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4,
+                   c->cells, c->stamp, n, c->L.key_end, &c->dst->err, c->st);
       c->prof.end(K_BUILD, (double)n);
       if (rec) {
         GP_CUDA(c, cudaMemcpyAsync(at<int4>(c, c->L.tape_rec) + tq * tcap, sorted, 16 * n,
@@ -757,23 +939,30 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                                    4 * n, cudaMemcpyDeviceToDevice, c->st));
       }
       c->prof.begin(K_ADVANCE);
-      launch_advance(c->P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->C,
+      launch_advance(batch, P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->C,
                      c->site_slot, c->dst, c->st);
       c->prof.end(K_ADVANCE, (double)n);
       if (rec) launch_tape_state(sorted, n, at<uint8_t>(c, c->L.tape_state) + tq * tcap, c->st);
       c->prof.begin(K_EMIT);
-      launch_emit(c->P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
+      launch_emit(batch, P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
                   c->sb.vals[0], c->L.cap, c->C, c->R, tpar, c->dst, c->st);
       c->prof.end(K_EMIT, (double)n);
     }
     const int64_t pending = c->n_nuclei - (int64_t)c->hst->nucleated;
     if (pending > 0) {
       const StepArgs S1 = step_args(c, c->step + 1);
-      launch_link_reached(c->P, c->R, &c->dst->linked, c->sms, c->st);
+      launch_link_reached(batch, P, c->R, &c->dst->linked, c->sms, c->st);
       c->prof.begin(K_NUCLEATE);
-      launch_nucleate(c->P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
-                      c->L.max_grains, c->rec[c->cur], c->sb.keys[0], c->sb.vals[0], c->L.cap,
-                      c->C, c->R, c->dst, c->st);
+      if (batch) {
+        launch_nucleate_batch(P, S1, c->npos, c->nmeta, c->nstate, c->n_nuclei, c->rec[c->cur],
+                              static_cast<uint64_t*>(c->sb.keys[0]), c->sb.vals[0], c->L.cap,
+                              c->C, c->R, c->dst, c->sms, c->st);
+        launch_finalize(c->dst, c->L.cap, c->st);
+      } else {
+        launch_nucleate(P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
+                        c->L.max_grains, c->rec[c->cur], static_cast<uint32_t*>(c->sb.keys[0]),
+                        c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->st);
+      }
       c->prof.end(K_NUCLEATE, 1.0);
     } else {
       c->prof.begin(K_FINALIZE);
@@ -799,6 +988,7 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
 gp_status gp_tape_begin(gp_ctx* c) {
   gp_status s = check_ctx(c);
   if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "the adjoint is for single-run contexts");
   if (c->L.tape_steps <= 0) return fail(c, GP_ERR_STATE, "no tape (gp_memory.tape_steps = 0)");
   if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
   c->tape_on = true;
@@ -819,7 +1009,7 @@ gp_status gp_adjoint(gp_ctx* c, const float* seed, int64_t n, int32_t flags, dou
     return fail(c, GP_ERR_STATE, "the taped steps do not end at the current step");
   if (n != c->n_live) return fail(c, GP_ERR_ARG, "seed length differs from the live particles");
   const size_t tcap = (size_t)c->L.cap;
-  float* lam_u = reinterpret_cast<float*>(c->sb.keys[1]);
+  float* lam_u = static_cast<float*>(c->sb.keys[1]);
   float* lam_s = reinterpret_cast<float*>(c->sb.vals[1]);
   double* gdev = at<double>(c, c->L.tape_grad);
   if (n > 0)
@@ -833,7 +1023,7 @@ gp_status gp_adjoint(gp_ctx* c, const float* seed, int64_t n, int32_t flags, dou
     if (nn > 0) GP_CUDA(c, cudaMemsetAsync(lam_s, 0, 4 * nn, c->st));
     const StepArgs S = step_args(c, c->tape_t[q]);
     const float t = (float)((double)c->tape_t[q] * c->dt);
-    launch_adj_step(c->P, S, t, at<int4>(c, c->L.tape_rec) + q * tcap,
+    launch_adj_step(step_params(c, c->tape_t[q]), S, t, at<int4>(c, c->L.tape_rec) + q * tcap,
                     at<uint8_t>(c, c->L.tape_state) + q * tcap,
                     at<int32_t>(c, c->L.tape_par) + q * tcap, lam_u, m, lam_s, gdev, c->st);
     if (q > 0)
@@ -987,24 +1177,31 @@ gp_status gp_get_reached(gp_ctx* c, int64_t cap, int32_t* grain, int32_t* site3,
 }
 
 gp_status gp_grain_map(gp_ctx* c, const gp_voxel_grid* g, int32_t* out, int32_t flags) {
+  return gp_run_grain_map(c, 0, g, out, flags);
+}
+
+gp_status gp_run_grain_map(gp_ctx* c, int32_t run, const gp_voxel_grid* g, int32_t* out,
+                           int32_t flags) {
   gp_status s = check_ctx(c);
   if (s) return s;
+  if (run < 0 || run >= c->L.nruns) return fail(c, GP_ERR_ARG, "no such run");
   if (!g || !out) return fail(c, GP_ERR_ARG, "null argument");
   for (int a = 0; a < 3; ++a)
     if (g->n[a] < 0) return fail(c, GP_ERR_ARG, "negative voxel count");
   const int64_t nv = (int64_t)g->n[0] * g->n[1] * g->n[2];
   if (nv == 0) return GP_OK;
   const int nvox[3] = {g->n[0], g->n[1], g->n[2]};
-  launch_link_reached(c->P, c->R, &c->dst->linked, c->sms, c->st);
+  launch_link_reached(c->batch, c->P, c->R, &c->dst->linked, c->sms, c->st);
   c->prof.begin(K_GRAIN_MAP);
   if (flags & GP_DEVICE_PTR) {
-    launch_grain_map(c->P, c->R, g->origin, g->spacing, nvox, out, 0, nv, c->st);
+    launch_grain_map(c->batch, c->P, run, c->R, g->origin, g->spacing, nvox, out, 0, nv, c->st);
   } else {
     int32_t* stg = reinterpret_cast<int32_t*>(c->pos4);
     const int64_t chunk = 4 * c->L.cap;
     for (int64_t v0 = 0; v0 < nv; v0 += chunk) {
       const int64_t m = std::min(chunk, nv - v0);
-      launch_grain_map(c->P, c->R, g->origin, g->spacing, nvox, stg, v0, m, c->st);
+      launch_grain_map(c->batch, c->P, run, c->R, g->origin, g->spacing, nvox, stg, v0, m,
+                       c->st);
       GP_CUDA(c, cudaMemcpyAsync(out + v0, stg, 4 * m, cudaMemcpyDeviceToHost, c->st));
       GP_CUDA(c, cudaStreamSynchronize(c->st));
     }
@@ -1012,6 +1209,49 @@ gp_status gp_grain_map(gp_ctx* c, const gp_voxel_grid* g, int32_t* out, int32_t 
   c->prof.end(K_GRAIN_MAP, (double)nv);
   GP_CUDA(c, cudaGetLastError());
   GP_CUDA(c, cudaStreamSynchronize(c->st));
+  return GP_OK;
+}
+
+gp_status gp_run_counts(gp_ctx* c, int32_t nruns, int64_t* live, int64_t* active) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (nruns != c->L.nruns) return fail(c, GP_ERR_ARG, "nruns differs from the context's runs");
+  std::vector<unsigned long long> h(2 * (size_t)nruns);
+  GP_CUDA(c, cudaMemsetAsync(c->rcount, 0, 16 * (size_t)nruns, c->st));
+  launch_run_counts(c->P, c->rec[c->cur], c->n_live, nruns, c->rcount, c->st);
+  GP_CUDA(c, cudaMemcpyAsync(h.data(), c->rcount, 16 * (size_t)nruns, cudaMemcpyDeviceToHost,
+                             c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  GP_CUDA(c, cudaGetLastError());
+  for (int r = 0; r < nruns; ++r) {
+    if (live) live[r] = (int64_t)h[2 * r];
+    if (active) active[r] = (int64_t)h[2 * r + 1];
+  }
+  return GP_OK;
+}
+
+gp_status gp_grain_table(gp_ctx* c, int64_t cap, float* c3, int32_t* run, int64_t* n_out) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (cap < 0) return fail(c, GP_ERR_ARG, "cap < 0");
+  s = sync_stats(c);
+  if (s) return s;
+  if (n_out) *n_out = c->n_grains;
+  const int64_t m = std::min(cap, c->n_grains);
+  if (m <= 0) return GP_OK;
+  std::vector<float4> G(4 * (size_t)m);
+  GP_CUDA(c, cudaMemcpyAsync(G.data(), c->gtab, sizeof(float4) * G.size(), cudaMemcpyDeviceToHost,
+                             c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  for (int64_t i = 0; i < m; ++i) {
+    const float4 q = G[4 * i];
+    if (c3) {
+      c3[3 * i] = q.x;
+      c3[3 * i + 1] = q.y;
+      c3[3 * i + 2] = q.z;
+    }
+    if (run) std::memcpy(run + i, &q.w, sizeof(int32_t));
+  }
   return GP_OK;
 }
 
@@ -1066,7 +1306,7 @@ bool sa_layout(int64_t n, uint64_t nseg, SaLayout* L) {
   L->vals0 = take(4 * m + 16);
   L->vals1 = take(4 * m + 16);
   L->status = take(4 * radix_status_words(n));
-  L->hist = take(4 * 4 * 256);
+  L->hist = take(4 * kSortMaxPasses * 256);
   L->tickets = take(64);
   L->err = take(64);
   L->flags = take(4 * m);
@@ -1082,11 +1322,11 @@ bool sa_layout(int64_t n, uint64_t nseg, SaLayout* L) {
 Params sa_params(const gp_domain* d, double h, const int nc[3]) {
   Params P{};
   for (int a = 0; a < 3; ++a) {
-    P.lo[a] = (float)d->lo[a];
-    P.hi[a] = (float)d->hi[a];
-    P.nc[a] = nc[a];
+    P.geo.lo[a] = (float)d->lo[a];
+    P.geo.hi[a] = (float)d->hi[a];
+    P.geo.nc[a] = nc[a];
   }
-  P.nsx = (nc[0] + kSegCells - 1) / kSegCells;
+  P.geo.nsx = (nc[0] + kSegCells - 1) / kSegCells;
   P.inv_c = (float)(1.0 / cell_edge(h));
   float hf = (float)h;
   P.rc2 = hf * hf;
@@ -1130,7 +1370,7 @@ static gp_status sa_sort(const float* x3, const uint8_t* state, int64_t n, const
   cudaDeviceGetAttribute(&sb->sms, cudaDevAttrMultiProcessorCount, dev);
   sb->prof = nullptr;
   if (cudaMemsetAsync(sb->err, 0, 64, st) != cudaSuccess) return GP_ERR_CUDA;
-  launch_keys_pos(*P, x3, state, n, sb->keys[0], sb->vals[0], st);
+  launch_keys_pos(*P, x3, state, n, (uint32_t*)sb->keys[0], sb->vals[0], st);
   uint64_t nm1 = *ncells - 1;
   int nbits = 0;
   while (nm1) {
@@ -1138,8 +1378,8 @@ static gp_status sa_sort(const float* x3, const uint8_t* state, int64_t n, const
     nm1 >>= 1;
   }
   if (state) nbits = 32;  // removed points carry key 0xffffffff and sort last
-  *w = radix_sort(*sb, n, nbits, st);
-  return GP_OK;
+  *w = radix_sort<uint32_t>(*sb, n, nbits, st);
+  return *w < 0 ? GP_ERR_ARG : GP_OK;
 }
 
 gp_status gp_hash_build(const float* x3, int64_t n, const gp_domain* domain, double h,
@@ -1163,11 +1403,12 @@ gp_status gp_hash_build(const float* x3, int64_t n, const gp_domain* domain, dou
                         &ncells, &w, &sb);
   if (s) return s;
   char* b = (char*)workspace;
-  if (cudaMemcpyAsync(keys_sorted, sb.keys[w], 4 * n, cudaMemcpyDeviceToDevice, st) ||
+  const uint32_t* skeys = (const uint32_t*)sb.keys[w];
+  if (cudaMemcpyAsync(keys_sorted, skeys, 4 * n, cudaMemcpyDeviceToDevice, st) ||
       cudaMemcpyAsync(ids_sorted, sb.vals[w], 4 * n, cudaMemcpyDeviceToDevice, st) ||
       cudaMemsetAsync(b + L.ncell, 0, 8, st))
     return GP_ERR_CUDA;
-  launch_cells(sb.keys[w], n, (uint32_t)ncells, (uint32_t*)(b + L.flags), (uint32_t*)(b + L.ofs),
+  launch_cells(skeys, n, (uint32_t)ncells, (uint32_t*)(b + L.flags), (uint32_t*)(b + L.ofs),
                (uint32_t*)(b + L.bsum), cell_keys, cell_start,
                (unsigned long long*)(b + L.ncell), st);
   unsigned long long nc = 0;
@@ -1202,14 +1443,15 @@ gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state
                         &w, &sb);
   if (s) return s;
   char* b = (char*)workspace;
-  if (cudaMemsetAsync(b + L.cells, 0, 16 * sa_segments(P.nc), st) ||
+  const uint32_t* skeys = (const uint32_t*)sb.keys[w];
+  if (cudaMemsetAsync(b + L.cells, 0, 16 * sa_segments(P.geo.nc), st) ||
       cudaMemsetAsync(b + L.ncell, 0, 8, st))
     return GP_ERR_CUDA;
   if (freeze && cudaMemsetAsync(freeze, 0, n, st)) return GP_ERR_CUDA;
-  launch_build_sa(P, x3, grain, state, sb.keys[w], sb.vals[w], n, (float4*)(b + L.pos4),
+  launch_build_sa(P, x3, grain, state, skeys, sb.vals[w], n, (float4*)(b + L.pos4),
                   (uint8_t*)(b + L.sstate), (uint4*)(b + L.cells), sb.err, st);
   launch_contact_sa(P, (const float4*)(b + L.pos4), (const uint8_t*)(b + L.sstate), sb.vals[w],
-                    sb.keys[w], (const uint4*)(b + L.cells), n, freeze, pairs,
+                    skeys, (const uint4*)(b + L.cells), n, freeze, pairs,
                     pair_cap, (unsigned long long*)(b + L.ncell), st);
   unsigned long long np = 0;
   uint32_t err = 0;

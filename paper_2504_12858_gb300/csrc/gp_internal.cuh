@@ -90,11 +90,27 @@ __host__ __device__ inline Rec rec_unpack(int4 v) {
 // ---------------------------------------------------------------------------------
 // simulation constants (passed by value to every kernel)
 // ---------------------------------------------------------------------------------
-struct Params {
+// Domain, hash geometry and analytic field of one simulation ("run").  A context
+// holds either one run (Params::geo) or a batch of independent runs (the table
+// Params::runs, indexed by the run id that each grain's table entry carries).
+// The runs of a batch take consecutive ranges of the cell keys, of the cell table
+// and of the reached-site heads.
+struct Geo {
   float lo[3], hi[3];
+  int nc[3];                 // hash cells per axis
+  int nsx;                   // segments of kSegCells cells per x row of the hash grid
+  unsigned long long key0;   // cell key of the run's cell 0
+  unsigned long long seg0;   // first cell-table entry of the run
+  unsigned long long head0;  // first reached-site head of the run
+  float G[3], xref[3];       // analytic field: T = T0 + G . (x - xref) + Tdot t
+  float dT_base;             // T_L - T0 - Tdot t_n
+  float dT_base1;            // T_L - T0 - Tdot t_{n+1} (nucleation)
+};
+
+struct Params {
+  Geo geo;           // the run of a single-run context
+  const Geo* runs;   // batch: one entry per run
   float inv_c;       // (float)(1/edge): cell index scale
-  int nc[3];         // hash cells per axis
-  int nsx;           // segments of kSegCells cells per x row of the hash grid
   float rc2;         // contact radius squared, hf * hf with hf = (float)h
   float dt_over_h;   // (float)(dt / h)
   int nterms;
@@ -102,19 +118,30 @@ struct Params {
   int bint[2];       // b as a small integer exponent (1..8), else -1 (powf)
   float TL;
   int thermal;       // 0 none, 1 analytic, 2 grid
-  float G[3], xref[3];
   const float* grid;
   int gn[3];
   float ginv[3];     // 1 / spacing
-  const float4* gtab;// grain table: 4 float4 per grain (c, rows of h R)
+  const float4* gtab;// grain table: 4 float4 per grain (c with the run id in w, rows of h R)
+  int hshift;        // one reached-site head per 2^hshift cells along each axis
 };
 
-// per-step thermal constants (computed on the host in double, rounded once)
+// per-step constants of the gridded field (computed on the host in double)
 struct StepArgs {
-  float dT_base;     // analytic: T_L - T0 - Tdot t
   float gshift[3];   // grid: origin + frame_vel t
   int parity;        // step & 1: which claimant bits of a site byte are live
 };
+
+// geometry of run `run` (a single-run context has only run 0)
+template <bool BATCH>
+__device__ __forceinline__ const Geo& geo_of(const Params& P, int run) {
+  if constexpr (BATCH) return P.runs[run];
+  else return P.geo;
+}
+
+// pos4.w / grain-table w word: grain id in the low 24 bits, run id in the high 8
+constexpr int kRunShift = 24;
+constexpr int kGrainMask = (1 << kRunShift) - 1;
+constexpr int kMaxRuns = 256;
 
 // ---------------------------------------------------------------------------------
 // geometry
@@ -166,17 +193,18 @@ __device__ __forceinline__ int cell1(float x, float lo, float inv, int n) {
   return min(max(c, 0), n - 1);
 }
 
-__device__ __forceinline__ uint32_t cell_key(const Params& P, float3 p, int& cx, int& cy,
-                                             int& cz) {
-  cx = cell1(p.x, P.lo[0], P.inv_c, P.nc[0]);
-  cy = cell1(p.y, P.lo[1], P.inv_c, P.nc[1]);
-  cz = cell1(p.z, P.lo[2], P.inv_c, P.nc[2]);
-  return (uint32_t)(((uint64_t)cz * P.nc[1] + cy) * P.nc[0] + cx);
+// cell of p in its run's hash grid (clamped) and the run-local linear cell index
+__device__ __forceinline__ uint32_t cell_local(const Geo& g, float inv_c, float3 p, int& cx,
+                                               int& cy, int& cz) {
+  cx = cell1(p.x, g.lo[0], inv_c, g.nc[0]);
+  cy = cell1(p.y, g.lo[1], inv_c, g.nc[1]);
+  cz = cell1(p.z, g.lo[2], inv_c, g.nc[2]);
+  return (uint32_t)(((uint64_t)cz * g.nc[1] + cy) * g.nc[0] + cx);
 }
 
-__device__ __forceinline__ bool inside(const Params& P, float3 p) {
-  return p.x >= P.lo[0] && p.x <= P.hi[0] && p.y >= P.lo[1] && p.y <= P.hi[1] &&
-         p.z >= P.lo[2] && p.z <= P.hi[2];
+__device__ __forceinline__ bool inside(const Geo& g, float3 p) {
+  return p.x >= g.lo[0] && p.x <= g.hi[0] && p.y >= g.lo[1] && p.y <= g.hi[1] &&
+         p.z >= g.lo[2] && p.z <= g.hi[2];
 }
 
 // squared distance with every product and sum rounded separately (no contraction)
@@ -234,12 +262,15 @@ __device__ __forceinline__ float grid_T(const Params& P, const StepArgs& S, floa
   return __fmaf_rn(f[2], e1 - e0, e0);
 }
 
-__device__ __forceinline__ float undercooling(const Params& P, const StepArgs& S, float3 p) {
+// undercooling at p; base = T_L - T0 - Tdot t of the analytic field at the time
+// of the sample (Geo::dT_base or Geo::dT_base1)
+__device__ __forceinline__ float undercooling(const Params& P, const Geo& g, const StepArgs& S,
+                                             float3 p, float base) {
   if (P.thermal == 1) {
-    float g = __fmul_rn(P.G[0], __fsub_rn(p.x, P.xref[0]));
-    g = __fmaf_rn(P.G[1], __fsub_rn(p.y, P.xref[1]), g);
-    g = __fmaf_rn(P.G[2], __fsub_rn(p.z, P.xref[2]), g);
-    return S.dT_base - g;
+    float v = __fmul_rn(g.G[0], __fsub_rn(p.x, g.xref[0]));
+    v = __fmaf_rn(g.G[1], __fsub_rn(p.y, g.xref[1]), v);
+    v = __fmaf_rn(g.G[2], __fsub_rn(p.z, g.xref[2]), v);
+    return base - v;
   }
   if (P.thermal == 2) return P.TL - grid_T(P, S, p);
   return 0.f;
@@ -500,23 +531,28 @@ struct ProfHook {
 };
 
 struct SortBufs {
-  uint32_t* keys[2];
+  void* keys[2];             // uint32 or uint64 keys, per the instantiation of radix_sort
   uint32_t* vals[2];
   uint32_t* status;          // look-back words: max_tiles * 256
-  uint32_t* hist;            // 4 passes * 256
-  uint32_t* ticket;          // 4 counters
+  uint32_t* hist;            // kSortMaxPasses * 256
+  uint32_t* ticket;          // kSortMaxPasses counters
   uint32_t* err;
   int64_t max_n;
   int sms;
   ProfHook* prof;
 };
 
+constexpr int kSortThreads = 256;
+constexpr int kSortMaxPasses = 5;   // keys of up to 40 bits
+template <class K> struct SortTile;
+template <> struct SortTile<uint32_t> { static constexpr int items = 15, tile = 256 * 15; };
+template <> struct SortTile<uint64_t> { static constexpr int items = 10, tile = 256 * 10; };
+
 // radix sort of (keys[0], vals[0]) over the low nbits of the keys; returns the
-// buffer index (0 or 1) holding the sorted result.
+// buffer index (0 or 1) holding the sorted result, or -1 if nbits exceeds the
+// key type or kSortMaxPasses digits.
+template <class K>
 int radix_sort(const SortBufs& B, int64_t n, int nbits, cudaStream_t st);
 size_t radix_status_words(int64_t n);
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 15;
-constexpr int kSortTile = kSortThreads * kSortItems;
 
 }  // namespace gp

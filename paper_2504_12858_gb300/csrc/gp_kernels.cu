@@ -14,6 +14,8 @@
 //   k_nucleate  nucleation activation at t_{n+1}
 // plus seeding, state decode, grain-id voxelisation and the stand-alone
 // hash / contact entry points.
+#include <algorithm>
+
 #include "gp_kernels.cuh"
 
 namespace gp {
@@ -35,30 +37,38 @@ constexpr uint32_t kNoEntry = 0xffffffffu;
 // An entry whose stamp is not the current build's is an empty segment.  A query
 // turns the 3 cells x-1..x+1 of a neighbour row into a candidate range directly
 // from the nibble counts; when a count is saturated it scans the segment's keys.
-__device__ __forceinline__ uint32_t seg_of(const Params& P, uint32_t key, uint32_t& xcell) {
-  const uint32_t row = key / (uint32_t)P.nc[0];
-  xcell = key - row * (uint32_t)P.nc[0];
-  return row * (uint32_t)P.nsx + (xcell >> kSegShift);
+// run-local segment of a run-local cell key (and the cell's x)
+__device__ __forceinline__ uint32_t seg_of(const Geo& g, uint32_t local, uint32_t& xcell) {
+  const uint32_t row = local / (uint32_t)g.nc[0];
+  xcell = local - row * (uint32_t)g.nc[0];
+  return row * (uint32_t)g.nsx + (xcell >> kSegShift);
+}
+
+__device__ __forceinline__ uint32_t ncells_of(const Geo& g) {
+  return (uint32_t)((uint64_t)g.nc[0] * g.nc[1] * g.nc[2]);
 }
 
 // Writes the entry of the segment that starts at sorted index j (if one does).
-__device__ __forceinline__ void seg_build(const Params& P, const uint32_t* __restrict__ skeys,
-                                          int64_t j, int64_t n, uint32_t key,
-                                          uint4* __restrict__ tab, uint32_t stamp,
-                                          uint32_t* err) {
+// The keys of the run are key0 + local; a key outside that range ends the run.
+template <class K>
+__device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ skeys, int64_t j,
+                                          int64_t n, K key, uint4* __restrict__ tab,
+                                          uint32_t stamp, uint32_t* err) {
+  const K k0 = (K)gm.key0;
+  const uint32_t nvalid = ncells_of(gm);
   uint32_t x0;
-  const uint32_t sg = seg_of(P, key, x0);
+  const uint32_t sg = seg_of(gm, (uint32_t)(key - k0), x0);
   if (j > 0) {
+    const K kp = __ldg(skeys + j - 1);
     uint32_t xp;
-    if (seg_of(P, __ldg(skeys + j - 1), xp) == sg) return;
+    if (kp >= k0 && (K)(kp - k0) < (K)nvalid && seg_of(gm, (uint32_t)(kp - k0), xp) == sg) return;
   }
-  const uint32_t nvalid = (uint32_t)((uint64_t)P.nc[0] * P.nc[1] * P.nc[2]);
   unsigned long long nib = 0;
   uint32_t c = 0;
-  uint32_t k = key;
+  K k = key;
   while (true) {
     uint32_t x;
-    seg_of(P, k, x);
+    seg_of(gm, (uint32_t)(k - k0), x);
     const int sh = 4 * (int)(x & (kSegCells - 1));
     if (((nib >> sh) & 15ull) < 15ull) nib += 1ull << sh;
     if (++c == 0xffffu) {
@@ -68,9 +78,10 @@ __device__ __forceinline__ void seg_build(const Params& P, const uint32_t* __res
     if (j + c >= n) break;
     k = __ldg(skeys + j + c);
     uint32_t xk;
-    if (k >= nvalid || seg_of(P, k, xk) != sg) break;
+    if (k < k0 || (K)(k - k0) >= (K)nvalid || seg_of(gm, (uint32_t)(k - k0), xk) != sg) break;
   }
-  tab[sg] = make_uint4((uint32_t)j, (stamp << 16) | c, (uint32_t)nib, (uint32_t)(nib >> 32));
+  tab[gm.seg0 + sg] =
+      make_uint4((uint32_t)j, (stamp << 16) | c, (uint32_t)nib, (uint32_t)(nib >> 32));
 }
 
 // sum of the 4-bit counts of cells 0..p-1 (p <= 16)
@@ -80,32 +91,36 @@ __device__ __forceinline__ uint32_t nib_prefix(unsigned long long nib, int p) {
   return (uint32_t)((b * 0x0101010101010101ull) >> 56);
 }
 
-// Finds the sorted particles i of another grain than g strictly closer than the
-// contact radius to p, among the particles of the 3x3x3 cells around (cx, cy, cz).
+// Finds the sorted particles i of another grain strictly closer than the contact
+// radius to p, among the particles of the 3x3x3 cells around (cx, cy, cz) of run
+// geometry gm.  gw is the pos4.w word of the querying particle (grain and run):
+// particles with the same word belong to the same grain.
 // PAIRS == false: returns at the first one.  PAIRS == true: visits all of them and
 // appends the pairs (idj, ids[i]) with idj < ids[i] to pairs (up to pair_cap,
 // counted in *npairs).  Returns whether any was found.
-template <bool PAIRS>
-__device__ __forceinline__ bool contact_scan(const Params& P, const uint4* __restrict__ tab,
-                                             uint32_t stamp, const uint32_t* __restrict__ skeys,
+template <bool PAIRS, class K>
+__device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
+                                             const uint4* __restrict__ tab, uint32_t stamp,
+                                             const K* __restrict__ skeys,
                                              const float4* __restrict__ pos4, int64_t n,
-                                             float3 p, int g, int cx, int cy, int cz,
+                                             float3 p, int gw, int cx, int cy, int cz,
                                              const uint32_t* __restrict__ ids = nullptr,
                                              uint32_t idj = 0, int32_t* pairs = nullptr,
                                              int64_t pair_cap = 0,
                                              unsigned long long* npairs = nullptr) {
   bool hit = false;
-  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nc[0] - 1);
+  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm.nc[0] - 1);
   const int sa = x0 >> kSegShift, sb = x1 >> kSegShift;
+  const uint4* __restrict__ rtab = tab + gm.seg0;
   for (int dz = -1; dz <= 1; ++dz) {
     const int z = cz + dz;
-    if (z < 0 || z >= P.nc[2]) continue;
+    if (z < 0 || z >= gm.nc[2]) continue;
     for (int dy = -1; dy <= 1; ++dy) {
       const int y = cy + dy;
-      if (y < 0 || y >= P.nc[1]) continue;
-      const uint32_t row = (uint32_t)z * (uint32_t)P.nc[1] + (uint32_t)y;
+      if (y < 0 || y >= gm.nc[1]) continue;
+      const uint32_t row = (uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y;
       for (int sgi = sa; sgi <= sb; ++sgi) {
-        const uint4 e = __ldg(tab + (size_t)row * P.nsx + sgi);
+        const uint4 e = __ldg(rtab + (size_t)row * gm.nsx + sgi);
         if ((e.y >> 16) != stamp) continue;
         const int base = sgi << kSegShift;
         const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
@@ -118,8 +133,8 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const uint4* __res
           end = e.x + nib_prefix(nib, c1 + 1);
         } else {
           // a cell holds 15 or more particles: locate the cells by their keys
-          const uint32_t klo = row * (uint32_t)P.nc[0] + (uint32_t)(base + c0);
-          const uint32_t khi = klo + (uint32_t)(c1 - c0);
+          const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
+          const K khi = klo + (K)(c1 - c0);
           i = e.x;
           end = e.x + (e.y & 0xffffu);
           while (i < end && __ldg(skeys + i) < klo) ++i;
@@ -130,7 +145,7 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const uint4* __res
         if ((int64_t)end > n) end = (uint32_t)n;
         for (; i < end; ++i) {
           const float4 o = __ldg(pos4 + i);
-          if (__float_as_int(o.w) == g) continue;
+          if (__float_as_int(o.w) == gw) continue;
           if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) {
             if (!PAIRS) return true;
             hit = true;
@@ -161,27 +176,38 @@ __device__ __forceinline__ void reached_append(const Reached& R, int g, int sx, 
   R.key[r] = pack_site(g, sx, sy, sz);
 }
 
-// nearest reached site strictly closer than sqrt(rc2); ties to the smaller grain.
-// Returns the grain or -1.  If any_only, returns on the first hit.
-__device__ int nearest_reached(const Params& P, const Reached& R, float3 p, bool any_only) {
+// reached-site head of the brick (2^hshift cells per axis) holding cell (x, y, z)
+__device__ __forceinline__ uint64_t head_index(const Geo& gm, int hs, int x, int y, int z) {
+  const int m = (1 << hs) - 1;
+  const uint64_t nbx = (uint64_t)((gm.nc[0] + m) >> hs), nby = (uint64_t)((gm.nc[1] + m) >> hs);
+  return gm.head0 + ((uint64_t)(z >> hs) * nby + (uint64_t)(y >> hs)) * nbx + (uint64_t)(x >> hs);
+}
+
+// nearest reached site of run gm strictly closer than sqrt(rc2); ties to the
+// smaller grain.  Returns the grain or -1.  If any_only, returns on the first hit.
+// The sites within the contact radius of p lie in the cells c-1..c+1 of p's cell
+// c along each axis (the cell edge exceeds the radius), hence in the bricks
+// holding those cells.
+__device__ int nearest_reached(const Params& P, const Geo& gm, const Reached& R, float3 p,
+                               bool any_only) {
   int c[3];
-  c[0] = __float2int_rd(__fmul_rn(__fsub_rn(p.x, P.lo[0]), P.inv_c));
-  c[1] = __float2int_rd(__fmul_rn(__fsub_rn(p.y, P.lo[1]), P.inv_c));
-  c[2] = __float2int_rd(__fmul_rn(__fsub_rn(p.z, P.lo[2]), P.inv_c));
+  c[0] = __float2int_rd(__fmul_rn(__fsub_rn(p.x, gm.lo[0]), P.inv_c));
+  c[1] = __float2int_rd(__fmul_rn(__fsub_rn(p.y, gm.lo[1]), P.inv_c));
+  c[2] = __float2int_rd(__fmul_rn(__fsub_rn(p.z, gm.lo[2]), P.inv_c));
+  const int hs = P.hshift;
+  int lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = max(c[a] - 1, 0) >> hs;
+    hi[a] = min(c[a] + 1, gm.nc[a] - 1) >> hs;
+  }
   float best = P.rc2;
   int bg = -1;
-  unsigned long long guard = *R.count + 1;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int z = min(max(c[2] + dz, 0), P.nc[2] - 1);
-    if (dz > -1 && z == min(max(c[2] + dz - 1, 0), P.nc[2] - 1)) continue;  // clamped repeat
-    for (int dy = -1; dy <= 1; ++dy) {
-      int y = min(max(c[1] + dy, 0), P.nc[1] - 1);
-      if (dy > -1 && y == min(max(c[1] + dy - 1, 0), P.nc[1] - 1)) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int x = min(max(c[0] + dx, 0), P.nc[0] - 1);
-        if (dx > -1 && x == min(max(c[0] + dx - 1, 0), P.nc[0] - 1)) continue;
-        uint32_t key = (uint32_t)(((uint64_t)z * P.nc[1] + y) * P.nc[0] + x);
-        uint32_t r = R.head[key];
+  const unsigned long long guard = *R.count + 1;
+  for (int bz = lo[2]; bz <= hi[2]; ++bz)
+    for (int by = lo[1]; by <= hi[1]; ++by)
+      for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+        uint32_t r = R.head[head_index(gm, hs, bx << hs, by << hs, bz << hs)];
         unsigned long long steps = 0;
         while (r != kNoEntry && steps++ < guard) {
           int g, sx, sy, sz;
@@ -200,8 +226,6 @@ __device__ int nearest_reached(const Params& P, const Reached& R, float3 p, bool
           r = R.next[r];
         }
       }
-    }
-  }
   return bg;
 }
 
@@ -232,53 +256,73 @@ __device__ __forceinline__ uint32_t bscan256(uint32_t v, uint32_t* s_warp, uint3
   return r;
 }
 
+// run of grain g (the w word of its table entry)
+template <bool BATCH>
+__device__ __forceinline__ int run_of(const float4& gc) {
+  if constexpr (BATCH) return __float_as_int(gc.w);
+  else return 0;
+}
+
+// cell key (key0 of the run + run-local cell) of a position
+template <class K>
+__device__ __forceinline__ K cell_key(const Params& P, const Geo& gm, float3 p) {
+  int cx, cy, cz;
+  return (K)gm.key0 + (K)cell_local(gm, P.inv_c, p, cx, cy, cz);
+}
+
 // ---------------------------------------------------------------------------------
 // k_keys: cell key and identity value of every stored particle
 // ---------------------------------------------------------------------------------
+template <bool BATCH, class K>
 __global__ void __launch_bounds__(256) k_keys(Params P, const int4* __restrict__ rec, int64_t n,
-                                              uint32_t* __restrict__ keys,
-                                              uint32_t* __restrict__ vals) {
+                                              K* __restrict__ keys, uint32_t* __restrict__ vals) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  Rec r = rec_unpack(__ldg(rec + i));
-  float3 p = part_pos(P.gtab, r.grain, r.sx, r.sy, r.sz, r.dir, r.ell);
-  int cx, cy, cz;
-  keys[i] = cell_key(P, p, cx, cy, cz);
+  const Rec r = rec_unpack(__ldg(rec + i));
+  float4 gc, r0, r1, r2;
+  grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+  const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
+  keys[i] = cell_key<K>(P, geo_of<BATCH>(P, run_of<BATCH>(gc)), p);
   vals[i] = (uint32_t)i;
 }
 
 // ---------------------------------------------------------------------------------
-// k_build: sorted store, sorted positions, cell table
+// k_build: sorted store, sorted positions (+ grain and run word), cell table
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_build(Params P, const uint32_t* __restrict__ skeys,
+template <bool BATCH, class K>
+__global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ skeys,
                                                const uint32_t* __restrict__ svals,
                                                const int4* __restrict__ rin,
                                                int4* __restrict__ rout, float4* __restrict__ pos4,
                                                uint4* __restrict__ tab,
-                                               uint32_t stamp, int64_t n, uint32_t ncells,
+                                               uint32_t stamp, int64_t n, K key_end,
                                                uint32_t* err) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const uint32_t id = __ldg(svals + j);
-  const uint32_t key = __ldg(skeys + j);
-  if ((int64_t)id >= n || key >= ncells) {  // only after a failed sort
+  const K key = __ldg(skeys + j);
+  if ((int64_t)id >= n || key >= key_end) {  // only after a failed sort
     atomicOr(err, ERR_TIMEOUT);
     return;
   }
   const int4 rv = __ldg(rin + id);
   rout[j] = rv;
-  Rec r = rec_unpack(rv);
-  float3 p = part_pos(P.gtab, r.grain, r.sx, r.sy, r.sz, r.dir, r.ell);
-  pos4[j] = make_float4(p.x, p.y, p.z, __int_as_float(r.grain));
-  seg_build(P, skeys, j, n, key, tab, stamp, err);
+  const Rec r = rec_unpack(rv);
+  float4 gc, r0, r1, r2;
+  grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+  const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
+  const int run = run_of<BATCH>(gc);
+  pos4[j] = make_float4(p.x, p.y, p.z, __int_as_float(r.grain | (run << kRunShift)));
+  seg_build<K>(geo_of<BATCH>(P, run), skeys, j, n, key, tab, stamp, err);
 }
 
 // ---------------------------------------------------------------------------------
 // k_advance: contact freeze, growth, advance, spawn claims (sorted store, in place)
 // ---------------------------------------------------------------------------------
+template <bool BATCH, class K>
 __global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
-                                                 const uint32_t* __restrict__ skeys,
+                                                 const K* __restrict__ skeys,
                                                  const uint4* __restrict__ tab,
                                                  uint32_t stamp, int64_t n, Claims C,
                                                  int32_t* __restrict__ site_slot, DevStats* st) {
@@ -292,16 +336,18 @@ __global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* 
       active = true;
       const float4 q = __ldg(pos4 + j);
       const float3 p = make_float3(q.x, q.y, q.z);
+      const int gw = __float_as_int(q.w);
+      const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
       g = r.grain;
       int cx, cy, cz;
-      cell_key(P, p, cx, cy, cz);
-      const bool hit = contact_scan<false>(P, tab, stamp, skeys, pos4, n, p, g, cx, cy, cz);
+      cell_local(gm, P.inv_c, p, cx, cy, cz);
+      const bool hit = contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
       if (hit) {
         froze = true;
         r.state = ST_FROZEN;
       } else {
         // thermal sample at (x_n, t_n), growth law, explicit Euler step of ell
-        const float dT = undercooling(P, S, p);
+        const float dT = undercooling(P, gm, S, p, gm.dT_base);
         float dl = __fmul_rn(growth_v(P, dT), P.dt_over_h);
         if (dl > 1.f) {
           dl = 1.f;
@@ -362,6 +408,7 @@ constexpr int kEmitTile = 256 * kEmitItems;
 
 // decides what record j emits: bit 6 = the record itself, bits 0..5 = children in
 // direction k; counts the statistics; appends the reached site of a crossing
+template <bool BATCH>
 __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs& S, const Rec& r,
                                                 bool valid, int32_t sslot, const Claims& C,
                                                 const Reached& R,
@@ -392,9 +439,10 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
   if (r.state != ST_ACTIVE) return 0;
   float4 gc, r0, r1, r2;
   grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+  const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
   if (!crossing) {
     const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
-    if (inside(P, p)) return 1u << 6;
+    if (inside(gm, p)) return 1u << 6;
     ++n_clip;
     return 0;
   }
@@ -424,20 +472,21 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
       continue;
     }
     if (k != r.dir) ++n_spawn;
-    if (inside(P, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
+    if (inside(gm, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
     else ++n_clip;
   }
   return mask;
 }
 
+template <bool BATCH, class K>
 __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32_t mask,
                                            unsigned long long o, int4* __restrict__ rout,
-                                           uint32_t* __restrict__ keys,
+                                           K* __restrict__ keys,
                                            uint32_t* __restrict__ vals, int64_t cap,
                                            int32_t* __restrict__ parent, int64_t j) {
   float4 gc, r0, r1, r2;
   grain_load(P.gtab, r.grain, gc, r0, r1, r2);
-  int cx, cy, cz;
+  const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
   if (mask & (1u << 6)) {
     if (o < (unsigned long long)cap) {
       Rec w = r;
@@ -445,7 +494,7 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
       rout[o] = rec_pack(w);
       const float3 p =
           add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
-      keys[o] = cell_key(P, p, cx, cy, cz);
+      keys[o] = cell_key<K>(P, gm, p);
       vals[o] = (uint32_t)o;
       if (parent) parent[o] = (int32_t)j;
     }
@@ -467,7 +516,7 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
       w.cross = 0;
       w.ell = r.ell;
       rout[o] = rec_pack(w);
-      keys[o] = cell_key(P, add_dir(sp, r0, r1, r2, k, r.ell), cx, cy, cz);
+      keys[o] = cell_key<K>(P, gm, add_dir(sp, r0, r1, r2, k, r.ell));
       vals[o] = (uint32_t)o;
       if (parent) parent[o] = (int32_t)j;
     }
@@ -475,10 +524,11 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
   }
 }
 
+template <bool BATCH, class K>
 __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* __restrict__ rs,
                                               const int32_t* __restrict__ site_slot, int64_t n,
                                               int4* __restrict__ rout,
-                                              uint32_t* __restrict__ keys,
+                                              K* __restrict__ keys,
                                               uint32_t* __restrict__ vals, int64_t cap,
                                               Claims C, Reached R, int32_t* __restrict__ parent,
                                               DevStats* st) {
@@ -495,7 +545,7 @@ __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* 
     const Rec r = valid ? rec_unpack(__ldg(rs + j)) : Rec{};
     const int32_t sslot = (valid && r.cross && r.state == ST_ACTIVE) ? __ldg(site_slot + j) : -1;
     const uint32_t m =
-        emit_decide(P, S, r, valid, sslot, C, R, n_frozen, n_spawn, n_lost, n_clip);
+        emit_decide<BATCH>(P, S, r, valid, sslot, C, R, n_frozen, n_spawn, n_lost, n_clip);
     masks |= m << (7 * it);
   }
   uint32_t cnt = 0;
@@ -512,7 +562,7 @@ __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* 
     if (!m) continue;
     const int64_t j = base + it * 256 + tid;
     const Rec r = rec_unpack(__ldg(rs + j));
-    emit_write(P, r, m, o, rout, keys, vals, cap, parent, j);
+    emit_write<BATCH, K>(P, r, m, o, rout, keys, vals, cap, parent, j);
     o += __popc(m);
   }
   warp_add(&st->n_frozen, n_frozen);
@@ -525,7 +575,8 @@ __global__ void k_emit_check(DevStats* st, int64_t cap) {
   if (st->n_out > (unsigned long long)cap) atomicOr(&st->err, ERR_CAPACITY);
 }
 
-// links the reached sites [linked, count) into the per-cell lists; grid-stride
+// links the reached sites [linked, count) into the per-brick lists; grid-stride
+template <bool BATCH>
 __global__ void k_link_reached(Params P, Reached R, const unsigned long long* linked) {
   const unsigned long long r0 = *linked;
   const unsigned long long r1 = min(*R.count, R.cap);
@@ -535,9 +586,10 @@ __global__ void k_link_reached(Params P, Reached R, const unsigned long long* li
     unpack_site(R.key[r], g, sx, sy, sz);
     float4 gc, q0, q1, q2;
     grain_load(P.gtab, g, gc, q0, q1, q2);
+    const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
     int cx, cy, cz;
-    const uint32_t key = cell_key(P, site_pos_g(gc, q0, q1, q2, sx, sy, sz), cx, cy, cz);
-    R.next[r] = atomicExch(R.head + key, (uint32_t)r);
+    cell_local(gm, P.inv_c, site_pos_g(gc, q0, q1, q2, sx, sy, sz), cx, cy, cz);
+    R.next[r] = atomicExch(R.head + head_index(gm, P.hshift, cx, cy, cz), (uint32_t)r);
   }
 }
 
@@ -561,7 +613,9 @@ __global__ void __launch_bounds__(256) k_nucleate(Params P, StepArgs S1, const f
     if (nstate[j] != 0) continue;
     const float4 q = npos[j];
     const float3 p = make_float3(q.x, q.y, q.z);
-    if (undercooling(P, S1, p) >= q.w && nearest_reached(P, R, p, true) < 0) nstate[j] = 1;
+    if (undercooling(P, P.geo, S1, p, P.geo.dT_base1) >= q.w &&
+        nearest_reached(P, P.geo, R, p, true) < 0)
+      nstate[j] = 1;
   }
   __threadfence_block();
   __syncthreads();
@@ -597,8 +651,7 @@ __global__ void __launch_bounds__(256) k_nucleate(Params P, StepArgs S1, const f
         const float3 c = make_float3(cq.x, cq.y, cq.z);
         // nucleus site reached
         reached_append(R, (int)g, 0, 0, 0);
-        int cx, cy, cz;
-        const uint32_t key = cell_key(P, c, cx, cy, cz);
+        const uint32_t key = cell_key<uint32_t>(P, P.geo, c);
         for (int k = 0; k < 6; ++k) {
           const unsigned long long o = nout + 6ull * rank + k;
           if (o < (unsigned long long)cap) {
@@ -629,6 +682,113 @@ __global__ void __launch_bounds__(256) k_nucleate(Params P, StepArgs S1, const f
     unsigned long long nl = nout + 6ull * add;
     st->n_live = nl > (unsigned long long)cap ? (unsigned long long)cap : nl;
   }
+}
+
+// ---------------------------------------------------------------------------------
+// batched nucleation.  Every registered site j of any run has a grain id reserved
+// at registration (nmeta[j] = {grain, run}; its table entry is already written).
+// k_nuc_test marks the sites that activate at t_{n+1} against the state after the
+// emit; k_nuc_activate then activates them (so no activation of this step can
+// suppress another one of the same step, as in the single-run kernel).
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_nuc_test(Params P, StepArgs S1,
+                                                  const float4* __restrict__ npos,
+                                                  const int2* __restrict__ nmeta, int* nstate,
+                                                  int m, Reached R) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    if (nstate[j] != 0) continue;
+    const float4 q = npos[j];
+    const float3 p = make_float3(q.x, q.y, q.z);
+    const Geo& gm = geo_of<true>(P, nmeta[j].y);
+    if (undercooling(P, gm, S1, p, gm.dT_base1) >= q.w && nearest_reached(P, gm, R, p, true) < 0)
+      nstate[j] = 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nuc_activate(Params P, const float4* __restrict__ npos,
+                                                      const int2* __restrict__ nmeta,
+                                                      int* nstate, int m, int4* rout,
+                                                      uint64_t* keys, uint32_t* vals,
+                                                      int64_t cap, Claims C, Reached R,
+                                                      DevStats* st) {
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count: every lane reaches the warp-wide claims
+  for (int j0 = blockIdx.x * blockDim.x; j0 < m; j0 += gridDim.x * blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    const bool cand = j < m && nstate[j] == 1;
+    if (!__any_sync(0xffffffffu, cand)) continue;
+    const int2 meta = cand ? nmeta[j] : make_int2(0, 0);
+    {
+      BlockCache bc;
+      for (int k = -1; k < 6; ++k) {
+        int tx = 0, ty = 0, tz = 0;
+        if (k >= 0) step_site(tx, ty, tz, k);
+        int sh = 0;
+        uint32_t* w = warp_claim_word(C, cand, meta.x, tx, ty, tz, true, sh, bc);
+        if (w) atomicOr(w, 0x80u << sh);
+      }
+    }
+    const uint32_t want = __ballot_sync(0xffffffffu, cand);
+    unsigned long long ob = 0;
+    if (lane == __ffs(want) - 1) ob = atomicAdd(&st->n_out, 6ull * __popc(want));
+    ob = __shfl_sync(0xffffffffu, ob, __ffs(want) - 1);
+    if (cand) {
+      nstate[j] = 2;
+      reached_append(R, meta.x, 0, 0, 0);
+      const float4 q = npos[j];
+      const uint64_t key = cell_key<uint64_t>(P, geo_of<true>(P, meta.y), make_float3(q.x, q.y, q.z));
+      const unsigned long long o0 = ob + 6ull * __popc(want & ((1u << lane) - 1u));
+      for (int k = 0; k < 6; ++k) {
+        const unsigned long long o = o0 + k;
+        if (o < (unsigned long long)cap) {
+          Rec rr;
+          rr.grain = meta.x;
+          rr.sx = rr.sy = rr.sz = 0;
+          rr.dir = k;
+          rr.state = ST_ACTIVE;
+          rr.cross = 0;
+          rr.ell = 0.f;
+          rout[o] = rec_pack(rr);
+          keys[o] = key;
+          vals[o] = (uint32_t)o;
+        } else {
+          atomicOr(&st->err, ERR_CAPACITY);
+        }
+      }
+    }
+    if (lane == 0) atomicAdd(&st->nucleated, (unsigned long long)__popc(want));
+  }
+}
+
+// per-run step constants of a batch: T_L - T0 - Tdot t at t_n and t_{n+1}, every
+// product and difference rounded once (the host computes a single run's the same way)
+__global__ void k_run_step(Geo* runs, const double2* th, int nruns, long long n, double dt) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nruns) return;
+  const double2 q = th[r];
+  const double t0 = __dmul_rn((double)n, dt), t1 = __dmul_rn((double)(n + 1), dt);
+  runs[r].dT_base = __double2float_rn(__dsub_rn(q.x, __dmul_rn(q.y, t0)));
+  runs[r].dT_base1 = __double2float_rn(__dsub_rn(q.x, __dmul_rn(q.y, t1)));
+}
+
+// live and ACTIVE particles of every run (counts: 2 per run)
+__global__ void __launch_bounds__(256) k_run_counts(Params P, const int4* __restrict__ rec,
+                                                    int64_t n, int nruns,
+                                                    unsigned long long* counts) {
+  __shared__ unsigned int s_c[2 * kMaxRuns];
+  for (int i = threadIdx.x; i < 2 * nruns; i += blockDim.x) s_c[i] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Rec r = rec_unpack(__ldg(rec + i));
+    const int run = __float_as_int(__ldg(P.gtab + 4 * (size_t)r.grain).w);
+    if (run < 0 || run >= nruns) continue;
+    atomicAdd(&s_c[2 * run], 1u);
+    if (r.state == ST_ACTIVE) atomicAdd(&s_c[2 * run + 1], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * nruns; i += blockDim.x)
+    if (s_c[i]) atomicAdd(counts + i, (unsigned long long)s_c[i]);
 }
 
 __global__ void k_finalize(DevStats* st, int64_t cap) {
@@ -677,7 +837,7 @@ __global__ void k_seed_shell(Params P, const int32_t* __restrict__ grains, int64
   int s[3] = {ts[0], ts[1], ts[2]};
   s[a] -= sg;
   const int dir = 2 * a + (sg > 0 ? 0 : 1);
-  if (ok) ok = inside(P, part_pos(P.gtab, g, s[0], s[1], s[2], dir, ell0));
+  if (ok) ok = inside(P.geo, part_pos(P.gtab, g, s[0], s[1], s[2], dir, ell0));
   if (ok) {
     unsigned long long o = atomicAdd(counter, 1ull);
     if (o >= (unsigned long long)cap) {
@@ -730,9 +890,10 @@ __global__ void k_positions(Params P, const int4* __restrict__ rec, int64_t n,
   x3[3 * i + 2] = p.z;
 }
 
-__global__ void k_grain_map(Params P, Reached R, double ox, double oy, double oz, double sx,
-                            double sy, double sz, int nx, int ny, int nz, int32_t* out,
-                            int64_t v0, int64_t nv) {
+template <bool BATCH>
+__global__ void k_grain_map(Params P, int run, Reached R, double ox, double oy, double oz,
+                            double sx, double sy, double sz, int nx, int ny, int nz,
+                            int32_t* out, int64_t v0, int64_t nv) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv) return;
   const int64_t v = v0 + i;
@@ -741,7 +902,7 @@ __global__ void k_grain_map(Params P, Reached R, double ox, double oy, double oz
   const int iz = (int)(v / ((int64_t)nx * ny));
   float3 p = make_float3((float)(ox + (ix + 0.5) * sx), (float)(oy + (iy + 0.5) * sy),
                          (float)(oz + (iz + 0.5) * sz));
-  out[i] = nearest_reached(P, R, p, false);
+  out[i] = nearest_reached(P, geo_of<BATCH>(P, run), R, p, false);
 }
 
 // ---------------------------------------------------------------------------------
@@ -753,7 +914,7 @@ __global__ void k_keys_pos(Params P, const float* __restrict__ x3, const uint8_t
   if (i >= n) return;
   float3 p = make_float3(x3[3 * i], x3[3 * i + 1], x3[3 * i + 2]);
   int cx, cy, cz;
-  uint32_t k = cell_key(P, p, cx, cy, cz);
+  uint32_t k = cell_local(P.geo, P.inv_c, p, cx, cy, cz);
   if (state && state[i] == ST_REMOVED) k = 0xffffffffu;
   keys[i] = k;
   vals[i] = (uint32_t)i;
@@ -823,11 +984,11 @@ __global__ void k_contact_sa(Params P, const float4* __restrict__ pos4,
   const int g = __float_as_int(q.w);
   const uint32_t idj = ids[j];
   int cx, cy, cz;
-  cell_key(P, p, cx, cy, cz);
+  cell_local(P.geo, P.inv_c, p, cx, cy, cz);
   const bool hit =
-      pairs ? contact_scan<true>(P, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz, ids, idj, pairs,
-                                 pair_cap, npairs)
-            : contact_scan<false>(P, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz);
+      pairs ? contact_scan<true, uint32_t>(P, P.geo, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz,
+                                           ids, idj, pairs, pair_cap, npairs)
+            : contact_scan<false, uint32_t>(P, P.geo, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz);
   if (freeze) freeze[idj] = (hit && stj == ST_ACTIVE) ? 1 : 0;
 }
 
@@ -845,8 +1006,8 @@ __global__ void k_build_sa(Params P, const float* __restrict__ x3, const int32_t
   pos4[j] = make_float4(x3[3 * id], x3[3 * id + 1], x3[3 * id + 2], __int_as_float(grain[id]));
   sstate[j] = state[id];
   const uint32_t key = skeys[j];
-  if (key >= (uint32_t)((uint64_t)P.nc[0] * P.nc[1] * P.nc[2])) return;  // removed points
-  seg_build(P, skeys, j, n, key, tab, 1u, err);
+  if (key >= ncells_of(P.geo)) return;  // removed points
+  seg_build<uint32_t>(P.geo, skeys, j, n, key, tab, 1u, err);
 }
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -856,46 +1017,76 @@ inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) /
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
-void launch_keys(const Params& P, const int4* rec, int64_t n, uint32_t* keys, uint32_t* vals,
-                 cudaStream_t st) {
-  if (n > 0) k_keys<<<blocks(n), 256, 0, st>>>(P, rec, n, keys, vals);
+// A batch context (batch == true) sorts uint64 keys, a single-run context uint32.
+void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* keys,
+                 uint32_t* vals, cudaStream_t st) {
+  if (n <= 0) return;
+  if (batch)
+    k_keys<true, uint64_t><<<blocks(n), 256, 0, st>>>(P, rec, n, (uint64_t*)keys, vals);
+  else
+    k_keys<false, uint32_t><<<blocks(n), 256, 0, st>>>(P, rec, n, (uint32_t*)keys, vals);
 }
 
-void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals, const int4* rin,
-                  int4* rout, float4* pos4, uint4* tab, uint32_t stamp, int64_t n,
-                  uint32_t* err, cudaStream_t st) {
-  const uint32_t ncells = (uint32_t)((uint64_t)P.nc[0] * P.nc[1] * P.nc[2]);
-  if (n > 0)
-    k_build<<<blocks(n), 256, 0, st>>>(P, skeys, svals, rin, rout, pos4, tab, stamp, n, ncells,
-                                       err);
+void launch_build(bool batch, const Params& P, const void* skeys, const uint32_t* svals,
+                  const int4* rin, int4* rout, float4* pos4, uint4* tab, uint32_t stamp,
+                  int64_t n, uint64_t key_end, uint32_t* err, cudaStream_t st) {
+  if (n <= 0) return;
+  if (batch)
+    k_build<true, uint64_t><<<blocks(n), 256, 0, st>>>(P, (const uint64_t*)skeys, svals, rin,
+                                                       rout, pos4, tab, stamp, n, key_end, err);
+  else
+    k_build<false, uint32_t><<<blocks(n), 256, 0, st>>>(P, (const uint32_t*)skeys, svals, rin,
+                                                        rout, pos4, tab, stamp, n,
+                                                        (uint32_t)key_end, err);
 }
 
-void launch_advance(const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
-                    const uint32_t* skeys, const uint4* tab, uint32_t stamp,
-                    int64_t n, const Claims& C, int32_t* site_slot, DevStats* dst,
-                    cudaStream_t st) {
-  if (n > 0)
-    k_advance<<<blocks(n), 256, 0, st>>>(P, S, rs, pos4, skeys, tab, stamp, n, C, site_slot,
-                                         dst);
+void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
+                    const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
+                    const Claims& C, int32_t* site_slot, DevStats* dst, cudaStream_t st) {
+  if (n <= 0) return;
+  if (batch)
+    k_advance<true, uint64_t><<<blocks(n), 256, 0, st>>>(
+        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, C, site_slot, dst);
+  else
+    k_advance<false, uint32_t><<<blocks(n), 256, 0, st>>>(
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, C, site_slot, dst);
 }
 
 int64_t emit_tiles(int64_t n) { return (n + kEmitTile - 1) / kEmitTile; }
 
-void launch_link_reached(const Params& P, const Reached& R, unsigned long long* linked, int sms,
-                         cudaStream_t st) {
-  k_link_reached<<<sms * 8, 256, 0, st>>>(P, R, linked);
+void launch_link_reached(bool batch, const Params& P, const Reached& R,
+                         unsigned long long* linked, int sms, cudaStream_t st) {
+  if (batch) k_link_reached<true><<<sms * 8, 256, 0, st>>>(P, R, linked);
+  else k_link_reached<false><<<sms * 8, 256, 0, st>>>(P, R, linked);
   k_link_done<<<1, 1, 0, st>>>(R, linked);
 }
 
-void launch_emit(const Params& P, const StepArgs& S, const int4* rs, const int32_t* site_slot,
-                 int64_t n, int4* rout, uint32_t* keys, uint32_t* vals, int64_t cap,
-                 const Claims& C, const Reached& R, int32_t* parent, DevStats* dst,
+void launch_emit(bool batch, const Params& P, const StepArgs& S, const int4* rs,
+                 const int32_t* site_slot, int64_t n, int4* rout, void* keys, uint32_t* vals,
+                 int64_t cap, const Claims& C, const Reached& R, int32_t* parent, DevStats* dst,
                  cudaStream_t st) {
   const int64_t nt = emit_tiles(n);
   if (nt == 0) return;
-  k_emit<<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout, keys, vals, cap, C, R,
-                                       parent, dst);
+  if (batch)
+    k_emit<true, uint64_t><<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout,
+                                                         (uint64_t*)keys, vals, cap, C, R,
+                                                         parent, dst);
+  else
+    k_emit<false, uint32_t><<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout,
+                                                          (uint32_t*)keys, vals, cap, C, R,
+                                                          parent, dst);
   k_emit_check<<<1, 1, 0, st>>>(dst, cap);
+}
+
+void launch_nucleate_batch(const Params& P, const StepArgs& S1, const float4* npos,
+                           const int2* nmeta, int* nstate, int m, int4* rout, uint64_t* keys,
+                           uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
+                           DevStats* dst, int sms, cudaStream_t st) {
+  if (m <= 0) return;
+  const unsigned nb = (unsigned)std::min<int64_t>(blocks(m), (int64_t)sms * 8);
+  k_nuc_test<<<nb, 256, 0, st>>>(P, S1, npos, nmeta, nstate, m, R);
+  k_nuc_activate<<<nb, 256, 0, st>>>(P, npos, nmeta, nstate, m, rout, keys, vals, cap, C, R,
+                                     dst);
 }
 
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
@@ -904,6 +1095,18 @@ void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, co
                      cudaStream_t st) {
   k_nucleate<<<1, 256, 0, st>>>(P, S1, npos, ngrain, nstate, m, gtab, max_grains, rout, keys,
                                 vals, cap, C, R, dst);
+}
+
+void launch_run_step(Geo* runs, const double2* th, int nruns, int64_t n, double dt,
+                     cudaStream_t st) {
+  k_run_step<<<(nruns + 255) / 256, 256, 0, st>>>(runs, th, nruns, (long long)n, dt);
+}
+
+void launch_run_counts(const Params& P, const int4* rec, int64_t n, int nruns,
+                       unsigned long long* counts, cudaStream_t st) {
+  if (n <= 0) return;
+  const unsigned nb = (unsigned)std::min<int64_t>(blocks(n), 152 * 8);
+  k_run_counts<<<nb, 256, 0, st>>>(P, rec, n, nruns, counts);
 }
 
 void launch_finalize(DevStats* dst, int64_t cap, cudaStream_t st) {
@@ -939,11 +1142,16 @@ void launch_positions(const Params& P, const int4* rec, int64_t n, float* x3, cu
   if (n > 0) k_positions<<<blocks(n), 256, 0, st>>>(P, rec, n, x3);
 }
 
-void launch_grain_map(const Params& P, const Reached& R, const double o[3], const double s[3],
-                      const int nvox[3], int32_t* out, int64_t v0, int64_t nv, cudaStream_t st) {
-  if (nv > 0)
-    k_grain_map<<<blocks(nv), 256, 0, st>>>(P, R, o[0], o[1], o[2], s[0], s[1], s[2], nvox[0],
-                                            nvox[1], nvox[2], out, v0, nv);
+void launch_grain_map(bool batch, const Params& P, int run, const Reached& R, const double o[3],
+                      const double s[3], const int nvox[3], int32_t* out, int64_t v0, int64_t nv,
+                      cudaStream_t st) {
+  if (nv <= 0) return;
+  if (batch)
+    k_grain_map<true><<<blocks(nv), 256, 0, st>>>(P, run, R, o[0], o[1], o[2], s[0], s[1], s[2],
+                                                  nvox[0], nvox[1], nvox[2], out, v0, nv);
+  else
+    k_grain_map<false><<<blocks(nv), 256, 0, st>>>(P, 0, R, o[0], o[1], o[2], s[0], s[1], s[2],
+                                                   nvox[0], nvox[1], nvox[2], out, v0, nv);
 }
 
 void launch_keys_pos(const Params& P, const float* x3, const uint8_t* state, int64_t n,

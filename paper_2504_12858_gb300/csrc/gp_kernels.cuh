@@ -5,22 +5,27 @@
 
 namespace gp {
 
-void launch_keys(const Params& P, const int4* rec, int64_t n, uint32_t* keys, uint32_t* vals,
-                 cudaStream_t st);
-void launch_build(const Params& P, const uint32_t* skeys, const uint32_t* svals, const int4* rin,
-                  int4* rout, float4* pos4, uint4* tab, uint32_t stamp, int64_t n,
-                  uint32_t* err, cudaStream_t st);
-void launch_advance(const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
-                    const uint32_t* skeys, const uint4* tab, uint32_t stamp,
-                    int64_t n, const Claims& C, int32_t* site_slot, DevStats* dst,
-                    cudaStream_t st);
+// batch == true: a context of several runs (uint64 cell keys); false: one run
+// (uint32 cell keys)
+void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* keys,
+                 uint32_t* vals, cudaStream_t st);
+void launch_build(bool batch, const Params& P, const void* skeys, const uint32_t* svals,
+                  const int4* rin, int4* rout, float4* pos4, uint4* tab, uint32_t stamp,
+                  int64_t n, uint64_t key_end, uint32_t* err, cudaStream_t st);
+void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
+                    const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
+                    const Claims& C, int32_t* site_slot, DevStats* dst, cudaStream_t st);
 int64_t emit_tiles(int64_t n);
-void launch_link_reached(const Params& P, const Reached& R, unsigned long long* linked, int sms,
-                         cudaStream_t st);
-void launch_emit(const Params& P, const StepArgs& S, const int4* rs, const int32_t* site_slot,
-                 int64_t n, int4* rout, uint32_t* keys, uint32_t* vals, int64_t cap,
-                 const Claims& C, const Reached& R, int32_t* parent, DevStats* dst,
+void launch_link_reached(bool batch, const Params& P, const Reached& R,
+                         unsigned long long* linked, int sms, cudaStream_t st);
+void launch_emit(bool batch, const Params& P, const StepArgs& S, const int4* rs,
+                 const int32_t* site_slot, int64_t n, int4* rout, void* keys, uint32_t* vals,
+                 int64_t cap, const Claims& C, const Reached& R, int32_t* parent, DevStats* dst,
                  cudaStream_t st);
+void launch_nucleate_batch(const Params& P, const StepArgs& S1, const float4* npos,
+                           const int2* nmeta, int* nstate, int m, int4* rout, uint64_t* keys,
+                           uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
+                           DevStats* dst, int sms, cudaStream_t st);
 // adjoint tape and reverse sweep (gp_adjoint.cu)
 void launch_tape_state(const int4* rs, int64_t n, uint8_t* out, cudaStream_t st);
 void launch_adj_step(const Params& P, const StepArgs& S, float t, const int4* rec,
@@ -33,6 +38,10 @@ void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, co
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,
                      cudaStream_t st);
 void launch_finalize(DevStats* dst, int64_t cap, cudaStream_t st);
+void launch_run_step(Geo* runs, const double2* th, int nruns, int64_t n, double dt,
+                     cudaStream_t st);
+void launch_run_counts(const Params& P, const int4* rec, int64_t n, int nruns,
+                       unsigned long long* counts, cudaStream_t st);
 void launch_append(const int4* src, int64_t m, int4* rout, int64_t base, cudaStream_t st);
 void launch_mark_sites(const Params& P, const int4* sites, int64_t m, int reached, int claimed,
                        const Claims& C, const Reached& R, cudaStream_t st);
@@ -44,8 +53,9 @@ void launch_seed_shell_sites(const Params& P, const int32_t* grains, int64_t ng,
                              const short4* soff, int64_t ns, const Claims& C, const Reached& R,
                              cudaStream_t st);
 void launch_positions(const Params& P, const int4* rec, int64_t n, float* x3, cudaStream_t st);
-void launch_grain_map(const Params& P, const Reached& R, const double o[3], const double s[3],
-                      const int nvox[3], int32_t* out, int64_t v0, int64_t nv, cudaStream_t st);
+void launch_grain_map(bool batch, const Params& P, int run, const Reached& R, const double o[3],
+                      const double s[3], const int nvox[3], int32_t* out, int64_t v0, int64_t nv,
+                      cudaStream_t st);
 void launch_keys_pos(const Params& P, const float* x3, const uint8_t* state, int64_t n,
                      uint32_t* keys, uint32_t* vals, cudaStream_t st);
 void launch_cells(const uint32_t* skeys, int64_t n, uint32_t nvalid_key, uint32_t* flags,

@@ -1,4 +1,5 @@
-// Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8-bit digits.
+// Stable LSD radix sort of (key, uint32 value) pairs, 8-bit digits; keys are
+// uint32 (one run) or uint64 (a batch of runs, whose cell keys exceed 32 bits).
 //
 // One histogram kernel reads the keys once and counts every digit of every
 // pass.  Each pass is then a single kernel ("onesweep", after Adinets & Merrill,
@@ -20,32 +21,35 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
-__global__ void __launch_bounds__(256) k_hist(const uint32_t* __restrict__ keys, int64_t n,
-                                              int npass, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[4 * 256];
-  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) sh[i] = 0;
+template <class K>
+__global__ void __launch_bounds__(256) k_hist(const K* __restrict__ keys, int64_t n, int npass,
+                                              uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[kSortMaxPasses * 256];
+  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n4 = n >> 2;
-  const uint4* k4 = reinterpret_cast<const uint4*>(keys);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-    uint4 v = __ldg(k4 + i);
-    uint32_t kk[4] = {v.x, v.y, v.z, v.w};
+  constexpr int V = 16 / sizeof(K);  // keys per 16-byte load
+  const int64_t nv = n / V;
+  const uint4* kv = reinterpret_cast<const uint4*>(keys);
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const uint4 v = __ldg(kv + i);
+    K kk[V];
+    memcpy(kk, &v, 16);
     const uint32_t m = __activemask();
-    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < V; ++q)
       for (int p = 0; p < npass; ++p) {
         // nearly sorted keys share digits across a warp: one shared atomic per
         // distinct digit instead of one per lane
-        const uint32_t d = (kk[q] >> (8 * p)) & 255u;
+        const uint32_t d = (uint32_t)(kk[q] >> (8 * p)) & 255u;
         const uint32_t peers = __match_any_sync(m, d);
         if (lane == __ffs(peers) - 1) atomicAdd(&sh[p * 256 + d], (uint32_t)__popc(peers));
       }
   }
-  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    uint32_t k = keys[i];
-    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
+  for (int64_t i = nv * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const K k = keys[i];
+    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p * 256 + ((uint32_t)(k >> (8 * p)) & 255u)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npass * 256; i += blockDim.x)
@@ -79,14 +83,17 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* s_
   return r;
 }
 
+template <class K>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
-    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
     uint32_t* status, uint32_t* ticket, uint32_t* err) {
   constexpr int W = kSortThreads / 32;
+  constexpr int kItems = SortTile<K>::items;
+  constexpr int kTile = SortTile<K>::tile;
   __shared__ uint32_t s_whist[W][256];
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ K s_keys[kTile];
+  __shared__ uint32_t s_vals[kTile];
   __shared__ uint32_t s_start[256];  // tile-local start of each digit
   __shared__ uint32_t s_gofs[256];   // global position of tile-local index 0 of each digit
   __shared__ uint32_t s_tmp[8];
@@ -97,22 +104,23 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
   for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t base = (int64_t)tile * kSortTile;
+  const int64_t base = (int64_t)tile * kTile;
 
   // only keys and ranks live in registers (values are read at the scatter, digits
   // recomputed), which keeps the kernel at four CTAs per SM
-  uint32_t k[kSortItems], rk[kSortItems];
-  const int64_t wbase = base + (int64_t)warp * kSortItems * 32;
+  K k[kItems];
+  uint32_t rk[kItems];
+  const int64_t wbase = base + (int64_t)warp * kItems * 32;
   const int64_t nvalid = n - wbase;  // items of this warp's run that exist
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < kItems; ++r) {
     int64_t idx = wbase + r * 32 + lane;
-    k[r] = idx < n ? kin[idx] : 0xffffffffu;
+    k[r] = idx < n ? kin[idx] : ~K(0);
   }
   const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
-    const int d = (r * 32 + lane) < nvalid ? (int)((k[r] >> shift) & 255u) : 256;
+  for (int r = 0; r < kItems; ++r) {
+    const int d = (r * 32 + lane) < nvalid ? (int)((uint32_t)(k[r] >> shift) & 255u) : 256;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = 0;
     if (d < 256) before = s_whist[warp][d];
@@ -167,10 +175,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
   __syncthreads();
 
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < kItems; ++r) {
     const int64_t idx = wbase + r * 32 + lane;
     if (idx < n) {
-      const uint32_t d = (k[r] >> shift) & 255u;
+      const uint32_t d = (uint32_t)(k[r] >> shift) & 255u;
       const uint32_t lp = s_start[d] + s_whist[warp][d] + rk[r];
       s_keys[lp] = k[r];
       s_vals[lp] = __ldg(vin + idx);
@@ -178,10 +186,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
   }
   __syncthreads();
   const int64_t rem = n - base;
-  const int tn = rem < kSortTile ? (int)rem : kSortTile;
+  const int tn = rem < kTile ? (int)rem : kTile;
   for (int i = tid; i < tn; i += kSortThreads) {
-    uint32_t key = s_keys[i];
-    uint32_t g = s_gofs[(key >> shift) & 255u] + (uint32_t)i;
+    const K key = s_keys[i];
+    uint32_t g = s_gofs[(uint32_t)(key >> shift) & 255u] + (uint32_t)i;
     if ((int64_t)g < n) {
       kout[g] = key;
       vout[g] = s_vals[i];
@@ -194,33 +202,41 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
 }  // namespace
 
 size_t radix_status_words(int64_t n) {
-  int64_t tiles = (n + kSortTile - 1) / kSortTile;
+  // the 64-bit tile is the smaller one
+  int64_t tiles = (n + SortTile<uint64_t>::tile - 1) / SortTile<uint64_t>::tile;
   return (size_t)(tiles < 1 ? 1 : tiles) * 256;
 }
 
+template <class K>
 int radix_sort(const SortBufs& B, int64_t n, int nbits, cudaStream_t st) {
   if (n <= 1 || nbits <= 0) return 0;
   const int npass = (nbits + 7) / 8;
-  const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+  if (npass > kSortMaxPasses || 8 * (int)sizeof(K) < nbits) return -1;
+  constexpr int kTile = SortTile<K>::tile;
+  const int64_t tiles = (n + kTile - 1) / kTile;
   cudaMemsetAsync(B.hist, 0, sizeof(uint32_t) * 256 * npass, st);
-  cudaMemsetAsync(B.ticket, 0, sizeof(uint32_t) * 4, st);
+  cudaMemsetAsync(B.ticket, 0, sizeof(uint32_t) * kSortMaxPasses, st);
   int hblocks = (int)((n / 4 + 255) / 256);
   if (hblocks > B.sms * 8) hblocks = B.sms * 8;
   if (hblocks < 1) hblocks = 1;
+  K* keys[2] = {static_cast<K*>(B.keys[0]), static_cast<K*>(B.keys[1])};
   if (B.prof) B.prof->begin(K_HIST);
-  k_hist<<<hblocks, 256, 0, st>>>(B.keys[0], n, npass, B.hist);
+  k_hist<K><<<hblocks, 256, 0, st>>>(keys[0], n, npass, B.hist);
   if (B.prof) B.prof->end(K_HIST, (double)n);
   int cur = 0;
   for (int p = 0; p < npass; ++p) {
     cudaMemsetAsync(B.status, 0, sizeof(uint32_t) * 256 * (size_t)tiles, st);
     if (B.prof) B.prof->begin(K_ONESWEEP);
-    k_onesweep<<<(unsigned)tiles, kSortThreads, 0, st>>>(
-        B.keys[cur], B.vals[cur], B.keys[cur ^ 1], B.vals[cur ^ 1], n, 8 * p, B.hist + 256 * p,
+    k_onesweep<K><<<(unsigned)tiles, kSortThreads, 0, st>>>(
+        keys[cur], B.vals[cur], keys[cur ^ 1], B.vals[cur ^ 1], n, 8 * p, B.hist + 256 * p,
         B.status, B.ticket + p, B.err);
     if (B.prof) B.prof->end(K_ONESWEEP, (double)n);
     cur ^= 1;
   }
   return cur;
 }
+
+template int radix_sort<uint32_t>(const SortBufs&, int64_t, int, cudaStream_t);
+template int radix_sort<uint64_t>(const SortBufs&, int64_t, int, cudaStream_t);
 
 }  // namespace gp

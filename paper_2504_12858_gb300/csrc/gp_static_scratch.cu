@@ -35,7 +35,7 @@ namespace {
 constexpr int64_t kMaxPoints = GP_STATIC_SCRATCH_MAX_POINTS;
 constexpr size_t kA = 256;
 constexpr size_t up(size_t x) { return (x + kA - 1) / kA * kA; }
-constexpr size_t kTiles = (kMaxPoints + kSortTile - 1) / kSortTile;
+constexpr size_t kTiles = (kMaxPoints + SortTile<uint32_t>::tile - 1) / SortTile<uint32_t>::tile;
 
 // byte offsets of the scratch regions
 constexpr size_t kKeys0 = 0;
@@ -44,7 +44,7 @@ constexpr size_t kVals0 = kKeys1 + up(4 * kMaxPoints + 16);
 constexpr size_t kVals1 = kVals0 + up(4 * kMaxPoints + 16);
 constexpr size_t kStatus = kVals1 + up(4 * kMaxPoints + 16);
 constexpr size_t kHist = kStatus + up(4 * 256 * kTiles);
-constexpr size_t kTickets = kHist + up(4 * 4 * 256);
+constexpr size_t kTickets = kHist + up(4 * kSortMaxPasses * 256);
 constexpr size_t kErr = kTickets + up(64);
 constexpr size_t kFlags = kErr + up(64);
 constexpr size_t kOfs = kFlags + up(4 * kMaxPoints);
@@ -96,10 +96,10 @@ extern "C" gp_status gp_hash_build_static(const float* x3, int64_t n, const gp_d
     if (!(ext >= 0) || !std::isfinite(ext)) return GP_ERR_ARG;
     const double v = std::ceil(ext / e);
     if (v > 4096.0) return GP_ERR_ARG;
-    P.nc[a] = v < 1 ? 1 : (int)v;
-    P.lo[a] = (float)domain->lo[a];
-    P.hi[a] = (float)domain->hi[a];
-    ncells *= (uint64_t)P.nc[a];
+    P.geo.nc[a] = v < 1 ? 1 : (int)v;
+    P.geo.lo[a] = (float)domain->lo[a];
+    P.geo.hi[a] = (float)domain->hi[a];
+    ncells *= (uint64_t)P.geo.nc[a];
   }
   if (ncells >= (1ull << 32)) return GP_ERR_ARG;
   P.inv_c = (float)(1.0 / e);
@@ -111,8 +111,10 @@ extern "C" gp_status gp_hash_build_static(const float* x3, int64_t n, const gp_d
   if (s != GP_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   SortBufs sb{};
-  sb.keys[0] = reinterpret_cast<uint32_t*>(b + kKeys0);
-  sb.keys[1] = reinterpret_cast<uint32_t*>(b + kKeys1);
+  uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(b + kKeys0),
+                       reinterpret_cast<uint32_t*>(b + kKeys1)};
+  sb.keys[0] = keys[0];
+  sb.keys[1] = keys[1];
   sb.vals[0] = reinterpret_cast<uint32_t*>(b + kVals0);
   sb.vals[1] = reinterpret_cast<uint32_t*>(b + kVals1);
   sb.status = reinterpret_cast<uint32_t*>(b + kStatus);
@@ -130,19 +132,20 @@ extern "C" gp_status gp_hash_build_static(const float* x3, int64_t n, const gp_d
   if (cudaMemsetAsync(b + kErr, 0, 64, st) != cudaSuccess ||
       cudaMemsetAsync(b + kNcell, 0, 64, st) != cudaSuccess)
     return GP_ERR_CUDA;
-  launch_keys_pos(P, x3, nullptr, n, sb.keys[0], sb.vals[0], st);
+  launch_keys_pos(P, x3, nullptr, n, keys[0], sb.vals[0], st);
   uint64_t nm1 = ncells - 1;
   int nbits = 0;
   while (nm1) {
     ++nbits;
     nm1 >>= 1;
   }
-  const int w = radix_sort(sb, n, nbits, st);
-  if (cudaMemcpyAsync(keys_sorted, sb.keys[w], 4 * n, cudaMemcpyDeviceToDevice, st) !=
+  const int w = radix_sort<uint32_t>(sb, n, nbits, st);
+  if (w < 0) return GP_ERR_ARG;
+  if (cudaMemcpyAsync(keys_sorted, keys[w], 4 * n, cudaMemcpyDeviceToDevice, st) !=
           cudaSuccess ||
       cudaMemcpyAsync(ids_sorted, sb.vals[w], 4 * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return GP_ERR_CUDA;
-  launch_cells(sb.keys[w], n, (uint32_t)ncells, reinterpret_cast<uint32_t*>(b + kFlags),
+  launch_cells(keys[w], n, (uint32_t)ncells, reinterpret_cast<uint32_t*>(b + kFlags),
                reinterpret_cast<uint32_t*>(b + kOfs), reinterpret_cast<uint32_t*>(b + kBsum),
                cell_keys, cell_start, reinterpret_cast<unsigned long long*>(b + kNcell), st);
   unsigned long long nc = 0;

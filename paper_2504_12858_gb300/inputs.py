@@ -183,31 +183,36 @@ def weld_fixture(seed: int = 3, n_grains: int = 10000, shell_n0: int = 50,
         grid=dict(T=T, origin=origin, spacing=sp, vel=(V, 0.0, 0.0)), shell_n0=shell_n0)
 
 
-def cet_runs(n_runs: int = 256, base_seed: int = 1000):
-    """Per-run parameters of the CET ensemble (Sec. 3.5 family).
+def cet_runs(n_runs: int = 256, base_seed: int = 1000, L_range=(0.5e-3, 2e-3),
+             seed_density: float = 50e6, nuc_density: float = 1e11, G_range=(100.0, 1e4),
+             Tdot_range=(0.5, 20.0), steps: int = 400):
+    """Per-run parameters of the columnar-to-equiaxed ensemble (Sec. 3.5 family).
 
-    Run r (seed base_seed + r): cube edge L ~ U[0.5, 2] mm, bottom seeds at
-    50 / mm^2 with dT_n = 0, bulk nucleation sites Poisson with density 1e11 m^-3
-    and dT_n ~ N(5, 1) truncated to >= 0, G ~ U[100, 1e4] K/m along +z,
-    Tdot ~ U[0.5, 20] K/s (cooling), A = 1e-5, n = 2, h = 2 um, dt = 1 ms.
+    Run r (seed base_seed + r): cube edge L ~ U[L_range], columnar seeds on the
+    bottom face (Poisson, seed_density per m^2, at least one) that start growing at
+    once, bulk nucleation sites (Poisson, nuc_density per m^3, uniform in the cube)
+    with dT_n ~ N(5, 1) K truncated to >= 0, T = T_L + G z - Tdot t with
+    G ~ U[G_range] K/m and Tdot ~ U[Tdot_range] K/s, v = 1e-5 dT^2, h = 2 um,
+    dt = 1 ms.  The defaults are the 256-run ensemble of 0.5-2 mm cubes over 400
+    steps, after which its runs hold between 45 and 8e5 particles.
     """
     runs = []
     for r in range(n_runs):
         g = rng(base_seed + r)
-        L = g.uniform(0.5e-3, 2e-3)
-        nb = max(1, g.poisson(50.0 * (L * 1e3) ** 2))
+        L = g.uniform(*L_range)
+        nb = max(1, g.poisson(seed_density * L ** 2))
         bottom = np.concatenate([g.random((nb, 2)) * L, np.zeros((nb, 1))], axis=1)
         qb = shoemake_quaternions(nb, g)
-        nv = g.poisson(1e11 * L ** 3)
+        nv = g.poisson(nuc_density * L ** 3)
         bulk = g.random((nv, 3)) * L
         dTn = truncated_normal(nv, 5.0, 1.0, 0.0, np.inf, g)
         qv = shoemake_quaternions(nv, g)
-        G = g.uniform(100.0, 1e4)
-        Tdot = g.uniform(0.5, 20.0)
+        G = g.uniform(*G_range)
+        Tdot = g.uniform(*Tdot_range)
         T_L = 1000.0
         runs.append(Workload(
             name=f"cet_run_{r}", lo=(0.0, 0.0, 0.0), hi=(L, L, L), h=2e-6, dt=1e-3,
-            a=(1e-5,), b=(2.0,), T_L=T_L, steps=1000, seeds=bottom, quats=qb,
+            a=(1e-5,), b=(2.0,), T_L=T_L, steps=steps, seeds=bottom, quats=qb,
             analytic=dict(T0=T_L, G=(0.0, 0.0, G), xref=(0.0, 0.0, 0.0), Tdot=-Tdot),
             nuclei=dict(pos=bulk, dTn=dTn, quat=qv)))
     return runs

@@ -100,6 +100,19 @@ SIGNATURES = {
                                        _P, _P, C.POINTER(C.c_int64), _P]),
     "gp_tape_begin": (C.c_int, [_P]),
     "gp_adjoint": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.POINTER(C.c_double)]),
+    "gp_batch_arena_bytes": (C.c_int, [C.c_int32, C.POINTER(gp_domain), C.c_double,
+                                       C.POINTER(gp_memory), C.POINTER(C.c_size_t)]),
+    "gp_batch_create": (C.c_int, [C.c_int32, C.POINTER(gp_domain), C.c_double, C.c_double,
+                                  C.POINTER(gp_growth_law), C.POINTER(gp_memory), _P,
+                                  C.POINTER(_P)]),
+    "gp_run_set_thermal_analytic": (C.c_int, [_P, C.c_int32, C.POINTER(gp_thermal_analytic)]),
+    "gp_run_add_grains": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, C.c_int32,
+                                    C.POINTER(C.c_int32)]),
+    "gp_run_nucleation_sites": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, _P,
+                                          C.POINTER(C.c_int32)]),
+    "gp_run_grain_map": (C.c_int, [_P, C.c_int32, C.POINTER(gp_voxel_grid), _P, C.c_int32]),
+    "gp_run_counts": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "gp_grain_table": (C.c_int, [_P, C.c_int64, _P, _P, C.POINTER(C.c_int64)]),
 }
 GP_STATIC_SCRATCH_MAX_POINTS = 262144
 
@@ -168,11 +181,18 @@ class Sim:
     def __init__(self, lo, hi, h, dt, a, b, T_L, capacity, reached_capacity=0,
                  claim_blocks=0, max_grains=0, max_nuclei=0, grid_nodes=0, tape_steps=0,
                  stream=None, device="cuda"):
+        self.lo, self.hi = tuple(lo), tuple(hi)
+        self._open([(lo, hi)], False, h, dt, a, b, T_L, capacity, reached_capacity,
+                   claim_blocks, max_grains, max_nuclei, grid_nodes, tape_steps, stream, device)
+
+    def _open(self, domains, batch, h, dt, a, b, T_L, capacity, reached_capacity, claim_blocks,
+              max_grains, max_nuclei, grid_nodes, tape_steps, stream, device):
         import torch
         self._torch = torch
         L = load()
-        self.lo, self.hi, self.h, self.dt = tuple(lo), tuple(hi), float(h), float(dt)
-        self._dom = domain(lo, hi)
+        self.h, self.dt = float(h), float(dt)
+        self.nruns = len(domains)
+        self._doms = (gp_domain * self.nruns)(*[domain(lo, hi) for lo, hi in domains])
         self._law = growth_law(a, b, T_L)
         mem = gp_memory()
         mem.capacity = int(capacity)
@@ -183,7 +203,11 @@ class Sim:
         mem.grid_nodes = int(grid_nodes)
         mem.tape_steps = int(tape_steps)
         nb = C.c_size_t(0)
-        self._check(L.gp_arena_bytes(C.byref(self._dom), self.h, C.byref(mem), C.byref(nb)))
+        if batch:
+            self._check(L.gp_batch_arena_bytes(self.nruns, self._doms, self.h, C.byref(mem),
+                                               C.byref(nb)))
+        else:
+            self._check(L.gp_arena_bytes(self._doms, self.h, C.byref(mem), C.byref(nb)))
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         self.arena = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
@@ -193,9 +217,14 @@ class Sim:
         self._mem = mem
         h_ = C.c_void_p()
         with torch.cuda.device(self.device):
-            self._check(L.gp_create(C.byref(self._dom), self.h, self.dt, C.byref(self._law),
-                                    C.byref(mem), C.c_void_p(self.stream.cuda_stream),
-                                    C.byref(h_)))
+            if batch:
+                self._check(L.gp_batch_create(self.nruns, self._doms, self.h, self.dt,
+                                              C.byref(self._law), C.byref(mem),
+                                              C.c_void_p(self.stream.cuda_stream), C.byref(h_)))
+            else:
+                self._check(L.gp_create(self._doms, self.h, self.dt, C.byref(self._law),
+                                        C.byref(mem), C.c_void_p(self.stream.cuda_stream),
+                                        C.byref(h_)))
         self._h = h_
 
     # -- plumbing --------------------------------------------------------------------
@@ -350,6 +379,69 @@ class Sim:
         return [dict(name=buf[i].name.decode(), launches=int(buf[i].launches),
                      total_ms=float(buf[i].total_ms), units=float(buf[i].units),
                      bytes_per_unit=float(buf[i].bytes_per_unit)) for i in range(n.value)]
+
+
+class Batch(Sim):
+    """A batch context (``gp_batch_create``): ``domains`` is a list of (lo, hi) per
+    run; the run-level calls take the run index first."""
+
+    def __init__(self, domains, h, dt, a, b, T_L, capacity, reached_capacity=0,
+                 claim_blocks=0, max_grains=0, max_nuclei=0, stream=None, device="cuda"):
+        self.domains = [(tuple(lo), tuple(hi)) for lo, hi in domains]
+        self._open(self.domains, True, h, dt, a, b, T_L, capacity, reached_capacity,
+                   claim_blocks, max_grains, max_nuclei, 0, 0, stream, device)
+
+    def gp_run_set_thermal_analytic(self, run, T0, G, xref, Tdot):
+        th = gp_thermal_analytic()
+        th.T0 = float(T0)
+        th.G[:] = [float(v) for v in G]
+        th.x_ref[:] = [float(v) for v in xref]
+        th.Tdot = float(Tdot)
+        self._check(load().gp_run_set_thermal_analytic(self._h, int(run), C.byref(th)))
+
+    def gp_run_add_grains(self, run, pos, quat, nucleate=True) -> int:
+        pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+        quat = np.ascontiguousarray(quat, np.float64).reshape(-1, 4)
+        first = C.c_int32(0)
+        self._check(load().gp_run_add_grains(self._h, int(run), pos.shape[0], _ptr(pos),
+                                             _ptr(quat), 1 if nucleate else 0, C.byref(first)))
+        return int(first.value)
+
+    def gp_run_nucleation_sites(self, run, pos, dTn, quat) -> int:
+        pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+        dTn = np.ascontiguousarray(dTn, np.float64).reshape(-1)
+        quat = np.ascontiguousarray(quat, np.float64).reshape(-1, 4)
+        first = C.c_int32(0)
+        self._check(load().gp_run_nucleation_sites(self._h, int(run), pos.shape[0], _ptr(pos),
+                                                   _ptr(dTn), _ptr(quat), C.byref(first)))
+        return int(first.value)
+
+    def gp_run_grain_map(self, run, origin, spacing, n):
+        g = gp_voxel_grid()
+        g.origin[:] = [float(v) for v in origin]
+        g.spacing[:] = [float(v) for v in spacing]
+        g.n[:] = [int(v) for v in n]
+        res = np.zeros((int(n[2]), int(n[1]), int(n[0])), np.int32)
+        self._check(load().gp_run_grain_map(self._h, int(run), C.byref(g), _ptr(res), 0))
+        return res
+
+    def gp_run_counts(self):
+        live = np.zeros(self.nruns, np.int64)
+        active = np.zeros(self.nruns, np.int64)
+        self._check(load().gp_run_counts(self._h, self.nruns, _ptr(live), _ptr(active)))
+        return live, active
+
+
+def grain_table(sim):
+    """(nucleus positions (n, 3) float32, run (n,) int32) of every grain of a context."""
+    L = load()
+    n = C.c_int64(0)
+    sim._check(L.gp_grain_table(sim._h, 0, None, None, C.byref(n)))
+    m = int(n.value)
+    c3 = np.zeros((m, 3), np.float32)
+    run = np.zeros(m, np.int32)
+    sim._check(L.gp_grain_table(sim._h, m, _ptr(c3), _ptr(run), C.byref(n)))
+    return c3, run
 
 
 def _workspace(n, lo, hi, h, device):

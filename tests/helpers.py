@@ -78,3 +78,23 @@ def oracle_front_run(theta):
     H, F, _, _, _ = front_outputs(p, w.h, len(w.seeds))
     sig, top = tip_signatures(p, len(w.seeds))
     return H, F, sig, top
+
+
+def nucleus_keys(sim, p, w):
+    """Replaces the grain ids of particles p of context sim by the index of the
+    grain's nucleus in workload w (columnar seeds first, then nucleation sites),
+    matched by binary32 position; grain numbering then compares across contexts."""
+    from paper_2504_12858_gb300 import native
+    c3, _ = native.grain_table(sim)
+    pts = []
+    if w.seeds is not None:
+        pts += [tuple(np.float32(v) for v in x) for x in w.seeds]
+    if w.nuclei:
+        pts += [tuple(np.float32(v) for v in x) for x in w.nuclei["pos"]]
+    index = {}
+    for i, t in enumerate(pts):
+        index.setdefault(t, i)
+    g2n = np.array([index.get(tuple(c), -1) for c in c3], np.int64)
+    q = dict(p)
+    q["grain"] = g2n[p["grain"]]
+    return q
