@@ -265,6 +265,80 @@ def adjoint_cost(dev):
             "forward_with_tape_plus_backward_ms": tg * 1e3, "cost_ratio": tg / tp}
 
 
+def batch_ensemble(dev, serial_every=8, graph_steps=20):
+    """The 256-run columnar-to-equiaxed ensemble (400 steps of 1 ms) in one batch
+    context: every kernel of a step covers all runs, sized on the device, and the
+    steps replay from CUDA graphs of graph_steps steps with the launch configuration
+    the autotuner picked on a rehearsal of the same ensemble.  Compared with the
+    same runs each in its own single-run context, one after the other (every
+    serial_every-th run, scaled to the ensemble).  All variants give identical
+    particles (batch parity tests); set-up is outside every timing."""
+    import torch
+    from paper_2504_12858_gb300 import ensemble, inputs, native
+    runs = inputs.cet_runs()
+    steps = runs[0].steps
+    mem = dict(capacity=int(3.2e7), reached_capacity=int(2.6e8), claim_blocks=int(2.4e6),
+               device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(b, n):
+        torch.cuda.synchronize(dev)
+        ev[0].record(b.stream)
+        b.gp_step(n)
+        ev[1].record(b.stream)
+        torch.cuda.synchronize(dev)
+        return ev[0].elapsed_time(ev[1]) / 1e3
+
+    def release(b):
+        b.close()
+        torch.cuda.empty_cache()
+
+    # rehearsal: the autotuner times its candidates on the ensemble at step 300
+    b = ensemble.batch_from(runs, **mem)
+    b.gp_step(300)
+    cfg = b.gp_autotune(trial_steps=3)
+    release(b)
+    # step by step with the default launches
+    b = ensemble.batch_from(runs, **mem)
+    t_eager = timed(b, steps)
+    release(b)
+    # the measured configuration: autotuned launches replayed from CUDA graphs
+    b = ensemble.batch_from(runs, **mem)
+    cfg["graph_steps"] = graph_steps
+    b.gp_set_launch_config(**cfg)
+    tb = timed(b, steps)
+    st = b.gp_stats()
+    live, _ = b.gp_run_counts()
+    arena_gb = b.arena_bytes / 1e9
+    release(b)
+    ts, sample = 0.0, list(range(0, len(runs), serial_every))
+    for r in sample:
+        w = runs[r]
+        an = w.analytic
+        cap = int(live[r] * 1.3) + 20000
+        s = native.Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=cap,
+                       reached_capacity=12 * cap, claim_blocks=max(8192, cap // 6),
+                       max_grains=len(w.seeds) + len(w.nuclei["pos"]) + 16,
+                       max_nuclei=len(w.nuclei["pos"]) + 16, device=dev)
+        s.gp_set_thermal_analytic(an["T0"], an["G"], an["xref"], an["Tdot"])
+        s.gp_add_grains(w.seeds, w.quats)
+        s.gp_nucleation_sites(w.nuclei["pos"], w.nuclei["dTn"], w.nuclei["quat"])
+        ts += timed(s, steps)
+        s.close()
+    scale = len(runs) / len(sample)
+    return {"workload": "cet_runs: 256 runs, 0.5-2 mm cubes, columnar + equiaxed nucleation, "
+                        "400 steps of 1 ms", "runs": len(runs), "steps": steps,
+            "batched_s": tb, "runs_per_s": len(runs) / tb,
+            "particle_steps_per_s": st["particle_steps"] / tb,
+            "launch_config": cfg, "batched_step_by_step_s": t_eager,
+            "particles_per_run": {"min": int(live.min()), "median": int(np.median(live)),
+                                  "max": int(live.max())},
+            "arena_gb": round(arena_gb, 1),
+            "serial_sample_runs": len(sample), "serial_s_scaled": ts * scale,
+            "serial_runs_per_s": len(runs) / (ts * scale),
+            "speedup_vs_serial": ts * scale / tb}
+
+
 def run_native(args, rank, world, local_rank):
     import torch
     from paper_2504_12858_gb300 import native
@@ -360,7 +434,11 @@ def run_native(args, rank, world, local_rank):
                            "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in prof),
                                                                1e-9), 4)} for k in prof}
     cb = cpu_baseline(args.cpu_grains, args.n0, 2) if (world == 1 and not args.no_cpu) else None
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
     adj = adjoint_cost(dev) if not args.no_extras else None
+    bat = batch_ensemble(dev) if not args.no_extras else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -376,9 +454,8 @@ def run_native(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": METRIC, "steps": args.e2e_steps,
                     "h2d_bytes_per_step": int(Th.numel() * 4),
                     "d2h_bytes_per_step": 160},
-            "clocks": clk, "gpu_launches": launches, "adjoint": adj}
+            "clocks": clk, "gpu_launches": launches, "adjoint": adj, "batch": bat}
     print(json.dumps(line), flush=True)
-    sim.close()
     return 0
 
 
@@ -401,7 +478,7 @@ def main():
     ap.add_argument("--ref-grains", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the adjoint-cost measurement on the calibration cube")
+                    help="skip the adjoint-cost and batched-ensemble measurements")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     if world > 1:

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -44,7 +45,7 @@ struct Layout {
   int64_t grid_nodes = 0;
   int64_t tape_steps = 0;
   // offsets into the arena
-  size_t rec0, rec1, pos4, sslot, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
+  size_t rec0, rec1, pos4, sslot, act, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
       rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, dstats, grid, runs,
       rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, total;
 };
@@ -165,8 +166,8 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->keys1 = take(kb * cap + 16);
   L->vals0 = take(4 * cap + 16);
   L->vals1 = take(4 * cap + 16);
-  L->sstatus = take(4 * radix_status_words(L->cap));
-  L->hist = take(4 * kSortMaxPasses * 256);
+  L->sstatus = take(4 * radix_status_words(L->cap, L->key_bytes));
+  L->hist = take(4 * 256 * (size_t)((L->nbits + 7) / 8));  // one histogram per digit
   L->tickets = take(4 * 8);
   L->cells = take(16 * (size_t)L->nseg);
   L->rkey = take(8 * (size_t)L->rcap);
@@ -178,18 +179,19 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->npos = take(16 * (size_t)L->max_nuclei);
   L->ngrain = take(64 * (size_t)L->max_nuclei);
   L->nstate = take(4 * (size_t)L->max_nuclei);
-  L->nmeta = take(8 * (size_t)L->max_nuclei);
   L->dstats = take(sizeof(DevStats));
   L->grid = take(4 * (size_t)L->grid_nodes);
-  L->runs = take(sizeof(Geo) * (size_t)nruns);
-  L->rtherm = take(16 * (size_t)nruns);
-  L->rcount = take(16 * (size_t)nruns);
   const size_t ts = (size_t)L->tape_steps;
   L->tape_rec = take(16 * cap * ts);
   L->tape_vals = take(4 * cap * ts);
   L->tape_state = take(cap * ts);
   L->tape_par = take(4 * cap * ts);
   L->tape_grad = take(8 * 8);
+  L->act = take(4 * cap);
+  L->nmeta = take(8 * (size_t)L->max_nuclei);
+  L->runs = take(sizeof(Geo) * (size_t)nruns);
+  L->rtherm = take(16 * (size_t)nruns);
+  L->rcount = take(16 * (size_t)nruns);
   L->total = o;
   return true;
 }
@@ -238,10 +240,11 @@ const char* kKernelNames[K_COUNT] = {"hist",      "onesweep", "keys", "build",
 //   keys      read record (16), write key + value (8)
 //   build     read value + key (8), gather record (16), write record (16), write
 //             position + grain (16)
-//   advance   read record (16) + own position (16), write record (16); neighbour
-//             positions are re-reads of the same cells (cache)
+//   advance   per ACTIVE particle: read list index (4), record (16) and own position
+//             (16), write record (16); neighbour positions are re-reads of the same
+//             cells (cache)
 //   emit      read record (16), write record (16) + key + value (8) per output
-const double kKernelBytes[K_COUNT] = {4, 16, 24, 56, 48, 40, 0, 0, 0, 0, 0, 0};
+const double kKernelBytes[K_COUNT] = {4, 16, 24, 56, 52, 40, 0, 0, 0, 0, 0, 0};
 
 struct Prof : ProfHook {
   cudaStream_t st = nullptr;
@@ -337,6 +340,7 @@ struct gp_ctx {
   int cur = 0;  // rec[cur] is the (unsorted) store
   float4* pos4 = nullptr;
   int32_t* site_slot = nullptr;  // claim-block slot of each crossing particle's reached site
+  uint32_t* act = nullptr;       // sorted indices of the ACTIVE particles (built per step)
   SortBufs sb{};
   uint4* cells = nullptr;
   uint32_t stamp = 0;
@@ -365,6 +369,10 @@ struct gp_ctx {
   std::string err;
   Prof prof;
   int sms = 152;
+  // batch: steps per captured CUDA graph (0: launches issued step by step) and the
+  // instantiated graphs by step count
+  int graph_steps = 0;
+  std::map<int, cudaGraphExec_t> graphs;
 };
 
 namespace {
@@ -473,12 +481,20 @@ gp_status sync_stats(gp_ctx* c) {
 gp_status push_counts(gp_ctx* c) {
   c->hst->n_live = (unsigned long long)c->n_live;
   c->hst->n_grains = (unsigned long long)c->n_grains;
+  c->hst->step = (unsigned long long)c->step;
+  GP_CUDA(c, cudaMemcpyAsync(&c->dst->step, &c->hst->step, sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, c->st));
   GP_CUDA(c, cudaMemcpyAsync(&c->dst->n_live, &c->hst->n_live, sizeof(unsigned long long),
                              cudaMemcpyHostToDevice, c->st));
   GP_CUDA(c, cudaMemcpyAsync(&c->dst->n_grains, &c->hst->n_grains, sizeof(unsigned long long),
                              cudaMemcpyHostToDevice, c->st));
   GP_CUDA(c, cudaStreamSynchronize(c->st));
   return GP_OK;
+}
+
+void drop_graphs(gp_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+  c->graphs.clear();
 }
 
 gp_status check_ctx(gp_ctx* c) {
@@ -560,6 +576,7 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   c->rec[1] = at<int4>(c, L.rec1);
   c->pos4 = at<float4>(c, L.pos4);
   c->site_slot = at<int32_t>(c, L.sslot);
+  c->act = at<uint32_t>(c, L.act);
   c->sb.keys[0] = c->base + L.keys0;
   c->sb.keys[1] = c->base + L.keys1;
   c->sb.vals[0] = at<uint32_t>(c, L.vals0);
@@ -595,6 +612,10 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   c->rtherm = at<double2>(c, L.rtherm);
   c->rcount = at<unsigned long long>(c, L.rcount);
   refresh_params(c);
+  c->P.launch.build_ctas = 8 * c->sms;
+  c->P.launch.advance_ctas = 4 * c->sms;
+  c->P.launch.emit_ctas = 8 * c->sms;
+  if (batch) c->sb.n_dev = &c->dst->n_live;  // device-sized sort
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemsetAsync(c->cells, 0, 16 * L.nseg, s);
@@ -607,6 +628,12 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   e = e ? e : cudaMemsetAsync(c->rtherm, 0, 16 * (size_t)L.nruns, s);
   e = e ? e : cudaMemcpyAsync(c->runs, c->geo.data(), sizeof(Geo) * c->geo.size(),
                               cudaMemcpyHostToDevice, s);
+  if (batch) {  // a batch's step and stamp counters live on the device
+    c->stamp = 1;
+    c->hst->stamp = 1;
+    e = e ? e : cudaMemcpyAsync(&c->dst->stamp, &c->hst->stamp, sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, s);
+  }
   e = e ? e : cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     gp_destroy(c);
@@ -657,6 +684,7 @@ gp_status gp_destroy(gp_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   c->prof.pending.clear();
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
   if (c->own && c->base) cudaFree(c->base);
   if (c->grid_own) cudaFree(c->grid_own);
   if (c->hst) cudaFreeHost(c->hst);
@@ -888,25 +916,130 @@ gp_status gp_run_nucleation_sites(gp_ctx* c, int32_t run, int64_t n, const doubl
                              cudaMemcpyHostToDevice, c->st));
   c->n_nuclei += (int)n;
   c->n_grains += n;
+  drop_graphs(c);  // captured steps launch the nucleation kernels for n_nuclei sites
   return push_counts(c);
 }
+
+}  // extern "C"
+
+namespace {
+
+// One step of a batch, every launch sized on the device (counts in DevStats), so
+// that a sequence of steps can be captured in a CUDA graph: run constants, sort,
+// build, advance, emit, nucleation, counters.
+void batch_step_launches(gp_ctx* c) {
+  const Params& P = c->P;
+  const int64_t cap = c->L.cap;
+  const StepArgs S{};  // parity and stamp are read on the device
+  cudaStream_t st = c->st;
+  const double units = (double)c->n_live;  // timing units (exact when stepped eagerly)
+  launch_run_step(c->runs, c->rtherm, c->L.nruns, c->dst, c->dt, st);
+  cudaMemsetAsync(&c->dst->n_out, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(&c->dst->n_frozen, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), st);
+  const int w = radix_sort<uint64_t>(c->sb, cap, c->L.nbits, st);
+  int4* sorted = c->rec[c->cur ^ 1];
+  c->prof.begin(K_BUILD);
+  launch_build(true, P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4, c->cells,
+               0, cap, c->L.key_end, c->act, c->dst, st);
+  c->prof.end(K_BUILD, units);
+  c->prof.begin(K_ADVANCE);
+  launch_advance(true, P, S, sorted, c->pos4, c->sb.keys[w], c->cells, 0, cap, c->act, c->C,
+                 c->site_slot, c->dst, st);
+  c->prof.end(K_ADVANCE, units);
+  c->prof.begin(K_EMIT);
+  launch_emit(true, P, S, sorted, c->site_slot, cap, c->rec[c->cur], c->sb.keys[0],
+              c->sb.vals[0], cap, c->C, c->R, nullptr, c->dst, st);
+  c->prof.end(K_EMIT, units);
+  if (c->n_nuclei > (int64_t)c->hst->nucleated || (c->graph_steps > 0 && c->n_nuclei > 0)) {
+    launch_link_reached(true, P, c->R, &c->dst->linked, c->sms, st);
+    c->prof.begin(K_NUCLEATE);
+    launch_nucleate_batch(P, StepArgs{}, c->npos, c->nmeta, c->nstate, c->n_nuclei,
+                          c->rec[c->cur], static_cast<uint64_t*>(c->sb.keys[0]), c->sb.vals[0],
+                          cap, c->C, c->R, c->dst, c->sms, st);
+    c->prof.end(K_NUCLEATE, 1.0);
+  }
+  launch_finalize(c->dst, cap, true, st);
+}
+
+// the instantiated graph of k batch steps (captured on first use)
+gp_status graph_for(gp_ctx* c, int k, cudaGraphExec_t* out) {
+  auto it = c->graphs.find(k);
+  if (it != c->graphs.end()) {
+    *out = it->second;
+    return GP_OK;
+  }
+  const bool prof = c->prof.on;
+  c->prof.on = false;
+  GP_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < k; ++i) batch_step_launches(c);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+  c->prof.on = prof;
+  GP_CUDA(c, e);
+  cudaGraphExec_t ge = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  GP_CUDA(c, e2);
+  c->graphs[k] = ge;
+  *out = ge;
+  return GP_OK;
+}
+
+gp_status step_batch(gp_ctx* c, int32_t nsteps) {
+  for (int r = 0; r < c->L.nruns; ++r)
+    if (!c->thermal_set[r]) return fail(c, GP_ERR_STATE, "a run has no thermal field");
+  if (c->graph_steps > 0 && c->st == nullptr)
+    return fail(c, GP_ERR_STATE, "CUDA graphs need a non-default stream");
+  if (c->n_live > 0 && !c->keys_valid) {
+    c->prof.begin(K_KEYS);
+    launch_keys(true, c->P, c->rec[c->cur], c->n_live, c->sb.keys[0], c->sb.vals[0], c->st);
+    c->prof.end(K_KEYS, (double)c->n_live);
+  }
+  c->keys_valid = true;
+  int64_t done = 0;
+  while (done < nsteps) {
+    const int k = c->graph_steps > 0 ? (int)std::min<int64_t>(c->graph_steps, nsteps - done) : 1;
+    if (c->stamp + (uint32_t)k > 0xffffu) {  // stamps are 16 bits in the cell table
+      GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
+      c->hst->stamp = 1;
+      GP_CUDA(c, cudaMemcpyAsync(&c->dst->stamp, &c->hst->stamp, sizeof(unsigned long long),
+                                 cudaMemcpyHostToDevice, c->st));
+      c->stamp = 1;
+    }
+    if (c->graph_steps > 0) {
+      cudaGraphExec_t ge = nullptr;
+      gp_status s = graph_for(c, k, &ge);
+      if (s) return s;
+      GP_CUDA(c, cudaGraphLaunch(ge, c->st));
+    } else {
+      batch_step_launches(c);
+    }
+    GP_CUDA(c, cudaGetLastError());
+    c->step += k;
+    c->stamp += (uint32_t)k;
+    done += k;
+    gp_status s = sync_stats(c);
+    if (s) return s;
+  }
+  return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 gp_status gp_step(gp_ctx* c, int32_t nsteps) {
   gp_status s = check_ctx(c);
   if (s) return s;
   if (nsteps < 0) return fail(c, GP_ERR_ARG, "nsteps < 0");
-  if (c->batch) {
-    for (int r = 0; r < c->L.nruns; ++r)
-      if (!c->thermal_set[r]) return fail(c, GP_ERR_STATE, "a run has no thermal field");
-  } else if (c->thermal == 0 && c->n_live > 0) {
-    return fail(c, GP_ERR_STATE, "no thermal field set");
-  }
-  const bool batch = c->batch;
+  if (c->batch) return step_batch(c, nsteps);
+  if (c->thermal == 0 && c->n_live > 0) return fail(c, GP_ERR_STATE, "no thermal field set");
+  const bool batch = false;
   for (int it = 0; it < nsteps; ++it) {
     const int64_t n = c->n_live;
     const StepArgs S = step_args(c, c->step);
     const Params P = step_params(c, c->step);
-    if (batch) launch_run_step(c->runs, c->rtherm, c->L.nruns, c->step, c->dt, c->st);
     const bool rec = c->tape_on && c->tape_pos < c->L.tape_steps;
     const size_t tq = (size_t)c->tape_pos, tcap = (size_t)c->L.cap;
     int32_t* tpar = rec ? at<int32_t>(c, c->L.tape_par) + tq * tcap : nullptr;
@@ -920,17 +1053,17 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
         c->prof.end(K_KEYS, (double)n);
         c->keys_valid = true;
       }
-      const int w = batch ? radix_sort<uint64_t>(c->sb, n, c->L.nbits, c->st)
-                          : radix_sort<uint32_t>(c->sb, n, c->L.nbits, c->st);
+      const int w = radix_sort<uint32_t>(c->sb, n, c->L.nbits, c->st);
       if (w < 0) return fail(c, GP_ERR_STATE, "cell keys wider than the sort supports");
       if (++c->stamp > 0xffffu) {
         GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
         c->stamp = 1;
       }
       int4* sorted = c->rec[c->cur ^ 1];
+      GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
       c->prof.begin(K_BUILD);
       launch_build(batch, P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4,
-                   c->cells, c->stamp, n, c->L.key_end, &c->dst->err, c->st);
+                   c->cells, c->stamp, n, c->L.key_end, c->act, c->dst, c->st);
       c->prof.end(K_BUILD, (double)n);
       if (rec) {
         GP_CUDA(c, cudaMemcpyAsync(at<int4>(c, c->L.tape_rec) + tq * tcap, sorted, 16 * n,
@@ -939,9 +1072,10 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                                    4 * n, cudaMemcpyDeviceToDevice, c->st));
       }
       c->prof.begin(K_ADVANCE);
-      launch_advance(batch, P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->C,
-                     c->site_slot, c->dst, c->st);
-      c->prof.end(K_ADVANCE, (double)n);
+      launch_advance(batch, P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->act,
+                     c->C, c->site_slot, c->dst, c->st);
+      // units: the ACTIVE particles entering the step (live minus frozen after the last step)
+      c->prof.end(K_ADVANCE, (double)(n - std::min<int64_t>(n, (int64_t)c->hst->n_frozen)));
       if (rec) launch_tape_state(sorted, n, at<uint8_t>(c, c->L.tape_state) + tq * tcap, c->st);
       c->prof.begin(K_EMIT);
       launch_emit(batch, P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
@@ -953,20 +1087,13 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       const StepArgs S1 = step_args(c, c->step + 1);
       launch_link_reached(batch, P, c->R, &c->dst->linked, c->sms, c->st);
       c->prof.begin(K_NUCLEATE);
-      if (batch) {
-        launch_nucleate_batch(P, S1, c->npos, c->nmeta, c->nstate, c->n_nuclei, c->rec[c->cur],
-                              static_cast<uint64_t*>(c->sb.keys[0]), c->sb.vals[0], c->L.cap,
-                              c->C, c->R, c->dst, c->sms, c->st);
-        launch_finalize(c->dst, c->L.cap, c->st);
-      } else {
-        launch_nucleate(P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
-                        c->L.max_grains, c->rec[c->cur], static_cast<uint32_t*>(c->sb.keys[0]),
-                        c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->st);
-      }
+      launch_nucleate(P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
+                      c->L.max_grains, c->rec[c->cur], static_cast<uint32_t*>(c->sb.keys[0]),
+                      c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->st);
       c->prof.end(K_NUCLEATE, 1.0);
     } else {
       c->prof.begin(K_FINALIZE);
-      launch_finalize(c->dst, c->L.cap, c->st);
+      launch_finalize(c->dst, c->L.cap, false, c->st);
       c->prof.end(K_FINALIZE, 1.0);
     }
     GP_CUDA(c, cudaGetLastError());
@@ -1230,6 +1357,85 @@ gp_status gp_run_counts(gp_ctx* c, int32_t nruns, int64_t* live, int64_t* active
   return GP_OK;
 }
 
+gp_status gp_get_launch_config(gp_ctx* c, gp_launch_config* out) {
+  if (!c || !out) return GP_ERR_ARG;
+  out->build_ctas_per_sm = c->P.launch.build_ctas / c->sms;
+  out->advance_ctas_per_sm = c->P.launch.advance_ctas / c->sms;
+  out->emit_ctas_per_sm = c->P.launch.emit_ctas / c->sms;
+  out->graph_steps = c->graph_steps;
+  return GP_OK;
+}
+
+gp_status gp_set_launch_config(gp_ctx* c, const gp_launch_config* cfg) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (!cfg) return fail(c, GP_ERR_ARG, "null configuration");
+  if (!c->batch) return fail(c, GP_ERR_STATE, "launch configurations apply to batch contexts");
+  auto ok = [](int v, int hi) { return v >= 1 && v <= hi; };
+  // resident CTAs per SM: 4 for the advance (64 registers a thread), 8 for the others
+  if (!ok(cfg->build_ctas_per_sm, 8) || !ok(cfg->advance_ctas_per_sm, 4) ||
+      !ok(cfg->emit_ctas_per_sm, 8) || cfg->graph_steps < 0 || cfg->graph_steps > 1000)
+    return fail(c, GP_ERR_ARG, "launch configuration out of range");
+  c->P.launch.build_ctas = cfg->build_ctas_per_sm * c->sms;
+  c->P.launch.advance_ctas = cfg->advance_ctas_per_sm * c->sms;
+  c->P.launch.emit_ctas = cfg->emit_ctas_per_sm * c->sms;
+  c->graph_steps = cfg->graph_steps;
+  drop_graphs(c);
+  return GP_OK;
+}
+
+gp_status gp_autotune(gp_ctx* c, int32_t trial_steps, gp_launch_config* best) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (!c->batch) return fail(c, GP_ERR_STATE, "the autotuner applies to batch contexts");
+  if (trial_steps < 1) return fail(c, GP_ERR_ARG, "trial_steps < 1");
+  gp_launch_config cur{};
+  gp_get_launch_config(c, &cur);
+  const int builds[] = {4, 8}, advances[] = {2, 4}, emits[] = {4, 8};
+  cudaEvent_t ev[2];
+  GP_CUDA(c, cudaEventCreate(&ev[0]));
+  GP_CUDA(c, cudaEventCreate(&ev[1]));
+  double best_cost = 1e300;
+  gp_launch_config pick = cur;
+  for (int b : builds)
+    for (int a : advances)
+      for (int e : emits) {
+        if (s) break;
+        gp_launch_config t = cur;
+        t.build_ctas_per_sm = b;
+        t.advance_ctas_per_sm = a;
+        t.emit_ctas_per_sm = e;
+        t.graph_steps = 0;
+        s = gp_set_launch_config(c, &t);
+        // cost of a configuration: device time per particle record of its trial steps
+        // (the steps are real steps: every configuration gives the same results)
+        double records = 0, ms = 0;
+        for (int i = 0; i < trial_steps && !s; ++i) {
+          records += (double)c->n_live;
+          cudaEventRecord(ev[0], c->st);
+          s = gp_step(c, 1);
+          cudaEventRecord(ev[1], c->st);
+          cudaEventSynchronize(ev[1]);
+          float t_ms = 0;
+          cudaEventElapsedTime(&t_ms, ev[0], ev[1]);
+          ms += t_ms;
+        }
+        const double cost = ms / std::max(records, 1.0);
+        if (!s && cost < best_cost) {
+          best_cost = cost;
+          pick = t;
+        }
+      }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (s) return s;
+  pick.graph_steps = cur.graph_steps;
+  s = gp_set_launch_config(c, &pick);
+  if (s) return s;
+  if (best) *best = pick;
+  return GP_OK;
+}
+
 gp_status gp_grain_table(gp_ctx* c, int64_t cap, float* c3, int32_t* run, int64_t* n_out) {
   gp_status s = check_ctx(c);
   if (s) return s;
@@ -1305,7 +1511,7 @@ bool sa_layout(int64_t n, uint64_t nseg, SaLayout* L) {
   L->keys1 = take(4 * m + 16);
   L->vals0 = take(4 * m + 16);
   L->vals1 = take(4 * m + 16);
-  L->status = take(4 * radix_status_words(n));
+  L->status = take(4 * radix_status_words(n, 4));
   L->hist = take(4 * kSortMaxPasses * 256);
   L->tickets = take(64);
   L->err = take(64);

@@ -123,6 +123,10 @@ struct Params {
   float ginv[3];     // 1 / spacing
   const float4* gtab;// grain table: 4 float4 per grain (c with the run id in w, rows of h R)
   int hshift;        // one reached-site head per 2^hshift cells along each axis
+  // grids of the device-sized (batch) launches, in CTAs over the whole GPU
+  struct {
+    int build_ctas, advance_ctas, emit_ctas;
+  } launch;
 };
 
 // per-step constants of the gridded field (computed on the host in double)
@@ -498,7 +502,9 @@ struct DevStats {
   uint32_t err;
   uint32_t pad;
   unsigned long long linked;       // reached sites linked into the per-cell lists
-  unsigned long long scratch[2];
+  unsigned long long n_act;        // ACTIVE particles listed by the last build
+  unsigned long long step;         // batch: index n of the step being computed
+  unsigned long long stamp;        // batch: cell-table stamp of the current build
 };
 
 // warp-aggregated 64-bit counter increment
@@ -540,6 +546,10 @@ struct SortBufs {
   int64_t max_n;
   int sms;
   ProfHook* prof;
+  // device-sized sort: the key count is read from *n_dev when the kernels run
+  // (persistent CTAs, look-back words cleared for max_n keys), so that the launches
+  // need no host round trip and can be captured in a CUDA graph
+  const unsigned long long* n_dev;
 };
 
 constexpr int kSortThreads = 256;
@@ -553,6 +563,6 @@ template <> struct SortTile<uint64_t> { static constexpr int items = 10, tile = 
 // key type or kSortMaxPasses digits.
 template <class K>
 int radix_sort(const SortBufs& B, int64_t n, int nbits, cudaStream_t st);
-size_t radix_status_words(int64_t n);
+size_t radix_status_words(int64_t n, int key_bytes);  // look-back words for n keys
 
 }  // namespace gp

@@ -296,24 +296,44 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
                                                int4* __restrict__ rout, float4* __restrict__ pos4,
                                                uint4* __restrict__ tab,
                                                uint32_t stamp, int64_t n, K key_end,
-                                               uint32_t* err) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const uint32_t id = __ldg(svals + j);
-  const K key = __ldg(skeys + j);
-  if ((int64_t)id >= n || key >= key_end) {  // only after a failed sort
-    atomicOr(err, ERR_TIMEOUT);
-    return;
+                                               uint32_t* __restrict__ act, DevStats* st) {
+  __shared__ uint32_t s_warp[8];
+  __shared__ unsigned long long s_base;
+  if constexpr (BATCH) {  // sizes of a batch step live on the device (graph capture)
+    n = (int64_t)st->n_live;
+    stamp = (uint32_t)st->stamp;
   }
-  const int4 rv = __ldg(rin + id);
-  rout[j] = rv;
-  const Rec r = rec_unpack(rv);
-  float4 gc, r0, r1, r2;
-  grain_load(P.gtab, r.grain, gc, r0, r1, r2);
-  const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
-  const int run = run_of<BATCH>(gc);
-  pos4[j] = make_float4(p.x, p.y, p.z, __int_as_float(r.grain | (run << kRunShift)));
-  seg_build<K>(geo_of<BATCH>(P, run), skeys, j, n, key, tab, stamp, err);
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < n;
+       j0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = j0 + threadIdx.x;
+    bool active = false;
+    if (j < n) {
+      const uint32_t id = __ldg(svals + j);
+      const K key = __ldg(skeys + j);
+      if ((int64_t)id >= n || key >= key_end) {  // only after a failed sort
+        atomicOr(&st->err, ERR_TIMEOUT);
+      } else {
+        const int4 rv = __ldg(rin + id);
+        rout[j] = rv;
+        const Rec r = rec_unpack(rv);
+        float4 gc, r0, r1, r2;
+        grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+        const float3 p =
+            add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
+        const int run = run_of<BATCH>(gc);
+        pos4[j] = make_float4(p.x, p.y, p.z, __int_as_float(r.grain | (run << kRunShift)));
+        seg_build<K>(geo_of<BATCH>(P, run), skeys, j, n, key, tab, stamp, &st->err);
+        active = r.state == ST_ACTIVE;
+      }
+    }
+    // list of the ACTIVE sorted indices, so that the advance runs on full warps; a
+    // CTA appends its (contiguous, ordered) share with one reservation
+    uint32_t tot;
+    const uint32_t ofs = bscan256(active ? 1u : 0u, s_warp, tot);
+    if (threadIdx.x == 0) s_base = tot ? atomicAdd(&st->n_act, (unsigned long long)tot) : 0ull;
+    __syncthreads();
+    if (active) act[s_base + ofs] = (uint32_t)j;  // s_base is rewritten only after the next scan
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -324,76 +344,90 @@ __global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* 
                                                  const float4* __restrict__ pos4,
                                                  const K* __restrict__ skeys,
                                                  const uint4* __restrict__ tab,
-                                                 uint32_t stamp, int64_t n, Claims C,
+                                                 uint32_t stamp, int64_t n,
+                                                 const uint32_t* __restrict__ act, Claims C,
                                                  int32_t* __restrict__ site_slot, DevStats* st) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool active = false, froze = false, clamped = false;
-  bool crossing = false;
-  int g = 0, sx = 0, sy = 0, sz = 0;
-  if (j < n) {
-    Rec r = rec_unpack(rs[j]);
-    if (r.state == ST_ACTIVE) {
-      active = true;
-      const float4 q = __ldg(pos4 + j);
-      const float3 p = make_float3(q.x, q.y, q.z);
-      const int gw = __float_as_int(q.w);
-      const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
-      g = r.grain;
-      int cx, cy, cz;
-      cell_local(gm, P.inv_c, p, cx, cy, cz);
-      const bool hit = contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
-      if (hit) {
-        froze = true;
-        r.state = ST_FROZEN;
-      } else {
-        // thermal sample at (x_n, t_n), growth law, explicit Euler step of ell
-        const float dT = undercooling(P, gm, S, p, gm.dT_base);
-        float dl = __fmul_rn(growth_v(P, dT), P.dt_over_h);
-        if (dl > 1.f) {
-          dl = 1.f;
-          clamped = true;
-        }
-        const float e = __fadd_rn(r.ell, dl);
-        // the target is reached within 2^-20 of a full spacing, so a step
-        // commensurate with h does not lose a step to binary32 rounding
-        if (e >= 1.f - 0x1p-20f) {
-          r.cross = 1;
-          r.ell = fmaxf(__fsub_rn(e, 1.f), 0.f);
-          crossing = true;
-          sx = r.sx;
-          sy = r.sy;
-          sz = r.sz;
-          step_site(sx, sy, sz, r.dir);
+  if constexpr (BATCH) {
+    n = (int64_t)st->n_live;
+    stamp = (uint32_t)st->stamp;
+    S.parity = (int)(st->step & 1ull);
+  }
+  // thread i advances the i-th listed ACTIVE particle (sorted index j); the loop is
+  // uniform over a CTA so that every lane reaches the warp-wide claims
+  const int64_t m = (int64_t)st->n_act;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < m;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    const int64_t j = i < m ? (int64_t)__ldg(act + i) : -1;
+    bool active = false, froze = false, clamped = false;
+    bool crossing = false;
+    int g = 0, sx = 0, sy = 0, sz = 0;
+    if (j >= 0) {
+      Rec r = rec_unpack(rs[j]);
+      if (r.state == ST_ACTIVE) {
+        active = true;
+        const float4 q = __ldg(pos4 + j);
+        const float3 p = make_float3(q.x, q.y, q.z);
+        const int gw = __float_as_int(q.w);
+        const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
+        g = r.grain;
+        int cx, cy, cz;
+        cell_local(gm, P.inv_c, p, cx, cy, cz);
+        const bool hit =
+            contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        if (hit) {
+          froze = true;
+          r.state = ST_FROZEN;
         } else {
-          r.ell = e;
+          // thermal sample at (x_n, t_n), growth law, explicit Euler step of ell
+          const float dT = undercooling(P, gm, S, p, gm.dT_base);
+          float dl = __fmul_rn(growth_v(P, dT), P.dt_over_h);
+          if (dl > 1.f) {
+            dl = 1.f;
+            clamped = true;
+          }
+          const float e = __fadd_rn(r.ell, dl);
+          // the target is reached within 2^-20 of a full spacing, so a step
+          // commensurate with h does not lose a step to binary32 rounding
+          if (e >= 1.f - 0x1p-20f) {
+            r.cross = 1;
+            r.ell = fmaxf(__fsub_rn(e, 1.f), 0.f);
+            crossing = true;
+            sx = r.sx;
+            sy = r.sy;
+            sz = r.sz;
+            step_site(sx, sy, sz, r.dir);
+          } else {
+            r.ell = e;
+          }
         }
+        rs[j] = rec_pack(r);
       }
-      rs[j] = rec_pack(r);
     }
-  }
-  // spawn claims: every outer direction k' at the reached site s' claims the target
-  // s' + e_k' for this step (claimant bit of its axis).  All lanes take part.
-  // The pool slot of the block holding s' is kept for the resolution in k_emit
-  // (most targets lie in that block).
-  if (__any_sync(0xffffffffu, crossing)) {
-    BlockCache bc;
-    int32_t sslot = -1;
-    for (int k = 0; k < 6; ++k) {
-      const bool have = crossing && is_outer(sx, sy, sz, k);
-      if (!__any_sync(0xffffffffu, have)) continue;  // warp-uniform
-      int tx = sx, ty = sy, tz = sz;
-      step_site(tx, ty, tz, k);
-      int sh = 0;
-      uint32_t* w = warp_claim_word(C, have, g, tx, ty, tz, true, sh, bc);
-      if (w) atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << sh);
-      if (have && (tx >> 3) == (sx >> 3) && (ty >> 3) == (sy >> 3) && (tz >> 3) == (sz >> 3))
-        sslot = (int32_t)bc.b;
+    // spawn claims: every outer direction k' at the reached site s' claims the target
+    // s' + e_k' for this step (claimant bit of its axis).  All lanes take part.
+    // The pool slot of the block holding s' is kept for the resolution in k_emit
+    // (most targets lie in that block).
+    if (__any_sync(0xffffffffu, crossing)) {
+      BlockCache bc;
+      int32_t sslot = -1;
+      for (int k = 0; k < 6; ++k) {
+        const bool have = crossing && is_outer(sx, sy, sz, k);
+        if (!__any_sync(0xffffffffu, have)) continue;  // warp-uniform
+        int tx = sx, ty = sy, tz = sz;
+        step_site(tx, ty, tz, k);
+        int sh = 0;
+        uint32_t* w = warp_claim_word(C, have, g, tx, ty, tz, true, sh, bc);
+        if (w) atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << sh);
+        if (have && (tx >> 3) == (sx >> 3) && (ty >> 3) == (sy >> 3) && (tz >> 3) == (sz >> 3))
+          sslot = (int32_t)bc.b;
+      }
+      if (crossing) site_slot[j] = sslot;
     }
-    if (crossing) site_slot[j] = sslot;
+    warp_add(&st->particle_steps, active ? 1u : 0u);
+    warp_add(&st->frozen_new, froze ? 1u : 0u);
+    warp_add(&st->clamped, clamped ? 1u : 0u);
   }
-  warp_add(&st->particle_steps, active ? 1u : 0u);
-  warp_add(&st->frozen_new, froze ? 1u : 0u);
-  warp_add(&st->clamped, clamped ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------------
@@ -534,36 +568,43 @@ __global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* 
                                               DevStats* st) {
   __shared__ uint32_t s_warp[8];
   __shared__ unsigned long long s_base;
-  const int tid = threadIdx.x;
-  const int64_t base = (int64_t)blockIdx.x * kEmitTile;
-  uint32_t masks = 0;  // 7 bits per item
-  uint32_t n_frozen = 0, n_spawn = 0, n_lost = 0, n_clip = 0;
-#pragma unroll 1
-  for (int it = 0; it < kEmitItems; ++it) {
-    const int64_t j = base + it * 256 + tid;
-    const bool valid = j < n;
-    const Rec r = valid ? rec_unpack(__ldg(rs + j)) : Rec{};
-    const int32_t sslot = (valid && r.cross && r.state == ST_ACTIVE) ? __ldg(site_slot + j) : -1;
-    const uint32_t m =
-        emit_decide<BATCH>(P, S, r, valid, sslot, C, R, n_frozen, n_spawn, n_lost, n_clip);
-    masks |= m << (7 * it);
+  if constexpr (BATCH) {
+    n = (int64_t)st->n_live;
+    S.parity = (int)(st->step & 1ull);
   }
-  uint32_t cnt = 0;
-#pragma unroll
-  for (int it = 0; it < kEmitItems; ++it) cnt += __popc((masks >> (7 * it)) & 0x7fu);
-  uint32_t tot;
-  const uint32_t ofs = bscan256(cnt, s_warp, tot);
-  if (tid == 0) s_base = tot ? atomicAdd(&st->n_out, (unsigned long long)tot) : 0ull;
-  __syncthreads();
-  unsigned long long o = s_base + ofs;
+  const int tid = threadIdx.x;
+  uint32_t n_frozen = 0, n_spawn = 0, n_lost = 0, n_clip = 0;
+  for (int64_t base = (int64_t)blockIdx.x * kEmitTile; base < n;
+       base += (int64_t)gridDim.x * kEmitTile) {
+    uint32_t masks = 0;  // 7 bits per item
 #pragma unroll 1
-  for (int it = 0; it < kEmitItems; ++it) {
-    const uint32_t m = (masks >> (7 * it)) & 0x7fu;
-    if (!m) continue;
-    const int64_t j = base + it * 256 + tid;
-    const Rec r = rec_unpack(__ldg(rs + j));
-    emit_write<BATCH, K>(P, r, m, o, rout, keys, vals, cap, parent, j);
-    o += __popc(m);
+    for (int it = 0; it < kEmitItems; ++it) {
+      const int64_t j = base + it * 256 + tid;
+      const bool valid = j < n;
+      const Rec r = valid ? rec_unpack(__ldg(rs + j)) : Rec{};
+      const int32_t sslot =
+          (valid && r.cross && r.state == ST_ACTIVE) ? __ldg(site_slot + j) : -1;
+      const uint32_t m =
+          emit_decide<BATCH>(P, S, r, valid, sslot, C, R, n_frozen, n_spawn, n_lost, n_clip);
+      masks |= m << (7 * it);
+    }
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int it = 0; it < kEmitItems; ++it) cnt += __popc((masks >> (7 * it)) & 0x7fu);
+    uint32_t tot;
+    const uint32_t ofs = bscan256(cnt, s_warp, tot);
+    if (tid == 0) s_base = tot ? atomicAdd(&st->n_out, (unsigned long long)tot) : 0ull;
+    __syncthreads();
+    unsigned long long o = s_base + ofs;  // s_base is rewritten only after the next scan
+#pragma unroll 1
+    for (int it = 0; it < kEmitItems; ++it) {
+      const uint32_t m = (masks >> (7 * it)) & 0x7fu;
+      if (!m) continue;
+      const int64_t j = base + it * 256 + tid;
+      const Rec r = rec_unpack(__ldg(rs + j));
+      emit_write<BATCH, K>(P, r, m, o, rout, keys, vals, cap, parent, j);
+      o += __popc(m);
+    }
   }
   warp_add(&st->n_frozen, n_frozen);
   warp_add(&st->spawned, n_spawn);
@@ -760,11 +801,14 @@ __global__ void __launch_bounds__(256) k_nuc_activate(Params P, const float4* __
   }
 }
 
-// per-run step constants of a batch: T_L - T0 - Tdot t at t_n and t_{n+1}, every
-// product and difference rounded once (the host computes a single run's the same way)
-__global__ void k_run_step(Geo* runs, const double2* th, int nruns, long long n, double dt) {
+// per-run step constants of a batch: T_L - T0 - Tdot t at t_n and t_{n+1} for the
+// step n held on the device, every product and difference rounded once (the host
+// computes a single run's values the same way)
+__global__ void k_run_step(Geo* runs, const double2* th, int nruns, const DevStats* st,
+                           double dt) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nruns) return;
+  const long long n = (long long)st->step;
   const double2 q = th[r];
   const double t0 = __dmul_rn((double)n, dt), t1 = __dmul_rn((double)(n + 1), dt);
   runs[r].dT_base = __double2float_rn(__dsub_rn(q.x, __dmul_rn(q.y, t0)));
@@ -791,9 +835,15 @@ __global__ void __launch_bounds__(256) k_run_counts(Params P, const int4* __rest
     if (s_c[i]) atomicAdd(counts + i, (unsigned long long)s_c[i]);
 }
 
-__global__ void k_finalize(DevStats* st, int64_t cap) {
+// end of a step: live count for the next step; a batch also advances its step and
+// cell-table stamp counters on the device
+__global__ void k_finalize(DevStats* st, int64_t cap, int counters) {
   unsigned long long nl = st->n_out;
   st->n_live = nl > (unsigned long long)cap ? (unsigned long long)cap : nl;
+  if (counters) {
+    st->step += 1;
+    st->stamp += 1;
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -1012,6 +1062,13 @@ __global__ void k_build_sa(Params P, const float* __restrict__ x3, const int32_t
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// grid of a device-sized (batch) launch: ctas_total CTAs (the launch configuration's
+// CTAs per SM times the SM count), fewer if n_max items need fewer
+inline unsigned persistent(int64_t n_max, int per_cta, int ctas_total) {
+  const int64_t need = (n_max + per_cta - 1) / per_cta;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, ctas_total));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -1029,27 +1086,28 @@ void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* 
 
 void launch_build(bool batch, const Params& P, const void* skeys, const uint32_t* svals,
                   const int4* rin, int4* rout, float4* pos4, uint4* tab, uint32_t stamp,
-                  int64_t n, uint64_t key_end, uint32_t* err, cudaStream_t st) {
+                  int64_t n, uint64_t key_end, uint32_t* act, DevStats* dst, cudaStream_t st) {
   if (n <= 0) return;
   if (batch)
-    k_build<true, uint64_t><<<blocks(n), 256, 0, st>>>(P, (const uint64_t*)skeys, svals, rin,
-                                                       rout, pos4, tab, stamp, n, key_end, err);
+    k_build<true, uint64_t><<<persistent(n, 256, P.launch.build_ctas), 256, 0, st>>>(
+        P, (const uint64_t*)skeys, svals, rin, rout, pos4, tab, stamp, n, key_end, act, dst);
   else
     k_build<false, uint32_t><<<blocks(n), 256, 0, st>>>(P, (const uint32_t*)skeys, svals, rin,
                                                         rout, pos4, tab, stamp, n,
-                                                        (uint32_t)key_end, err);
+                                                        (uint32_t)key_end, act, dst);
 }
 
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
-                    const Claims& C, int32_t* site_slot, DevStats* dst, cudaStream_t st) {
+                    const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
+                    cudaStream_t st) {
   if (n <= 0) return;
   if (batch)
-    k_advance<true, uint64_t><<<blocks(n), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, C, site_slot, dst);
+    k_advance<true, uint64_t><<<persistent(n, 256, P.launch.advance_ctas), 256, 0, st>>>(
+        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst);
   else
     k_advance<false, uint32_t><<<blocks(n), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, C, site_slot, dst);
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst);
 }
 
 int64_t emit_tiles(int64_t n) { return (n + kEmitTile - 1) / kEmitTile; }
@@ -1068,9 +1126,8 @@ void launch_emit(bool batch, const Params& P, const StepArgs& S, const int4* rs,
   const int64_t nt = emit_tiles(n);
   if (nt == 0) return;
   if (batch)
-    k_emit<true, uint64_t><<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout,
-                                                         (uint64_t*)keys, vals, cap, C, R,
-                                                         parent, dst);
+    k_emit<true, uint64_t><<<persistent(n, kEmitTile, P.launch.emit_ctas), 256, 0, st>>>(
+        P, S, rs, site_slot, n, rout, (uint64_t*)keys, vals, cap, C, R, parent, dst);
   else
     k_emit<false, uint32_t><<<(unsigned)nt, 256, 0, st>>>(P, S, rs, site_slot, n, rout,
                                                           (uint32_t*)keys, vals, cap, C, R,
@@ -1097,9 +1154,9 @@ void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, co
                                 vals, cap, C, R, dst);
 }
 
-void launch_run_step(Geo* runs, const double2* th, int nruns, int64_t n, double dt,
+void launch_run_step(Geo* runs, const double2* th, int nruns, const DevStats* dst, double dt,
                      cudaStream_t st) {
-  k_run_step<<<(nruns + 255) / 256, 256, 0, st>>>(runs, th, nruns, (long long)n, dt);
+  k_run_step<<<(nruns + 255) / 256, 256, 0, st>>>(runs, th, nruns, dst, dt);
 }
 
 void launch_run_counts(const Params& P, const int4* rec, int64_t n, int nruns,
@@ -1109,8 +1166,8 @@ void launch_run_counts(const Params& P, const int4* rec, int64_t n, int nruns,
   k_run_counts<<<nb, 256, 0, st>>>(P, rec, n, nruns, counts);
 }
 
-void launch_finalize(DevStats* dst, int64_t cap, cudaStream_t st) {
-  k_finalize<<<1, 1, 0, st>>>(dst, cap);
+void launch_finalize(DevStats* dst, int64_t cap, bool batch, cudaStream_t st) {
+  k_finalize<<<1, 1, 0, st>>>(dst, cap, batch ? 1 : 0);
 }
 
 void launch_append(const int4* src, int64_t m, int4* rout, int64_t base, cudaStream_t st) {

@@ -9,12 +9,16 @@ namespace gp {
 // (uint32 cell keys)
 void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* keys,
                  uint32_t* vals, cudaStream_t st);
+// the build lists the sorted indices of the ACTIVE particles in act (count in
+// dst->n_act, which must be zero before the build); the advance runs over that list.
+// A batch reads its counts, stamp and step from dst and uses persistent grids.
 void launch_build(bool batch, const Params& P, const void* skeys, const uint32_t* svals,
                   const int4* rin, int4* rout, float4* pos4, uint4* tab, uint32_t stamp,
-                  int64_t n, uint64_t key_end, uint32_t* err, cudaStream_t st);
+                  int64_t n, uint64_t key_end, uint32_t* act, DevStats* dst, cudaStream_t st);
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
-                    const Claims& C, int32_t* site_slot, DevStats* dst, cudaStream_t st);
+                    const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
+                    cudaStream_t st);
 int64_t emit_tiles(int64_t n);
 void launch_link_reached(bool batch, const Params& P, const Reached& R,
                          unsigned long long* linked, int sms, cudaStream_t st);
@@ -37,8 +41,8 @@ void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, co
                      int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,
                      cudaStream_t st);
-void launch_finalize(DevStats* dst, int64_t cap, cudaStream_t st);
-void launch_run_step(Geo* runs, const double2* th, int nruns, int64_t n, double dt,
+void launch_finalize(DevStats* dst, int64_t cap, bool batch, cudaStream_t st);
+void launch_run_step(Geo* runs, const double2* th, int nruns, const DevStats* dst, double dt,
                      cudaStream_t st);
 void launch_run_counts(const Params& P, const int4* rec, int64_t n, int nruns,
                        unsigned long long* counts, cudaStream_t st);

@@ -11,6 +11,8 @@
 // leave as contiguous runs.  Tiles are numbered by an atomic ticket, so a CTA
 // only ever waits for tiles whose CTAs are already resident; every wait is
 // bounded and reports ERR_TIMEOUT instead of spinning forever.
+#include <algorithm>
+
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -21,35 +23,70 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 
-template <class K>
-__global__ void __launch_bounds__(256) k_hist(const K* __restrict__ keys, int64_t n, int npass,
-                                              uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[kSortMaxPasses * 256];
-  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) sh[i] = 0;
+// Counts every digit of every pass: 32-bit keys, four per 16-byte load.  With
+// n_dev the key count is read on the device.
+__global__ void __launch_bounds__(256) k_hist32(const uint32_t* __restrict__ keys, int64_t n,
+                                                const unsigned long long* n_dev, int npass,
+                                                uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[4 * 256];
+  if (n_dev) n = (int64_t)*n_dev;
+  for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int V = 16 / sizeof(K);  // keys per 16-byte load
-  const int64_t nv = n / V;
-  const uint4* kv = reinterpret_cast<const uint4*>(keys);
-  const int lane = threadIdx.x & 31;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-    const uint4 v = __ldg(kv + i);
-    K kk[V];
-    memcpy(kk, &v, 16);
+  const int64_t n4 = n >> 2;
+  const uint4* k4 = reinterpret_cast<const uint4*>(keys);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    uint4 v = __ldg(k4 + i);
+    uint32_t kk[4] = {v.x, v.y, v.z, v.w};
     const uint32_t m = __activemask();
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int q = 0; q < V; ++q)
+    for (int q = 0; q < 4; ++q)
       for (int p = 0; p < npass; ++p) {
         // nearly sorted keys share digits across a warp: one shared atomic per
         // distinct digit instead of one per lane
+        const uint32_t d = (kk[q] >> (8 * p)) & 255u;
+        const uint32_t peers = __match_any_sync(m, d);
+        if (lane == __ffs(peers) - 1) atomicAdd(&sh[p * 256 + d], (uint32_t)__popc(peers));
+      }
+  }
+  for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint32_t k = keys[i];
+    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// the same for 64-bit keys (up to kSortMaxPasses digits), two per 16-byte load
+__global__ void __launch_bounds__(256) k_hist64(const uint64_t* __restrict__ keys, int64_t n,
+                                                const unsigned long long* n_dev, int npass,
+                                                uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[kSortMaxPasses * 256];
+  if (n_dev) n = (int64_t)*n_dev;
+  for (int i = threadIdx.x; i < kSortMaxPasses * 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n2 = n >> 1;
+  const uint4* k2 = reinterpret_cast<const uint4*>(keys);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    uint4 v = __ldg(k2 + i);
+    uint64_t kk[2] = {(uint64_t)v.x | ((uint64_t)v.y << 32), (uint64_t)v.z | ((uint64_t)v.w << 32)};
+    const uint32_t m = __activemask();
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      for (int p = 0; p < npass; ++p) {
         const uint32_t d = (uint32_t)(kk[q] >> (8 * p)) & 255u;
         const uint32_t peers = __match_any_sync(m, d);
         if (lane == __ffs(peers) - 1) atomicAdd(&sh[p * 256 + d], (uint32_t)__popc(peers));
       }
   }
-  for (int64_t i = nv * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const K k = keys[i];
-    for (int p = 0; p < npass; ++p) atomicAdd(&sh[p * 256 + ((uint32_t)(k >> (8 * p)) & 255u)], 1u);
+  for (int64_t i = (n2 << 1) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t k = keys[i];
+    for (int p = 0; p < npass; ++p)
+      atomicAdd(&sh[p * 256 + ((uint32_t)(k >> (8 * p)) & 255u)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npass * 256; i += blockDim.x)
@@ -86,8 +123,8 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t* s_
 template <class K>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
-    uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist,
-    uint32_t* status, uint32_t* ticket, uint32_t* err) {
+    uint32_t* __restrict__ vout, int64_t n, const unsigned long long* n_dev, int shift,
+    const uint32_t* __restrict__ hist, uint32_t* status, uint32_t* ticket, uint32_t* err) {
   constexpr int W = kSortThreads / 32;
   constexpr int kItems = SortTile<K>::items;
   constexpr int kTile = SortTile<K>::tile;
@@ -99,137 +136,152 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
   __shared__ uint32_t s_tmp[8];
   __shared__ uint32_t s_tile;
 
+  if (n_dev) n = (int64_t)*n_dev;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(ticket, 1u);
-  for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int64_t base = (int64_t)tile * kTile;
+  // a CTA takes tiles in ticket order until none is left (one tile per CTA when the
+  // grid covers all tiles; a persistent grid otherwise)
+  while (true) {
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if ((int64_t)tile >= ntiles) break;
+    const int64_t base = (int64_t)tile * kTile;
 
-  // only keys and ranks live in registers (values are read at the scatter, digits
-  // recomputed), which keeps the kernel at four CTAs per SM
-  K k[kItems];
-  uint32_t rk[kItems];
-  const int64_t wbase = base + (int64_t)warp * kItems * 32;
-  const int64_t nvalid = n - wbase;  // items of this warp's run that exist
+    // only keys and ranks live in registers (values are read at the scatter, digits
+    // recomputed), which keeps the kernel at four CTAs per SM
+    K k[kItems];
+    uint32_t rk[kItems];
+    const int64_t wbase = base + (int64_t)warp * kItems * 32;
+    const int64_t nvalid = n - wbase;  // items of this warp's run that exist
 #pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    int64_t idx = wbase + r * 32 + lane;
-    k[r] = idx < n ? kin[idx] : ~K(0);
-  }
-  const uint32_t lt_mask = (1u << lane) - 1u;
-#pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    const int d = (r * 32 + lane) < nvalid ? (int)((uint32_t)(k[r] >> shift) & 255u) : 256;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t before = 0;
-    if (d < 256) before = s_whist[warp][d];
-    rk[r] = before + __popc(peers & lt_mask);
-    __syncwarp();
-    if (d < 256 && lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-
-  // per digit (one thread each): warp-exclusive offsets and the tile count
-  const int d = tid;
-  uint32_t cnt = 0;
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    uint32_t c = s_whist[w][d];
-    s_whist[w][d] = cnt;
-    cnt += c;
-  }
-  const uint32_t start = block_excl_scan_256(cnt, s_tmp);
-  s_start[d] = start;
-
-  // global digit base: exclusive scan of the whole-array histogram
-  const uint32_t dbase = block_excl_scan_256(hist[d], s_tmp);
-
-  // decoupled look-back over preceding tiles, digit d
-  uint32_t* my = status + (size_t)tile * 256 + d;
-  uint32_t excl = 0;
-  if (tile == 0) {
-    atomicExch(my, kFlagInc | cnt);
-  } else {
-    atomicExch(my, kFlagAgg | cnt);
-    int64_t pred = (int64_t)tile - 1;
-    uint32_t spins = 0;
-    while (pred >= 0) {
-      uint32_t s = *((volatile uint32_t*)(status + (size_t)pred * 256 + d));
-      uint32_t flag = s & ~kValMask;
-      if (flag == 0u) {
-        if (++spins > kSpinLimit) {
-          atomicOr(err, ERR_TIMEOUT);
-          break;
-        }
-        continue;
-      }
-      excl += s & kValMask;
-      if (flag == kFlagInc) break;
-      --pred;
+    for (int r = 0; r < kItems; ++r) {
+      int64_t idx = wbase + r * 32 + lane;
+      k[r] = idx < n ? kin[idx] : ~K(0);
     }
-    atomicExch(my, kFlagInc | ((excl + cnt) & kValMask));
-  }
-  s_gofs[d] = dbase + excl - start;  // wraps modulo 2^32; the sum below is exact
-  __syncthreads();
-
+    const uint32_t lt_mask = (1u << lane) - 1u;
 #pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    const int64_t idx = wbase + r * 32 + lane;
-    if (idx < n) {
-      const uint32_t d = (uint32_t)(k[r] >> shift) & 255u;
-      const uint32_t lp = s_start[d] + s_whist[warp][d] + rk[r];
-      s_keys[lp] = k[r];
-      s_vals[lp] = __ldg(vin + idx);
+    for (int r = 0; r < kItems; ++r) {
+      const int d = (r * 32 + lane) < nvalid ? (int)((uint32_t)(k[r] >> shift) & 255u) : 256;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = 0;
+      if (d < 256) before = s_whist[warp][d];
+      rk[r] = before + __popc(peers & lt_mask);
+      __syncwarp();
+      if (d < 256 && lane == __ffs(peers) - 1) s_whist[warp][d] = before + __popc(peers);
+      __syncwarp();
     }
-  }
-  __syncthreads();
-  const int64_t rem = n - base;
-  const int tn = rem < kTile ? (int)rem : kTile;
-  for (int i = tid; i < tn; i += kSortThreads) {
-    const K key = s_keys[i];
-    uint32_t g = s_gofs[(uint32_t)(key >> shift) & 255u] + (uint32_t)i;
-    if ((int64_t)g < n) {
-      kout[g] = key;
-      vout[g] = s_vals[i];
+    __syncthreads();
+
+    // per digit (one thread each): warp-exclusive offsets and the tile count
+    const int d = tid;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint32_t c = s_whist[w][d];
+      s_whist[w][d] = cnt;
+      cnt += c;
+    }
+    const uint32_t start = block_excl_scan_256(cnt, s_tmp);
+    s_start[d] = start;
+
+    // global digit base: exclusive scan of the whole-array histogram
+    const uint32_t dbase = block_excl_scan_256(hist[d], s_tmp);
+
+    // decoupled look-back over preceding tiles, digit d
+    uint32_t* my = status + (size_t)tile * 256 + d;
+    uint32_t excl = 0;
+    if (tile == 0) {
+      atomicExch(my, kFlagInc | cnt);
     } else {
-      atomicOr(err, ERR_TIMEOUT);
+      atomicExch(my, kFlagAgg | cnt);
+      int64_t pred = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      while (pred >= 0) {
+        uint32_t s = *((volatile uint32_t*)(status + (size_t)pred * 256 + d));
+        uint32_t flag = s & ~kValMask;
+        if (flag == 0u) {
+          if (++spins > kSpinLimit) {
+            atomicOr(err, ERR_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        excl += s & kValMask;
+        if (flag == kFlagInc) break;
+        --pred;
+      }
+      atomicExch(my, kFlagInc | ((excl + cnt) & kValMask));
     }
+    s_gofs[d] = dbase + excl - start;  // wraps modulo 2^32; the sum below is exact
+    __syncthreads();
+
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int64_t idx = wbase + r * 32 + lane;
+      if (idx < n) {
+        const uint32_t d = (uint32_t)(k[r] >> shift) & 255u;
+        const uint32_t lp = s_start[d] + s_whist[warp][d] + rk[r];
+        s_keys[lp] = k[r];
+        s_vals[lp] = __ldg(vin + idx);
+      }
+    }
+    __syncthreads();
+    const int64_t rem = n - base;
+    const int tn = rem < kTile ? (int)rem : kTile;
+    for (int i = tid; i < tn; i += kSortThreads) {
+      const K key = s_keys[i];
+      uint32_t g = s_gofs[(uint32_t)(key >> shift) & 255u] + (uint32_t)i;
+      if ((int64_t)g < n) {
+        kout[g] = key;
+        vout[g] = s_vals[i];
+      } else {
+        atomicOr(err, ERR_TIMEOUT);
+      }
+    }
+    __syncthreads();  // the shared arrays are reused by the next tile
   }
 }
 
 }  // namespace
 
-size_t radix_status_words(int64_t n) {
-  // the 64-bit tile is the smaller one
-  int64_t tiles = (n + SortTile<uint64_t>::tile - 1) / SortTile<uint64_t>::tile;
+size_t radix_status_words(int64_t n, int key_bytes) {
+  const int tile = key_bytes == 8 ? SortTile<uint64_t>::tile : SortTile<uint32_t>::tile;
+  const int64_t tiles = (n + tile - 1) / tile;
   return (size_t)(tiles < 1 ? 1 : tiles) * 256;
 }
 
 template <class K>
 int radix_sort(const SortBufs& B, int64_t n, int nbits, cudaStream_t st) {
-  if (n <= 1 || nbits <= 0) return 0;
+  const bool dev = B.n_dev != nullptr;  // n is then an upper bound only
+  if ((!dev && n <= 1) || nbits <= 0) return 0;
   const int npass = (nbits + 7) / 8;
   if (npass > kSortMaxPasses || 8 * (int)sizeof(K) < nbits) return -1;
   constexpr int kTile = SortTile<K>::tile;
-  const int64_t tiles = (n + kTile - 1) / kTile;
+  const int64_t nmax = dev ? B.max_n : n;
+  const int64_t tiles = (nmax + kTile - 1) / kTile;
+  // one tile per CTA, or a persistent grid of four resident CTAs per SM
+  const int64_t grid = dev ? std::min<int64_t>(tiles, 4 * (int64_t)B.sms) : tiles;
   cudaMemsetAsync(B.hist, 0, sizeof(uint32_t) * 256 * npass, st);
   cudaMemsetAsync(B.ticket, 0, sizeof(uint32_t) * kSortMaxPasses, st);
-  int hblocks = (int)((n / 4 + 255) / 256);
+  int hblocks = (int)((nmax / 4 + 255) / 256);
   if (hblocks > B.sms * 8) hblocks = B.sms * 8;
   if (hblocks < 1) hblocks = 1;
   K* keys[2] = {static_cast<K*>(B.keys[0]), static_cast<K*>(B.keys[1])};
   if (B.prof) B.prof->begin(K_HIST);
-  k_hist<K><<<hblocks, 256, 0, st>>>(keys[0], n, npass, B.hist);
+  if constexpr (sizeof(K) == 4)
+    k_hist32<<<hblocks, 256, 0, st>>>(keys[0], n, B.n_dev, npass, B.hist);
+  else
+    k_hist64<<<hblocks, 256, 0, st>>>(keys[0], n, B.n_dev, npass, B.hist);
   if (B.prof) B.prof->end(K_HIST, (double)n);
   int cur = 0;
   for (int p = 0; p < npass; ++p) {
     cudaMemsetAsync(B.status, 0, sizeof(uint32_t) * 256 * (size_t)tiles, st);
     if (B.prof) B.prof->begin(K_ONESWEEP);
-    k_onesweep<K><<<(unsigned)tiles, kSortThreads, 0, st>>>(
-        keys[cur], B.vals[cur], keys[cur ^ 1], B.vals[cur ^ 1], n, 8 * p, B.hist + 256 * p,
-        B.status, B.ticket + p, B.err);
+    k_onesweep<K><<<(unsigned)grid, kSortThreads, 0, st>>>(
+        keys[cur], B.vals[cur], keys[cur ^ 1], B.vals[cur ^ 1], n, B.n_dev, 8 * p,
+        B.hist + 256 * p, B.status, B.ticket + p, B.err);
     if (B.prof) B.prof->end(K_ONESWEEP, (double)n);
     cur ^= 1;
   }

@@ -60,6 +60,11 @@ class gp_stats_t(C.Structure):
     _fields_ = [(f, C.c_int64) for f in STATS_FIELDS] + [("reserved", C.c_int64 * 5)]
 
 
+class gp_launch_config(C.Structure):
+    _fields_ = [("build_ctas_per_sm", C.c_int32), ("advance_ctas_per_sm", C.c_int32),
+                ("emit_ctas_per_sm", C.c_int32), ("graph_steps", C.c_int32)]
+
+
 class gp_kernel_prof(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
                 ("units", C.c_double), ("bytes_per_unit", C.c_double)]
@@ -113,6 +118,9 @@ SIGNATURES = {
     "gp_run_grain_map": (C.c_int, [_P, C.c_int32, C.POINTER(gp_voxel_grid), _P, C.c_int32]),
     "gp_run_counts": (C.c_int, [_P, C.c_int32, _P, _P]),
     "gp_grain_table": (C.c_int, [_P, C.c_int64, _P, _P, C.POINTER(C.c_int64)]),
+    "gp_get_launch_config": (C.c_int, [_P, C.POINTER(gp_launch_config)]),
+    "gp_set_launch_config": (C.c_int, [_P, C.POINTER(gp_launch_config)]),
+    "gp_autotune": (C.c_int, [_P, C.c_int32, C.POINTER(gp_launch_config)]),
 }
 GP_STATIC_SCRATCH_MAX_POINTS = 262144
 
@@ -424,6 +432,24 @@ class Batch(Sim):
         res = np.zeros((int(n[2]), int(n[1]), int(n[0])), np.int32)
         self._check(load().gp_run_grain_map(self._h, int(run), C.byref(g), _ptr(res), 0))
         return res
+
+    def gp_get_launch_config(self) -> dict:
+        cfg = gp_launch_config()
+        self._check(load().gp_get_launch_config(self._h, C.byref(cfg)))
+        return {f: int(getattr(cfg, f)) for f, _ in gp_launch_config._fields_}
+
+    def gp_set_launch_config(self, **kw):
+        cfg = gp_launch_config()
+        cur = self.gp_get_launch_config()
+        cur.update(kw)
+        for f, v in cur.items():
+            setattr(cfg, f, int(v))
+        self._check(load().gp_set_launch_config(self._h, C.byref(cfg)))
+
+    def gp_autotune(self, trial_steps=2) -> dict:
+        cfg = gp_launch_config()
+        self._check(load().gp_autotune(self._h, int(trial_steps), C.byref(cfg)))
+        return {f: int(getattr(cfg, f)) for f, _ in gp_launch_config._fields_}
 
     def gp_run_counts(self):
         live = np.zeros(self.nruns, np.int64)

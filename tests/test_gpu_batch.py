@@ -108,3 +108,47 @@ def test_batch_errors():
         b.gp_set_thermal_grid(np.zeros((2, 2, 2), np.float32), (0, 0, 0), (1, 1, 1))
     with pytest.raises(native.GPError):
         b.gp_tape_begin()
+
+
+def _state(b):
+    p = _canon(b.gp_get_particles())
+    st = b.gp_stats()
+    return p, {k: st[k] for k in ("n_live", "n_active", "n_reached", "particle_steps",
+                                  "n_spawned", "n_nucleated", "n_clipped", "n_frozen_new")}
+
+
+def test_graphs_launch_configs_and_autotuner_keep_results_identical():
+    """The batch step sizes every launch on the device; replaying it from captured
+    CUDA graphs, with other persistent grids, or with the autotuner's choice gives
+    the same particles and counters, bit for bit."""
+    native.load()
+    runs = small_ensemble(n_runs=4, steps=300)
+    ref = ensemble.batch_from(runs, capacity=2_000_000, reached_capacity=6_000_000)
+    ref.gp_step(300)
+    p0, s0 = _state(ref)
+    ref.close()
+    assert s0["n_nucleated"] > 0 and s0["n_live"] > 10000
+
+    g = ensemble.batch_from(runs, capacity=2_000_000, reached_capacity=6_000_000)
+    g.gp_set_launch_config(build_ctas_per_sm=2, advance_ctas_per_sm=1, emit_ctas_per_sm=3,
+                           graph_steps=25)
+    g.gp_step(130)          # 5 graphs of 25 steps and one of 5
+    g.gp_step(170)
+    p1, s1 = _state(g)
+    g.close()
+
+    t = ensemble.batch_from(runs, capacity=2_000_000, reached_capacity=6_000_000)
+    t.gp_step(100)
+    cfg = t.gp_autotune(trial_steps=2)         # 8 candidates x 2 real steps
+    assert t.gp_stats()["step"] == 116
+    t.gp_set_launch_config(graph_steps=16)
+    t.gp_step(184)
+    p2, s2 = _state(t)
+    t.close()
+    assert cfg["build_ctas_per_sm"] in (4, 8) and cfg["advance_ctas_per_sm"] in (2, 4)
+
+    for p, s in ((p1, s1), (p2, s2)):
+        assert s == s0
+        for k in ("grain", "site", "dir", "state"):
+            assert np.array_equal(p[k], p0[k]), k
+        assert np.array_equal(p["ell"].view(np.uint32), p0["ell"].view(np.uint32))

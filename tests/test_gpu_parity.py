@@ -83,7 +83,12 @@ def test_contact_bit_exact(n, ng, seed):
 # ----------------------------------------------------------------------------------
 # a3-a6: single grain in a uniform melt (Sec. 2.1.2 octahedron), GPU vs closed form
 # ----------------------------------------------------------------------------------
-@pytest.mark.parametrize("a,b,dT", [((1e-5,), (2.0,), 4.3), ((8.315e-6, 9.628e-7), (2.49, 3.622), 3.1)])
+@pytest.mark.parametrize("a,b,dT", [
+    ((1e-5,), (2.0,), 4.3),                           # Eq. (1), integer exponent
+    ((8.26e-6, 8.18e-5), (2.0, 3.0), 1.7),            # Eq. (2), Sec. 3.3 coefficients
+    ((8.315e-6, 9.628e-7), (2.49, 3.622), 3.1),       # Eq. (2), Sec. 4.1 coefficients
+    ((1.834e-4,), (2.282,), 0.6),                     # Eq. (1), Sec. 3.4 coefficients
+])
 def test_single_grain_octahedron_on_gpu(a, b, dT):
     v = sum(ai * dT ** bi for ai, bi in zip(a, b))
     h = 2e-6
@@ -111,6 +116,73 @@ def test_single_grain_octahedron_on_gpu(a, b, dT):
     assert st["particle_steps"] == ost["particle_steps"]
     assert st["n_reached"] == ost["reached"] + 1   # + the nucleus site
     assert st["error_flags"] == 0
+
+
+# ----------------------------------------------------------------------------------
+# Single grain in a temperature gradient (Sec. 3.1): a = 1e-4, b = 2, dT0 = 2 K,
+# cooling 0.1 K/s, G = 250 K/m along z, Euler angles (20, 20, 20), lambda_0 = 200 um,
+# 5 s.  Each primary tip moves along its rotated <100> axis d with
+# dr/dt = a dT(c + r d, t)^b; the GPU's binary32 Euler tips must match the FP64
+# oracle, stay within the Euler error of an RK4 solution of that ODE, and converge
+# to it at first order when dt halves.
+# ----------------------------------------------------------------------------------
+def _rk4_tip(dz, a, b, dT0, Tdot, G, t_end, nsub=20000):
+    def f(t, r):
+        dT = dT0 - G * dz * r - Tdot * t
+        return a * dT ** b if dT > 0 else 0.0
+    r, t = 0.0, 0.0
+    hs = t_end / nsub
+    for _ in range(nsub):
+        k1 = f(t, r)
+        k2 = f(t + hs / 2, r + hs / 2 * k1)
+        k3 = f(t + hs / 2, r + hs / 2 * k2)
+        k4 = f(t + hs, r + hs * k3)
+        r += hs / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        t += hs
+    return r
+
+
+def _gradient_case(dt, t_end=5.0):
+    a, b, dT0, Tdot, G, T_L, h, half = 1e-4, 2.0, 2.0, -0.1, 250.0, 1000.0, 200e-6, 4e-3
+    c = np.array([[half, half, half]])
+    w = inputs.Workload(name="gradient", lo=(0, 0, 0), hi=(2 * half,) * 3, h=h, dt=dt, a=(a,),
+                        b=(b,), T_L=T_L, steps=int(round(t_end / dt)), seeds=c,
+                        quats=inputs.euler_zxz_to_quaternion(20.0, 20.0, 20.0)[None],
+                        analytic=dict(T0=T_L - dT0, G=(0.0, 0.0, G), xref=tuple(c[0]),
+                                      Tdot=Tdot))
+    return w, (a, b, dT0, Tdot, G)
+
+
+def _tips(p, c, R):
+    out = []
+    for k in range(6):
+        ax, sg = k // 2, (1 if k % 2 == 0 else -1)
+        others = [q for q in range(3) if q != ax]
+        m = ((p["dir"] == k) & (p["site"][:, ax] * sg >= 0)
+             & (p["site"][:, others] == 0).all(axis=1))
+        assert m.sum() == 1
+        out.append(np.linalg.norm(p["x"][m][0].astype(np.float64) - c))
+    return np.array(out)
+
+
+def test_gradient_single_grain_on_gpu_matches_oracle_and_ode():
+    tips = {}
+    for dt in (0.01, 0.005):
+        w, (a, b, dT0, Tdot, G) = _gradient_case(dt)
+        s = sim_from(w, capacity=400000)
+        s.gp_step(w.steps)
+        o = oracle_from(w)
+        o.step(w.steps)
+        c, R = o.grain(0)
+        tg, to = _tips(s.gp_get_particles(), c, R), _tips(o.particles(), c, R)
+        assert np.allclose(tg, to, rtol=1e-5), (tg, to)
+        assert keyset(s.gp_get_particles()) == keyset(o.particles())
+        tips[dt] = tg
+    ref = np.array([_rk4_tip((1 if k % 2 == 0 else -1) * R[2, k // 2], a, b, dT0, Tdot, G, 5.0)
+                    for k in range(6)])
+    e1, e2 = np.abs(tips[0.01] - ref), np.abs(tips[0.005] - ref)
+    assert (e1 / ref).max() < 5e-3
+    assert ((e1 / e2 > 1.8) & (e1 / e2 < 2.2)).all(), e1 / e2
 
 
 # ----------------------------------------------------------------------------------
