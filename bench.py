@@ -265,20 +265,45 @@ def adjoint_cost(dev):
             "forward_with_tape_plus_backward_ms": tg * 1e3, "cost_ratio": tg / tp}
 
 
-def batch_ensemble(dev, serial_every=8, graph_steps=20):
+def run_cost(w) -> float:
+    """Relative work of one ensemble run for sharding: the envelope area grows with
+    the growth distance squared (v ~ dT^2 with dT ~ Tdot t) and the number of
+    grains with the volume, so cost ~ L^3 Tdot^4 (plus a constant per run)."""
+    L = w.hi[0] - w.lo[0]
+    return (L * 1e3) ** 3 * abs(w.analytic["Tdot"]) ** 4 + 1.0
+
+
+def shard_runs(costs, world):
+    """Longest-processing-time assignment of runs to ranks: run indices per rank."""
+    order = sorted(range(len(costs)), key=lambda i: -costs[i])
+    loads, parts = [0.0] * world, [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: loads[k])
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def batch_ensemble(dev, rank=0, world=1, serial_every=8, graph_steps=20):
     """The 256-run columnar-to-equiaxed ensemble (400 steps of 1 ms) in one batch
-    context: every kernel of a step covers all runs, sized on the device, and the
-    steps replay from CUDA graphs of graph_steps steps with the launch configuration
-    the autotuner picked on a rehearsal of the same ensemble.  Compared with the
-    same runs each in its own single-run context, one after the other (every
-    serial_every-th run, scaled to the ensemble).  All variants give identical
-    particles (batch parity tests); set-up is outside every timing."""
+    context per GPU: every kernel of a step covers all runs of the context, sized
+    on the device, and the steps replay from CUDA graphs of graph_steps steps with
+    the launch configuration the autotuner picked on a rehearsal of the same runs.
+    With several ranks the runs are sharded by estimated work (no collective: the
+    runs are independent) and the time is the slowest rank's.  On one GPU it is
+    compared with the same runs each in its own single-run context, one after the
+    other (every serial_every-th run, scaled to the ensemble).  All variants give
+    identical particles (batch parity tests); set-up is outside every timing."""
     import torch
     from paper_2504_12858_gb300 import ensemble, inputs, native
-    runs = inputs.cet_runs()
+    runs_all = inputs.cet_runs()
+    mine = shard_runs([run_cost(w) for w in runs_all], world)[rank]
+    runs = [runs_all[i] for i in mine]
     steps = runs[0].steps
-    mem = dict(capacity=int(3.2e7), reached_capacity=int(2.6e8), claim_blocks=int(2.4e6),
-               device=dev)
+    f = len(runs) / len(runs_all) * 1.5 if world > 1 else 1.0
+    mem = dict(capacity=int(3.2e7 * min(f, 1.0)) + 100000,
+               reached_capacity=int(2.6e8 * min(f, 1.0)) + 1000000,
+               claim_blocks=int(2.4e6 * min(f, 1.0)) + 20000, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def timed(b, n):
@@ -306,11 +331,25 @@ def batch_ensemble(dev, serial_every=8, graph_steps=20):
     b = ensemble.batch_from(runs, **mem)
     cfg["graph_steps"] = graph_steps
     b.gp_set_launch_config(**cfg)
+    barrier(world)
     tb = timed(b, steps)
     st = b.gp_stats()
     live, _ = b.gp_run_counts()
     arena_gb = b.arena_bytes / 1e9
     release(b)
+    tb_ms, psteps = reduce_timing(tb * 1e3, float(st["particle_steps"]), world)
+    tb = tb_ms / 1e3
+    out = {"workload": "cet_runs: 256 runs, 0.5-2 mm cubes, columnar + equiaxed nucleation, "
+                       "400 steps of 1 ms", "runs": len(runs_all), "steps": steps,
+           "sharding": f"{world} rank(s), runs by estimated work, no collective",
+           "batched_s": tb, "runs_per_s": len(runs_all) / tb,
+           "particle_steps_per_s": psteps / tb,
+           "launch_config": cfg, "batched_step_by_step_s_rank0": t_eager,
+           "particles_per_run_rank0": {"min": int(live.min()), "median": int(np.median(live)),
+                                       "max": int(live.max())},
+           "arena_gb_rank0": round(arena_gb, 1)}
+    if world > 1 or rank != 0:
+        return out
     ts, sample = 0.0, list(range(0, len(runs), serial_every))
     for r in sample:
         w = runs[r]
@@ -326,17 +365,10 @@ def batch_ensemble(dev, serial_every=8, graph_steps=20):
         ts += timed(s, steps)
         s.close()
     scale = len(runs) / len(sample)
-    return {"workload": "cet_runs: 256 runs, 0.5-2 mm cubes, columnar + equiaxed nucleation, "
-                        "400 steps of 1 ms", "runs": len(runs), "steps": steps,
-            "batched_s": tb, "runs_per_s": len(runs) / tb,
-            "particle_steps_per_s": st["particle_steps"] / tb,
-            "launch_config": cfg, "batched_step_by_step_s": t_eager,
-            "particles_per_run": {"min": int(live.min()), "median": int(np.median(live)),
-                                  "max": int(live.max())},
-            "arena_gb": round(arena_gb, 1),
-            "serial_sample_runs": len(sample), "serial_s_scaled": ts * scale,
-            "serial_runs_per_s": len(runs) / (ts * scale),
-            "speedup_vs_serial": ts * scale / tb}
+    out.update({"serial_sample_runs": len(sample), "serial_s_scaled": ts * scale,
+                "serial_runs_per_s": len(runs) / (ts * scale),
+                "speedup_vs_serial": ts * scale / tb})
+    return out
 
 
 def run_native(args, rank, world, local_rank):
@@ -414,6 +446,10 @@ def run_native(args, rank, world, local_rank):
 
     if rank != 0:
         sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        if not args.no_extras:
+            batch_ensemble(dev, rank, world)   # this rank's shard of the ensemble
         return 0
 
     # roofline of the dominant kernel (largest device time in the timed region)
@@ -438,7 +474,7 @@ def run_native(args, rank, world, local_rank):
     del sim
     torch.cuda.empty_cache()
     adj = adjoint_cost(dev) if not args.no_extras else None
-    bat = batch_ensemble(dev) if not args.no_extras else None
+    bat = batch_ensemble(dev, rank, world) if not args.no_extras else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -446,6 +482,7 @@ def run_native(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD_NAME, "grains": args.grains, "shell_n0": args.n0,
                        "plate_mm": list(args.plate),
                        "particles_at_start": n_start,
+                       "live_at_timed_start": st0["n_live"],
                        "active_at_timed_start": st0["n_active"],
                        "live_at_end": st1["n_live"], "parallelism": f"replicas x{world}",
                        "claim_blocks_used": round(st1["n_claim_blocks"] / blocks, 3),

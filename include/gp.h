@@ -85,6 +85,21 @@ typedef struct {
   int32_t flags;
 } gp_thermal_grid;
 
+/* Composition field for a local liquidus T_L(w) = T_m + m_L w(x, t): ΔT then is
+ * T_L(w(x, t)) - T(x, t) instead of taking T_L at the nominal composition.
+ * Sec. 2.1.2 states that the velocity may depend on T and w; Sec. 2.1.3 notes the
+ * extension of the nominal liquidus to the local composition; Sec. 3.3 / 3.4 take
+ * the undercooling with respect to the local solute concentration.  w is tabulated
+ * like gp_thermal_grid (node-centred, x fastest, moving with frame_vel, trilinear
+ * after clamping); m_L is the liquidus slope in K per unit of w. */
+typedef struct {
+  const float* w;
+  int32_t n[3];
+  double origin[3], spacing[3], frame_vel[3];
+  double T_m, m_L;
+  int32_t flags;
+} gp_solute_grid;
+
 /* Voxel grid for gp_grain_map: voxel centres origin + (i + 1/2) spacing. */
 typedef struct {
   double origin[3], spacing[3];
@@ -109,6 +124,7 @@ typedef struct {
                                25 bytes per particle and step); default 0 (none)   */
   void* arena;
   size_t arena_bytes;
+  int64_t solute_nodes;     /* composition-grid nodes reserved in the arena; default 0 */
 } gp_memory;
 
 typedef struct {
@@ -180,6 +196,12 @@ gp_status gp_seed_shell(gp_ctx* ctx, int64_t n, const int32_t* grains, int32_t n
 
 gp_status gp_set_thermal_analytic(gp_ctx* ctx, const gp_thermal_analytic* th);
 gp_status gp_set_thermal_grid(gp_ctx* ctx, const gp_thermal_grid* th);
+
+/* Sets (or replaces) the composition field of a single-run context; the grid is
+ * copied into the arena (gp_memory.solute_nodes) or, for a library-allocated
+ * context, into memory the library allocates.  GP_ERR_STATE on a batch context;
+ * gp_tape_begin refuses a context with a composition field. */
+gp_status gp_set_solute_grid(gp_ctx* ctx, const gp_solute_grid* sg);
 
 /* Registers n pending nucleation sites (Sec. 2.1.1): position pos3 (n x 3),
  * nucleation undercooling dTn (n) and orientation quat4 (n x 4).  A site becomes

@@ -70,6 +70,7 @@ def lib():
         "go_destroy": (None, [vp]),
         "go_set_thermal_analytic": (None, [vp, d, P_D, P_D, d]),
         "go_set_thermal_grid": (None, [vp, P_F, P_I32, P_D, P_D, P_D]),
+        "go_set_solute_grid": (None, [vp, P_F, P_I32, P_D, P_D, P_D, d, d]),
         "go_add_grains": (i64, [vp, i64, P_D, P_D, C.c_int]),
         "go_seed_shell": (None, [vp, i64, P_I32, i32, d, C.c_int]),
         "go_nucleation_sites": (None, [vp, i64, P_D, P_D, P_D]),
@@ -145,6 +146,13 @@ class Oracle:
         nz, ny, nx = T.shape
         lib().go_set_thermal_grid(self._p, T.reshape(-1), np.array([nx, ny, nz], np.int32),
                                   _d3(origin), _d3(spacing), _d3(vel))
+
+    def set_solute_grid(self, w, origin, spacing, Tm, mL, vel=(0.0, 0.0, 0.0)):
+        """Local liquidus T_m + m_L w(x) from a node-centred composition grid (nz, ny, nx)."""
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        nz, ny, nx = w.shape
+        lib().go_set_solute_grid(self._p, w.reshape(-1), np.array([nx, ny, nz], np.int32),
+                                 _d3(origin), _d3(spacing), _d3(vel), float(Tm), float(mL))
 
     def add_grains(self, pos, quat, nucleate=True) -> int:
         pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)

@@ -151,23 +151,35 @@ struct Sim {
     site_pos(p.grain, p.s, p.ell, p.k, x);
   }
 
-  // Trilinear sample of a node-centred grid moving with velocity gvel
+  // Composition-dependent liquidus T_L(w) = T_m + m_L w(x, t) with w trilinear on its
+  // own moving grid (Sec. 2.1.3 notes that the nominal liquidus extends to a local
+  // composition; Sec. 3.3/3.4 take the undercooling with respect to the local
+  // solute concentration).  Unset: the nominal T_L of the growth law.
+  bool solute = false;
+  std::vector<float> wgrid;
+  int wn[3] = {0, 0, 0};
+  double worigin[3] = {0, 0, 0}, wspacing[3] = {1, 1, 1}, wvel[3] = {0, 0, 0};
+  double Tm = 0, mL = 0;
+
+  // Trilinear sample of a node-centred grid moving with velocity vel
   // (reading r14: replaces OpenFOAM's cellPointFace interpolation of Sec. 2.3).
-  double grid_T(const double x[3], double t) const {
+  static double trilinear(const std::vector<float>& g, const int n[3], const double origin[3],
+                          const double spacing[3], const double vel[3], const double x[3],
+                          double t) {
     int i0[3];
     double f[3];
     for (int a = 0; a < 3; ++a) {
-      double u = (x[a] - gvel[a] * t - gorigin[a]) / gspacing[a];
-      double umax = (double)(gn[a] - 1);
+      double u = (x[a] - vel[a] * t - origin[a]) / spacing[a];
+      double umax = (double)(n[a] - 1);
       if (u < 0) u = 0;
       if (u > umax) u = umax;
       int i = (int)std::floor(u);
-      if (i > gn[a] - 2) i = gn[a] - 2;
+      if (i > n[a] - 2) i = n[a] - 2;
       i0[a] = i;
       f[a] = u - i;
     }
     auto at = [&](int i, int j, int k) {
-      return (double)grid[((size_t)k * gn[1] + j) * gn[0] + i];
+      return (double)g[((size_t)k * n[1] + j) * n[0] + i];
     };
     double c[2][2];
     for (int dk = 0; dk < 2; ++dk)
@@ -180,15 +192,24 @@ struct Sim {
     double e1 = c[1][0] + f[1] * (c[1][1] - c[1][0]);
     return e0 + f[2] * (e1 - e0);
   }
+  double grid_T(const double x[3], double t) const {
+    return trilinear(grid, gn, gorigin, gspacing, gvel, x, t);
+  }
+  double liquidus(const double x[3], double t) const {
+    if (!solute) return TL;
+    return Tm + mL * trilinear(wgrid, wn, worigin, wspacing, wvel, x, t);
+  }
 
-  // Total undercooling Delta T = T_L - T(x, t)  (Sec. 2.1.2, before Eq. 1).
+  // Total undercooling Delta T = T_L - T(x, t)  (Sec. 2.1.2, before Eq. 1), with the
+  // local liquidus when a composition field is set.
   double undercooling(const double x[3], double t) const {
+    const double tl = liquidus(x, t);
     if (thermal_mode == 1) {
       double T = T0 + G[0] * (x[0] - xref[0]) + G[1] * (x[1] - xref[1]) +
                  G[2] * (x[2] - xref[2]) + Tdot * t;
-      return TL - T;
+      return tl - T;
     }
-    if (thermal_mode == 2) return TL - grid_T(x, t);
+    if (thermal_mode == 2) return tl - grid_T(x, t);
     return 0.0;
   }
 
@@ -587,6 +608,24 @@ void go_set_thermal_analytic(void* s, double T0, const double G[3], const double
     S->xref[i] = xref[i];
   }
   S->Tdot = Tdot;
+}
+
+// Composition field w (node-centred, x fastest, moving at vel) and the linear
+// liquidus T_L(w) = T_m + m_L w.
+void go_set_solute_grid(void* s, const float* w, const int32_t n[3], const double origin[3],
+                        const double spacing[3], const double vel[3], double Tm, double mL) {
+  Sim* S = (Sim*)s;
+  S->solute = true;
+  size_t tot = (size_t)n[0] * n[1] * n[2];
+  S->wgrid.assign(w, w + tot);
+  for (int i = 0; i < 3; ++i) {
+    S->wn[i] = n[i];
+    S->worigin[i] = origin[i];
+    S->wspacing[i] = spacing[i];
+    S->wvel[i] = vel[i];
+  }
+  S->Tm = Tm;
+  S->mL = mL;
 }
 
 void go_set_thermal_grid(void* s, const float* T, const int32_t n[3], const double origin[3],

@@ -43,10 +43,11 @@ struct Layout {
   int64_t cap = 0, rcap = 0, blocks = 0, buckets = 0;
   int max_grains = 0, max_nuclei = 0;
   int64_t grid_nodes = 0;
+  int64_t solute_nodes = 0;
   int64_t tape_steps = 0;
   // offsets into the arena
   size_t rec0, rec1, pos4, sslot, act, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
-      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, dstats, grid, runs,
+      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, dstats, grid, sgrid, runs,
       rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, total;
 };
 
@@ -145,8 +146,9 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   }
   L->max_nuclei = m->max_nuclei > 0 ? m->max_nuclei : 4096;
   L->grid_nodes = m->grid_nodes > 0 ? m->grid_nodes : 0;
+  L->solute_nodes = m->solute_nodes > 0 ? m->solute_nodes : 0;
   L->tape_steps = m->tape_steps > 0 ? m->tape_steps : 0;
-  if (batch && (L->grid_nodes || L->tape_steps)) {
+  if (batch && (L->grid_nodes || L->tape_steps || L->solute_nodes)) {
     *why = "a batch of runs takes analytic fields only and no adjoint tape";
     return false;
   }
@@ -189,6 +191,7 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->tape_grad = take(8 * 8);
   L->act = take(4 * cap);
   L->nmeta = take(8 * (size_t)L->max_nuclei);
+  L->sgrid = take(4 * (size_t)L->solute_nodes);
   L->runs = take(sizeof(Geo) * (size_t)nruns);
   L->rtherm = take(16 * (size_t)nruns);
   L->rcount = take(16 * (size_t)nruns);
@@ -335,6 +338,10 @@ struct gp_ctx {
   double gorigin[3] = {0, 0, 0}, gvel[3] = {0, 0, 0};
   float* grid_own = nullptr;  // cudaMalloc'ed grid when the arena has none
   size_t grid_own_bytes = 0;
+  // composition field (local liquidus)
+  double worigin[3] = {0, 0, 0}, wvel[3] = {0, 0, 0};
+  float* wgrid_own = nullptr;
+  size_t wgrid_own_bytes = 0;
   // device views
   int4* rec[2] = {nullptr, nullptr};
   int cur = 0;  // rec[cur] is the (unsorted) store
@@ -440,7 +447,10 @@ void refresh_params(gp_ctx* c) {
 StepArgs step_args(const gp_ctx* c, int64_t n) {
   StepArgs S{};
   const double t = (double)n * c->dt;
-  for (int a = 0; a < 3; ++a) S.gshift[a] = (float)(c->gorigin[a] + c->gvel[a] * t);
+  for (int a = 0; a < 3; ++a) {
+    S.gshift[a] = (float)(c->gorigin[a] + c->gvel[a] * t);
+    S.wshift[a] = (float)(c->worigin[a] + c->wvel[a] * t);
+  }
   S.parity = (int)(n & 1);
   return S;
 }
@@ -687,6 +697,7 @@ gp_status gp_destroy(gp_ctx* c) {
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
   if (c->own && c->base) cudaFree(c->base);
   if (c->grid_own) cudaFree(c->grid_own);
+  if (c->wgrid_own) cudaFree(c->wgrid_own);
   if (c->hst) cudaFreeHost(c->hst);
   delete c;
   return GP_OK;
@@ -869,6 +880,50 @@ gp_status gp_set_thermal_grid(gp_ctx* c, const gp_thermal_grid* th) {
     c->P.ginv[a] = (float)(1.0 / th->spacing[a]);
     c->gorigin[a] = th->origin[a];
     c->gvel[a] = th->frame_vel[a];
+  }
+  return GP_OK;
+}
+
+gp_status gp_set_solute_grid(gp_ctx* c, const gp_solute_grid* sg) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "a batch of runs takes the nominal liquidus");
+  if (!sg || !sg->w) return fail(c, GP_ERR_ARG, "null composition grid");
+  if (!std::isfinite(sg->T_m) || !std::isfinite(sg->m_L))
+    return fail(c, GP_ERR_ARG, "T_m and m_L must be finite");
+  for (int a = 0; a < 3; ++a)
+    if (sg->n[a] < 2 || !(sg->spacing[a] > 0))
+      return fail(c, GP_ERR_ARG, "grid needs n >= 2 and spacing > 0");
+  const size_t nodes = (size_t)sg->n[0] * sg->n[1] * sg->n[2];
+  float* dstp = nullptr;
+  if ((int64_t)nodes <= c->L.solute_nodes) {
+    dstp = at<float>(c, c->L.sgrid);
+  } else if (c->own) {
+    if (c->wgrid_own_bytes < 4 * nodes) {
+      if (c->wgrid_own) cudaFree(c->wgrid_own);
+      c->wgrid_own = nullptr;
+      c->wgrid_own_bytes = 0;
+      GP_CUDA(c, cudaMalloc((void**)&c->wgrid_own, 4 * nodes));
+      c->wgrid_own_bytes = 4 * nodes;
+    }
+    dstp = c->wgrid_own;
+  } else {
+    return fail(c, GP_ERR_CAPACITY, "composition grid larger than gp_memory.solute_nodes");
+  }
+  GP_CUDA(c, cudaMemcpyAsync(dstp, sg->w, 4 * nodes,
+                             (sg->flags & GP_DEVICE_PTR) ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyHostToDevice,
+                             c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  c->P.solute = 1;
+  c->P.wgrid = dstp;
+  c->P.Tm = (float)sg->T_m;
+  c->P.mL = (float)sg->m_L;
+  for (int a = 0; a < 3; ++a) {
+    c->P.wn[a] = sg->n[a];
+    c->P.winv[a] = (float)(1.0 / sg->spacing[a]);
+    c->worigin[a] = sg->origin[a];
+    c->wvel[a] = sg->frame_vel[a];
   }
   return GP_OK;
 }
@@ -1116,6 +1171,7 @@ gp_status gp_tape_begin(gp_ctx* c) {
   gp_status s = check_ctx(c);
   if (s) return s;
   if (c->batch) return fail(c, GP_ERR_STATE, "the adjoint is for single-run contexts");
+  if (c->P.solute) return fail(c, GP_ERR_STATE, "the adjoint takes the nominal liquidus");
   if (c->L.tape_steps <= 0) return fail(c, GP_ERR_STATE, "no tape (gp_memory.tape_steps = 0)");
   if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
   c->tape_on = true;

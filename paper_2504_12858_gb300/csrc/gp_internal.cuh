@@ -123,6 +123,12 @@ struct Params {
   float ginv[3];     // 1 / spacing
   const float4* gtab;// grain table: 4 float4 per grain (c with the run id in w, rows of h R)
   int hshift;        // one reached-site head per 2^hshift cells along each axis
+  // local liquidus T_m + m_L w(x) from a composition grid (solute != 0)
+  int solute;
+  const float* wgrid;
+  int wn[3];
+  float winv[3];
+  float Tm, mL;
   // grids of the device-sized (batch) launches, in CTAs over the whole GPU
   struct {
     int build_ctas, advance_ctas, emit_ctas;
@@ -132,6 +138,7 @@ struct Params {
 // per-step constants of the gridded field (computed on the host in double)
 struct StepArgs {
   float gshift[3];   // grid: origin + frame_vel t
+  float wshift[3];   // composition grid: origin + frame_vel t
   int parity;        // step & 1: which claimant bits of a site byte are live
 };
 
@@ -236,23 +243,26 @@ __device__ __forceinline__ void step_site(int& sx, int& sy, int& sz, int k) {
 // ---------------------------------------------------------------------------------
 // thermal field and growth law
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ float grid_T(const Params& P, const StepArgs& S, float3 p) {
-  float u[3] = {__fmul_rn(__fsub_rn(p.x, S.gshift[0]), P.ginv[0]),
-                __fmul_rn(__fsub_rn(p.y, S.gshift[1]), P.ginv[1]),
-                __fmul_rn(__fsub_rn(p.z, S.gshift[2]), P.ginv[2])};
+// trilinear sample of a node-centred binary32 grid g (n nodes per axis, 1/spacing
+// inv) whose node 0 sits at shift; clamped to the table
+__device__ __forceinline__ float trilinear(const float* __restrict__ g, const int n[3],
+                                           const float inv[3], const float shift[3], float3 p) {
+  float u[3] = {__fmul_rn(__fsub_rn(p.x, shift[0]), inv[0]),
+                __fmul_rn(__fsub_rn(p.y, shift[1]), inv[1]),
+                __fmul_rn(__fsub_rn(p.z, shift[2]), inv[2])};
   int i0[3];
   float f[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    float um = (float)(P.gn[a] - 1);
+    float um = (float)(n[a] - 1);
     float v = fminf(fmaxf(u[a], 0.f), um);
-    int i = min(__float2int_rd(v), P.gn[a] - 2);
+    int i = min(__float2int_rd(v), n[a] - 2);
     i0[a] = i;
     f[a] = v - (float)i;
   }
-  const int nx = P.gn[0];
-  const size_t plane = (size_t)P.gn[0] * P.gn[1];
-  const float* b = P.grid + (size_t)i0[2] * plane + (size_t)i0[1] * nx + i0[0];
+  const int nx = n[0];
+  const size_t plane = (size_t)n[0] * n[1];
+  const float* b = g + (size_t)i0[2] * plane + (size_t)i0[1] * nx + i0[0];
   float t000 = __ldg(b), t100 = __ldg(b + 1);
   float t010 = __ldg(b + nx), t110 = __ldg(b + nx + 1);
   float t001 = __ldg(b + plane), t101 = __ldg(b + plane + 1);
@@ -266,18 +276,30 @@ __device__ __forceinline__ float grid_T(const Params& P, const StepArgs& S, floa
   return __fmaf_rn(f[2], e1 - e0, e0);
 }
 
+__device__ __forceinline__ float grid_T(const Params& P, const StepArgs& S, float3 p) {
+  return trilinear(P.grid, P.gn, P.ginv, S.gshift, p);
+}
+
 // undercooling at p; base = T_L - T0 - Tdot t of the analytic field at the time
 // of the sample (Geo::dT_base or Geo::dT_base1)
 __device__ __forceinline__ float undercooling(const Params& P, const Geo& g, const StepArgs& S,
                                              float3 p, float base) {
+  float dT = 0.f;
   if (P.thermal == 1) {
     float v = __fmul_rn(g.G[0], __fsub_rn(p.x, g.xref[0]));
     v = __fmaf_rn(g.G[1], __fsub_rn(p.y, g.xref[1]), v);
     v = __fmaf_rn(g.G[2], __fsub_rn(p.z, g.xref[2]), v);
-    return base - v;
+    dT = base - v;
+  } else if (P.thermal == 2) {
+    dT = P.TL - grid_T(P, S, p);
+  } else {
+    return 0.f;
   }
-  if (P.thermal == 2) return P.TL - grid_T(P, S, p);
-  return 0.f;
+  if (P.solute) {  // local liquidus: add T_m + m_L w(x) - T_L
+    const float liq = __fmaf_rn(P.mL, trilinear(P.wgrid, P.wn, P.winv, S.wshift, p), P.Tm);
+    dT = __fadd_rn(__fsub_rn(liq, P.TL), dT);
+  }
+  return dT;
 }
 
 __device__ __forceinline__ float ipow(float x, int n) {

@@ -105,6 +105,7 @@ class Workload:
     grid: dict = None                 # T (nz, ny, nx) float32, origin, spacing, vel
     shell_n0: int = 0                 # > 0: seed each grain as a shell of n0 lattice shells
     nuclei: dict = None               # pos (m,3), dTn (m,), quat (m,4)
+    solute: dict = None               # w (nz, ny, nx) float32, origin, spacing, vel, Tm, mL
     extra: dict = field(default_factory=dict)
 
 

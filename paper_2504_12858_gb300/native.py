@@ -39,6 +39,12 @@ class gp_thermal_grid(C.Structure):
                 ("spacing", C.c_double * 3), ("frame_vel", C.c_double * 3), ("flags", C.c_int32)]
 
 
+class gp_solute_grid(C.Structure):
+    _fields_ = [("w", C.c_void_p), ("n", C.c_int32 * 3), ("origin", C.c_double * 3),
+                ("spacing", C.c_double * 3), ("frame_vel", C.c_double * 3), ("T_m", C.c_double),
+                ("m_L", C.c_double), ("flags", C.c_int32)]
+
+
 class gp_voxel_grid(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("spacing", C.c_double * 3), ("n", C.c_int32 * 3)]
 
@@ -48,7 +54,7 @@ class gp_memory(C.Structure):
                 ("claim_blocks", C.c_int64), ("max_grains", C.c_int32),
                 ("max_nuclei", C.c_int32), ("grid_nodes", C.c_int64),
                 ("tape_steps", C.c_int64), ("arena", C.c_void_p),
-                ("arena_bytes", C.c_size_t)]
+                ("arena_bytes", C.c_size_t), ("solute_nodes", C.c_int64)]
 
 
 STATS_FIELDS = ["step", "n_live", "n_active", "n_frozen", "n_grains", "n_reached",
@@ -83,6 +89,7 @@ SIGNATURES = {
     "gp_seed_shell": (C.c_int, [_P, C.c_int64, _P, C.c_int32, C.c_double]),
     "gp_set_thermal_analytic": (C.c_int, [_P, C.POINTER(gp_thermal_analytic)]),
     "gp_set_thermal_grid": (C.c_int, [_P, C.POINTER(gp_thermal_grid)]),
+    "gp_set_solute_grid": (C.c_int, [_P, C.POINTER(gp_solute_grid)]),
     "gp_nucleation_sites": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "gp_step": (C.c_int, [_P, C.c_int32]),
     "gp_grain_map": (C.c_int, [_P, C.POINTER(gp_voxel_grid), _P, C.c_int32]),
@@ -188,13 +195,14 @@ class Sim:
 
     def __init__(self, lo, hi, h, dt, a, b, T_L, capacity, reached_capacity=0,
                  claim_blocks=0, max_grains=0, max_nuclei=0, grid_nodes=0, tape_steps=0,
-                 stream=None, device="cuda"):
+                 stream=None, device="cuda", solute_nodes=0):
         self.lo, self.hi = tuple(lo), tuple(hi)
         self._open([(lo, hi)], False, h, dt, a, b, T_L, capacity, reached_capacity,
-                   claim_blocks, max_grains, max_nuclei, grid_nodes, tape_steps, stream, device)
+                   claim_blocks, max_grains, max_nuclei, grid_nodes, tape_steps, stream, device,
+                   solute_nodes)
 
     def _open(self, domains, batch, h, dt, a, b, T_L, capacity, reached_capacity, claim_blocks,
-              max_grains, max_nuclei, grid_nodes, tape_steps, stream, device):
+              max_grains, max_nuclei, grid_nodes, tape_steps, stream, device, solute_nodes=0):
         import torch
         self._torch = torch
         L = load()
@@ -210,6 +218,7 @@ class Sim:
         mem.max_nuclei = int(max_nuclei)
         mem.grid_nodes = int(grid_nodes)
         mem.tape_steps = int(tape_steps)
+        mem.solute_nodes = int(solute_nodes)
         nb = C.c_size_t(0)
         if batch:
             self._check(L.gp_batch_arena_bytes(self.nruns, self._doms, self.h, C.byref(mem),
@@ -294,6 +303,27 @@ class Sim:
         th.spacing[:] = [float(v) for v in spacing]
         th.frame_vel[:] = [float(v) for v in vel]
         self._check(load().gp_set_thermal_grid(self._h, C.byref(th)))
+
+    def gp_set_solute_grid(self, w, origin, spacing, T_m, m_L, vel=(0.0, 0.0, 0.0)):
+        """w: numpy (host) or torch CUDA float32 tensor of shape (nz, ny, nx)."""
+        sg = gp_solute_grid()
+        keep = w
+        if hasattr(w, "data_ptr") and getattr(w, "is_cuda", False):
+            assert w.dtype == self._torch.float32 and w.is_contiguous()
+            sg.w = w.data_ptr()
+            sg.flags = GP_DEVICE_PTR
+        else:
+            keep = np.ascontiguousarray(w, np.float32)
+            sg.w = keep.ctypes.data
+            sg.flags = 0
+        nz, ny, nx = keep.shape
+        sg.n[:] = [nx, ny, nz]
+        sg.origin[:] = [float(v) for v in origin]
+        sg.spacing[:] = [float(v) for v in spacing]
+        sg.frame_vel[:] = [float(v) for v in vel]
+        sg.T_m = float(T_m)
+        sg.m_L = float(m_L)
+        self._check(load().gp_set_solute_grid(self._h, C.byref(sg)))
 
     def gp_nucleation_sites(self, pos, dTn, quat):
         pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)

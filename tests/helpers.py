@@ -12,6 +12,9 @@ def oracle_from(w: inputs.Workload, nucleate=True):
                                w.analytic["Tdot"])
     if w.grid:
         o.set_thermal_grid(w.grid["T"], w.grid["origin"], w.grid["spacing"], w.grid["vel"])
+    if w.solute:
+        sd = w.solute
+        o.set_solute_grid(sd["w"], sd["origin"], sd["spacing"], sd["Tm"], sd["mL"], sd["vel"])
     if w.seeds is not None and len(w.seeds):
         o.add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0)
         if w.shell_n0:
@@ -24,6 +27,8 @@ def oracle_from(w: inputs.Workload, nucleate=True):
 def sim_from(w: inputs.Workload, capacity, nucleate=True, **kw):
     from paper_2504_12858_gb300.native import Sim
     grid_nodes = int(np.prod(w.grid["T"].shape)) if w.grid else 0
+    if w.solute:
+        kw.setdefault("solute_nodes", int(np.prod(w.solute["w"].shape)))
     s = Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=capacity, grid_nodes=grid_nodes,
             max_grains=max(16, 2 * (len(w.seeds) if w.seeds is not None else 0) +
                            (len(w.nuclei["pos"]) if w.nuclei else 0)), **kw)
@@ -32,6 +37,9 @@ def sim_from(w: inputs.Workload, capacity, nucleate=True, **kw):
                                   w.analytic["Tdot"])
     if w.grid:
         s.gp_set_thermal_grid(w.grid["T"], w.grid["origin"], w.grid["spacing"], w.grid["vel"])
+    if w.solute:
+        sd = w.solute
+        s.gp_set_solute_grid(sd["w"], sd["origin"], sd["spacing"], sd["Tm"], sd["mL"], sd["vel"])
     if w.seeds is not None and len(w.seeds):
         s.gp_add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0)
         if w.shell_n0:

@@ -73,3 +73,17 @@ def test_clock_parser(tmp_path):
     assert r["sm_max_mhz"] == 2070.0
     assert r["sm_mhz"] == pytest.approx(2025.0)
     assert r["reasons"] == ["sw_power_cap"]
+
+
+def test_ensemble_sharding_covers_every_run_once_and_balances_work():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2504_12858_gb300 import inputs
+    runs = inputs.cet_runs()
+    costs = [bench.run_cost(w) for w in runs]
+    for world in (1, 2, 4, 8):
+        parts = bench.shard_runs(costs, world)
+        assert sorted(i for p in parts for i in p) == list(range(len(runs)))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        # greedy LPT: no rank exceeds the mean by more than the largest single run
+        assert max(loads) <= sum(costs) / world + max(costs) + 1e-9

@@ -186,6 +186,60 @@ def test_gradient_single_grain_on_gpu_matches_oracle_and_ode():
 
 
 # ----------------------------------------------------------------------------------
+# Local liquidus T_m + m_L w(x) from a composition grid (Sec. 2.1.3, 3.3/3.4)
+# ----------------------------------------------------------------------------------
+def test_solute_gradient_on_gpu_matches_oracle_and_thermal_gradient():
+    w, _ = _gradient_case(0.01)
+    half = w.hi[0] / 2
+    nz = 17
+    z = np.linspace(0.0, w.hi[0], nz)
+    wz = (10.0 + 125.0 * (z - half)).astype(np.float32)   # m_L dw/dz = -2 * 125 = -G
+    ws = inputs.Workload(**{**w.__dict__, "name": "solute_gradient",
+                            "analytic": dict(w.analytic, G=(0.0, 0.0, 0.0)),
+                            "solute": dict(w=np.broadcast_to(wz[:, None, None], (nz, 2, 2)).copy(),
+                                           origin=(0.0, 0.0, 0.0),
+                                           spacing=(w.hi[0], w.hi[0], w.hi[0] / (nz - 1)),
+                                           vel=(0.0, 0.0, 0.0), Tm=w.T_L + 20.0, mL=-2.0)})
+    o = oracle_from(ws)
+    o.step(ws.steps)
+    c, R = o.grain(0)
+    sg = sim_from(ws, capacity=400000)
+    sg.gp_step(ws.steps)
+    st = sim_from(w, capacity=400000)
+    st.gp_step(w.steps)
+    t_sol, t_orc, t_th = (_tips(sg.gp_get_particles(), c, R), _tips(o.particles(), c, R),
+                          _tips(st.gp_get_particles(), c, R))
+    assert np.allclose(t_sol, t_orc, rtol=1e-5)
+    assert np.allclose(t_sol, t_th, rtol=1e-5)
+    assert keyset(sg.gp_get_particles()) == keyset(o.particles())
+
+
+def test_grain_map_with_composition_field_matches_oracle():
+    w = _polycrystal(seed=11, n_grains=10, L=50e-6, steps=45)
+    g = inputs.rng(12)
+    n = 9
+    xs = np.linspace(0.0, 50e-6, n)
+    Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+    wf = (2.0 + 0.6 * np.sin(2 * np.pi * X / 50e-6 + g.uniform(0, 6))
+          * np.cos(2 * np.pi * Z / 40e-6)).astype(np.float32)       # +-3.9 K of liquidus
+    ws = inputs.Workload(**{**w.__dict__, "solute": dict(w=wf, origin=(0.0, 0.0, 0.0),
+                                                         spacing=(50e-6 / (n - 1),) * 3,
+                                                         vel=(0.0, 0.0, 0.0),
+                                                         Tm=w.T_L + 13.0, mL=-6.5)})
+    o = oracle_from(ws)
+    s = sim_from(ws, capacity=400000)
+    o.step(ws.steps)
+    s.gp_step(ws.steps)
+    nv, sp = (50, 50, 50), (1e-6,) * 3
+    mo = o.grain_map((0, 0, 0), sp, nv)
+    ms = s.gp_grain_map((0, 0, 0), sp, nv)
+    assert (mo == ms).mean() >= 0.995
+    plain = sim_from(w, capacity=400000)
+    plain.gp_step(w.steps)
+    assert (plain.gp_grain_map((0, 0, 0), sp, nv) != ms).mean() > 0.01   # the field acts
+
+
+# ----------------------------------------------------------------------------------
 # whole step from an identical state (oracle-produced), FP32 vs FP64
 # ----------------------------------------------------------------------------------
 def _polycrystal(seed=5, n_grains=12, L=60e-6, steps=35, field="gradient"):

@@ -226,6 +226,71 @@ def test_gradient_single_grain_converges_to_ode():
 
 
 # ----------------------------------------------------------------------------------
+# Local liquidus T_L(w) = T_m + m_L w(x) (Sec. 2.1.3 extends the nominal liquidus to
+# the local composition; Sec. 3.3/3.4 take the undercooling with respect to the
+# local solute concentration).  (1) A uniform composition at which T_m + m_L w is
+# exactly the nominal T_L changes nothing.  (2) A composition linear in z with
+# m_L dw/dz = -G under a uniform temperature is the thermal gradient G of the
+# Sec. 3.1 case: the tips must coincide with that (RK4-pinned) case.
+# ----------------------------------------------------------------------------------
+def _w_grid_linear_z(w0, gw, zc, L=8e-3, nz=17):
+    z = np.linspace(0.0, L, nz)
+    w = (w0 + gw * (z - zc)).astype(np.float32)
+    return np.broadcast_to(w[:, None, None], (nz, 2, 2)).copy(), (0.0, 0.0, 0.0), (L, L, L / (nz - 1))
+
+
+def test_uniform_composition_at_nominal_liquidus_changes_nothing():
+    T_L = 1000.0
+    runs = []
+    for solute in (False, True):
+        o = Oracle((0, 0, 0), (60e-6,) * 3, 2e-6, 1.3e-3, (1e-5,), (2.0,), T_L)
+        o.set_thermal_analytic(T_L - 4.0, (3e4, -2e4, 1e4), (30e-6,) * 3, -20.0)
+        if solute:   # 1013 - 6.5 * 2 = 1000 exactly
+            o.set_solute_grid(np.full((3, 3, 3), 2.0, np.float32), (0, 0, 0), (30e-6,) * 3,
+                              1013.0, -6.5)
+        g = inputs.rng(5)
+        o.add_grains(g.random((8, 3)) * 60e-6, inputs.shoemake_quaternions(8, g))
+        o.step(30)
+        runs.append(o.particles())
+    a, b = runs
+    assert len(a["grain"]) == len(b["grain"]) > 400
+    for k in ("grain", "site", "dir", "state"):
+        assert np.array_equal(a[k], b[k])
+    assert np.array_equal(a["x"], b["x"])
+
+
+def test_solute_gradient_equals_thermal_gradient():
+    a, b, dT0, Tdot, G, T_L, h, half = 1e-4, 2.0, 2.0, -0.1, 250.0, 1000.0, 200e-6, 4e-3
+    c = np.array([half, half, half])
+    q = inputs.euler_zxz_to_quaternion(20.0, 20.0, 20.0)
+    tips = []
+    for solute in (False, True):
+        o = Oracle((0, 0, 0), (2 * half,) * 3, h, 0.01, (a,), (b,), T_L)
+        if solute:   # T_L(z) = 1020 - 2 (10 + 125 (z - z_c)) = T_L - G (z - z_c)
+            o.set_thermal_analytic(T_L - dT0, (0.0, 0.0, 0.0), c, Tdot)
+            w, org, sp = _w_grid_linear_z(10.0, 125.0, half)
+            o.set_solute_grid(w, org, sp, T_L + 20.0, -2.0)
+        else:
+            o.set_thermal_analytic(T_L - dT0, (0.0, 0.0, G), c, Tdot)
+        o.add_grains(c[None], q[None])
+        o.step(500)
+        p = o.particles()
+        cc, R = o.grain(0)
+        t = []
+        for k in range(6):
+            ax, sg = k // 2, (1 if k % 2 == 0 else -1)
+            others = [i for i in range(3) if i != ax]
+            m = ((p["dir"] == k) & (p["site"][:, ax] * sg >= 0)
+                 & (p["site"][:, others] == 0).all(axis=1))
+            assert m.sum() == 1
+            t.append(np.linalg.norm(p["x"][m][0] - cc))
+        tips.append(np.array(t))
+        assert o.undercooling(c + np.array([0, 0, 1e-3]), 1.0) == pytest.approx(
+            dT0 - G * 1e-3 + 0.1, rel=1e-12)
+    assert np.allclose(tips[0], tips[1], rtol=1e-10, atol=0)
+
+
+# ----------------------------------------------------------------------------------
 # Trilinear sampling: exact on a field that is linear in x, y, z; moving frame.
 # ----------------------------------------------------------------------------------
 def test_trilinear_grid_exact_on_linear_field():
