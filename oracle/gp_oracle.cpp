@@ -34,6 +34,7 @@
 #include <cstring>
 #include <map>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 namespace {
@@ -48,7 +49,9 @@ inline int sign_of(int k) { return (k & 1) ? -1 : +1; }
 
 struct Grain {
   double c[3];
-  double R[9];  // row-major, crystal -> lab
+  double R[9];      // row-major, crystal -> lab
+  double dTn = 0;   // nucleation undercooling of its seed (0 for grains placed directly)
+  int dormant = 0;  // melted entirely; its seed waits to nucleate again (reading r17)
 };
 
 struct Particle {
@@ -90,7 +93,7 @@ struct Nucleus {
 
 struct Stats {
   int64_t steps, particle_steps, n_frozen_new, n_spawned, n_claims_lost,
-      n_clipped, n_clamped, n_nucleated, n_reached;
+      n_clipped, n_clamped, n_nucleated, n_reached, n_melted, n_walkback;
 };
 
 // Unit quaternion (w,x,y,z) -> rotation matrix (crystal -> lab).  The paper gives
@@ -131,6 +134,7 @@ struct Sim {
   int gn[3] = {0, 0, 0};
   double gorigin[3] = {0, 0, 0}, gspacing[3] = {1, 1, 1}, gvel[3] = {0, 0, 0};
   int64_t step = 0;
+  bool melting = false;  // melting walk-back (Sec. 2.1.3), reading r17
   std::vector<Grain> grains;
   std::vector<Particle> parts;
   std::unordered_map<SiteKey, uint8_t, SiteKeyHash> claimed;
@@ -338,10 +342,87 @@ struct Sim {
     }
   }
 
+  // Melting (Sec. 2.1.3): where the temperature rises above the liquidus the solid
+  // melts, and the envelope is redefined by walking back to the tracking points at
+  // the edge between undercooled and superheated melt.  Reading r17, at t_n before
+  // the spatial hash:
+  //  (M1) every reached site with Delta T < 0 at its position melts: it is no
+  //       longer reached and no longer claimed;
+  //  (M2) every live particle whose position has Delta T < 0, or whose site has
+  //       melted, is removed, and its (never reached) target is released;
+  //  (M3) walk-back: for every site melted in (M1), the first direction k = 0..5
+  //       whose neighbour m - e_k is still reached gets a new ACTIVE particle at that
+  //       neighbour heading k to the melted site, which it claims.  The surviving
+  //       site and the melted one straddle the Delta T = 0 surface, closer to it than
+  //       the paper's search distance of 2 lambda_0;
+  //  (M4) a grain left without reached sites is melted entirely: its seed stays and
+  //       nucleates again, with the same grain id, once its nucleation undercooling
+  //       is reached and it lies in no grain (the nucleation pass below).
+  void melt(double t) {
+    std::vector<SiteKey> kept, melted;
+    kept.reserve(reached.size());
+    for (const SiteKey& r : reached) {
+      int32_t sr[3] = {r.x, r.y, r.z};
+      double q[3];
+      site_pos(r.g, sr, 0.0, 0, q);
+      if (undercooling(q, t) < 0) {
+        melted.push_back(r);
+        claimed.erase(r);
+      } else {
+        kept.push_back(r);
+      }
+    }
+    reached.swap(kept);
+    st.n_melted += (int64_t)melted.size();
+    std::unordered_set<SiteKey, SiteKeyHash> alive(reached.begin(), reached.end());
+    std::vector<Particle> out;
+    out.reserve(parts.size());
+    for (const Particle& p : parts) {
+      double x[3];
+      part_pos(p, x);
+      if (undercooling(x, t) < 0 || !alive.count(SiteKey{p.grain, p.s[0], p.s[1], p.s[2]})) {
+        SiteKey tk{p.grain, p.s[0], p.s[1], p.s[2]};
+        if (axis_of(p.k) == 0) tk.x += sign_of(p.k);
+        if (axis_of(p.k) == 1) tk.y += sign_of(p.k);
+        if (axis_of(p.k) == 2) tk.z += sign_of(p.k);
+        if (!alive.count(tk)) claimed.erase(tk);
+        continue;
+      }
+      out.push_back(p);
+    }
+    for (const SiteKey& m : melted) {
+      for (int k = 0; k < 6; ++k) {
+        SiteKey nb = m;
+        if (axis_of(k) == 0) nb.x -= sign_of(k);
+        if (axis_of(k) == 1) nb.y -= sign_of(k);
+        if (axis_of(k) == 2) nb.z -= sign_of(k);
+        if (!alive.count(nb)) continue;
+        Particle w;
+        w.grain = m.g;
+        w.s[0] = nb.x;
+        w.s[1] = nb.y;
+        w.s[2] = nb.z;
+        w.k = k;
+        w.ell = 0.0;
+        w.state = ACTIVE;
+        claimed[m] = 1;
+        out.push_back(w);
+        ++st.n_walkback;
+        break;
+      }
+    }
+    parts.swap(out);
+    std::vector<int64_t> count(grains.size(), 0);
+    for (const SiteKey& r : reached) ++count[r.g];
+    for (const SiteKey& m : melted)
+      if (count[m.g] == 0) grains[m.g].dormant = 1;
+  }
+
   // One timestep n -> n+1, in the order fixed for this implementation:
-  // hash + contact, sample, advance, spawn, clip, nucleate.
+  // [melting], hash + contact, sample, advance, spawn, clip, nucleate.
   void step_once() {
     const double t = (double)step * dt;
+    if (melting) melt(t);
     const size_t N = parts.size();
     std::vector<std::array<double, 3>> X(N);
     for (size_t i = 0; i < N; ++i) part_pos(parts[i], X[i].data());
@@ -477,10 +558,21 @@ struct Sim {
       if (nu.done) continue;
       if (undercooling(nu.p, t1) >= nu.dTn && !suppressed(nu.p)) act.push_back(j);
     }
+    std::vector<int32_t> again;  // seeds of grains melted entirely (reading r17, M4)
+    for (size_t g = 0; g < grains.size(); ++g)
+      if (grains[g].dormant && undercooling(grains[g].c, t1) >= grains[g].dTn &&
+          !suppressed(grains[g].c))
+        again.push_back((int32_t)g);
     for (size_t j : act) {
       Nucleus& nu = nuclei[j];
       nu.done = 1;
       int32_t g = new_grain(nu.p, nu.q);
+      grains[g].dTn = nu.dTn;
+      nucleate(g);
+      ++st.n_nucleated;
+    }
+    for (int32_t g : again) {
+      grains[g].dormant = 0;
       nucleate(g);
       ++st.n_nucleated;
     }
@@ -809,7 +901,12 @@ void go_get_stats(void* s, int64_t* out) {
   out[6] = S->st.n_clamped;
   out[7] = S->st.n_nucleated;
   out[8] = S->st.n_reached;
+  out[9] = S->st.n_melted;
+  out[10] = S->st.n_walkback;
 }
+
+// Enables (1) or disables (0) the melting walk-back pass (reading r17).
+void go_set_melting(void* s, int on) { ((Sim*)s)->melting = on != 0; }
 
 void go_get_grain(void* s, int32_t g, double c[3], double R[9]) {
   Sim* S = (Sim*)s;

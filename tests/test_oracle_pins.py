@@ -524,3 +524,97 @@ def test_commensurate_step_spawns_on_schedule():
         assert len(g) == (2 * k + 1) * (2 * k * k + 2 * k + 3) // 3
         assert o.n_particles == 4 * (k + 1) ** 2 + 2
         assert np.all(o.particles()["ell"] < 1e-9)
+
+
+# ----------------------------------------------------------------------------------
+# Melting walk-back (Sec. 2.1.3, reading r17).  A grain with lattice axes along the
+# lab axes is grown, then the melt above a plane between two lattice planes is
+# superheated by a vanishing amount (so nothing grows in that step).  The state
+# after the step is rebuilt here from the state before it: reached sites above the
+# plane melt; particles above the plane or on a melted site go, and release their
+# targets; every melted site of the first layer above the plane gets one particle
+# from the surviving site below it, heading up (+z, the first direction whose
+# neighbour survives).
+# ----------------------------------------------------------------------------------
+def _keyset(grain, site, extra=None):
+    out = set()
+    for i in range(len(grain)):
+        k = (int(grain[i]), *(int(v) for v in site[i]))
+        out.add(k + ((int(extra[i]),) if extra is not None else ()))
+    return out
+
+
+def test_melting_above_a_plane_walks_back_to_the_surviving_layer():
+    h, dT, T_L = 2e-6, 5.0, 1000.0
+    v = 1e-5 * dT ** 2
+    dt = 0.37 * h / v
+    c = np.array([60e-6, 60e-6, 60e-6])
+    o = Oracle((0, 0, 0), (120e-6,) * 3, h, dt, (1e-5,), (2.0,), T_L)
+    o.set_thermal_analytic(T_L - dT, (0, 0, 0), (0, 0, 0), 0.0)
+    o.add_grains(c[None], np.array([[1.0, 0.0, 0.0, 0.0]]))
+    o.step(40)
+    p0 = o.particles()
+    g0, s0 = o.reached()
+    cg, cs = o.claimed()
+    zc = 3                                   # lattice plane z = 3 survives, z = 4 melts
+    z_cut = c[2] + (zc + 0.5) * h
+    o.set_thermal_analytic(T_L, (0.0, 0.0, 1.0), (0.0, 0.0, z_cut), 0.0)   # dT = z_cut - z
+    o.set_melting(True)
+    o.step(1)
+    p1 = o.particles()
+    g1, s1 = o.reached()
+    st = o.stats()
+
+    alive = s0[:, 2] <= zc
+    assert _keyset(g1, s1) == _keyset(g0[alive], s0[alive])
+    assert st["melted"] == int((~alive).sum()) > 100
+    alive_set = _keyset(g0[alive], s0[alive])
+    keep = (p0["x"][:, 2] < z_cut) & np.array([(int(g), *map(int, s)) in alive_set
+                                                 for g, s in zip(p0["grain"], p0["site"])])
+    expect = _keyset(p0["grain"][keep], p0["site"][keep], p0["dir"][keep])
+    walk = set()
+    for g, s in zip(g0[~alive], s0[~alive]):
+        if s[2] == zc + 1 and (int(g), int(s[0]), int(s[1]), zc) in alive_set:
+            walk.add((int(g), int(s[0]), int(s[1]), zc, 4))
+    assert st["walkback"] == len(walk) > 50
+    assert _keyset(p1["grain"], p1["site"], p1["dir"]) == expect | walk
+    # the old particles kept their progress (the superheat grows nothing); the new start at 0
+    i0 = {(int(g), *map(int, s), int(d)): e for g, s, d, e in
+          zip(p0["grain"], p0["site"], p0["dir"], p0["ell"])}
+    for g, s, d, e in zip(p1["grain"], p1["site"], p1["dir"], p1["ell"]):
+        k = (int(g), *map(int, s), int(d))
+        assert abs(e - (0.0 if k in walk else i0[k])) < 1e-9
+    # claims: melted sites and the targets of removed particles are released; the
+    # walk-back targets are claimed again
+    removed = ~keep
+    tgt = p0["site"][removed].copy()
+    ax = p0["dir"][removed] // 2
+    sg = np.where(p0["dir"][removed] % 2 == 0, 1, -1)
+    tgt[np.arange(len(tgt)), ax] += sg
+    released = _keyset(p0["grain"][removed], tgt) | _keyset(g0[~alive], s0[~alive])
+    expect_claimed = (_keyset(cg, cs) - released) | {(k[0], k[1], k[2], zc + 1) for k in walk}
+    ng, ns = o.claimed()
+    assert _keyset(ng, ns) == expect_claimed
+
+
+def test_grain_melted_entirely_nucleates_again_from_its_seed():
+    h, T_L = 2e-6, 1000.0
+    o = Oracle((0, 0, 0), (80e-6,) * 3, h, 2e-3, (1e-5,), (2.0,), T_L)
+    c = np.array([[40e-6, 40e-6, 40e-6]])
+    o.nucleation_sites(c, np.array([0.5]), inputs.shoemake_quaternions(1, inputs.rng(2)))
+    o.set_melting(True)
+    o.set_thermal_analytic(T_L - 5.0, (0, 0, 0), (0, 0, 0), 0.0)
+    o.step(30)
+    assert o.n_grains == 1 and o.n_particles > 100
+    o.set_thermal_analytic(T_L + 1.0, (0, 0, 0), (0, 0, 0), 0.0)     # superheat everywhere
+    o.step(3)
+    assert o.n_particles == 0 and len(o.reached()[0]) == 0
+    o.set_thermal_analytic(T_L - 0.4, (0, 0, 0), (0, 0, 0), 0.0)     # below its dT_n = 0.5
+    o.step(3)
+    assert o.n_particles == 0 and o.stats()["nucleated"] == 1
+    o.set_thermal_analytic(T_L - 0.6, (0, 0, 0), (0, 0, 0), 0.0)
+    o.step(1)
+    p = o.particles()
+    assert o.n_grains == 1 and o.stats()["nucleated"] == 2
+    assert sorted(p["dir"].tolist()) == list(range(6)) and (p["grain"] == 0).all()
+    assert (p["site"] == 0).all()
