@@ -143,7 +143,9 @@ typedef struct {
   int64_t n_nucleated;
   int64_t n_claim_blocks; /* claim blocks in use (at most gp_memory.claim_blocks)   */
   int64_t error_flags;    /* sticky device error bits (0 when healthy)             */
-  int64_t reserved[5];
+  int64_t n_melted;       /* reached sites melted (cumulative, gp_set_melting)     */
+  int64_t n_walkback;     /* particles re-activated by the walk-back (cumulative)  */
+  int64_t reserved[3];
 } gp_stats_t;
 
 /* Per-kernel timing collected with CUDA events when profiling is enabled. */
@@ -196,6 +198,25 @@ gp_status gp_seed_shell(gp_ctx* ctx, int64_t n, const int32_t* grains, int32_t n
 
 gp_status gp_set_thermal_analytic(gp_ctx* ctx, const gp_thermal_analytic* th);
 gp_status gp_set_thermal_grid(gp_ctx* ctx, const gp_thermal_grid* th);
+
+/* Melting (Sec. 2.1.3).  With enable != 0 every step of a single-run context starts,
+ * at t_n, with a melting pass in which:
+ *   - every reached lattice site whose position has Delta T < 0 melts: it is no
+ *     longer reached nor claimed (gp_get_reached and the grain map skip it);
+ *   - every particle whose position has Delta T < 0, or whose site has melted, is
+ *     removed, and its target is released;
+ *   - walk-back: each melted site m gets one new ACTIVE particle (ell = 0), from
+ *     its neighbour m - e_k for the first direction k = 0..5 whose neighbour is
+ *     still reached, heading to m, which it claims (the two sites straddle the
+ *     Delta T = 0 surface, within the paper's search distance of 2 lambda_0);
+ *   - a grain left without reached sites keeps its seed, which nucleates again,
+ *     with the same grain id and six particles, once its nucleation undercooling is
+ *     reached (0 for grains from gp_add_grains) and no reached site lies within h.
+ * The pass visits every reached site, so it costs about the reached-site list per
+ * step.  Grains seeded with gp_seed_shell record only their outer shell, so their
+ * interior counts as liquid.  GP_ERR_STATE on a batch context or while the adjoint
+ * tape records. */
+gp_status gp_set_melting(gp_ctx* ctx, int32_t enable);
 
 /* Sets (or replaces) the composition field of a single-run context; the grid is
  * copied into the arena (gp_memory.solute_nodes) or, for a library-allocated

@@ -47,7 +47,8 @@ struct Layout {
   int64_t tape_steps = 0;
   // offsets into the arena
   size_t rec0, rec1, pos4, sslot, act, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
-      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, dstats, grid, sgrid, runs,
+      rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, gflags, gdtn, dstats, grid,
+      sgrid, runs,
       rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, total;
 };
 
@@ -192,6 +193,8 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->act = take(4 * cap);
   L->nmeta = take(8 * (size_t)L->max_nuclei);
   L->sgrid = take(4 * (size_t)L->solute_nodes);
+  L->gflags = take(4 * (size_t)L->max_grains);
+  L->gdtn = take(4 * (size_t)L->max_grains);
   L->runs = take(sizeof(Geo) * (size_t)nruns);
   L->rtherm = take(16 * (size_t)nruns);
   L->rcount = take(16 * (size_t)nruns);
@@ -370,6 +373,9 @@ struct gp_ctx {
   bool keys_valid = false;
   bool broken = false;
   // adjoint tape: taped steps (sorted count n, count after the step m, step index)
+  bool melting = false;  // melting walk-back pass at the start of every step
+  uint8_t* gflags = nullptr;
+  float* gdtn = nullptr;  // nucleation undercooling of each grain's seed
   bool tape_on = false;
   int64_t tape_pos = 0;
   std::vector<int64_t> tape_n, tape_m, tape_t;
@@ -617,6 +623,8 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   c->npos = at<float4>(c, L.npos);
   c->ngrain = at<float4>(c, L.ngrain);
   c->nstate = at<int>(c, L.nstate);
+  c->gflags = at<uint8_t>(c, L.gflags);
+  c->gdtn = at<float>(c, L.gdtn);
   c->nmeta = at<int2>(c, L.nmeta);
   c->runs = at<Geo>(c, L.runs);
   c->rtherm = at<double2>(c, L.rtherm);
@@ -635,6 +643,8 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   e = e ? e : cudaMemsetAsync(c->dst, 0, sizeof(DevStats), s);
   e = e ? e : cudaMemsetAsync(c->gtab, 0, 64 * (size_t)L.max_grains, s);
   e = e ? e : cudaMemsetAsync(c->nstate, 0, 4 * (size_t)L.max_nuclei, s);
+  e = e ? e : cudaMemsetAsync(c->gflags, 0, 4 * (size_t)L.max_grains, s);
+  e = e ? e : cudaMemsetAsync(c->gdtn, 0, 4 * (size_t)L.max_grains, s);
   e = e ? e : cudaMemsetAsync(c->rtherm, 0, 16 * (size_t)L.nruns, s);
   e = e ? e : cudaMemcpyAsync(c->runs, c->geo.data(), sizeof(Geo) * c->geo.size(),
                               cudaMemcpyHostToDevice, s);
@@ -884,6 +894,15 @@ gp_status gp_set_thermal_grid(gp_ctx* c, const gp_thermal_grid* th) {
   return GP_OK;
 }
 
+gp_status gp_set_melting(gp_ctx* c, int32_t enable) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "melting applies to single-run contexts");
+  if (enable && c->tape_on) return fail(c, GP_ERR_STATE, "the adjoint tape is recording");
+  c->melting = enable != 0;
+  return GP_OK;
+}
+
 gp_status gp_set_solute_grid(gp_ctx* c, const gp_solute_grid* sg) {
   gp_status s = check_ctx(c);
   if (s) return s;
@@ -1092,9 +1111,21 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
   if (c->thermal == 0 && c->n_live > 0) return fail(c, GP_ERR_STATE, "no thermal field set");
   const bool batch = false;
   for (int it = 0; it < nsteps; ++it) {
-    const int64_t n = c->n_live;
     const StepArgs S = step_args(c, c->step);
     const Params P = step_params(c, c->step);
+    if (c->melting) {
+      // melting walk-back at t_n (Sec. 2.1.3); the compacted store lands in the other
+      // record buffer, which becomes the store
+      launch_melt(P, S, c->R, c->C, reinterpret_cast<unsigned long long*>(c->pos4),
+                  2 * c->L.cap, c->gflags, (int)c->n_grains, c->rec[c->cur], c->rec[c->cur ^ 1],
+                  c->n_live, c->L.cap, c->dst, c->sms, c->st);
+      GP_CUDA(c, cudaGetLastError());
+      c->cur ^= 1;
+      c->keys_valid = false;
+      s = sync_stats(c);
+      if (s) return s;
+    }
+    const int64_t n = c->n_live;
     const bool rec = c->tape_on && c->tape_pos < c->L.tape_steps;
     const size_t tq = (size_t)c->tape_pos, tcap = (size_t)c->L.cap;
     int32_t* tpar = rec ? at<int32_t>(c, c->L.tape_par) + tq * tcap : nullptr;
@@ -1137,20 +1168,31 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                   c->sb.vals[0], c->L.cap, c->C, c->R, tpar, c->dst, c->st);
       c->prof.end(K_EMIT, (double)n);
     }
-    const int64_t pending = c->n_nuclei - (int64_t)c->hst->nucleated;
-    if (pending > 0) {
-      const StepArgs S1 = step_args(c, c->step + 1);
+    // pending sites: registered minus activated (re-nucleations of dormant seeds
+    // count as nucleations too, so they are subtracted back)
+    const int64_t pending =
+        c->n_nuclei - ((int64_t)c->hst->nucleated - (int64_t)c->hst->renucleated);
+    const int64_t dormant = (int64_t)c->hst->n_dormant;
+    const StepArgs S1 = step_args(c, c->step + 1);
+    if (pending > 0 || dormant > 0)
       launch_link_reached(batch, P, c->R, &c->dst->linked, c->sms, c->st);
+    if (dormant > 0)  // before any activation of the step
+      launch_dormant_test(P, S1, c->R, c->gdtn, c->gflags, (int)c->n_grains, c->st);
+    if (pending > 0) {
       c->prof.begin(K_NUCLEATE);
       launch_nucleate(P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
                       c->L.max_grains, c->rec[c->cur], static_cast<uint32_t*>(c->sb.keys[0]),
-                      c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->st);
+                      c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->gdtn, c->st);
       c->prof.end(K_NUCLEATE, 1.0);
     } else {
       c->prof.begin(K_FINALIZE);
       launch_finalize(c->dst, c->L.cap, false, c->st);
       c->prof.end(K_FINALIZE, 1.0);
     }
+    if (dormant > 0)
+      launch_renucleate(P, c->gflags, (int)c->n_grains, c->rec[c->cur],
+                        static_cast<uint32_t*>(c->sb.keys[0]), c->sb.vals[0], c->L.cap, c->C,
+                        c->R, c->dst, c->st);
     GP_CUDA(c, cudaGetLastError());
     const int64_t stepped = c->step;
     ++c->step;
@@ -1171,6 +1213,7 @@ gp_status gp_tape_begin(gp_ctx* c) {
   gp_status s = check_ctx(c);
   if (s) return s;
   if (c->batch) return fail(c, GP_ERR_STATE, "the adjoint is for single-run contexts");
+  if (c->melting) return fail(c, GP_ERR_STATE, "the adjoint holds no melting events");
   if (c->P.solute) return fail(c, GP_ERR_STATE, "the adjoint takes the nominal liquidus");
   if (c->L.tape_steps <= 0) return fail(c, GP_ERR_STATE, "no tape (gp_memory.tape_steps = 0)");
   if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
@@ -1241,6 +1284,8 @@ gp_status gp_stats(gp_ctx* c, gp_stats_t* o) {
   o->n_nucleated = (int64_t)d.nucleated;
   o->n_claim_blocks = (int64_t)d.claim_used;
   o->error_flags = (int64_t)d.err;
+  o->n_melted = (int64_t)d.melted;
+  o->n_walkback = (int64_t)d.walkback;
   return GP_OK;
 }
 
@@ -1341,11 +1386,11 @@ gp_status gp_get_reached(gp_ctx* c, int64_t cap, int32_t* grain, int32_t* site3,
   s = sync_stats(c);
   if (s) return s;
   const int64_t n = (int64_t)std::min<unsigned long long>(c->hst->reached, c->L.rcap);
-  if (n_out) *n_out = n;
-  const int64_t m = std::min(n, cap);
-  if (m <= 0) return GP_OK;
-  std::vector<unsigned long long> k(m);
-  GP_CUDA(c, cudaMemcpy(k.data(), c->R.key, 8 * m, cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> k(n);
+  if (n > 0) GP_CUDA(c, cudaMemcpy(k.data(), c->R.key, 8 * n, cudaMemcpyDeviceToHost));
+  k.erase(std::remove(k.begin(), k.end(), kDeadSite), k.end());  // melted sites
+  if (n_out) *n_out = (int64_t)k.size();
+  const int64_t m = std::min((int64_t)k.size(), cap);
   for (int64_t i = 0; i < m; ++i) {
     int g, x, y, z;
     unpack_site(k[i], g, x, y, z);

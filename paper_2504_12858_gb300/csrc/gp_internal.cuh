@@ -322,7 +322,8 @@ __device__ __forceinline__ float growth_v(const Params& P, float dT) {
 // ---------------------------------------------------------------------------------
 // lattice-site claim table: open addressing over 8^3-site blocks of a grain; each
 // block holds one byte per site: bit 7 = claimed, bits 0..2 = claimant axes of an
-// even step, bits 3..5 = claimant axes of an odd step.
+// even step, bits 3..5 = claimant axes of an odd step, bit 6 = reached and not
+// melted (maintained by the melting pass only).
 // ---------------------------------------------------------------------------------
 // The blocks live in a dense pool, handed out in order of first claim (so blocks
 // claimed by nearby particles sit close together in memory); an open-addressing
@@ -482,6 +483,10 @@ __device__ inline uint32_t* claim_lookup(const Claims& C, int g, int tx, int ty,
 // ---------------------------------------------------------------------------------
 // reached lattice sites: append-only list, linked per hash cell for range queries
 // ---------------------------------------------------------------------------------
+// an entry of the reached-site list whose site has melted (never a packed site: the
+// grain field would exceed every grain id)
+constexpr unsigned long long kDeadSite = ~0ull;
+
 struct Reached {
   unsigned long long* key;  // packed (grain, site)
   uint32_t* next;           // next entry in the same cell, 0xFFFFFFFF ends
@@ -527,6 +532,12 @@ struct DevStats {
   unsigned long long n_act;        // ACTIVE particles listed by the last build
   unsigned long long step;         // batch: index n of the step being computed
   unsigned long long stamp;        // batch: cell-table stamp of the current build
+  unsigned long long melted;       // reached sites melted (cumulative)
+  unsigned long long walkback;     // particles re-activated by the walk-back (cumulative)
+  unsigned long long n_dormant;    // grains melted entirely whose seed waits
+  unsigned long long n_mlist;      // sites melted by the last melting pass
+  unsigned long long removed;      // particles removed by the last melting pass
+  unsigned long long renucleated;  // re-nucleations of dormant seeds (cumulative)
 };
 
 // warp-aggregated 64-bit counter increment

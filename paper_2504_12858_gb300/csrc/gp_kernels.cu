@@ -210,8 +210,13 @@ __device__ int nearest_reached(const Params& P, const Geo& gm, const Reached& R,
         uint32_t r = R.head[head_index(gm, hs, bx << hs, by << hs, bz << hs)];
         unsigned long long steps = 0;
         while (r != kNoEntry && steps++ < guard) {
+          const unsigned long long key = R.key[r];
+          if (key == kDeadSite) {  // melted
+            r = R.next[r];
+            continue;
+          }
           int g, sx, sy, sz;
-          unpack_site(R.key[r], g, sx, sy, sz);
+          unpack_site(key, g, sx, sy, sz);
           float4 gc, r0, r1, r2;
           grain_load(P.gtab, g, gc, r0, r1, r2);
           float3 q = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
@@ -623,8 +628,10 @@ __global__ void k_link_reached(Params P, Reached R, const unsigned long long* li
   const unsigned long long r1 = min(*R.count, R.cap);
   for (unsigned long long r = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
        r < r1; r += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = R.key[r];
+    if (key == kDeadSite) continue;  // melted before it was linked: never linked
     int g, sx, sy, sz;
-    unpack_site(R.key[r], g, sx, sy, sz);
+    unpack_site(key, g, sx, sy, sz);
     float4 gc, q0, q1, q2;
     grain_load(P.gtab, g, gc, q0, q1, q2);
     const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
@@ -646,7 +653,8 @@ __global__ void __launch_bounds__(256) k_nucleate(Params P, StepArgs S1, const f
                                                   const float4* ngrain, int* nstate, int m,
                                                   float4* gtab, int max_grains, int4* rout,
                                                   uint32_t* keys, uint32_t* vals, int64_t cap,
-                                                  Claims C, Reached R, DevStats* st) {
+                                                  Claims C, Reached R, DevStats* st,
+                                                  float* gdtn) {
   __shared__ uint32_t s_warp[8];
   __shared__ uint32_t s_run;
   // phase 1: candidates (nstate: 0 pending, 1 candidate, 2 done)
@@ -688,6 +696,7 @@ __global__ void __launch_bounds__(256) k_nucleate(Params P, StepArgs S1, const f
         atomicOr(&st->err, ERR_GRAINS);
       } else {
         for (int q = 0; q < 4; ++q) gtab[4 * g + q] = ngrain[4 * j + q];
+        if (gdtn) gdtn[g] = npos[j].w;  // for a later re-nucleation (melting)
         const float4 cq = ngrain[4 * j];
         const float3 c = make_float3(cq.x, cq.y, cq.z);
         // nucleus site reached
@@ -833,6 +842,231 @@ __global__ void __launch_bounds__(256) k_run_counts(Params P, const int4* __rest
   __syncthreads();
   for (int i = threadIdx.x; i < 2 * nruns; i += blockDim.x)
     if (s_c[i]) atomicAdd(counts + i, (unsigned long long)s_c[i]);
+}
+
+// ---------------------------------------------------------------------------------
+// melting walk-back (Sec. 2.1.3), single-run contexts, at t_n before the hash:
+//   k_melt_sites      every reached site: superheated -> melted (list entry dead,
+//                     claim byte cleared, appended to the melted list); else its
+//                     claim byte gets the "reached and not melted" bit 6
+//   k_melt_particles  particles superheated or on a site without bit 6 are removed
+//                     and release their (never reached) targets
+//   k_walkback        per melted site, the first direction k whose neighbour m - e_k
+//                     keeps bit 6 sends a new particle from it to m, which it claims
+//   k_compact         drops the removed records from the store
+//   k_melt_grains     grains with melted sites and none left become dormant
+// gflags per grain: byte 0 = has an unmelted site, byte 1 = lost a site in this pass,
+// byte 2 = dormant, byte 3 = re-nucleates this step.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_melt_sites(Params P, StepArgs S, Reached R, Claims C,
+                                                    unsigned long long* mlist, int64_t mcap,
+                                                    uint8_t* gflags, DevStats* st) {
+  const unsigned long long n = min(*R.count, R.cap);
+  // warp-uniform trip count: every lane reaches the warp-wide claim lookups
+  for (unsigned long long r0 = (unsigned long long)blockIdx.x * blockDim.x; r0 < n;
+       r0 += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long r = r0 + threadIdx.x;
+    const unsigned long long key = r < n ? R.key[r] : kDeadSite;
+    const bool valid = key != kDeadSite;
+    int g = 0, sx = 0, sy = 0, sz = 0;
+    bool melt = false;
+    if (valid) {
+      unpack_site(key, g, sx, sy, sz);
+      float4 gc, q0, q1, q2;
+      grain_load(P.gtab, g, gc, q0, q1, q2);
+      const float3 x = site_pos_g(gc, q0, q1, q2, sx, sy, sz);
+      melt = undercooling(P, P.geo, S, x, P.geo.dT_base) < 0.f;
+    }
+    BlockCache bc;
+    int sh = 0;
+    uint32_t* w = warp_claim_word(C, valid, g, sx, sy, sz, true, sh, bc);
+    if (w) {
+      if (melt) atomicAnd(w, ~(0xffu << sh));
+      else atomicOr(w, 0x40u << sh);
+    }
+    warp_add(&st->melted, melt ? 1u : 0u);
+    if (melt) {
+      R.key[r] = kDeadSite;
+      const unsigned long long i = atomicAdd(&st->n_mlist, 1ull);
+      if ((int64_t)i < mcap) mlist[i] = key;
+      else atomicOr(&st->err, ERR_CAPACITY);
+      gflags[4 * (size_t)g + 1] = 1;
+    } else if (valid) {
+      gflags[4 * (size_t)g] = 1;
+    }
+  }
+}
+
+// claim byte of site t of grain g (nullptr if its block was never claimed)
+__device__ __forceinline__ uint32_t* site_byte(const Claims& C, int g, int tx, int ty, int tz,
+                                               int& sh, BlockCache& bc) {
+  return claim_lookup(C, g, tx, ty, tz, sh, bc);
+}
+
+__global__ void __launch_bounds__(256) k_melt_particles(Params P, StepArgs S, int4* rec,
+                                                        int64_t n, Claims C, DevStats* st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool removed = false;
+  if (i < n) {
+    Rec r = rec_unpack(rec[i]);
+    if (r.state == ST_ACTIVE || r.state == ST_FROZEN) {
+      const float3 x = part_pos(P.gtab, r.grain, r.sx, r.sy, r.sz, r.dir, r.ell);
+      BlockCache bc;
+      int sh = 0;
+      const uint32_t* w = site_byte(C, r.grain, r.sx, r.sy, r.sz, sh, bc);
+      const bool alive = w && (((*(volatile const uint32_t*)w) >> sh) & 0x40u);
+      if (!alive || undercooling(P, P.geo, S, x, P.geo.dT_base) < 0.f) {
+        removed = true;
+        r.state = ST_REMOVED;
+        rec[i] = rec_pack(r);
+        int tx = r.sx, ty = r.sy, tz = r.sz;
+        step_site(tx, ty, tz, r.dir);
+        uint32_t* wt = site_byte(C, r.grain, tx, ty, tz, sh, bc);
+        if (wt && !(((*(volatile uint32_t*)wt) >> sh) & 0x40u)) atomicAnd(wt, ~(0xffu << sh));
+      }
+    }
+  }
+  warp_add(&st->removed, removed ? 1u : 0u);
+}
+
+__global__ void __launch_bounds__(256) k_walkback(Params P, const unsigned long long* mlist,
+                                                  Claims C, int4* rec, int64_t cap,
+                                                  DevStats* st) {
+  const unsigned long long m = st->n_mlist;
+  for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
+       q += (unsigned long long)gridDim.x * blockDim.x) {
+    int g, mx, my, mz;
+    unpack_site(mlist[q], g, mx, my, mz);
+    BlockCache bc;
+    for (int k = 0; k < 6; ++k) {
+      int nx = mx, ny = my, nz = mz;
+      step_site(nx, ny, nz, k ^ 1);  // m - e_k
+      int sh = 0;
+      const uint32_t* w = site_byte(C, g, nx, ny, nz, sh, bc);
+      if (!w || !(((*(volatile const uint32_t*)w) >> sh) & 0x40u)) continue;
+      const unsigned long long o = atomicAdd(&st->n_live, 1ull);
+      if (o < (unsigned long long)cap) {
+        Rec r;
+        r.grain = g;
+        r.sx = nx;
+        r.sy = ny;
+        r.sz = nz;
+        r.dir = k;
+        r.state = ST_ACTIVE;
+        r.cross = 0;
+        r.ell = 0.f;
+        rec[o] = rec_pack(r);
+      } else {
+        atomicOr(&st->err, ERR_CAPACITY);
+      }
+      int shm = 0;
+      uint32_t* wm = site_byte(C, g, mx, my, mz, shm, bc);
+      if (wm) atomicOr(wm, 0x80u << shm);
+      atomicAdd(&st->walkback, 1ull);
+      break;
+    }
+  }
+}
+
+// copies the records of rin[0, n_live) that are not REMOVED to rout (one reservation
+// per CTA); n_live becomes their count
+__global__ void __launch_bounds__(256) k_compact(const int4* __restrict__ rin, int4* rout,
+                                                 const unsigned long long* n_in,
+                                                 unsigned long long* n_out) {
+  __shared__ uint32_t s_warp[8];
+  __shared__ unsigned long long s_base;
+  const int64_t n = (int64_t)*n_in;
+  for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < n;
+       j0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = j0 + threadIdx.x;
+    int4 v = make_int4(0, 0, 0, 0);
+    bool keep = false;
+    if (j < n) {
+      v = rin[j];
+      keep = rec_unpack(v).state != ST_REMOVED;
+    }
+    uint32_t tot;
+    const uint32_t ofs = bscan256(keep ? 1u : 0u, s_warp, tot);
+    if (threadIdx.x == 0) s_base = tot ? atomicAdd(n_out, (unsigned long long)tot) : 0ull;
+    __syncthreads();
+    if (keep) rout[s_base + ofs] = v;  // s_base is rewritten only after the next scan
+  }
+}
+
+__global__ void k_melt_grains(uint8_t* gflags, int ng, DevStats* st) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    uint8_t* f = gflags + 4 * (size_t)g;
+    if (f[1] && !f[0] && !f[2]) {
+      f[2] = 1;
+      atomicAdd(&st->n_dormant, 1ull);
+    }
+    f[0] = 0;
+    f[1] = 0;
+  }
+}
+
+// seeds of dormant grains that nucleate again at t_{n+1}: tested before any
+// activation of the step (as the pending sites are)
+__global__ void k_dormant_test(Params P, StepArgs S1, Reached R, const float* gdtn,
+                               uint8_t* gflags, int ng) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    uint8_t* f = gflags + 4 * (size_t)g;
+    if (!f[2]) continue;
+    const float4 c = __ldg(P.gtab + 4 * (size_t)g);
+    const float3 p = make_float3(c.x, c.y, c.z);
+    if (undercooling(P, P.geo, S1, p, P.geo.dT_base1) >= gdtn[g] &&
+        nearest_reached(P, P.geo, R, p, true) < 0)
+      f[3] = 1;
+  }
+}
+
+// re-nucleation of the marked seeds, after the step's new nuclei: six particles at
+// the nucleus with the grain's own id, nucleus reached and claimed, targets claimed
+__global__ void __launch_bounds__(256) k_renucleate(Params P, uint8_t* gflags, int ng, int4* rout,
+                                                    uint32_t* keys, uint32_t* vals, int64_t cap,
+                                                    Claims C, Reached R, DevStats* st) {
+  for (int g0 = blockIdx.x * blockDim.x; g0 < ng; g0 += gridDim.x * blockDim.x) {
+    const int g = g0 + threadIdx.x;
+    const bool cand = g < ng && gflags[4 * (size_t)g + 3];
+    if (!__any_sync(0xffffffffu, cand)) continue;
+    {
+      BlockCache bc;
+      for (int k = -1; k < 6; ++k) {
+        int tx = 0, ty = 0, tz = 0;
+        if (k >= 0) step_site(tx, ty, tz, k);
+        int sh = 0;
+        uint32_t* w = warp_claim_word(C, cand, g, tx, ty, tz, true, sh, bc);
+        if (w) atomicOr(w, 0x80u << sh);
+      }
+    }
+    if (!cand) continue;
+    gflags[4 * (size_t)g + 2] = 0;
+    gflags[4 * (size_t)g + 3] = 0;
+    atomicAdd(&st->n_dormant, ~0ull);  // minus one
+    atomicAdd(&st->nucleated, 1ull);
+    atomicAdd(&st->renucleated, 1ull);
+    reached_append(R, g, 0, 0, 0);
+    const float4 c = __ldg(P.gtab + 4 * (size_t)g);
+    const uint32_t key = cell_key<uint32_t>(P, P.geo, make_float3(c.x, c.y, c.z));
+    const unsigned long long o0 = atomicAdd(&st->n_live, 6ull);
+    for (int k = 0; k < 6; ++k) {
+      const unsigned long long o = o0 + k;
+      if (o < (unsigned long long)cap) {
+        Rec rr;
+        rr.grain = g;
+        rr.sx = rr.sy = rr.sz = 0;
+        rr.dir = k;
+        rr.state = ST_ACTIVE;
+        rr.cross = 0;
+        rr.ell = 0.f;
+        rout[o] = rec_pack(rr);
+        keys[o] = key;
+        vals[o] = (uint32_t)o;
+      } else {
+        atomicOr(&st->err, ERR_CAPACITY);
+      }
+    }
+  }
 }
 
 // end of a step: live count for the next step; a batch also advances its step and
@@ -1149,9 +1383,9 @@ void launch_nucleate_batch(const Params& P, const StepArgs& S1, const float4* np
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
                      int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,
-                     cudaStream_t st) {
+                     float* gdtn, cudaStream_t st) {
   k_nucleate<<<1, 256, 0, st>>>(P, S1, npos, ngrain, nstate, m, gtab, max_grains, rout, keys,
-                                vals, cap, C, R, dst);
+                                vals, cap, C, R, dst, gdtn);
 }
 
 void launch_run_step(Geo* runs, const double2* th, int nruns, const DevStats* dst, double dt,
@@ -1164,6 +1398,35 @@ void launch_run_counts(const Params& P, const int4* rec, int64_t n, int nruns,
   if (n <= 0) return;
   const unsigned nb = (unsigned)std::min<int64_t>(blocks(n), 152 * 8);
   k_run_counts<<<nb, 256, 0, st>>>(P, rec, n, nruns, counts);
+}
+
+void launch_melt(const Params& P, const StepArgs& S, const Reached& R, const Claims& C,
+                 unsigned long long* mlist, int64_t mcap, uint8_t* gflags, int ng, int4* rec,
+                 int4* rtmp, int64_t n, int64_t cap, DevStats* dst, int sms, cudaStream_t st) {
+  cudaMemsetAsync(&dst->n_mlist, 0, sizeof(unsigned long long), st);
+  cudaMemsetAsync(&dst->removed, 0, sizeof(unsigned long long), st);
+  k_melt_sites<<<sms * 8, 256, 0, st>>>(P, S, R, C, mlist, mcap, gflags, dst);
+  if (n > 0) k_melt_particles<<<blocks(n), 256, 0, st>>>(P, S, rec, n, C, dst);
+  k_walkback<<<sms * 4, 256, 0, st>>>(P, mlist, C, rec, cap, dst);
+  // the store (walk-back particles appended) is compacted into rtmp
+  cudaMemcpyAsync(&dst->n_out, &dst->n_live, sizeof(unsigned long long),
+                  cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(&dst->n_live, 0, sizeof(unsigned long long), st);
+  k_compact<<<sms * 8, 256, 0, st>>>(rec, rtmp, &dst->n_out, &dst->n_live);
+  if (ng > 0) k_melt_grains<<<(ng + 255) / 256, 256, 0, st>>>(gflags, ng, dst);
+}
+
+void launch_dormant_test(const Params& P, const StepArgs& S1, const Reached& R, const float* gdtn,
+                         uint8_t* gflags, int ng, cudaStream_t st) {
+  if (ng > 0) k_dormant_test<<<(ng + 255) / 256, 256, 0, st>>>(P, S1, R, gdtn, gflags, ng);
+}
+
+void launch_renucleate(const Params& P, uint8_t* gflags, int ng, int4* rout, uint32_t* keys,
+                       uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
+                       DevStats* dst, cudaStream_t st) {
+  if (ng > 0)
+    k_renucleate<<<(ng + 255) / 256, 256, 0, st>>>(P, gflags, ng, rout, keys, vals, cap, C, R,
+                                                   dst);
 }
 
 void launch_finalize(DevStats* dst, int64_t cap, bool batch, cudaStream_t st) {

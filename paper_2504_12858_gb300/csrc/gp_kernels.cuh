@@ -40,7 +40,18 @@ void launch_adj_unsort(const float* lam_s, const uint32_t* vals, int64_t n, floa
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
                      int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,
-                     cudaStream_t st);
+                     float* gdtn, cudaStream_t st);
+// melting walk-back pass at t_n (single run): melts superheated reached sites,
+// removes particles in the melt, re-activates the walk-back particles, compacts the
+// store from rec into rtmp (the caller swaps them), marks fully melted grains
+void launch_melt(const Params& P, const StepArgs& S, const Reached& R, const Claims& C,
+                 unsigned long long* mlist, int64_t mcap, uint8_t* gflags, int ng, int4* rec,
+                 int4* rtmp, int64_t n, int64_t cap, DevStats* dst, int sms, cudaStream_t st);
+void launch_dormant_test(const Params& P, const StepArgs& S1, const Reached& R, const float* gdtn,
+                         uint8_t* gflags, int ng, cudaStream_t st);
+void launch_renucleate(const Params& P, uint8_t* gflags, int ng, int4* rout, uint32_t* keys,
+                       uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
+                       DevStats* dst, cudaStream_t st);
 void launch_finalize(DevStats* dst, int64_t cap, bool batch, cudaStream_t st);
 void launch_run_step(Geo* runs, const double2* th, int nruns, const DevStats* dst, double dt,
                      cudaStream_t st);

@@ -59,11 +59,12 @@ class gp_memory(C.Structure):
 
 STATS_FIELDS = ["step", "n_live", "n_active", "n_frozen", "n_grains", "n_reached",
                 "particle_steps", "n_frozen_new", "n_spawned", "n_claims_lost", "n_clipped",
-                "n_clamped", "n_nucleated", "n_claim_blocks", "error_flags"]
+                "n_clamped", "n_nucleated", "n_claim_blocks", "error_flags", "n_melted",
+                "n_walkback"]
 
 
 class gp_stats_t(C.Structure):
-    _fields_ = [(f, C.c_int64) for f in STATS_FIELDS] + [("reserved", C.c_int64 * 5)]
+    _fields_ = [(f, C.c_int64) for f in STATS_FIELDS] + [("reserved", C.c_int64 * 3)]
 
 
 class gp_launch_config(C.Structure):
@@ -90,6 +91,7 @@ SIGNATURES = {
     "gp_set_thermal_analytic": (C.c_int, [_P, C.POINTER(gp_thermal_analytic)]),
     "gp_set_thermal_grid": (C.c_int, [_P, C.POINTER(gp_thermal_grid)]),
     "gp_set_solute_grid": (C.c_int, [_P, C.POINTER(gp_solute_grid)]),
+    "gp_set_melting": (C.c_int, [_P, C.c_int32]),
     "gp_nucleation_sites": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "gp_step": (C.c_int, [_P, C.c_int32]),
     "gp_grain_map": (C.c_int, [_P, C.POINTER(gp_voxel_grid), _P, C.c_int32]),
@@ -303,6 +305,9 @@ class Sim:
         th.spacing[:] = [float(v) for v in spacing]
         th.frame_vel[:] = [float(v) for v in vel]
         self._check(load().gp_set_thermal_grid(self._h, C.byref(th)))
+
+    def gp_set_melting(self, enable=True):
+        self._check(load().gp_set_melting(self._h, 1 if enable else 0))
 
     def gp_set_solute_grid(self, w, origin, spacing, T_m, m_L, vel=(0.0, 0.0, 0.0)):
         """w: numpy (host) or torch CUDA float32 tensor of shape (nz, ny, nx)."""
