@@ -72,6 +72,7 @@ def lib():
         "go_set_thermal_grid": (None, [vp, P_F, P_I32, P_D, P_D, P_D]),
         "go_set_solute_grid": (None, [vp, P_F, P_I32, P_D, P_D, P_D, d, d]),
         "go_set_melting": (None, [vp, C.c_int]),
+        "go_set_periodic": (None, [vp, C.c_int]),
         "go_add_grains": (i64, [vp, i64, P_D, P_D, C.c_int]),
         "go_seed_shell": (None, [vp, i64, P_I32, i32, d, C.c_int]),
         "go_nucleation_sites": (None, [vp, i64, P_D, P_D, P_D]),
@@ -154,6 +155,10 @@ class Oracle:
         nz, ny, nx = w.shape
         lib().go_set_solute_grid(self._p, w.reshape(-1), np.array([nx, ny, nz], np.int32),
                                  _d3(origin), _d3(spacing), _d3(vel), float(Tm), float(mL))
+
+    def set_periodic(self, axes):
+        """Periodic axes, a bit per axis (1 = x, 2 = y, 4 = z)."""
+        lib().go_set_periodic(self._p, int(axes))
 
     def set_melting(self, on=True):
         """Melting walk-back pass at the start of every step (Sec. 2.1.3)."""

@@ -206,7 +206,9 @@ struct Sim {
 
   // Total undercooling Delta T = T_L - T(x, t)  (Sec. 2.1.2, before Eq. 1), with the
   // local liquidus when a composition field is set.
-  double undercooling(const double x[3], double t) const {
+  double undercooling(const double xin[3], double t) const {
+    double x[3] = {xin[0], xin[1], xin[2]};
+    wrap(x);  // fields are sampled at the position inside the domain
     const double tl = liquidus(x, t);
     if (thermal_mode == 1) {
       double T = T0 + G[0] * (x[0] - xref[0]) + G[1] * (x[1] - xref[1]) +
@@ -226,19 +228,55 @@ struct Sim {
     return v;
   }
 
+  // Periodic axes (Sec. 3.4 applies periodic conditions on the faces normal to x
+  // and y), reading r18: along a periodic axis a point is identified with its images
+  // x + m L (L = hi - lo); positions are wrapped into [lo, hi), distances take the
+  // nearest image, and nothing is clipped.  The lattice of a grain is unbounded, so
+  // a grain crossing the face continues on the other side.
+  int periodic = 0;  // bit a set: axis a is periodic
+  bool per(int a_) const { return (periodic >> a_) & 1; }
+  void wrap(double x[3]) const {
+    for (int a_ = 0; a_ < 3; ++a_) {
+      if (!per(a_)) continue;
+      const double L = hi[a_] - lo[a_];
+      double u = x[a_] - lo[a_];
+      u -= L * std::floor(u / L);
+      x[a_] = lo[a_] + u;
+    }
+  }
+  double dist2(const double a[3], const double b[3]) const {
+    double d2 = 0;
+    for (int a_ = 0; a_ < 3; ++a_) {
+      double d = a[a_] - b[a_];
+      if (per(a_)) {
+        const double L = hi[a_] - lo[a_];
+        d -= L * std::round(d / L);
+      }
+      d2 += d * d;
+    }
+    return d2;
+  }
+
   bool inside(const double x[3]) const {
     for (int a_ = 0; a_ < 3; ++a_)
-      if (!(x[a_] >= lo[a_] && x[a_] <= hi[a_])) return false;
+      if (!per(a_) && !(x[a_] >= lo[a_] && x[a_] <= hi[a_])) return false;
     return true;
   }
 
   // Cell list in FP64.  The cell edge is the contact radius h enlarged by 2^-9
   // (reading r3), so two points closer than h always lie in neighbouring cells.
+  // Along a periodic axis the period is divided into floor(L / edge) equal cells
+  // (at least 3), each no narrower than that edge, and neighbours wrap around.
   // Returns the cell index triple, clamped to the domain grid.
   double cell_edge() const { return h * (1.0 + 1.0 / 512.0); }
-  void cell_of(const double x[3], int c[3], const int n[3]) const {
+  double edge(int a_, const int n[3]) const {
+    return per(a_) ? (hi[a_] - lo[a_]) / n[a_] : cell_edge();
+  }
+  void cell_of(const double xin[3], int c[3], const int n[3]) const {
+    double x[3] = {xin[0], xin[1], xin[2]};
+    wrap(x);
     for (int a_ = 0; a_ < 3; ++a_) {
-      int v = (int)std::floor((x[a_] - lo[a_]) / cell_edge());
+      int v = (int)std::floor((x[a_] - lo[a_]) / edge(a_, n));
       if (v < 0) v = 0;
       if (v > n[a_] - 1) v = n[a_] - 1;
       c[a_] = v;
@@ -246,9 +284,16 @@ struct Sim {
   }
   void ncells(int n[3]) const {
     for (int a_ = 0; a_ < 3; ++a_) {
-      int v = (int)std::ceil((hi[a_] - lo[a_]) / cell_edge());
+      const double L = hi[a_] - lo[a_];
+      int v = per(a_) ? (int)std::floor(L / cell_edge()) : (int)std::ceil(L / cell_edge());
       n[a_] = v < 1 ? 1 : v;
     }
+  }
+  // cell c + d along axis a: wrapped on a periodic axis, else -1 outside the grid
+  int nb_cell(int c, int d, int a_, const int n[3]) const {
+    int v = c + d;
+    if (per(a_)) return (v + n[a_]) % n[a_];
+    return (v < 0 || v >= n[a_]) ? -1 : v;
   }
 
   // Sec. 2.1.2 (impingement): "the advance of particles is naturally stopped when
@@ -277,16 +322,14 @@ struct Sim {
       for (int dz = -1; dz <= 1 && !hit; ++dz)
         for (int dy = -1; dy <= 1 && !hit; ++dy)
           for (int dx = -1; dx <= 1 && !hit; ++dx) {
-            int cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
-            if (cx < 0 || cy < 0 || cz < 0 || cx >= n[0] || cy >= n[1] || cz >= n[2])
-              continue;
+            int cx = nb_cell(c[0], dx, 0, n), cy = nb_cell(c[1], dy, 1, n),
+                cz = nb_cell(c[2], dz, 2, n);
+            if (cx < 0 || cy < 0 || cz < 0) continue;
             auto it = cells.find(((int64_t)cz * n[1] + cy) * n[0] + cx);
             if (it == cells.end()) continue;
             for (int64_t j : it->second) {
               if (parts[j].grain == parts[i].grain) continue;
-              double ex = X[i][0] - X[j][0], ey = X[i][1] - X[j][1],
-                     ez = X[i][2] - X[j][2];
-              if (ex * ex + ey * ey + ez * ez < rc2) {
+              if (dist2(X[i].data(), X[j].data()) < rc2) {
                 hit = true;
                 break;
               }
@@ -307,8 +350,7 @@ struct Sim {
       int32_t s[3] = {r.x, r.y, r.z};
       double q[3];
       site_pos(r.g, s, 0.0, 0, q);
-      double ex = p[0] - q[0], ey = p[1] - q[1], ez = p[2] - q[2];
-      if (ex * ex + ey * ey + ez * ez < rc2) return true;
+      if (dist2(p, q) < rc2) return true;
     }
     return false;
   }
@@ -587,22 +629,24 @@ struct Sim {
                    const std::unordered_map<int64_t, std::vector<size_t>>& cells,
                    const int n[3], const std::vector<std::array<double, 3>>& RP) const {
     double rc2 = h * h;
+    double pw[3] = {p[0], p[1], p[2]};
+    wrap(pw);
     int c[3];
-    for (int a_ = 0; a_ < 3; ++a_) c[a_] = (int)std::floor((p[a_] - lo[a_]) / cell_edge());
+    for (int a_ = 0; a_ < 3; ++a_) c[a_] = (int)std::floor((pw[a_] - lo[a_]) / edge(a_, n));
     double best = rc2;
     int32_t bg = -1;
     for (int dz = -1; dz <= 1; ++dz)
       for (int dy = -1; dy <= 1; ++dy)
         for (int dx = -1; dx <= 1; ++dx) {
-          int cx = std::min(std::max(c[0] + dx, 0), n[0] - 1);
-          int cy = std::min(std::max(c[1] + dy, 0), n[1] - 1);
-          int cz = std::min(std::max(c[2] + dz, 0), n[2] - 1);
+          int d3[3] = {dx, dy, dz}, cc[3];
+          for (int a_ = 0; a_ < 3; ++a_)
+            cc[a_] = per(a_) ? (((c[a_] + d3[a_]) % n[a_]) + n[a_]) % n[a_]
+                             : std::min(std::max(c[a_] + d3[a_], 0), n[a_] - 1);
           // clamping may visit a boundary cell more than once; harmless.
-          auto it = cells.find(((int64_t)cz * n[1] + cy) * n[0] + cx);
+          auto it = cells.find(((int64_t)cc[2] * n[1] + cc[1]) * n[0] + cc[0]);
           if (it == cells.end()) continue;
           for (size_t r : it->second) {
-            double ex = p[0] - RP[r][0], ey = p[1] - RP[r][1], ez = p[2] - RP[r][2];
-            double d2 = ex * ex + ey * ey + ez * ez;
+            double d2 = dist2(pw, RP[r].data());
             int32_t g = reached[r].g;
             if (d2 >= rc2) continue;
             if (d2 < best || (d2 == best && g < bg)) {
@@ -905,6 +949,10 @@ void go_get_stats(void* s, int64_t* out) {
   out[10] = S->st.n_walkback;
 }
 
+// Axes with periodic conditions: bit a set for axis a (reading r18).  A periodic
+// axis needs at least three cells of the contact search along it.
+void go_set_periodic(void* s, int axes) { ((Sim*)s)->periodic = axes & 7; }
+
 // Enables (1) or disables (0) the melting walk-back pass (reading r17).
 void go_set_melting(void* s, int on) { ((Sim*)s)->melting = on != 0; }
 
@@ -963,8 +1011,7 @@ void go_grain_map_bruteforce(void* s, const double origin[3], const double spaci
         double best = rc2;
         int32_t bg = -1;
         for (size_t r = 0; r < RP.size(); ++r) {
-          double ex = p[0] - RP[r][0], ey = p[1] - RP[r][1], ez = p[2] - RP[r][2];
-          double d2 = ex * ex + ey * ey + ez * ez;
+          double d2 = S->dist2(p, RP[r].data());
           if (d2 >= rc2) continue;
           int32_t g = S->reached[r].g;
           if (d2 < best || (d2 == best && g < bg)) {
@@ -994,8 +1041,7 @@ void go_contact_f64(void* s, uint8_t* freeze, int bruteforce) {
     if (S->parts[i].state != ACTIVE) continue;
     for (size_t j = 0; j < N; ++j) {
       if (S->parts[j].state == REMOVED || S->parts[j].grain == S->parts[i].grain) continue;
-      double ex = X[i][0] - X[j][0], ey = X[i][1] - X[j][1], ez = X[i][2] - X[j][2];
-      if (ex * ex + ey * ey + ez * ez < rc2) {
+      if (S->dist2(X[i].data(), X[j].data()) < rc2) {
         freeze[i] = 1;
         break;
       }
