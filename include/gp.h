@@ -199,6 +199,17 @@ gp_status gp_seed_shell(gp_ctx* ctx, int64_t n, const int32_t* grains, int32_t n
 gp_status gp_set_thermal_analytic(gp_ctx* ctx, const gp_thermal_analytic* th);
 gp_status gp_set_thermal_grid(gp_ctx* ctx, const gp_thermal_grid* th);
 
+/* Periodic axes of a single-run context (Sec. 3.4 applies periodic conditions on
+ * the faces normal to x and y): axes is a bit mask (1 = x, 2 = y, 4 = z).  Along a
+ * periodic axis a point is identified with its images x + m L (L = hi - lo):
+ * positions wrap into [lo, hi) for the hash, the fields and the grain map, distances
+ * take the nearest image, and nothing is clipped.  A grain's lattice is unbounded,
+ * so a grain crossing a periodic face continues on the other side.  The contact
+ * cells divide each period into floor(L / edge) equal cells, at least three
+ * (GP_ERR_ARG otherwise).  GP_ERR_STATE on a batch context or while the adjoint tape
+ * records; the adjoint refuses periodic contexts. */
+gp_status gp_set_periodic(gp_ctx* ctx, int32_t axes);
+
 /* Melting (Sec. 2.1.3).  With enable != 0 every step of a single-run context starts,
  * at t_n, with a melting pass in which:
  *   - every reached lattice site whose position has Delta T < 0 melts: it is no

@@ -373,6 +373,7 @@ struct gp_ctx {
   bool keys_valid = false;
   bool broken = false;
   // adjoint tape: taped steps (sorted count n, count after the step m, step index)
+  int periodic = 0;      // periodic axes (bit per axis), single run
   bool melting = false;  // melting walk-back pass at the start of every step
   uint8_t* gflags = nullptr;
   float* gdtn = nullptr;  // nucleation undercooling of each grain's seed
@@ -419,6 +420,7 @@ T* at(gp_ctx* c, size_t off) {
 void refresh_params(gp_ctx* c) {
   Params& P = c->P;
   c->geo.assign(c->L.nruns, Geo{});
+  const float inv_c = (float)(1.0 / cell_edge(c->h));
   for (int r = 0; r < c->L.nruns; ++r) {
     Geo& g = c->geo[r];
     const RunLayout& R = c->L.run[r];
@@ -426,14 +428,22 @@ void refresh_params(gp_ctx* c) {
       g.lo[a] = (float)c->dom[r].lo[a];
       g.hi[a] = (float)c->dom[r].hi[a];
       g.nc[a] = R.nc[a];
+      g.inv[a] = inv_c;
+      if ((c->periodic >> a) & 1) {  // the period in floor(L / edge) equal cells
+        const double L = c->dom[r].hi[a] - c->dom[r].lo[a];
+        g.nc[a] = (int)std::floor(L / cell_edge(c->h));
+        g.inv[a] = (float)(g.nc[a] / L);
+      }
     }
-    g.nsx = R.nsx;
+    g.nsx = (g.nc[0] + kSegCells - 1) / kSegCells;
     g.key0 = R.key0;
     g.seg0 = R.seg0;
     g.head0 = R.head0;
   }
   P.geo = c->geo[0];
   P.runs = c->batch ? c->runs : nullptr;
+  P.periodic = c->periodic;
+  for (int a = 0; a < 3; ++a) P.per_L[a] = (float)(c->dom[0].hi[a] - c->dom[0].lo[a]);
   P.hshift = c->L.hshift;
   P.inv_c = (float)(1.0 / cell_edge(c->h));
   float hf = (float)c->h;
@@ -894,6 +904,44 @@ gp_status gp_set_thermal_grid(gp_ctx* c, const gp_thermal_grid* th) {
   return GP_OK;
 }
 
+gp_status gp_set_periodic(gp_ctx* c, int32_t axes) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "periodic axes apply to single-run contexts");
+  if (c->tape_on) return fail(c, GP_ERR_STATE, "the adjoint tape is recording");
+  if (axes < 0 || axes > 7) return fail(c, GP_ERR_ARG, "axes is a bit mask of x, y, z");
+  for (int a = 0; a < 3; ++a)
+    if (((axes >> a) & 1) &&
+        std::floor((c->dom[0].hi[a] - c->dom[0].lo[a]) / cell_edge(c->h)) < 3)
+      return fail(c, GP_ERR_ARG, "a periodic axis needs at least three contact cells");
+  // the thermal constants set so far live in P.geo: keep them across the refresh
+  const Geo keep = c->P.geo;
+  c->periodic = axes;
+  const Params old = c->P;
+  refresh_params(c);
+  c->P.thermal = old.thermal;
+  c->P.grid = old.grid;
+  for (int a = 0; a < 3; ++a) {
+    c->P.gn[a] = old.gn[a];
+    c->P.ginv[a] = old.ginv[a];
+    c->P.wn[a] = old.wn[a];
+    c->P.winv[a] = old.winv[a];
+    c->P.geo.G[a] = keep.G[a];
+    c->P.geo.xref[a] = keep.xref[a];
+  }
+  c->P.solute = old.solute;
+  c->P.wgrid = old.wgrid;
+  c->P.Tm = old.Tm;
+  c->P.mL = old.mL;
+  c->P.launch = old.launch;
+  // cell geometry changed: keys are recomputed and the reached sites relinked
+  c->keys_valid = false;
+  GP_CUDA(c, cudaMemsetAsync(c->R.head, 0xff, 4 * c->L.nheads, c->st));
+  GP_CUDA(c, cudaMemsetAsync(&c->dst->linked, 0, sizeof(unsigned long long), c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  return GP_OK;
+}
+
 gp_status gp_set_melting(gp_ctx* c, int32_t enable) {
   gp_status s = check_ctx(c);
   if (s) return s;
@@ -1214,6 +1262,7 @@ gp_status gp_tape_begin(gp_ctx* c) {
   if (s) return s;
   if (c->batch) return fail(c, GP_ERR_STATE, "the adjoint is for single-run contexts");
   if (c->melting) return fail(c, GP_ERR_STATE, "the adjoint holds no melting events");
+  if (c->periodic) return fail(c, GP_ERR_STATE, "the adjoint takes non-periodic domains");
   if (c->P.solute) return fail(c, GP_ERR_STATE, "the adjoint takes the nominal liquidus");
   if (c->L.tape_steps <= 0) return fail(c, GP_ERR_STATE, "no tape (gp_memory.tape_steps = 0)");
   if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
@@ -1635,6 +1684,7 @@ Params sa_params(const gp_domain* d, double h, const int nc[3]) {
   }
   P.geo.nsx = (nc[0] + kSegCells - 1) / kSegCells;
   P.inv_c = (float)(1.0 / cell_edge(h));
+  for (int a = 0; a < 3; ++a) P.geo.inv[a] = P.inv_c;
   float hf = (float)h;
   P.rc2 = hf * hf;
   return P;

@@ -98,6 +98,7 @@ __host__ __device__ inline Rec rec_unpack(int4 v) {
 struct Geo {
   float lo[3], hi[3];
   int nc[3];                 // hash cells per axis
+  float inv[3];              // 1 / cell edge per axis (the contact search's cells)
   int nsx;                   // segments of kSegCells cells per x row of the hash grid
   unsigned long long key0;   // cell key of the run's cell 0
   unsigned long long seg0;   // first cell-table entry of the run
@@ -123,6 +124,10 @@ struct Params {
   float ginv[3];     // 1 / spacing
   const float4* gtab;// grain table: 4 float4 per grain (c with the run id in w, rows of h R)
   int hshift;        // one reached-site head per 2^hshift cells along each axis
+  // periodic axes of a single run (bit a): positions wrap into [lo, hi), distances
+  // take the nearest image, no clip; per_L = hi - lo
+  int periodic;
+  float per_L[3];
   // local liquidus T_m + m_L w(x) from a composition grid (solute != 0)
   int solute;
   const float* wgrid;
@@ -205,12 +210,39 @@ __device__ __forceinline__ int cell1(float x, float lo, float inv, int n) {
 }
 
 // cell of p in its run's hash grid (clamped) and the run-local linear cell index
-__device__ __forceinline__ uint32_t cell_local(const Geo& g, float inv_c, float3 p, int& cx,
-                                               int& cy, int& cz) {
-  cx = cell1(p.x, g.lo[0], inv_c, g.nc[0]);
-  cy = cell1(p.y, g.lo[1], inv_c, g.nc[1]);
-  cz = cell1(p.z, g.lo[2], inv_c, g.nc[2]);
+__device__ __forceinline__ uint32_t cell_local(const Geo& g, float3 p, int& cx, int& cy,
+                                               int& cz) {
+  cx = cell1(p.x, g.lo[0], g.inv[0], g.nc[0]);
+  cy = cell1(p.y, g.lo[1], g.inv[1], g.nc[1]);
+  cz = cell1(p.z, g.lo[2], g.inv[2], g.nc[2]);
   return (uint32_t)(((uint64_t)cz * g.nc[1] + cy) * g.nc[0] + cx);
+}
+
+// position wrapped into [lo, hi) along the periodic axes (single-run contexts)
+__device__ __forceinline__ float wrap1(float x, float lo, float L) {
+  float u = __fsub_rn(x, lo);
+  u = __fsub_rn(u, __fmul_rn(L, floorf(__fdiv_rn(u, L))));
+  return __fadd_rn(lo, u);
+}
+__device__ __forceinline__ float3 wrap_pos(const Params& P, const Geo& g, float3 p) {
+  if (P.periodic & 1) p.x = wrap1(p.x, g.lo[0], P.per_L[0]);
+  if (P.periodic & 2) p.y = wrap1(p.y, g.lo[1], P.per_L[1]);
+  if (P.periodic & 4) p.z = wrap1(p.z, g.lo[2], P.per_L[2]);
+  return p;
+}
+// difference a - b along axis a_ taken to the nearest image on a periodic axis
+__device__ __forceinline__ float dmin1(float d, float L, bool per) {
+  if (per) {
+    if (d > 0.5f * L) d = __fsub_rn(d, L);
+    else if (d < -0.5f * L) d = __fadd_rn(d, L);
+  }
+  return d;
+}
+__device__ __forceinline__ float dist2_per(const Params& P, float3 a, float3 b) {
+  const float dx = dmin1(__fsub_rn(a.x, b.x), P.per_L[0], P.periodic & 1);
+  const float dy = dmin1(__fsub_rn(a.y, b.y), P.per_L[1], P.periodic & 2);
+  const float dz = dmin1(__fsub_rn(a.z, b.z), P.per_L[2], P.periodic & 4);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
 __device__ __forceinline__ bool inside(const Geo& g, float3 p) {

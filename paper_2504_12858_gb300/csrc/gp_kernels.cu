@@ -165,6 +165,75 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
   return hit;
 }
 
+// contact_scan (first hit only) for a single run with periodic axes: neighbour rows
+// and cells wrap around the periodic faces and distances take the nearest image.
+// With at least three cells per periodic axis the 27 cells are distinct.
+template <class K>
+__device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __restrict__ tab,
+                                 uint32_t stamp, const K* __restrict__ skeys,
+                                 const float4* __restrict__ pos4, int64_t n, float3 p, int gw,
+                                 int cx, int cy, int cz) {
+  // x windows of consecutive cells (two where the neighbourhood wraps)
+  int wx0[2], wx1[2], nw = 1;
+  const int nx = gm.nc[0];
+  if (!(P.periodic & 1)) {
+    wx0[0] = max(cx - 1, 0);
+    wx1[0] = min(cx + 1, nx - 1);
+  } else if (cx == 0) {
+    wx0[0] = 0; wx1[0] = 1; wx0[1] = nx - 1; wx1[1] = nx - 1; nw = 2;
+  } else if (cx == nx - 1) {
+    wx0[0] = nx - 2; wx1[0] = nx - 1; wx0[1] = 0; wx1[1] = 0; nw = 2;
+  } else {
+    wx0[0] = cx - 1;
+    wx1[0] = cx + 1;
+  }
+  const uint4* __restrict__ rtab = tab + gm.seg0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int z = cz + dz;
+    if (P.periodic & 4) z = (z + gm.nc[2]) % gm.nc[2];
+    else if (z < 0 || z >= gm.nc[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int y = cy + dy;
+      if (P.periodic & 2) y = (y + gm.nc[1]) % gm.nc[1];
+      else if (y < 0 || y >= gm.nc[1]) continue;
+      const uint32_t row = (uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y;
+      for (int wi = 0; wi < nw; ++wi) {
+        const int x0 = wx0[wi], x1 = wx1[wi];
+        for (int sgi = x0 >> kSegShift; sgi <= (x1 >> kSegShift); ++sgi) {
+          const uint4 e = __ldg(rtab + (size_t)row * gm.nsx + sgi);
+          if ((e.y >> 16) != stamp) continue;
+          const int base = sgi << kSegShift;
+          const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
+          const unsigned long long nib = ((unsigned long long)e.w << 32) | e.z;
+          uint32_t i, end;
+          const bool saturated =
+              ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
+          if (!saturated) {
+            i = e.x + nib_prefix(nib, c0);
+            end = e.x + nib_prefix(nib, c1 + 1);
+          } else {
+            const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
+            const K khi = klo + (K)(c1 - c0);
+            i = e.x;
+            end = e.x + (e.y & 0xffffu);
+            while (i < end && __ldg(skeys + i) < klo) ++i;
+            uint32_t e2 = i;
+            while (e2 < end && __ldg(skeys + e2) <= khi) ++e2;
+            end = e2;
+          }
+          if ((int64_t)end > n) end = (uint32_t)n;
+          for (; i < end; ++i) {
+            const float4 o = __ldg(pos4 + i);
+            if (__float_as_int(o.w) == gw) continue;
+            if (dist2_per(P, p, make_float3(o.x, o.y, o.z)) < P.rc2) return true;
+          }
+        }
+      }
+    }
+  }
+  return false;
+}
+
 // appends one reached site to the list (linking into the per-cell lists happens
 // lazily, before a query needs it: k_link_reached)
 __device__ __forceinline__ void reached_append(const Reached& R, int g, int sx, int sy, int sz) {
@@ -188,12 +257,61 @@ __device__ __forceinline__ uint64_t head_index(const Geo& gm, int hs, int x, int
 // The sites within the contact radius of p lie in the cells c-1..c+1 of p's cell
 // c along each axis (the cell edge exceeds the radius), hence in the bricks
 // holding those cells.
+// the same over wrapped cells and nearest-image distances (periodic axes of a single
+// run, one head per cell)
+__device__ int nearest_reached_per(const Params& P, const Geo& gm, const Reached& R, float3 p,
+                                   bool any_only) {
+  p = wrap_pos(P, gm, p);
+  int c[3];
+  cell_local(gm, p, c[0], c[1], c[2]);
+  int cl[3][3], nl[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    nl[a] = 0;
+    for (int d = -1; d <= 1; ++d) {
+      int v = c[a] + d;
+      if ((P.periodic >> a) & 1) v = (v + gm.nc[a]) % gm.nc[a];
+      else if (v < 0 || v >= gm.nc[a]) continue;
+      cl[a][nl[a]++] = v;
+    }
+  }
+  float best = P.rc2;
+  int bg = -1;
+  const unsigned long long guard = *R.count + 1;
+  for (int iz = 0; iz < nl[2]; ++iz)
+    for (int iy = 0; iy < nl[1]; ++iy)
+      for (int ix = 0; ix < nl[0]; ++ix) {
+        uint32_t r = R.head[head_index(gm, 0, cl[0][ix], cl[1][iy], cl[2][iz])];
+        unsigned long long steps = 0;
+        while (r != kNoEntry && steps++ < guard) {
+          const unsigned long long key = R.key[r];
+          if (key != kDeadSite) {
+            int g, sx, sy, sz;
+            unpack_site(key, g, sx, sy, sz);
+            float4 gc, r0, r1, r2;
+            grain_load(P.gtab, g, gc, r0, r1, r2);
+            const float d2 = dist2_per(P, p, site_pos_g(gc, r0, r1, r2, sx, sy, sz));
+            if (d2 < P.rc2) {
+              if (any_only) return g;
+              if (d2 < best || (d2 == best && g < bg)) {
+                best = d2;
+                bg = g;
+              }
+            }
+          }
+          r = R.next[r];
+        }
+      }
+  return bg;
+}
+
 __device__ int nearest_reached(const Params& P, const Geo& gm, const Reached& R, float3 p,
                                bool any_only) {
+  if (P.periodic) return nearest_reached_per(P, gm, R, p, any_only);
   int c[3];
-  c[0] = __float2int_rd(__fmul_rn(__fsub_rn(p.x, gm.lo[0]), P.inv_c));
-  c[1] = __float2int_rd(__fmul_rn(__fsub_rn(p.y, gm.lo[1]), P.inv_c));
-  c[2] = __float2int_rd(__fmul_rn(__fsub_rn(p.z, gm.lo[2]), P.inv_c));
+  c[0] = __float2int_rd(__fmul_rn(__fsub_rn(p.x, gm.lo[0]), gm.inv[0]));
+  c[1] = __float2int_rd(__fmul_rn(__fsub_rn(p.y, gm.lo[1]), gm.inv[1]));
+  c[2] = __float2int_rd(__fmul_rn(__fsub_rn(p.z, gm.lo[2]), gm.inv[2]));
   const int hs = P.hshift;
   int lo[3], hi[3];
 #pragma unroll
@@ -272,7 +390,15 @@ __device__ __forceinline__ int run_of(const float4& gc) {
 template <class K>
 __device__ __forceinline__ K cell_key(const Params& P, const Geo& gm, float3 p) {
   int cx, cy, cz;
-  return (K)gm.key0 + (K)cell_local(gm, P.inv_c, p, cx, cy, cz);
+  if (P.periodic) p = wrap_pos(P, gm, p);
+  return (K)gm.key0 + (K)cell_local(gm, p, cx, cy, cz);
+}
+
+// inside the domain along the axes that are not periodic
+__device__ __forceinline__ bool inside_np(const Params& P, const Geo& g, float3 p) {
+  return ((P.periodic & 1) || (p.x >= g.lo[0] && p.x <= g.hi[0])) &&
+         ((P.periodic & 2) || (p.y >= g.lo[1] && p.y <= g.hi[1])) &&
+         ((P.periodic & 4) || (p.z >= g.lo[2] && p.z <= g.hi[2]));
 }
 
 // ---------------------------------------------------------------------------------
@@ -326,7 +452,8 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
         const float3 p =
             add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
         const int run = run_of<BATCH>(gc);
-        pos4[j] = make_float4(p.x, p.y, p.z, __int_as_float(r.grain | (run << kRunShift)));
+        const float3 pw = P.periodic ? wrap_pos(P, P.geo, p) : p;
+        pos4[j] = make_float4(pw.x, pw.y, pw.z, __int_as_float(r.grain | (run << kRunShift)));
         seg_build<K>(geo_of<BATCH>(P, run), skeys, j, n, key, tab, stamp, &st->err);
         active = r.state == ST_ACTIVE;
       }
@@ -344,7 +471,7 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
 // ---------------------------------------------------------------------------------
 // k_advance: contact freeze, growth, advance, spawn claims (sorted store, in place)
 // ---------------------------------------------------------------------------------
-template <bool BATCH, class K>
+template <bool BATCH, class K, bool PER = false>
 __global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
                                                  const K* __restrict__ skeys,
@@ -377,9 +504,12 @@ __global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* 
         const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
         g = r.grain;
         int cx, cy, cz;
-        cell_local(gm, P.inv_c, p, cx, cy, cz);
-        const bool hit =
-            contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        cell_local(gm, p, cx, cy, cz);
+        bool hit;
+        if constexpr (PER)
+          hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        else
+          hit = contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
         if (hit) {
           froze = true;
           r.state = ST_FROZEN;
@@ -481,7 +611,7 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
   const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
   if (!crossing) {
     const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
-    if (inside(gm, p)) return 1u << 6;
+    if (inside_np(P, gm, p)) return 1u << 6;
     ++n_clip;
     return 0;
   }
@@ -511,7 +641,7 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
       continue;
     }
     if (k != r.dir) ++n_spawn;
-    if (inside(gm, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
+    if (inside_np(P, gm, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
     else ++n_clip;
   }
   return mask;
@@ -636,7 +766,8 @@ __global__ void k_link_reached(Params P, Reached R, const unsigned long long* li
     grain_load(P.gtab, g, gc, q0, q1, q2);
     const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
     int cx, cy, cz;
-    cell_local(gm, P.inv_c, site_pos_g(gc, q0, q1, q2, sx, sy, sz), cx, cy, cz);
+    const float3 q = site_pos_g(gc, q0, q1, q2, sx, sy, sz);
+    cell_local(gm, P.periodic ? wrap_pos(P, gm, q) : q, cx, cy, cz);
     R.next[r] = atomicExch(R.head + head_index(gm, P.hshift, cx, cy, cz), (uint32_t)r);
   }
 }
@@ -874,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_melt_sites(Params P, StepArgs S, Reache
       unpack_site(key, g, sx, sy, sz);
       float4 gc, q0, q1, q2;
       grain_load(P.gtab, g, gc, q0, q1, q2);
-      const float3 x = site_pos_g(gc, q0, q1, q2, sx, sy, sz);
+      const float3 x = wrap_pos(P, P.geo, site_pos_g(gc, q0, q1, q2, sx, sy, sz));
       melt = undercooling(P, P.geo, S, x, P.geo.dT_base) < 0.f;
     }
     BlockCache bc;
@@ -910,7 +1041,8 @@ __global__ void __launch_bounds__(256) k_melt_particles(Params P, StepArgs S, in
   if (i < n) {
     Rec r = rec_unpack(rec[i]);
     if (r.state == ST_ACTIVE || r.state == ST_FROZEN) {
-      const float3 x = part_pos(P.gtab, r.grain, r.sx, r.sy, r.sz, r.dir, r.ell);
+      const float3 x =
+          wrap_pos(P, P.geo, part_pos(P.gtab, r.grain, r.sx, r.sy, r.sz, r.dir, r.ell));
       BlockCache bc;
       int sh = 0;
       const uint32_t* w = site_byte(C, r.grain, r.sx, r.sy, r.sz, sh, bc);
@@ -1121,7 +1253,7 @@ __global__ void k_seed_shell(Params P, const int32_t* __restrict__ grains, int64
   int s[3] = {ts[0], ts[1], ts[2]};
   s[a] -= sg;
   const int dir = 2 * a + (sg > 0 ? 0 : 1);
-  if (ok) ok = inside(P.geo, part_pos(P.gtab, g, s[0], s[1], s[2], dir, ell0));
+  if (ok) ok = inside_np(P, P.geo, part_pos(P.gtab, g, s[0], s[1], s[2], dir, ell0));
   if (ok) {
     unsigned long long o = atomicAdd(counter, 1ull);
     if (o >= (unsigned long long)cap) {
@@ -1198,7 +1330,7 @@ __global__ void k_keys_pos(Params P, const float* __restrict__ x3, const uint8_t
   if (i >= n) return;
   float3 p = make_float3(x3[3 * i], x3[3 * i + 1], x3[3 * i + 2]);
   int cx, cy, cz;
-  uint32_t k = cell_local(P.geo, P.inv_c, p, cx, cy, cz);
+  uint32_t k = cell_local(P.geo, p, cx, cy, cz);
   if (state && state[i] == ST_REMOVED) k = 0xffffffffu;
   keys[i] = k;
   vals[i] = (uint32_t)i;
@@ -1268,7 +1400,7 @@ __global__ void k_contact_sa(Params P, const float4* __restrict__ pos4,
   const int g = __float_as_int(q.w);
   const uint32_t idj = ids[j];
   int cx, cy, cz;
-  cell_local(P.geo, P.inv_c, p, cx, cy, cz);
+  cell_local(P.geo, p, cx, cy, cz);
   const bool hit =
       pairs ? contact_scan<true, uint32_t>(P, P.geo, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz,
                                            ids, idj, pairs, pair_cap, npairs)
@@ -1339,6 +1471,9 @@ void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, co
   if (batch)
     k_advance<true, uint64_t><<<persistent(n, 256, P.launch.advance_ctas), 256, 0, st>>>(
         P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst);
+  else if (P.periodic)
+    k_advance<false, uint32_t, true><<<blocks(n), 256, 0, st>>>(
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst);
   else
     k_advance<false, uint32_t><<<blocks(n), 256, 0, st>>>(
         P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst);

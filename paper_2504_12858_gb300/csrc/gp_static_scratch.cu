@@ -103,6 +103,7 @@ extern "C" gp_status gp_hash_build_static(const float* x3, int64_t n, const gp_d
   }
   if (ncells >= (1ull << 32)) return GP_ERR_ARG;
   P.inv_c = (float)(1.0 / e);
+  for (int a = 0; a < 3; ++a) P.geo.inv[a] = P.inv_c;
   float hf = (float)h;
   P.rc2 = hf * hf;
 

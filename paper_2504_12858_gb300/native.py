@@ -92,6 +92,7 @@ SIGNATURES = {
     "gp_set_thermal_grid": (C.c_int, [_P, C.POINTER(gp_thermal_grid)]),
     "gp_set_solute_grid": (C.c_int, [_P, C.POINTER(gp_solute_grid)]),
     "gp_set_melting": (C.c_int, [_P, C.c_int32]),
+    "gp_set_periodic": (C.c_int, [_P, C.c_int32]),
     "gp_nucleation_sites": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "gp_step": (C.c_int, [_P, C.c_int32]),
     "gp_grain_map": (C.c_int, [_P, C.POINTER(gp_voxel_grid), _P, C.c_int32]),
@@ -305,6 +306,10 @@ class Sim:
         th.spacing[:] = [float(v) for v in spacing]
         th.frame_vel[:] = [float(v) for v in vel]
         self._check(load().gp_set_thermal_grid(self._h, C.byref(th)))
+
+    def gp_set_periodic(self, axes):
+        """Periodic axes, a bit per axis (1 = x, 2 = y, 4 = z)."""
+        self._check(load().gp_set_periodic(self._h, int(axes)))
 
     def gp_set_melting(self, enable=True):
         self._check(load().gp_set_melting(self._h, 1 if enable else 0))
