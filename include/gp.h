@@ -351,7 +351,7 @@ gp_status gp_run_counts(gp_ctx* ctx, int32_t nruns, int64_t* live, int64_t* acti
 
 /* Launches of a batch step.  Every kernel of a batch step sizes itself on the
  * device: the counts live in device memory and the grids are persistent
- * (*_ctas_per_sm resident CTAs per SM over the whole GPU: build 1..8, advance 1..4,
+ * (*_ctas_per_sm resident CTAs per SM over the whole GPU: build 1..8, advance 1..5,
  * emit 1..8).  graph_steps > 0 captures graph_steps consecutive steps in a CUDA
  * graph on first use and replays it (no host round trip inside a graph; the
  * context's stream must not be the legacy default stream); 0 issues the launches
@@ -364,7 +364,7 @@ gp_status gp_get_launch_config(gp_ctx* ctx, gp_launch_config* out);
 gp_status gp_set_launch_config(gp_ctx* ctx, const gp_launch_config* cfg);
 
 /* Autotuner of the batch launches: runs trial_steps real steps of the simulation
- * with each candidate configuration (build 4/8, advance 2/4, emit 4/8 CTAs per SM),
+ * with each candidate configuration (build 4/8, advance 2/5, emit 4/8 CTAs per SM),
  * times them with CUDA events, keeps the configuration with the least device time
  * per particle record (graph_steps unchanged) and writes it to *best (optional). */
 gp_status gp_autotune(gp_ctx* ctx, int32_t trial_steps, gp_launch_config* best);

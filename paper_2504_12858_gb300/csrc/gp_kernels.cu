@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
 // k_advance: contact freeze, growth, advance, spawn claims (sorted store, in place)
 // ---------------------------------------------------------------------------------
 template <bool BATCH, class K, bool PER = false>
-__global__ void __launch_bounds__(256, 4) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
+__global__ void __launch_bounds__(256, 5) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
                                                  const K* __restrict__ skeys,
                                                  const uint4* __restrict__ tab,
