@@ -219,6 +219,32 @@ def cet_runs(n_runs: int = 256, base_seed: int = 1000, L_range=(0.5e-3, 2e-3),
     return runs
 
 
+def thin_sample(lambda0: float = 48e-6, steps: int = 200) -> Workload:
+    """Directional solidification of a quasi-2D thin sample (Sec. 3.3, Table S2).
+
+    Growth along +y in a frozen temperature field T = T_L + G y + Tdot t with
+    G = 1900 K/m and Tdot = -0.1634 K/s (pulling at 86 um/s), T_L = 937.65 K; v from
+    Eq. (2) with a1 = 8.26e-6, b1 = 2, a2 = 8.18e-5, b2 = 3; dt = 0.1 s; h = lambda0.
+    Fifteen nuclei at y = 0.15 um, x = L_x / 2 + i 360 um (i = -7..7), mid-thickness,
+    rotated about the sample normal z by psi = 4 deg (i <= -5), 30 deg (|i| <= 4) and
+    11 deg (i >= 5).  The sample is 400 um thick and 2 mm long (Table S2); its width
+    is taken as 15 x 360 um = 5.4 mm so that every nucleus lies in it (the table's
+    4 mm width is shorter than the nucleus row).
+    """
+    Lx, Ly, Lz = 15 * 360e-6, 2e-3, 400e-6
+    i = np.arange(-7, 8)
+    seeds = np.stack([Lx / 2 + i * 360e-6, np.full(15, 0.15e-6), np.full(15, Lz / 2)], 1)
+    psi = np.where(i <= -5, 4.0, np.where(i >= 5, 11.0, 30.0))
+    quats = np.array([euler_zxz_to_quaternion(p, 0.0, 0.0) for p in psi])
+    T_L = 937.65
+    return Workload(name=f"thin_sample_{lambda0 * 1e6:.0f}um", lo=(0.0, 0.0, 0.0),
+                    hi=(Lx, Ly, Lz), h=lambda0, dt=0.1, a=(8.26e-6, 8.18e-5), b=(2.0, 3.0),
+                    T_L=T_L, steps=steps, seeds=seeds, quats=quats,
+                    analytic=dict(T0=T_L, G=(0.0, 1900.0, 0.0), xref=(0.0, 0.0, 0.0),
+                                  Tdot=-0.1634),
+                    extra=dict(psi=psi))
+
+
 def adjoint_cube(seed: int = 5, n_grains: int = 32, steps: int = 200, A: float = 1e-5,
                  n: float = 2.0, G: float = 1e3, Tdot: float = 10.0) -> Workload:
     """Calibration case of the adjoint: the 200 um single-grain cube with 32 grains

@@ -106,3 +106,31 @@ def nucleus_keys(sim, p, w):
     q = dict(p)
     q["grain"] = g2n[p["grain"]]
     return q
+
+
+def gb_angle_deg(grain_map, spacing, y_range, left_ids, right_ids):
+    """Angle (degrees, from the growth direction y) of the grain boundary between the
+    grains left_ids (smaller x) and right_ids (larger x) in a 2D grain map indexed
+    [y, x]: per row, the midpoint between the last left-group voxel and the next
+    right-group voxel after it; a straight line is fitted over y_range.  Negative:
+    the boundary moves towards -x (the right-hand grains overgrow the left-hand ones)."""
+    left = np.isin(grain_map, left_ids)
+    right = np.isin(grain_map, right_ids)
+    ys, xs = [], []
+    for j in range(grain_map.shape[0]):
+        y = (j + 0.5) * spacing
+        if not (y_range[0] <= y <= y_range[1]):
+            continue
+        li = np.nonzero(left[j])[0]
+        if li.size == 0:
+            continue
+        k = li.max()
+        ri = np.nonzero(right[j, k + 1:])[0]
+        if ri.size == 0:
+            continue
+        xs.append((k + 0.5 + (k + 1 + ri[0] + 0.5)) / 2 * spacing)
+        ys.append(y)
+    if len(ys) < 5:
+        return float("nan"), len(ys)
+    slope = np.polyfit(ys, xs, 1)[0]
+    return float(np.degrees(np.arctan(slope))), len(ys)
