@@ -620,8 +620,13 @@ struct SortBufs {
 constexpr int kSortThreads = 256;
 constexpr int kSortMaxPasses = 5;   // keys of up to 40 bits
 template <class K> struct SortTile;
-template <> struct SortTile<uint32_t> { static constexpr int items = 15, tile = 256 * 15; };
-template <> struct SortTile<uint64_t> { static constexpr int items = 10, tile = 256 * 10; };
+// keys per thread, keys per tile and resident CTAs per SM of a onesweep pass
+template <> struct SortTile<uint32_t> {
+  static constexpr int items = 12, tile = 256 * 12, ctas = 5;
+};
+template <> struct SortTile<uint64_t> {
+  static constexpr int items = 10, tile = 256 * 10, ctas = 4;
+};
 
 // radix sort of (keys[0], vals[0]) over the low nbits of the keys; returns the
 // buffer index (0 or 1) holding the sorted result, or -1 if nbits exceeds the
