@@ -496,7 +496,7 @@ gp_status sync_stats(gp_ctx* c) {
     if (e & ERR_GRAINS) return fail(c, GP_ERR_CAPACITY, "grain capacity exceeded");
     if (e & ERR_HASH_FULL) return fail(c, GP_ERR_HASH_FULL, "claim table full (raise claim_blocks)");
     if (e & ERR_TIMEOUT) return fail(c, GP_ERR_TIMEOUT, "bounded device wait gave up");
-    if (e & ERR_CELL_OVERFLOW) return fail(c, GP_ERR_CAPACITY, "more than 65535 particles in a cell");
+    if (e & ERR_CELL_OVERFLOW) return fail(c, GP_ERR_CAPACITY, "32767 or more particles in a row of 16 hash cells");
     if (e & ERR_SITE_RANGE) return fail(c, GP_ERR_ARG, "lattice site outside [-4095, 4095]");
     return fail(c, GP_ERR_STATE, "device error");
   }

@@ -23,7 +23,7 @@ enum : uint32_t {
   ERR_HASH_FULL = 2u,     // claim table probe limit / load exceeded
   ERR_TIMEOUT = 4u,       // a bounded look-back wait gave up
   ERR_REACHED_CAP = 8u,   // reached-site list full
-  ERR_CELL_OVERFLOW = 16u,// more than 65535 particles in one hash cell
+  ERR_CELL_OVERFLOW = 16u,// 32767 or more particles in one segment of 16 hash cells
   ERR_GRAINS = 32u,       // grain table full
   ERR_SITE_RANGE = 64u,   // lattice site outside [-4095, 4095]
 };
@@ -34,6 +34,7 @@ constexpr uint32_t kSpinLimit = 1u << 22;  // polls (~seconds) before a look-bac
 constexpr int kBrickWords = 128;           // 8^3 sites, one byte each, 4 per word
 constexpr int kSegShift = 4;               // the cell table has one entry per 16 cells of a row
 constexpr int kSegCells = 1 << kSegShift;
+constexpr uint32_t kSegMaxCount = 0x7fffu;  // particles per segment (15-bit count)
 
 // ---------------------------------------------------------------------------------
 // particle record: 16 bytes, loaded and stored as one int4
@@ -478,19 +479,21 @@ __device__ inline uint32_t* warp_claim_word(const Claims& C, bool have, int g, i
   const bool cached = have && bx == bc.bx && by == bc.by && bz == bc.bz &&
                       (bc.b >= 0 || !insert);
   const bool need = have && !cached;
-  const unsigned long long key = need ? block_key(g, bx, by, bz) : 0ull;
-  const uint32_t peers = __match_any_sync(0xffffffffu, key);
-  const int leader = __ffs(peers) - 1;
-  long long r = -1;
-  if (need && lane == leader) r = claim_probe(C, key, insert);
-  __syncwarp();
-  if (need && lane == leader && r <= -2) r = claim_wait(C, (uint32_t)(-2 - r));
-  r = __shfl_sync(0xffffffffu, r, leader);
-  if (need) {
-    bc.bx = bx;
-    bc.by = by;
-    bc.bz = bz;
-    bc.b = r;
+  if (__any_sync(0xffffffffu, need)) {  // most targets share the cached block
+    const unsigned long long key = need ? block_key(g, bx, by, bz) : 0ull;
+    const uint32_t peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    long long r = -1;
+    if (need && lane == leader) r = claim_probe(C, key, insert);
+    __syncwarp();
+    if (need && lane == leader && r <= -2) r = claim_wait(C, (uint32_t)(-2 - r));
+    r = __shfl_sync(0xffffffffu, r, leader);
+    if (need) {
+      bc.bx = bx;
+      bc.by = by;
+      bc.bz = bz;
+      bc.b = r;
+    }
   }
   if (!have || bc.b < 0) return nullptr;
   return block_word(C, bc.b, tx, ty, tz, shift);

@@ -31,9 +31,10 @@ constexpr uint32_t kNoEntry = 0xffffffffu;
 // one row of the hash grid ("segment") are contiguous.  The table holds one
 // 16-byte entry per segment:
 //   x: sorted index of the segment's first particle
-//   y: build stamp (high 16 bits) | particle count of the segment (low 16 bits)
+//   y: build stamp (high 16 bits) | saturation flag (bit 15) | particle count of
+//      the segment (low 15 bits)
 //   z, w: particle count of each of the 16 cells, 4 bits each (cell 0 in the low
-//         nibble of z), saturated at 15
+//         nibble of z), saturated at 15; the flag is set when any count is
 // An entry whose stamp is not the current build's is an empty segment.  A query
 // turns the 3 cells x-1..x+1 of a neighbour row into a candidate range directly
 // from the nibble counts; when a count is saturated it scans the segment's keys.
@@ -71,7 +72,7 @@ __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ s
     seg_of(gm, (uint32_t)(k - k0), x);
     const int sh = 4 * (int)(x & (kSegCells - 1));
     if (((nib >> sh) & 15ull) < 15ull) nib += 1ull << sh;
-    if (++c == 0xffffu) {
+    if (++c == kSegMaxCount) {
       atomicOr(err, ERR_CELL_OVERFLOW);
       break;
     }
@@ -80,15 +81,24 @@ __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ s
     uint32_t xk;
     if (k < k0 || (K)(k - k0) >= (K)nvalid || seg_of(gm, (uint32_t)(k - k0), xk) != sg) break;
   }
-  tab[gm.seg0 + sg] =
-      make_uint4((uint32_t)j, (stamp << 16) | c, (uint32_t)nib, (uint32_t)(nib >> 32));
+  const bool sat = ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
+  tab[gm.seg0 + sg] = make_uint4((uint32_t)j, (stamp << 16) | (sat ? 0x8000u : 0u) | c,
+                                 (uint32_t)nib, (uint32_t)(nib >> 32));
 }
 
-// sum of the 4-bit counts of cells 0..p-1 (p <= 16)
-__device__ __forceinline__ uint32_t nib_prefix(unsigned long long nib, int p) {
-  const unsigned long long m = p >= 16 ? nib : (nib & ((1ull << (4 * p)) - 1ull));
-  const unsigned long long b = (m & 0x0f0f0f0f0f0f0f0full) + ((m >> 4) & 0x0f0f0f0f0f0f0f0full);
-  return (uint32_t)((b * 0x0101010101010101ull) >> 56);
+// sum of the eight 4-bit counts in v (each byte sums two counts, at most 30)
+__device__ __forceinline__ uint32_t nib_sum8(uint32_t v) {
+  const uint32_t b = (v & 0x0f0f0f0fu) + ((v >> 4) & 0x0f0f0f0fu);
+  return (b * 0x01010101u) >> 24;
+}
+// mask of the low q 4-bit counts of a word (q >= 0)
+__device__ __forceinline__ uint32_t low_nibbles(int q) {
+  return q >= 8 ? 0xffffffffu : ((1u << (4 * q)) - 1u);
+}
+// sum of the 4-bit counts of cells 0..p-1 (p <= 16) of an entry's z (cells 0-7)
+// and w (cells 8-15)
+__device__ __forceinline__ uint32_t nib_prefix(uint32_t z, uint32_t w, int p) {
+  return nib_sum8(z & low_nibbles(p)) + nib_sum8(w & low_nibbles(max(p - 8, 0)));
 }
 
 // Finds the sorted particles i of another grain strictly closer than the contact
@@ -124,19 +134,16 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
         if ((e.y >> 16) != stamp) continue;
         const int base = sgi << kSegShift;
         const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
-        const unsigned long long nib = ((unsigned long long)e.w << 32) | e.z;
         uint32_t i, end;
-        const bool saturated =
-            ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
-        if (!saturated) {
-          i = e.x + nib_prefix(nib, c0);
-          end = e.x + nib_prefix(nib, c1 + 1);
+        if (!(e.y & 0x8000u)) {
+          i = e.x + nib_prefix(e.z, e.w, c0);
+          end = e.x + nib_prefix(e.z, e.w, c1 + 1);
         } else {
           // a cell holds 15 or more particles: locate the cells by their keys
           const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
           const K khi = klo + (K)(c1 - c0);
           i = e.x;
-          end = e.x + (e.y & 0xffffu);
+          end = e.x + (e.y & kSegMaxCount);
           while (i < end && __ldg(skeys + i) < klo) ++i;
           uint32_t e2 = i;
           while (e2 < end && __ldg(skeys + e2) <= khi) ++e2;
@@ -204,18 +211,15 @@ __device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __
           if ((e.y >> 16) != stamp) continue;
           const int base = sgi << kSegShift;
           const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
-          const unsigned long long nib = ((unsigned long long)e.w << 32) | e.z;
           uint32_t i, end;
-          const bool saturated =
-              ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
-          if (!saturated) {
-            i = e.x + nib_prefix(nib, c0);
-            end = e.x + nib_prefix(nib, c1 + 1);
+          if (!(e.y & 0x8000u)) {
+            i = e.x + nib_prefix(e.z, e.w, c0);
+            end = e.x + nib_prefix(e.z, e.w, c1 + 1);
           } else {
             const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
             const K khi = klo + (K)(c1 - c0);
             i = e.x;
-            end = e.x + (e.y & 0xffffu);
+            end = e.x + (e.y & kSegMaxCount);
             while (i < end && __ldg(skeys + i) < klo) ++i;
             uint32_t e2 = i;
             while (e2 < end && __ldg(skeys + e2) <= khi) ++e2;
