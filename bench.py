@@ -168,6 +168,25 @@ def ncu_traffic(kernel: str):
     return None if k is None else float(k["dram_bytes_per_unit"])
 
 
+def ncu_step_traffic():
+    """DRAM bytes per particle-step of the whole step (every step kernel), from the
+    committed one-pass ncu capture of the default bench's timed steps, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("sources_digest") != kernel_sources_digest() or "step" not in d:
+        return None
+    return float(d["step"]["dram_bytes_per_particle_step"])
+
+
+# algorithmic bytes of one particle-step for the whole step: read and write the
+# 16-byte record, write and read back the 8-byte (cell key, index) pair
+B_ALG_STEP = 48
+
+
 # ----------------------------------------------------------------------------------
 # CPU oracle on a bounded sample (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------------
@@ -380,7 +399,8 @@ def run_native(args, rank, world, local_rank):
     w = fixture(args.grains, args.n0, args.plate)
     per_grain = 4 * (args.n0 + 1) ** 2 + 2
     n0_est = args.grains * per_grain
-    total_steps = args.warmup + args.steps + args.e2e_steps
+    e2e_steps = args.e2e_steps or args.steps
+    total_steps = args.warmup + max(args.steps, e2e_steps)
     # the envelopes grow by about 4 % per step; every crossing records a reached site
     capacity = int(args.capacity or min((1 << 30) - 1, int(n0_est * 1.05 ** total_steps * 1.3)
                                         + 1000000))
@@ -388,14 +408,19 @@ def run_native(args, rank, world, local_rank):
     # claim blocks: an envelope growing from 50 to 70 lattice shells touches about
     # 1200 blocks of 8^3 sites (plus reservations lost to insertion races)
     blocks = args.claim_blocks or args.grains * 2000
-    sim = native.Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=capacity,
-                     reached_capacity=reached, claim_blocks=blocks,
-                     max_grains=args.grains + 16, grid_nodes=int(np.prod(w.grid["T"].shape)),
-                     device=dev)
     g = w.grid
-    sim.gp_set_thermal_grid(g["T"], g["origin"], g["spacing"], g["vel"])
-    sim.gp_add_grains(w.seeds, w.quats, nucleate=False)
-    sim.gp_seed_shell(np.arange(args.grains), args.n0)
+
+    def make_sim():
+        s = native.Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=capacity,
+                       reached_capacity=reached, claim_blocks=blocks,
+                       max_grains=args.grains + 16, grid_nodes=int(np.prod(g["T"].shape)),
+                       device=dev)
+        s.gp_set_thermal_grid(g["T"], g["origin"], g["spacing"], g["vel"])
+        s.gp_add_grains(w.seeds, w.quats, nucleate=False)
+        s.gp_seed_shell(np.arange(args.grains), args.n0)
+        return s
+
+    sim = make_sim()
     n_start = sim.gp_stats()["n_live"]
     stream = sim.stream
 
@@ -422,32 +447,37 @@ def run_native(args, rank, world, local_rank):
     units_local = float(st1["particle_steps"] - st0["particle_steps"])
     ms, units = reduce_timing(ms_local, units_local, world)
     value = units / (ms / 1e3)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
 
-    # end to end through the C ABI with host buffers: the thermal table is copied
-    # from pinned host memory every step (as a coupled thermal solver would supply
-    # it) and the step statistics are read back to the host every step
+    # end to end through the C ABI with host buffers, on a second context from the same
+    # start (the same warm-up steps untimed, then the same steps as the timed region):
+    # the thermal table is copied from pinned host memory every step (as a coupled
+    # thermal solver would supply it) and the step statistics are read back every step
+    sim = make_sim()
+    sim.gp_step(args.warmup)
     Th = torch.from_numpy(np.ascontiguousarray(g["T"])).pin_memory()
     Th_np = Th.numpy()
-    e2e_units = 0.0
     torch.cuda.synchronize(dev)
     barrier(world)
     t0 = time.perf_counter()
     sa = sim.gp_stats()
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         sim.gp_set_thermal_grid(Th_np, g["origin"], g["spacing"], g["vel"])
         sim.gp_step(1)
         sim.gp_stats()
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     sb = sim.gp_stats()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
     e2e_units = float(sb["particle_steps"] - sa["particle_steps"])
     e2e_ms, e2e_units = reduce_timing(e2e_s * 1e3, e2e_units, world)
     e2e_value = e2e_units / (e2e_ms / 1e3)
 
     if rank != 0:
-        sim.close()
-        del sim
-        torch.cuda.empty_cache()
         if not args.no_extras:
             batch_ensemble(dev, rank, world)   # this rank's shard of the ensemble
         return 0
@@ -465,14 +495,21 @@ def run_native(args, rank, world, local_rank):
                 "traffic": None if tb is None else tb * per_launch_units,
                 "algorithmic_bytes_per_launch": dom["bytes_per_unit"] * per_launch_units,
                 "avg_launch_ms": dom["total_ms"] / max(dom["launches"], 1)}
+    # the whole step against the copy bandwidth: measured DRAM bytes per particle-step
+    # (one-pass ncu capture of the default run) and the algorithmic 48 B
+    default_run = (args.grains, args.n0, tuple(args.plate), args.warmup, args.steps) == \
+        (10000, 50, (4.0, 2.0, 1.0), 3, 10)
+    sb = ncu_step_traffic() if default_run else None
+    step_roof = {"peak": peak, "unit": "GB/s", "peak_source": peak_kind,
+                 "algorithmic_bytes_per_particle_step": B_ALG_STEP,
+                 "algorithmic_frac": value * B_ALG_STEP / 1e9 / peak,
+                 "dram_bytes_per_particle_step": sb,
+                 "dram_frac": None if sb is None else value * sb / 1e9 / peak}
     launches = sum(k["launches"] for k in prof)
     kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
                            "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in prof),
                                                                1e-9), 4)} for k in prof}
     cb = cpu_baseline(args.cpu_grains, args.n0, 2) if (world == 1 and not args.no_cpu) else None
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
     adj = adjoint_cost(dev) if not args.no_extras else None
     bat = batch_ensemble(dev, rank, world) if not args.no_extras else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
@@ -487,8 +524,9 @@ def run_native(args, rank, world, local_rank):
                        "live_at_end": st1["n_live"], "parallelism": f"replicas x{world}",
                        "claim_blocks_used": round(st1["n_claim_blocks"] / blocks, 3),
                        "l2": "inputs larger than L2 (particle store > 1.5 GB)"},
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cb,
-            "e2e": {"value": e2e_value, "unit": METRIC, "steps": args.e2e_steps,
+            "roofline": roof, "step_roofline": step_roof, "kernels": kernels,
+            "cpu_baseline": cb,
+            "e2e": {"value": e2e_value, "unit": METRIC, "steps": e2e_steps,
                     "h2d_bytes_per_step": int(Th.numel() * 4),
                     "d2h_bytes_per_step": 160},
             "clocks": clk, "gpu_launches": launches, "adjoint": adj, "batch": bat}
@@ -510,7 +548,8 @@ def main():
     ap.add_argument("--plate", type=float, nargs=3, default=(4.0, 2.0, 1.0),
                     help="plate size in mm (smaller plates with proportionally fewer grains "
                          "keep the grain density; used for profiling captures)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="end-to-end steps (default: as many as --steps, on the same states)")
     ap.add_argument("--cpu-grains", type=int, default=100)
     ap.add_argument("--ref-grains", type=int, default=40)
     ap.add_argument("--no-cpu", action="store_true")

@@ -80,6 +80,44 @@ def test_contact_bit_exact(n, ng, seed):
     assert np.array_equal(fr2, fr_o)
 
 
+def test_contact_bit_exact_crowded_cells():
+    """Cells holding 15 or more points (saturated 4-bit counts): the search locates
+    their range by the keys instead of the counts."""
+    g = inputs.rng(11)
+    h = 2e-6
+    lo, hi = np.zeros(3), np.array([60e-6, 40e-6, 20e-6])
+    sparse = g.random((6000, 3)) * hi
+    crowd = np.array([21e-6, 13e-6, 7e-6]) + g.random((3000, 3)) * 6e-6  # ~110 per cell
+    one_cell = np.array([41e-6, 31e-6, 11e-6]) + g.random((40, 3)) * 1.9e-6
+    x = np.concatenate([sparse, crowd, one_cell]).astype(np.float32)
+    x = x[g.permutation(len(x))]
+    grain = g.integers(0, 4, len(x)).astype(np.int32)
+    state = g.choice(np.array([0, 0, 1], np.uint8), len(x))
+    fr_o, pairs_o = oracle.contact_f32(x, grain, state, lo, hi, h, want_pairs=True)
+    fr, pairs, m = native.gp_contact(torch.from_numpy(x).to(DEV), torch.from_numpy(grain).to(DEV),
+                                     torch.from_numpy(state).to(DEV), lo, hi, h, want_pairs=True,
+                                     pair_cap=4 * len(pairs_o) + 16)
+    assert m == len(pairs_o)
+    assert np.array_equal(fr, fr_o)
+    assert np.array_equal(pairs, pairs_o)
+
+
+def test_contact_segment_overflow_is_an_error():
+    """A row of 16 hash cells with 32767 or more points exceeds the cell table's
+    15-bit count: the call fails instead of returning a truncated search."""
+    g = inputs.rng(12)
+    h = 2e-6
+    lo, hi = np.zeros(3), np.array([40e-6, 40e-6, 40e-6])
+    # one row of cells (y, z inside one cell), x over the row's first 16 cells
+    x = (np.array([1e-6, 4.2e-6, 4.2e-6]) + g.random((33000, 3)) * np.array([30e-6, 1.6e-6, 1.6e-6])
+         ).astype(np.float32)
+    grain = np.zeros(len(x), np.int32)
+    state = np.zeros(len(x), np.uint8)
+    with pytest.raises(native.GPError):
+        native.gp_contact(torch.from_numpy(x).to(DEV), torch.from_numpy(grain).to(DEV),
+                          torch.from_numpy(state).to(DEV), lo, hi, h)
+
+
 # ----------------------------------------------------------------------------------
 # a3-a6: single grain in a uniform melt (Sec. 2.1.2 octahedron), GPU vs closed form
 # ----------------------------------------------------------------------------------
