@@ -351,8 +351,8 @@ gp_status gp_run_counts(gp_ctx* ctx, int32_t nruns, int64_t* live, int64_t* acti
 
 /* Launches of a batch step.  Every kernel of a batch step sizes itself on the
  * device: the counts live in device memory and the grids are persistent
- * (*_ctas_per_sm resident CTAs per SM over the whole GPU: build 1..8, advance 1..5,
- * emit 1..8).  graph_steps > 0 captures graph_steps consecutive steps in a CUDA
+ * (*_ctas_per_sm CTAs per SM over the whole GPU: build 1..8, advance 1..8, emit
+ * 1..8; eight, eight and six are resident at once).  graph_steps > 0 captures graph_steps consecutive steps in a CUDA
  * graph on first use and replays it (no host round trip inside a graph; the
  * context's stream must not be the legacy default stream); 0 issues the launches
  * step by step.  Results do not depend on the configuration. */

@@ -641,8 +641,8 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   c->rcount = at<unsigned long long>(c, L.rcount);
   refresh_params(c);
   c->P.launch.build_ctas = 8 * c->sms;
-  c->P.launch.advance_ctas = 5 * c->sms;
-  c->P.launch.emit_ctas = 8 * c->sms;
+  c->P.launch.advance_ctas = 8 * c->sms;
+  c->P.launch.emit_ctas = 6 * c->sms;
   if (batch) c->sb.n_dev = &c->dst->n_live;  // device-sized sort
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
@@ -1522,8 +1522,9 @@ gp_status gp_set_launch_config(gp_ctx* c, const gp_launch_config* cfg) {
   if (!cfg) return fail(c, GP_ERR_ARG, "null configuration");
   if (!c->batch) return fail(c, GP_ERR_STATE, "launch configurations apply to batch contexts");
   auto ok = [](int v, int hi) { return v >= 1 && v <= hi; };
-  // resident CTAs per SM: 5 for the advance (51 registers a thread), 8 for the others
-  if (!ok(cfg->build_ctas_per_sm, 8) || !ok(cfg->advance_ctas_per_sm, 5) ||
+  // resident CTAs per SM: 8 for the build and the advance (32 registers a thread), 6
+  // for the emit (40); a larger grid only queues CTAs
+  if (!ok(cfg->build_ctas_per_sm, 8) || !ok(cfg->advance_ctas_per_sm, 8) ||
       !ok(cfg->emit_ctas_per_sm, 8) || cfg->graph_steps < 0 || cfg->graph_steps > 1000)
     return fail(c, GP_ERR_ARG, "launch configuration out of range");
   c->P.launch.build_ctas = cfg->build_ctas_per_sm * c->sms;
@@ -1541,7 +1542,7 @@ gp_status gp_autotune(gp_ctx* c, int32_t trial_steps, gp_launch_config* best) {
   if (trial_steps < 1) return fail(c, GP_ERR_ARG, "trial_steps < 1");
   gp_launch_config cur{};
   gp_get_launch_config(c, &cur);
-  const int builds[] = {4, 8}, advances[] = {2, 5}, emits[] = {4, 8};
+  const int builds[] = {4, 8}, advances[] = {4, 8}, emits[] = {4, 6};
   cudaEvent_t ev[2];
   GP_CUDA(c, cudaEventCreate(&ev[0]));
   GP_CUDA(c, cudaEventCreate(&ev[1]));

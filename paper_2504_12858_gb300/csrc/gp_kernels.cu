@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
 // k_advance: contact freeze, growth, advance, spawn claims (sorted store, in place)
 // ---------------------------------------------------------------------------------
 template <bool BATCH, class K, bool PER = false>
-__global__ void __launch_bounds__(256, 5) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
+__global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
                                                  const K* __restrict__ skeys,
                                                  const uint4* __restrict__ tab,
@@ -738,7 +738,7 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
 }
 
 template <bool BATCH, class K, int ITEMS>
-__global__ void __launch_bounds__(256) k_emit(Params P, StepArgs S, const int4* __restrict__ rs,
+__global__ void __launch_bounds__(256, 6) k_emit(Params P, StepArgs S, const int4* __restrict__ rs,
                                               const int32_t* __restrict__ site_slot, int64_t n,
                                               int4* __restrict__ rout,
                                               K* __restrict__ keys,
