@@ -625,7 +625,7 @@ constexpr int kSortMaxPasses = 5;   // keys of up to 40 bits
 template <class K> struct SortTile;
 // keys per thread, keys per tile and resident CTAs per SM of a onesweep pass
 template <> struct SortTile<uint32_t> {
-  static constexpr int items = 12, tile = 256 * 12, ctas = 5;
+  static constexpr int items = 12, tile = 256 * 12, ctas = 6;
 };
 template <> struct SortTile<uint64_t> {
   static constexpr int items = 10, tile = 256 * 10, ctas = 4;
