@@ -168,6 +168,20 @@ def ncu_traffic(kernel: str):
     return None if k is None else float(k["dram_bytes_per_unit"])
 
 
+def ncu_issue(kernel: str):
+    """Share of the issue slots busy in `kernel` (ncu smsp__issue_active, small-case
+    capture of the same sources), if recorded for the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("sources_digest") != kernel_sources_digest():
+        return None
+    k = d.get("kernels", {}).get(kernel, {})
+    return None if "issue_slots_busy" not in k else float(k["issue_slots_busy"])
+
+
 def ncu_step_traffic():
     """DRAM bytes per particle-step of the whole step (every step kernel), from the
     committed one-pass ncu capture of the default bench's timed steps, if it was taken
@@ -493,6 +507,7 @@ def run_native(args, rank, world, local_rank):
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tb is None else tb * per_launch_units,
+                "issue_slots_busy": ncu_issue(dom["name"]),
                 "algorithmic_bytes_per_launch": dom["bytes_per_unit"] * per_launch_units,
                 "avg_launch_ms": dom["total_ms"] / max(dom["launches"], 1)}
     # the whole step against the copy bandwidth: measured DRAM bytes per particle-step
