@@ -86,11 +86,14 @@ __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ s
                                  (uint32_t)nib, (uint32_t)(nib >> 32));
 }
 
-// sum of the eight 4-bit counts in v (each byte sums two counts, at most 30)
-__device__ __forceinline__ uint32_t nib_sum8(uint32_t v) {
-  const uint32_t b = (v & 0x0f0f0f0fu) + ((v >> 4) & 0x0f0f0f0fu);
-  return (b * 0x01010101u) >> 24;
+// the eight 4-bit counts of v summed in pairs, one pair per byte (at most 30 each)
+__device__ __forceinline__ uint32_t nib_pairs(uint32_t v) {
+  return (v & 0x0f0f0f0fu) + ((v >> 4) & 0x0f0f0f0fu);
 }
+// sum of the four bytes of b (exact while that sum is below 256)
+__device__ __forceinline__ uint32_t byte_sum(uint32_t b) { return (b * 0x01010101u) >> 24; }
+// sum of the eight 4-bit counts in v
+__device__ __forceinline__ uint32_t nib_sum8(uint32_t v) { return byte_sum(nib_pairs(v)); }
 // mask of the low q 4-bit counts of a word (q >= 0)
 __device__ __forceinline__ uint32_t low_nibbles(int q) {
   return q >= 8 ? 0xffffffffu : ((1u << (4 * q)) - 1u);
@@ -120,24 +123,25 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                              unsigned long long* npairs = nullptr) {
   bool hit = false;
   const int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm.nc[0] - 1);
-  const int sa = x0 >> kSegShift, sb = x1 >> kSegShift;
+  const int y0 = max(cy - 1, 0), y1 = min(cy + 1, gm.nc[1] - 1);
+  const int z0 = max(cz - 1, 0), z1 = min(cz + 1, gm.nc[2] - 1);
   const uint4* __restrict__ rtab = tab + gm.seg0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int z = cz + dz;
-    if (z < 0 || z >= gm.nc[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int y = cy + dy;
-      if (y < 0 || y >= gm.nc[1]) continue;
-      const uint32_t row = (uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y;
-      for (int sgi = sa; sgi <= sb; ++sgi) {
+  // segments outermost: the cells c0..c1 of a segment, and so the masks of the counts
+  // before c0 and up to c1, are the same in all nine rows
+  for (int sgi = x0 >> kSegShift; sgi <= (x1 >> kSegShift); ++sgi) {
+    const int base = sgi << kSegShift;
+    const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
+    const uint32_t mz0 = low_nibbles(c0), mw0 = low_nibbles(max(c0 - 8, 0));
+    const uint32_t mz1 = low_nibbles(c1 + 1), mw1 = low_nibbles(max(c1 - 7, 0));
+    for (int z = z0; z <= z1; ++z) {
+      for (int y = y0; y <= y1; ++y) {
+        const uint32_t row = (uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y;
         const uint4 e = __ldg(rtab + (size_t)row * gm.nsx + sgi);
         if ((e.y >> 16) != stamp) continue;
-        const int base = sgi << kSegShift;
-        const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
         uint32_t i, end;
         if (!(e.y & 0x8000u)) {
-          i = e.x + nib_prefix(e.z, e.w, c0);
-          end = e.x + nib_prefix(e.z, e.w, c1 + 1);
+          i = e.x + byte_sum(nib_pairs(e.z & mz0) + nib_pairs(e.w & mw0));
+          end = e.x + byte_sum(nib_pairs(e.z & mz1) + nib_pairs(e.w & mw1));
         } else {
           // a cell holds 15 or more particles: locate the cells by their keys
           const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
