@@ -132,7 +132,7 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
     const int base = sgi << kSegShift;
     const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
     const uint32_t mz0 = low_nibbles(c0), mw0 = low_nibbles(max(c0 - 8, 0));
-    const uint32_t mz1 = low_nibbles(c1 + 1), mw1 = low_nibbles(max(c1 - 7, 0));
+    const uint32_t rz = low_nibbles(c1 + 1) & ~mz0, rw = low_nibbles(max(c1 - 7, 0)) & ~mw0;
     for (int z = z0; z <= z1; ++z) {
       for (int y = y0; y <= y1; ++y) {
         const uint32_t row = (uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y;
@@ -140,8 +140,10 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
         if ((e.y >> 16) != stamp) continue;
         uint32_t i, end;
         if (!(e.y & 0x8000u)) {
+          const uint32_t cnt = byte_sum(nib_pairs(e.z & rz) + nib_pairs(e.w & rw));
+          if (cnt == 0) continue;  // cells c0..c1 of this row are empty
           i = e.x + byte_sum(nib_pairs(e.z & mz0) + nib_pairs(e.w & mw0));
-          end = e.x + byte_sum(nib_pairs(e.z & mz1) + nib_pairs(e.w & mw1));
+          end = i + cnt;
         } else {
           // a cell holds 15 or more particles: locate the cells by their keys
           const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
