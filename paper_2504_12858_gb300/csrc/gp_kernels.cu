@@ -524,15 +524,15 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
     bool active = false, froze = false, clamped = false;
     bool crossing = false;
     int g = 0, sx = 0, sy = 0, sz = 0;
-    if (j >= 0) {
-      Rec r = rec_unpack(rs[j]);
-      if (r.state == ST_ACTIVE) {
+    // only the state word is read before the contact search; the record is read after
+    // it, so that it does not occupy registers during the search
+    if (j >= 0 && ((((uint32_t)__ldg(&rs[j].z)) >> 20) & 3u) == (uint32_t)ST_ACTIVE) {
+      {
         active = true;
         const float4 q = __ldg(pos4 + j);
         const float3 p = make_float3(q.x, q.y, q.z);
         const int gw = __float_as_int(q.w);
         const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
-        g = r.grain;
         int cx, cy, cz;
         cell_local(gm, p, cx, cy, cz);
         bool hit;
@@ -540,6 +540,8 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
           hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
         else
           hit = contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        Rec r = rec_unpack(rs[j]);
+        g = r.grain;
         if (hit) {
           froze = true;
           r.state = ST_FROZEN;
