@@ -527,49 +527,47 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
     // only the state word is read before the contact search; the record is read after
     // it, so that it does not occupy registers during the search
     if (j >= 0 && ((((uint32_t)__ldg(&rs[j].z)) >> 20) & 3u) == (uint32_t)ST_ACTIVE) {
-      {
-        active = true;
-        const float4 q = __ldg(pos4 + j);
-        const float3 p = make_float3(q.x, q.y, q.z);
-        const int gw = __float_as_int(q.w);
-        const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
-        int cx, cy, cz;
-        cell_local(gm, p, cx, cy, cz);
-        bool hit;
-        if constexpr (PER)
-          hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
-        else
-          hit = contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
-        Rec r = rec_unpack(rs[j]);
-        g = r.grain;
-        if (hit) {
-          froze = true;
-          r.state = ST_FROZEN;
-        } else {
-          // thermal sample at (x_n, t_n), growth law, explicit Euler step of ell
-          const float dT = undercooling(P, gm, S, p, gm.dT_base);
-          float dl = __fmul_rn(growth_v(P, dT), P.dt_over_h);
-          if (dl > 1.f) {
-            dl = 1.f;
-            clamped = true;
-          }
-          const float e = __fadd_rn(r.ell, dl);
-          // the target is reached within 2^-20 of a full spacing, so a step
-          // commensurate with h does not lose a step to binary32 rounding
-          if (e >= 1.f - 0x1p-20f) {
-            r.cross = 1;
-            r.ell = fmaxf(__fsub_rn(e, 1.f), 0.f);
-            crossing = true;
-            sx = r.sx;
-            sy = r.sy;
-            sz = r.sz;
-            step_site(sx, sy, sz, r.dir);
-          } else {
-            r.ell = e;
-          }
+      active = true;
+      const float4 q = __ldg(pos4 + j);
+      const float3 p = make_float3(q.x, q.y, q.z);
+      const int gw = __float_as_int(q.w);
+      const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
+      int cx, cy, cz;
+      cell_local(gm, p, cx, cy, cz);
+      bool hit;
+      if constexpr (PER)
+        hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+      else
+        hit = contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+      Rec r = rec_unpack(rs[j]);
+      g = r.grain;
+      if (hit) {
+        froze = true;
+        r.state = ST_FROZEN;
+      } else {
+        // thermal sample at (x_n, t_n), growth law, explicit Euler step of ell
+        const float dT = undercooling(P, gm, S, p, gm.dT_base);
+        float dl = __fmul_rn(growth_v(P, dT), P.dt_over_h);
+        if (dl > 1.f) {
+          dl = 1.f;
+          clamped = true;
         }
-        rs[j] = rec_pack(r);
+        const float e = __fadd_rn(r.ell, dl);
+        // the target is reached within 2^-20 of a full spacing, so a step
+        // commensurate with h does not lose a step to binary32 rounding
+        if (e >= 1.f - 0x1p-20f) {
+          r.cross = 1;
+          r.ell = fmaxf(__fsub_rn(e, 1.f), 0.f);
+          crossing = true;
+          sx = r.sx;
+          sy = r.sy;
+          sz = r.sz;
+          step_site(sx, sy, sz, r.dir);
+        } else {
+          r.ell = e;
+        }
       }
+      rs[j] = rec_pack(r);
     }
     // spawn claims: every outer direction k' at the reached site s' claims the target
     // s' + e_k' for this step (claimant bit of its axis).  All lanes take part.
