@@ -656,16 +656,18 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
     return 1u << 6;
   }
   if (r.state != ST_ACTIVE) return 0;
-  float4 gc, r0, r1, r2;
-  grain_load(P.gtab, r.grain, gc, r0, r1, r2);
-  const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
   if (!crossing) {
+    float4 gc, r0, r1, r2;
+    grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+    const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
     const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
     if (inside_np(P, gm, p)) return 1u << 6;
     ++n_clip;
     return 0;
   }
-  const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
+  // claims first, the geometry of the winners after: the grain's frame is not held in
+  // registers across the claim-word reads
+  uint32_t wins = 0;
   BlockCache bc;
   if (sslot >= 0) {  // block of s', looked up by k_advance
     bc.bx = sx >> 3;
@@ -690,9 +692,19 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
       ++n_lost;
       continue;
     }
-    if (k != r.dir) ++n_spawn;
-    if (inside_np(P, gm, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
-    else ++n_clip;
+    wins |= 1u << k;
+  }
+  if (wins) {
+    float4 gc, r0, r1, r2;
+    grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+    const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
+    const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
+    for (int k = 0; k < 6; ++k) {
+      if (!((wins >> k) & 1u)) continue;
+      if (k != r.dir) ++n_spawn;
+      if (inside_np(P, gm, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
+      else ++n_clip;
+    }
   }
   return mask;
 }
