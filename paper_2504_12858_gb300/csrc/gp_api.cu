@@ -107,7 +107,15 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
       return false;
     }
     R.nsx = (R.nc[0] + kSegCells - 1) / kSegCells;
-    R.nseg = (uint64_t)R.nsx * R.nc[1] * R.nc[2];
+    // the particle step orders cells in tiles of 16 x 4 x 4 (x fastest): the key range
+    // and the cell table cover whole tiles
+    const uint64_t tiles = (uint64_t)R.nsx * ((R.nc[1] + 3) / 4) * ((R.nc[2] + 3) / 4);
+    R.ncells = tiles * 256;
+    R.nseg = tiles * 16;
+    if (R.ncells >= (1ull << 32)) {
+      *why = "domain too large for the spatial hash (2^32 cells in whole tiles)";
+      return false;
+    }
     const int hm = (1 << L->hshift) - 1;
     R.nheads = (uint64_t)((R.nc[0] + hm) >> L->hshift) * ((R.nc[1] + hm) >> L->hshift) *
                ((R.nc[2] + hm) >> L->hshift);
@@ -436,6 +444,8 @@ void refresh_params(gp_ctx* c) {
       }
     }
     g.nsx = (g.nc[0] + kSegCells - 1) / kSegCells;
+    g.tx = g.nsx;
+    g.ty = (g.nc[1] + 3) / 4;
     g.key0 = R.key0;
     g.seg0 = R.seg0;
     g.head0 = R.head0;

@@ -101,6 +101,7 @@ struct Geo {
   int nc[3];                 // hash cells per axis
   float inv[3];              // 1 / cell edge per axis (the contact search's cells)
   int nsx;                   // segments of kSegCells cells per x row of the hash grid
+  int tx, ty;                // tiles of 16 x 4 x 4 cells along x and y (tiled cell order)
   unsigned long long key0;   // cell key of the run's cell 0
   unsigned long long seg0;   // first cell-table entry of the run
   unsigned long long head0;  // first reached-site head of the run

@@ -34,42 +34,72 @@ constexpr uint32_t kNoEntry = 0xffffffffu;
 //   y: build stamp (high 16 bits) | saturation flag (bit 15) | particle count of
 //      the segment (low 15 bits)
 //   z, w: particle count of each of the 16 cells, 4 bits each (cell 0 in the low
-//         nibble of z), saturated at 15; the flag is set when any count is
+//         nibble of z), saturated at 15; the flag is set when any count saturates
 // An entry whose stamp is not the current build's is an empty segment.  A query
 // turns the 3 cells x-1..x+1 of a neighbour row into a candidate range directly
 // from the nibble counts; when a count is saturated it scans the segment's keys.
-// run-local segment of a run-local cell key (and the cell's x)
+// Two cell orders.  Linear (the stand-alone hash): local = (z ny + y) nx + x, segments
+// of 16 cells along x, nsx per row.  Tiled (the particle step): tiles of 16 x 4 x 4
+// cells in (z, y, x) order, x fastest inside a tile, so that a cell's nine neighbour
+// rows are segments of one tile (or of its neighbours) and their particles lie close
+// together in the sorted store: local = tile * 256 + ((z & 3) * 4 + (y & 3)) * 16 + (x & 15)
+// and the segment of a cell is local / 16.  On the 4 x 2 x 1 mm weld plate the tiled
+// order made the step 13 % faster than linear rows (build, emit and advance all gain
+// from the 3D locality of consecutive records).
+// run-local segment of a run-local cell key (and the cell's x within its segment)
+template <bool TILED>
 __device__ __forceinline__ uint32_t seg_of(const Geo& g, uint32_t local, uint32_t& xcell) {
-  const uint32_t row = local / (uint32_t)g.nc[0];
-  xcell = local - row * (uint32_t)g.nc[0];
-  return row * (uint32_t)g.nsx + (xcell >> kSegShift);
+  if constexpr (TILED) {
+    xcell = local & (kSegCells - 1);
+    return local >> kSegShift;
+  } else {
+    const uint32_t row = local / (uint32_t)g.nc[0];
+    xcell = local - row * (uint32_t)g.nc[0];
+    return row * (uint32_t)g.nsx + (xcell >> kSegShift);
+  }
 }
 
+template <bool TILED>
 __device__ __forceinline__ uint32_t ncells_of(const Geo& g) {
-  return (uint32_t)((uint64_t)g.nc[0] * g.nc[1] * g.nc[2]);
+  if constexpr (TILED)
+    return (uint32_t)((uint64_t)g.tx * g.ty * ((g.nc[2] + 3) >> 2) * 256);
+  else
+    return (uint32_t)((uint64_t)g.nc[0] * g.nc[1] * g.nc[2]);
+}
+
+// tiled segment of neighbour row (y, z) in x segment sx16 (the tile column)
+__device__ __forceinline__ uint32_t seg_tiled(const Geo& g, int sx16, int y, int z) {
+  return ((((uint32_t)(z >> 2) * (uint32_t)g.ty + (uint32_t)(y >> 2)) * (uint32_t)g.tx +
+           (uint32_t)sx16) << 4) | (uint32_t)(((z & 3) << 2) | (y & 3));
+}
+
+// tiled run-local cell of cell coordinates
+__device__ __forceinline__ uint32_t local_tiled(const Geo& g, int cx, int cy, int cz) {
+  return (seg_tiled(g, cx >> kSegShift, cy, cz) << kSegShift) | (uint32_t)(cx & (kSegCells - 1));
 }
 
 // Writes the entry of the segment that starts at sorted index j (if one does).
 // The keys of the run are key0 + local; a key outside that range ends the run.
-template <class K>
+template <class K, bool TILED>
 __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ skeys, int64_t j,
                                           int64_t n, K key, uint4* __restrict__ tab,
                                           uint32_t stamp, uint32_t* err) {
   const K k0 = (K)gm.key0;
-  const uint32_t nvalid = ncells_of(gm);
+  const uint32_t nvalid = ncells_of<TILED>(gm);
   uint32_t x0;
-  const uint32_t sg = seg_of(gm, (uint32_t)(key - k0), x0);
+  const uint32_t sg = seg_of<TILED>(gm, (uint32_t)(key - k0), x0);
   if (j > 0) {
     const K kp = __ldg(skeys + j - 1);
     uint32_t xp;
-    if (kp >= k0 && (K)(kp - k0) < (K)nvalid && seg_of(gm, (uint32_t)(kp - k0), xp) == sg) return;
+    if (kp >= k0 && (K)(kp - k0) < (K)nvalid && seg_of<TILED>(gm, (uint32_t)(kp - k0), xp) == sg)
+      return;
   }
   unsigned long long nib = 0;
   uint32_t c = 0;
   K k = key;
   while (true) {
     uint32_t x;
-    seg_of(gm, (uint32_t)(k - k0), x);
+    seg_of<TILED>(gm, (uint32_t)(k - k0), x);
     const int sh = 4 * (int)(x & (kSegCells - 1));
     if (((nib >> sh) & 15ull) < 15ull) nib += 1ull << sh;
     if (++c == kSegMaxCount) {
@@ -79,7 +109,8 @@ __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ s
     if (j + c >= n) break;
     k = __ldg(skeys + j + c);
     uint32_t xk;
-    if (k < k0 || (K)(k - k0) >= (K)nvalid || seg_of(gm, (uint32_t)(k - k0), xk) != sg) break;
+    if (k < k0 || (K)(k - k0) >= (K)nvalid || seg_of<TILED>(gm, (uint32_t)(k - k0), xk) != sg)
+      break;
   }
   const bool sat = ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
   tab[gm.seg0 + sg] = make_uint4((uint32_t)j, (stamp << 16) | (sat ? 0x8000u : 0u) | c,
@@ -111,7 +142,7 @@ __device__ __forceinline__ uint32_t nib_prefix(uint32_t z, uint32_t w, int p) {
 // PAIRS == false: returns at the first one.  PAIRS == true: visits all of them and
 // appends the pairs (idj, ids[i]) with idj < ids[i] to pairs (up to pair_cap,
 // counted in *npairs).  Returns whether any was found.
-template <bool PAIRS, class K>
+template <bool PAIRS, class K, bool TILED>
 __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                              const uint4* __restrict__ tab, uint32_t stamp,
                                              const K* __restrict__ skeys,
@@ -135,8 +166,10 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
     const uint32_t rz = low_nibbles(c1 + 1) & ~mz0, rw = low_nibbles(max(c1 - 7, 0)) & ~mw0;
     for (int z = z0; z <= z1; ++z) {
       for (int y = y0; y <= y1; ++y) {
-        const uint32_t row = (uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y;
-        const uint4 e = __ldg(rtab + (size_t)row * gm.nsx + sgi);
+        const uint32_t sg = TILED ? seg_tiled(gm, sgi, y, z)
+                                  : ((uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y) *
+                                            (uint32_t)gm.nsx + (uint32_t)sgi;
+        const uint4 e = __ldg(rtab + sg);
         if ((e.y >> 16) != stamp) continue;
         uint32_t i, end;
         if (!(e.y & 0x8000u)) {
@@ -146,7 +179,10 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
           end = i + cnt;
         } else {
           // a cell holds 15 or more particles: locate the cells by their keys
-          const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
+          const K klo = (K)gm.key0 +
+                        (K)(TILED ? (sg << kSegShift) + (uint32_t)c0
+                                  : ((uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y) *
+                                            (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
           const K khi = klo + (K)(c1 - c0);
           i = e.x;
           end = e.x + (e.y & kSegMaxCount);
@@ -209,11 +245,11 @@ __device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __
       int y = cy + dy;
       if (P.periodic & 2) y = (y + gm.nc[1]) % gm.nc[1];
       else if (y < 0 || y >= gm.nc[1]) continue;
-      const uint32_t row = (uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y;
       for (int wi = 0; wi < nw; ++wi) {
         const int x0 = wx0[wi], x1 = wx1[wi];
         for (int sgi = x0 >> kSegShift; sgi <= (x1 >> kSegShift); ++sgi) {
-          const uint4 e = __ldg(rtab + (size_t)row * gm.nsx + sgi);
+          const uint32_t sg = seg_tiled(gm, sgi, y, z);
+          const uint4 e = __ldg(rtab + sg);
           if ((e.y >> 16) != stamp) continue;
           const int base = sgi << kSegShift;
           const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
@@ -222,7 +258,7 @@ __device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __
             i = e.x + nib_prefix(e.z, e.w, c0);
             end = e.x + nib_prefix(e.z, e.w, c1 + 1);
           } else {
-            const K klo = (K)gm.key0 + (K)(row * (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
+            const K klo = (K)gm.key0 + (K)((sg << kSegShift) + (uint32_t)c0);
             const K khi = klo + (K)(c1 - c0);
             i = e.x;
             end = e.x + (e.y & kSegMaxCount);
@@ -401,7 +437,8 @@ template <class K>
 __device__ __forceinline__ K cell_key(const Params& P, const Geo& gm, float3 p) {
   int cx, cy, cz;
   if (P.periodic) p = wrap_pos(P, gm, p);
-  return (K)gm.key0 + (K)cell_local(gm, p, cx, cy, cz);
+  cell_local(gm, p, cx, cy, cz);
+  return (K)gm.key0 + (K)local_tiled(gm, cx, cy, cz);
 }
 
 // inside the domain along the axes that are not periodic
@@ -469,7 +506,7 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
           const int run = run_of<BATCH>(gc);
           const float3 pw = P.periodic ? wrap_pos(P, P.geo, p) : p;
           pos4[j] = make_float4(pw.x, pw.y, pw.z, __int_as_float(r.grain | (run << kRunShift)));
-          seg_build<K>(geo_of<BATCH>(P, run), skeys, j, n, key, tab, stamp, &st->err);
+          seg_build<K, true>(geo_of<BATCH>(P, run), skeys, j, n, key, tab, stamp, &st->err);
           if (r.state == ST_ACTIVE) amask |= 1u << it;
         }
       }
@@ -538,7 +575,7 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
       if constexpr (PER)
         hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
       else
-        hit = contact_scan<false, K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        hit = contact_scan<false, K, true>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
       Rec r = rec_unpack(rs[j]);
       g = r.grain;
       if (hit) {
@@ -1473,9 +1510,9 @@ __global__ void k_contact_sa(Params P, const float4* __restrict__ pos4,
   int cx, cy, cz;
   cell_local(P.geo, p, cx, cy, cz);
   const bool hit =
-      pairs ? contact_scan<true, uint32_t>(P, P.geo, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz,
+      pairs ? contact_scan<true, uint32_t, false>(P, P.geo, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz,
                                            ids, idj, pairs, pair_cap, npairs)
-            : contact_scan<false, uint32_t>(P, P.geo, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz);
+            : contact_scan<false, uint32_t, false>(P, P.geo, tab, 1u, skeys, pos4, n, p, g, cx, cy, cz);
   if (freeze) freeze[idj] = (hit && stj == ST_ACTIVE) ? 1 : 0;
 }
 
@@ -1493,8 +1530,8 @@ __global__ void k_build_sa(Params P, const float* __restrict__ x3, const int32_t
   pos4[j] = make_float4(x3[3 * id], x3[3 * id + 1], x3[3 * id + 2], __int_as_float(grain[id]));
   sstate[j] = state[id];
   const uint32_t key = skeys[j];
-  if (key >= ncells_of(P.geo)) return;  // removed points
-  seg_build<uint32_t>(P.geo, skeys, j, n, key, tab, 1u, err);
+  if (key >= ncells_of<false>(P.geo)) return;  // removed points
+  seg_build<uint32_t, false>(P.geo, skeys, j, n, key, tab, 1u, err);
 }
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
