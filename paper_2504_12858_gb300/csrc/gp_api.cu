@@ -107,11 +107,13 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
       return false;
     }
     R.nsx = (R.nc[0] + kSegCells - 1) / kSegCells;
-    // the particle step orders cells in tiles of 16 x 4 x 4 (x fastest): the key range
+    // the particle step orders cells in tiles of 16 x 8 x 8 (x fastest): the key range
     // and the cell table cover whole tiles
-    const uint64_t tiles = (uint64_t)R.nsx * ((R.nc[1] + 3) / 4) * ((R.nc[2] + 3) / 4);
-    R.ncells = tiles * 256;
-    R.nseg = tiles * 16;
+    const int ty = (R.nc[1] + (1 << kTileYShift) - 1) >> kTileYShift;
+    const int tz = (R.nc[2] + (1 << kTileZShift) - 1) >> kTileZShift;
+    const uint64_t tiles = (uint64_t)R.nsx * ty * tz;
+    R.nseg = tiles << (kTileYShift + kTileZShift);
+    R.ncells = R.nseg << kSegShift;
     if (R.ncells >= (1ull << 32)) {
       *why = "domain too large for the spatial hash (2^32 cells in whole tiles)";
       return false;
@@ -445,7 +447,7 @@ void refresh_params(gp_ctx* c) {
     }
     g.nsx = (g.nc[0] + kSegCells - 1) / kSegCells;
     g.tx = g.nsx;
-    g.ty = (g.nc[1] + 3) / 4;
+    g.ty = (g.nc[1] + (1 << kTileYShift) - 1) >> kTileYShift;
     g.key0 = R.key0;
     g.seg0 = R.seg0;
     g.head0 = R.head0;

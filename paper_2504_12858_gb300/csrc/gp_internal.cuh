@@ -35,6 +35,9 @@ constexpr int kBrickWords = 128;           // 8^3 sites, one byte each, 4 per wo
 constexpr int kSegShift = 4;               // the cell table has one entry per 16 cells of a row
 constexpr int kSegCells = 1 << kSegShift;
 constexpr uint32_t kSegMaxCount = 0x7fffu;  // particles per segment (15-bit count)
+// tiles of the particle step's cell order: 16 x 2^kTileYShift x 2^kTileZShift cells
+constexpr int kTileYShift = 3;
+constexpr int kTileZShift = 3;
 
 // ---------------------------------------------------------------------------------
 // particle record: 16 bytes, loaded and stored as one int4
@@ -101,7 +104,7 @@ struct Geo {
   int nc[3];                 // hash cells per axis
   float inv[3];              // 1 / cell edge per axis (the contact search's cells)
   int nsx;                   // segments of kSegCells cells per x row of the hash grid
-  int tx, ty;                // tiles of 16 x 4 x 4 cells along x and y (tiled cell order)
+  int tx, ty;                // tiles along x and y (tiled cell order)
   unsigned long long key0;   // cell key of the run's cell 0
   unsigned long long seg0;   // first cell-table entry of the run
   unsigned long long head0;  // first reached-site head of the run
