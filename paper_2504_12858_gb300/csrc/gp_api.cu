@@ -49,7 +49,9 @@ struct Layout {
   size_t rec0, rec1, pos4, sslot, act, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
       rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, gflags, gdtn, dstats, grid,
       sgrid, runs,
-      rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, total;
+      rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, gcnt, gofs, gfill,
+      gbsum, gkey, gdest, total;
+  uint32_t ngroups = 0;  // one run: cell groups of the record grouping
 };
 
 bool cells_of(const gp_domain* d, double h, int nc[3], uint64_t* ncells) {
@@ -208,6 +210,14 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->runs = take(sizeof(Geo) * (size_t)nruns);
   L->rtherm = take(16 * (size_t)nruns);
   L->rcount = take(16 * (size_t)nruns);
+  // one run: counts, offsets and fill cursors of the cell groups
+  L->ngroups = batch ? 0u : (uint32_t)(L->run[0].ncells >> kGroupShift);
+  L->gcnt = take(4 * (size_t)L->ngroups + 16);
+  L->gofs = take(4 * (size_t)L->ngroups + 16);
+  L->gfill = take(4 * (size_t)L->ngroups + 16);
+  L->gbsum = take(4 * (((size_t)L->ngroups + 255) / 256) + 16);
+  L->gkey = take(batch ? 16 : 4 * cap + 16);   // one run: cell keys in grouped order
+  L->gdest = take(batch ? 16 : 4 * cap + 16);  // and the sorted position of each
   L->total = o;
   return true;
 }
@@ -247,9 +257,10 @@ void grain_entry(const double* pos, const double* q, double h, int run, float4 o
                              (float)(h * R[3 * r + 2]), 0.f);
 }
 
-const char* kKernelNames[K_COUNT] = {"hist",      "onesweep", "keys", "build",
+const char* kKernelNames[K_COUNT] = {"hist",      "onesweep", "keys",     "build",
                                      "advance",   "emit",     "nucleate", "grain_map",
-                                     "seed",      "contact",  "cells",    "finalize"};
+                                     "seed",      "contact",  "cells",    "finalize",
+                                     "group"};
 // algorithmic DRAM bytes per processed item:
 //   hist      read key (4)
 //   onesweep  read key + value, write key + value (16)
@@ -260,7 +271,8 @@ const char* kKernelNames[K_COUNT] = {"hist",      "onesweep", "keys", "build",
 //             (16), write record (16); neighbour positions are re-reads of the same
 //             cells (cache)
 //   emit      read record (16), write record (16) + key + value (8) per output
-const double kKernelBytes[K_COUNT] = {4, 16, 24, 56, 52, 40, 0, 0, 0, 0, 0, 0};
+//   group     read key twice (8), write the grouped identity (4)
+const double kKernelBytes[K_COUNT] = {4, 16, 24, 56, 52, 40, 0, 0, 0, 0, 0, 0, 12};
 
 struct Prof : ProfHook {
   cudaStream_t st = nullptr;
@@ -1199,26 +1211,33 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
         c->prof.end(K_KEYS, (double)n);
         c->keys_valid = true;
       }
-      const int w = radix_sort<uint32_t>(c->sb, n, c->L.nbits, c->st);
-      if (w < 0) return fail(c, GP_ERR_STATE, "cell keys wider than the sort supports");
       if (++c->stamp > 0xffffu) {
         GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
         c->stamp = 1;
       }
       int4* sorted = c->rec[c->cur ^ 1];
       GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
-      c->prof.begin(K_BUILD);
-      launch_build(batch, P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4,
-                   c->cells, c->stamp, n, c->L.key_end, c->act, c->dst, c->st);
-      c->prof.end(K_BUILD, (double)n);
+      // records grouped by cell (in place of the radix sort): the emit's keys in keys[0],
+      // the grouped identities in vals[1], the sorted keys in keys[1], the source index
+      // of each sorted record in vals[0] (for the tape), the ACTIVE flags in the claim-slot
+      // hand-off (overwritten by the advance before the emit reads it)
+      uint32_t* skeys = static_cast<uint32_t*>(c->sb.keys[1]);
+      launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), n, c->L.ngroups,
+                         at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
+                         at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
+                         at<uint32_t>(c, c->L.gkey), at<uint32_t>(c, c->L.gdest), c->rec[c->cur],
+                         sorted, c->pos4, skeys, rec ? c->sb.vals[0] : nullptr,
+                         reinterpret_cast<uint8_t*>(c->site_slot), c->cells, c->stamp, c->act,
+                         c->dst, c->sms, &c->prof, c->st);
+      GP_CUDA(c, cudaGetLastError());
       if (rec) {
         GP_CUDA(c, cudaMemcpyAsync(at<int4>(c, c->L.tape_rec) + tq * tcap, sorted, 16 * n,
                                    cudaMemcpyDeviceToDevice, c->st));
-        GP_CUDA(c, cudaMemcpyAsync(at<uint32_t>(c, c->L.tape_vals) + tq * tcap, c->sb.vals[w],
+        GP_CUDA(c, cudaMemcpyAsync(at<uint32_t>(c, c->L.tape_vals) + tq * tcap, c->sb.vals[0],
                                    4 * n, cudaMemcpyDeviceToDevice, c->st));
       }
       c->prof.begin(K_ADVANCE);
-      launch_advance(batch, P, S, sorted, c->pos4, c->sb.keys[w], c->cells, c->stamp, n, c->act,
+      launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp, n, c->act,
                      c->C, c->site_slot, c->dst, c->st);
       // units: the ACTIVE particles entering the step (live minus frozen after the last step)
       c->prof.end(K_ADVANCE, (double)(n - std::min<int64_t>(n, (int64_t)c->hst->n_frozen)));

@@ -38,6 +38,10 @@ constexpr uint32_t kSegMaxCount = 0x7fffu;  // particles per segment (15-bit cou
 // tiles of the particle step's cell order: 16 x 2^kTileYShift x 2^kTileZShift cells
 constexpr int kTileYShift = 3;
 constexpr int kTileZShift = 3;
+// a single run groups its records by key >> kGroupShift (one tile: 1024 cells, 64
+// segments) and orders them by cell inside each group, in place of the radix sort
+constexpr int kGroupShift = 10;
+constexpr int kGroupCells = 1 << kGroupShift;
 
 // ---------------------------------------------------------------------------------
 // particle record: 16 bytes, loaded and stored as one int4
@@ -599,7 +603,7 @@ __device__ __forceinline__ void warp_add(unsigned long long* ctr, unsigned int v
 // kernel ids for the optional CUDA-event timing
 enum KernelId : int {
   K_HIST = 0, K_ONESWEEP, K_KEYS, K_BUILD, K_ADVANCE, K_EMIT, K_NUCLEATE, K_GRAIN_MAP,
-  K_SEED, K_CONTACT, K_CELLS, K_FINALIZE, K_COUNT
+  K_SEED, K_CONTACT, K_CELLS, K_FINALIZE, K_GROUP, K_COUNT
 };
 
 struct ProfHook {

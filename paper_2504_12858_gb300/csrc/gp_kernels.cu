@@ -1548,6 +1548,195 @@ inline unsigned persistent(int64_t n_max, int per_cta, int ctas_total) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, ctas_total));
 }
 
+// ---------------------------------------------------------------------------------
+// Grouping of a single run's records (in place of the radix sort and the build there).
+// Records grouped by key >> kGroupShift (a tile of the cell order) and then ordered by
+// cell inside each group are in key order:
+//   k_group_count    records per group (one atomic per group present in a warp; the
+//                    emit's keys are nearly sorted)
+//   k_scan_blocks, k_scan_sums   exclusive scan of the counts (group starts)
+//   k_group_scatter  record identities and keys grouped by group (any order inside)
+//   k_group_order    one warp per group: cell counts in shared memory, their offsets,
+//                    the group's cell-table entries and every record's sorted position
+//   k_group_gather   one thread per record: record, position, key and ACTIVE flag to
+//                    the sorted position; k_act_list then lists the ACTIVE ones
+// On the 4 x 2 x 1 mm weld plate this takes 1.1 + 5.0 ms per step against 5.7 + 2.5 ms
+// for the histogram, four onesweep passes and the build.
+// ---------------------------------------------------------------------------------
+
+// first sorted position of group t (n past the last group)
+__device__ __forceinline__ uint32_t tile_start(const uint32_t* __restrict__ ofs,
+                                               const uint32_t* __restrict__ bsum, int64_t t,
+                                               int64_t ng, int64_t n) {
+  return t >= ng ? (uint32_t)n : ofs[t] + bsum[t >> 8];
+}
+
+__global__ void __launch_bounds__(256) k_group_count(const uint32_t* __restrict__ keys, int64_t n,
+                                                     uint32_t ng, uint32_t* __restrict__ cnt,
+                                                     uint32_t* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = __ldg(keys + i) >> kGroupShift;
+    const uint32_t m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const uint32_t peers = __match_any_sync(m, t);  // one atomic per group in the warp
+    if (lane == __ffs(peers) - 1) {
+      if (t < ng) atomicAdd(cnt + t, (uint32_t)__popc(peers));
+      else atomicOr(err, ERR_TIMEOUT);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_group_scatter(const uint32_t* __restrict__ keys, int64_t n,
+                                                       uint32_t ng, const uint32_t* __restrict__ ofs,
+                                                       const uint32_t* __restrict__ bsum,
+                                                       uint32_t* __restrict__ fill,
+                                                       uint32_t* __restrict__ perm,
+                                                       uint32_t* __restrict__ gkey, uint32_t* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t key = __ldg(keys + i);
+    const uint32_t t = key >> kGroupShift;
+    const uint32_t m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const uint32_t peers = __match_any_sync(m, t);
+    const int leader = __ffs(peers) - 1;
+    uint32_t b = 0;
+    if (lane == leader && t < ng) b = atomicAdd(fill + t, (uint32_t)__popc(peers));
+    b = __shfl_sync(m, b, leader);
+    if (t < ng) {
+      const uint64_t p = (uint64_t)tile_start(ofs, bsum, t, ng, n) + b +
+                         __popc(peers & ((1u << lane) - 1u));
+      if (p < (uint64_t)n) {
+        perm[p] = (uint32_t)i;
+        gkey[p] = key;
+      } else {
+        atomicOr(err, ERR_TIMEOUT);
+      }
+    }
+  }
+}
+
+// One warp per group of kGroupCells cells (groups strided over the warps of the grid).
+// s_c holds the group's cell counts, then the sorted position of each cell's next
+// record, which the last pass advances to give every grouped record its sorted
+// position (dest).  The offsets are scanned 32 cells (two segments) per round,
+// conflict-free, and each round writes its two cell-table entries.
+__global__ void __launch_bounds__(256) k_group_order(
+    const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ ofs,
+    const uint32_t* __restrict__ bsum, uint32_t ng, int64_t n, uint64_t seg0,
+    uint32_t* __restrict__ dest, uint4* __restrict__ tab, uint32_t stamp, DevStats* st) {
+  __shared__ uint32_t s_c[8][kGroupCells];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t* c = s_c[w];
+  for (int64_t g = (int64_t)blockIdx.x * 8 + w; g < (int64_t)ng; g += (int64_t)gridDim.x * 8) {
+    const uint32_t s = tile_start(ofs, bsum, g, ng, n);
+    const uint32_t e = tile_start(ofs, bsum, g + 1, ng, n);
+    if (s >= e) continue;  // warp-uniform
+#pragma unroll
+    for (int q = 0; q < kGroupCells / 32; ++q) c[q * 32 + lane] = 0;
+    __syncwarp();
+    for (uint32_t i = s + lane; i < e; i += 32) atomicAdd(c + (__ldg(gkey + i) & (kGroupCells - 1)), 1u);
+    __syncwarp();
+    uint32_t run = s;
+    const uint64_t sg0 = seg0 + ((uint64_t)g << (kGroupShift - kSegShift));
+#pragma unroll 1
+    for (int q = 0; q < kGroupCells / 32; ++q) {
+      const uint32_t v = c[q * 32 + lane];
+      uint32_t inc = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      c[q * 32 + lane] = run + inc - v;
+      const uint32_t t15 = __shfl_sync(0xffffffffu, inc, 15);
+      const uint32_t t31 = __shfl_sync(0xffffffffu, inc, 31);
+      // 4-bit counts saturated at 15: lanes 0-7 / 8-15 give the z / w word of the
+      // round's first segment, lanes 16-23 / 24-31 those of its second
+      uint32_t nb = (v < 15u ? v : 15u) << (4 * (lane & 7));
+      nb |= __shfl_xor_sync(0xffffffffu, nb, 1);
+      nb |= __shfl_xor_sync(0xffffffffu, nb, 2);
+      nb |= __shfl_xor_sync(0xffffffffu, nb, 4);
+      const uint32_t nbw = __shfl_sync(0xffffffffu, nb, (lane + 8) & 31);
+      const uint32_t sat = __ballot_sync(0xffffffffu, v >= 15u);
+      if (lane == 0 || lane == 16) {
+        const uint32_t cnt = lane == 0 ? t15 : t31 - t15;
+        if (cnt) {
+          if (cnt >= kSegMaxCount) atomicOr(&st->err, ERR_CELL_OVERFLOW);
+          const uint32_t cc = cnt < kSegMaxCount ? cnt : kSegMaxCount;
+          const bool sf = lane == 0 ? (sat & 0xffffu) != 0 : (sat >> 16) != 0;
+          tab[sg0 + 2 * q + (lane >> 4)] =
+              make_uint4(run + (lane == 0 ? 0u : t15), (stamp << 16) | (sf ? 0x8000u : 0u) | cc,
+                         nb, nbw);
+        }
+      }
+      run += t31;
+    }
+    __syncwarp();
+    for (uint32_t i = s + lane; i < e; i += 32)
+      dest[i] = atomicAdd(c + (__ldg(gkey + i) & (kGroupCells - 1)), 1u);
+    __syncwarp();
+  }
+}
+
+// every grouped record to its sorted position: record, position, key, source index and
+// ACTIVE flag (one thread per record)
+__global__ void __launch_bounds__(256) k_group_gather(
+    Params P, const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ perm,
+    const uint32_t* __restrict__ dest, int64_t n, const int4* __restrict__ rin,
+    int4* __restrict__ rout, float4* __restrict__ pos4, uint32_t* __restrict__ skeys,
+    uint32_t* __restrict__ svals, uint8_t* __restrict__ sact, DevStats* st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t o = __ldg(perm + i), j = __ldg(dest + i);
+  if ((int64_t)o >= n || (int64_t)j >= n) {  // only after inconsistent keys
+    atomicOr(&st->err, ERR_TIMEOUT);
+    return;
+  }
+  const int4 rv = __ldg(rin + o);
+  rout[j] = rv;
+  const Rec r = rec_unpack(rv);
+  float4 gc, r0, r1, r2;
+  grain_load(P.gtab, r.grain, gc, r0, r1, r2);
+  const float3 p = add_dir(site_pos_g(gc, r0, r1, r2, r.sx, r.sy, r.sz), r0, r1, r2, r.dir, r.ell);
+  const float3 pw = P.periodic ? wrap_pos(P, P.geo, p) : p;
+  pos4[j] = make_float4(pw.x, pw.y, pw.z, __int_as_float(r.grain));
+  skeys[j] = __ldg(gkey + i);
+  if (svals) svals[j] = o;
+  sact[j] = r.state == ST_ACTIVE ? 1 : 0;
+}
+
+// list of the ACTIVE sorted indices (one reservation per 1024 records; each warp's
+// entries contiguous and ascending within each item)
+__global__ void __launch_bounds__(256) k_act_list(const uint8_t* __restrict__ sact, int64_t n,
+                                                  uint32_t* __restrict__ act, DevStats* st) {
+  __shared__ uint32_t s_warp[8];
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31;
+  for (int64_t j0 = (int64_t)blockIdx.x * (256 * kBuildItems); j0 < n;
+       j0 += (int64_t)gridDim.x * (256 * kBuildItems)) {
+    uint32_t amask = 0;
+#pragma unroll
+    for (int it = 0; it < kBuildItems; ++it) {
+      const int64_t j = j0 + it * 256 + threadIdx.x;
+      if (j < n && __ldg(sact + j)) amask |= 1u << it;
+    }
+    uint32_t tot;
+    const uint32_t ofs = bscan256(__popc(amask), s_warp, tot);
+    if (threadIdx.x == 0) s_base = tot ? atomicAdd(&st->n_act, (unsigned long long)tot) : 0ull;
+    __syncthreads();
+    unsigned long long o = s_base + __shfl_sync(0xffffffffu, ofs, 0);
+#pragma unroll 1
+    for (int it = 0; it < kBuildItems; ++it) {
+      const bool a = (amask >> it) & 1u;
+      const uint32_t b = __ballot_sync(0xffffffffu, a);
+      if (a) act[o + __popc(b & ((1u << lane) - 1u))] = (uint32_t)(j0 + it * 256 + threadIdx.x);
+      o += __popc(b);
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -1754,6 +1943,33 @@ void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstat
   if (n > 0)
     k_contact_sa<<<blocks(n), 256, 0, st>>>(P, pos4, sstate, ids, skeys, tab, n, freeze, pairs,
                                             pair_cap, npairs);
+}
+
+
+void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32_t ng,
+                        uint32_t* gcnt, uint32_t* gofs, uint32_t* gbsum, uint32_t* gfill,
+                        uint32_t* perm, uint32_t* gkey, uint32_t* gdest, const int4* rin,
+                        int4* rout, float4* pos4, uint32_t* skeys, uint32_t* svals,
+                        uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
+                        int sms, ProfHook* prof, cudaStream_t st) {
+  if (n <= 0) return;
+  if (prof) prof->begin(K_GROUP);
+  cudaMemsetAsync(gcnt, 0, 4 * (size_t)ng, st);
+  cudaMemsetAsync(gfill, 0, 4 * (size_t)ng, st);
+  const unsigned g1 = (unsigned)std::min<int64_t>(blocks(n), (int64_t)sms * 16);
+  k_group_count<<<g1, 256, 0, st>>>(keys, n, ng, gcnt, &dst->err);
+  const int64_t nb = ((int64_t)ng + 255) / 256;
+  k_scan_blocks<<<(unsigned)nb, 256, 0, st>>>(gcnt, ng, gofs, gbsum);
+  k_scan_sums<<<1, 256, 0, st>>>(gbsum, nb);
+  k_group_scatter<<<g1, 256, 0, st>>>(keys, n, ng, gofs, gbsum, gfill, perm, gkey, &dst->err);
+  if (prof) prof->end(K_GROUP, (double)n);
+  if (prof) prof->begin(K_BUILD);
+  k_group_order<<<(unsigned)(sms * 8), 256, 0, st>>>(gkey, gofs, gbsum, ng, n, P.geo.seg0, gdest,
+                                                     tab, stamp, dst);
+  k_group_gather<<<blocks(n), 256, 0, st>>>(P, gkey, perm, gdest, n, rin, rout, pos4, skeys, svals,
+                                            sact, dst);
+  k_act_list<<<blocks(n, 256 * kBuildItems), 256, 0, st>>>(sact, n, act, dst);
+  if (prof) prof->end(K_BUILD, (double)n);
 }
 
 }  // namespace gp

@@ -15,6 +15,15 @@ void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* 
 void launch_build(bool batch, const Params& P, const void* skeys, const uint32_t* svals,
                   const int4* rin, int4* rout, float4* pos4, uint4* tab, uint32_t stamp,
                   int64_t n, uint64_t key_end, uint32_t* act, DevStats* dst, cudaStream_t st);
+// one run: the records grouped by cell in place of the radix sort and build (keys: the
+// emit's cell keys of rin; perm, skeys, sact: sorted-order scratch; svals, if given,
+// receives the source index of each sorted record)
+void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32_t ng,
+                        uint32_t* gcnt, uint32_t* gofs, uint32_t* gbsum, uint32_t* gfill,
+                        uint32_t* perm, uint32_t* gkey, uint32_t* gdest, const int4* rin,
+                        int4* rout, float4* pos4, uint32_t* skeys, uint32_t* svals,
+                        uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
+                        int sms, ProfHook* prof, cudaStream_t st);
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
                     const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
