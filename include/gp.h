@@ -151,7 +151,7 @@ typedef struct {
 /* Per-kernel timing collected with CUDA events when profiling is enabled. */
 typedef struct {
   char name[32];
-  int64_t launches;
+  int64_t launches;       /* kernel launches (some entries time several kernels)  */
   double total_ms;
   double units;           /* items processed (particles, keys, voxels) summed     */
   double bytes_per_unit;  /* algorithmic DRAM bytes per item                      */

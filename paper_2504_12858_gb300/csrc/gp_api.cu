@@ -281,6 +281,7 @@ struct Prof : ProfHook {
     cudaEvent_t a, b;
     int kid;
     double units;
+    int kernels;
   };
   std::vector<Ev> pending;
   std::vector<cudaEvent_t> pool;
@@ -304,11 +305,11 @@ struct Prof : ProfHook {
     cur = get();
     cudaEventRecord(cur, st);
   }
-  void end(int kid, double u) override {
+  void end(int kid, double u, int kernels = 1) override {
     if (!on || !cur) return;
     cudaEvent_t e = get();
     cudaEventRecord(e, st);
-    pending.push_back({cur, e, kid, u});
+    pending.push_back({cur, e, kid, u, kernels});
     cur = nullptr;
     if (pending.size() > 4096) flush();
   }
@@ -318,7 +319,7 @@ struct Prof : ProfHook {
     for (auto& p : pending) {
       float t = 0;
       cudaEventElapsedTime(&t, p.a, p.b);
-      launches[p.kid] += 1;
+      launches[p.kid] += p.kernels;
       ms[p.kid] += t;
       units[p.kid] += p.units;
       pool.push_back(p.a);
@@ -1096,14 +1097,14 @@ void batch_step_launches(gp_ctx* c) {
   c->prof.begin(K_EMIT);
   launch_emit(true, P, S, sorted, c->site_slot, cap, c->rec[c->cur], c->sb.keys[0],
               c->sb.vals[0], cap, c->C, c->R, nullptr, c->dst, st);
-  c->prof.end(K_EMIT, units);
+  c->prof.end(K_EMIT, units, 2);  // k_emit, k_emit_check
   if (c->n_nuclei > (int64_t)c->hst->nucleated || (c->graph_steps > 0 && c->n_nuclei > 0)) {
     launch_link_reached(true, P, c->R, &c->dst->linked, c->sms, st);
     c->prof.begin(K_NUCLEATE);
     launch_nucleate_batch(P, StepArgs{}, c->npos, c->nmeta, c->nstate, c->n_nuclei,
                           c->rec[c->cur], static_cast<uint64_t*>(c->sb.keys[0]), c->sb.vals[0],
                           cap, c->C, c->R, c->dst, c->sms, st);
-    c->prof.end(K_NUCLEATE, 1.0);
+    c->prof.end(K_NUCLEATE, 1.0, 2);  // k_nuc_test, k_nuc_activate
   }
   launch_finalize(c->dst, cap, true, st);
 }
@@ -1245,7 +1246,7 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       c->prof.begin(K_EMIT);
       launch_emit(batch, P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
                   c->sb.vals[0], c->L.cap, c->C, c->R, tpar, c->dst, c->st);
-      c->prof.end(K_EMIT, (double)n);
+      c->prof.end(K_EMIT, (double)n, 2);  // k_emit, k_emit_check
     }
     // pending sites: registered minus activated (re-nucleations of dormant seeds
     // count as nucleations too, so they are subtracted back)

@@ -608,7 +608,8 @@ enum KernelId : int {
 
 struct ProfHook {
   virtual void begin(int kid) = 0;
-  virtual void end(int kid, double units) = 0;
+  // kernels: how many kernel launches the timed segment holds
+  virtual void end(int kid, double units, int kernels = 1) = 0;
   virtual ~ProfHook() {}
 };
 

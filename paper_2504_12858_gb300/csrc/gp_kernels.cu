@@ -1643,6 +1643,7 @@ __global__ void __launch_bounds__(256) k_group_order(
 #pragma unroll 1
     for (int q = 0; q < kGroupCells / 32; ++q) {
       const uint32_t v = c[q * 32 + lane];
+      if (!__any_sync(0xffffffffu, v != 0u)) continue;  // no record in these 32 cells
       uint32_t inc = v;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -1962,14 +1963,14 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
   k_scan_blocks<<<(unsigned)nb, 256, 0, st>>>(gcnt, ng, gofs, gbsum);
   k_scan_sums<<<1, 256, 0, st>>>(gbsum, nb);
   k_group_scatter<<<g1, 256, 0, st>>>(keys, n, ng, gofs, gbsum, gfill, perm, gkey, &dst->err);
-  if (prof) prof->end(K_GROUP, (double)n);
+  if (prof) prof->end(K_GROUP, (double)n, 4);
   if (prof) prof->begin(K_BUILD);
   k_group_order<<<(unsigned)(sms * 8), 256, 0, st>>>(gkey, gofs, gbsum, ng, n, P.geo.seg0, gdest,
                                                      tab, stamp, dst);
   k_group_gather<<<blocks(n), 256, 0, st>>>(P, gkey, perm, gdest, n, rin, rout, pos4, skeys, svals,
                                             sact, dst);
   k_act_list<<<blocks(n, 256 * kBuildItems), 256, 0, st>>>(sact, n, act, dst);
-  if (prof) prof->end(K_BUILD, (double)n);
+  if (prof) prof->end(K_BUILD, (double)n, 3);
 }
 
 }  // namespace gp
