@@ -1636,7 +1636,15 @@ __global__ void __launch_bounds__(256) k_group_order(
 #pragma unroll
     for (int q = 0; q < kGroupCells / 32; ++q) c[q * 32 + lane] = 0;
     __syncwarp();
-    for (uint32_t i = s + lane; i < e; i += 32) atomicAdd(c + (__ldg(gkey + i) & (kGroupCells - 1)), 1u);
+    // four keys of the lane in flight at a time
+    for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
+      uint32_t k[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) k[u] = i0 + 32 * u < e ? __ldg(gkey + i0 + 32 * u) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + 32 * u < e) atomicAdd(c + (k[u] & (kGroupCells - 1)), 1u);
+    }
     __syncwarp();
     uint32_t run = s;
     const uint64_t sg0 = seg0 + ((uint64_t)g << (kGroupShift - kSegShift));
@@ -1675,8 +1683,14 @@ __global__ void __launch_bounds__(256) k_group_order(
       run += t31;
     }
     __syncwarp();
-    for (uint32_t i = s + lane; i < e; i += 32)
-      dest[i] = atomicAdd(c + (__ldg(gkey + i) & (kGroupCells - 1)), 1u);
+    for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
+      uint32_t k[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) k[u] = i0 + 32 * u < e ? __ldg(gkey + i0 + 32 * u) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + 32 * u < e) dest[i0 + 32 * u] = atomicAdd(c + (k[u] & (kGroupCells - 1)), 1u);
+    }
     __syncwarp();
   }
 }
