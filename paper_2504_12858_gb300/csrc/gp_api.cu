@@ -1087,8 +1087,8 @@ void batch_step_launches(gp_ctx* c) {
   const int w = radix_sort<uint64_t>(c->sb, cap, c->L.nbits, st);
   int4* sorted = c->rec[c->cur ^ 1];
   c->prof.begin(K_BUILD);
-  launch_build(true, P, c->sb.keys[w], c->sb.vals[w], c->rec[c->cur], sorted, c->pos4, c->cells,
-               0, cap, c->L.key_end, c->act, c->dst, st);
+  launch_build(P, static_cast<const uint64_t*>(c->sb.keys[w]), c->sb.vals[w], c->rec[c->cur], sorted,
+               c->pos4, c->cells, cap, c->L.key_end, c->act, c->dst, st);
   c->prof.end(K_BUILD, units);
   c->prof.begin(K_ADVANCE);
   launch_advance(true, P, S, sorted, c->pos4, c->sb.keys[w], c->cells, 0, cap, c->act, c->C,

@@ -1767,17 +1767,12 @@ void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* 
     k_keys<false, uint32_t><<<blocks(n), 256, 0, st>>>(P, rec, n, (uint32_t*)keys, vals);
 }
 
-void launch_build(bool batch, const Params& P, const void* skeys, const uint32_t* svals,
-                  const int4* rin, int4* rout, float4* pos4, uint4* tab, uint32_t stamp,
-                  int64_t n, uint64_t key_end, uint32_t* act, DevStats* dst, cudaStream_t st) {
+void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals, const int4* rin,
+                  int4* rout, float4* pos4, uint4* tab, int64_t n, uint64_t key_end, uint32_t* act,
+                  DevStats* dst, cudaStream_t st) {
   if (n <= 0) return;
-  if (batch)
-    k_build<true, uint64_t><<<persistent(n, 256 * kBuildItems, P.launch.build_ctas), 256, 0, st>>>(
-        P, (const uint64_t*)skeys, svals, rin, rout, pos4, tab, stamp, n, key_end, act, dst);
-  else
-    k_build<false, uint32_t><<<blocks(n, 256 * kBuildItems), 256, 0, st>>>(P, (const uint32_t*)skeys, svals, rin,
-                                                        rout, pos4, tab, stamp, n,
-                                                        (uint32_t)key_end, act, dst);
+  k_build<true, uint64_t><<<persistent(n, 256 * kBuildItems, P.launch.build_ctas), 256, 0, st>>>(
+      P, skeys, svals, rin, rout, pos4, tab, 0, n, key_end, act, dst);
 }
 
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,

@@ -9,12 +9,12 @@ namespace gp {
 // (uint32 cell keys)
 void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* keys,
                  uint32_t* vals, cudaStream_t st);
-// the build lists the sorted indices of the ACTIVE particles in act (count in
-// dst->n_act, which must be zero before the build); the advance runs over that list.
-// A batch reads its counts, stamp and step from dst and uses persistent grids.
-void launch_build(bool batch, const Params& P, const void* skeys, const uint32_t* svals,
-                  const int4* rin, int4* rout, float4* pos4, uint4* tab, uint32_t stamp,
-                  int64_t n, uint64_t key_end, uint32_t* act, DevStats* dst, cudaStream_t st);
+// batch: the build after the radix sort; it lists the sorted indices of the ACTIVE
+// particles in act (count in dst->n_act, which must be zero before the build), reads its
+// counts and stamp from dst and uses a persistent grid.  The advance runs over that list.
+void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals, const int4* rin,
+                  int4* rout, float4* pos4, uint4* tab, int64_t n, uint64_t key_end, uint32_t* act,
+                  DevStats* dst, cudaStream_t st);
 // one run: the records grouped by cell in place of the radix sort and build (keys: the
 // emit's cell keys of rin; perm, skeys, sact: sorted-order scratch; svals, if given,
 // receives the source index of each sorted record)
