@@ -291,8 +291,8 @@ gp_status gp_profile_read(gp_ctx* ctx, int32_t max, gp_kernel_prof* out, int32_t
 /* ---- adjoint of the advance ---------------------------------------------------- */
 
 /* Starts recording the adjoint tape: the next steps (at most gp_memory.tape_steps)
- * store the particle records before the advance, the order of the spatial sort,
- * the state after the contact search and the parent of every particle of the
+ * store the particle records before the advance, the permutation that ordered them
+ * by cell, the state after the contact search and the parent of every particle of the
  * following step.  Recording restarts at every call.  Needs an analytic field. */
 gp_status gp_tape_begin(gp_ctx* ctx);
 
