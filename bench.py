@@ -147,10 +147,17 @@ def measured_peak():
 
 
 def kernel_sources_digest():
+    """Digest of the CUDA sources with comments and blank space removed, so that the
+    committed ncu figures stay valid across edits that change no code."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_12858_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(f.encode())
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

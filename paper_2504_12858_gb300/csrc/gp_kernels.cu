@@ -3,9 +3,12 @@
 // Per timestep (all on the context stream):
 //   k_keys      cell keys of the store (only after host-side edits; the emit
 //               kernel writes them otherwise)
-//   radix sort  (key, store index), gp_sort.cu
-//   k_build     gather the store into cell order, positions + grain as float4,
-//               segment table of the cell runs, stamped with the build number
+//   ordering    one run: k_group_count, k_group_scatter, k_group_order and
+//               k_group_gather group the records by tile of the cell order and order
+//               them by cell inside each tile; a batch: radix sort of (key, store
+//               index), gp_sort.cu, then k_build.  Either way the store lands in cell
+//               order with positions + grain as float4, the segment table of the cell
+//               runs (stamped with the build number) and the list of ACTIVE particles
 //   k_advance   contact freeze over the 27 neighbour cells, thermal sample,
 //               growth law, explicit Euler advance, spawn claims
 //   k_emit      claim resolution, reached sites, domain clip, compaction of the
