@@ -87,3 +87,30 @@ def test_ensemble_sharding_covers_every_run_once_and_balances_work():
         loads = [sum(costs[i] for i in p) for p in parts]
         # greedy LPT: no rank exceeds the mean by more than the largest single run
         assert max(loads) <= sum(costs) / world + max(costs) + 1e-9
+
+
+def test_kernel_digest_ignores_comments_and_catches_code(tmp_path, monkeypatch):
+    """The committed ncu figures are matched to the kernel sources by a digest that
+    comment and blank-space edits leave unchanged and any code edit changes; on a
+    mismatch the bench reports no traffic."""
+    sys.path.insert(0, ROOT)
+    import json
+    import shutil
+    import bench
+    src = os.path.join(ROOT, "paper_2504_12858_gb300", "csrc")
+    root = tmp_path / "r"
+    shutil.copytree(src, root / "paper_2504_12858_gb300" / "csrc")
+    (root / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    d0 = bench.kernel_sources_digest()
+    f = root / "paper_2504_12858_gb300" / "csrc" / "gp_sort.cu"
+    text = f.read_text()
+    f.write_text("// a new comment line\n" + text.replace("\n", "\n\n", 3) + "\n/* block */\n")
+    assert bench.kernel_sources_digest() == d0
+    json.dump({"sources_digest": d0, "kernels": {"advance": {"dram_bytes_per_unit": 7.0}},
+               "step": {"dram_bytes_per_particle_step": 9.0}},
+              open(root / "profiles" / "ncu_traffic.json", "w"))
+    assert bench.ncu_traffic("advance") == 7.0 and bench.ncu_step_traffic() == 9.0
+    f.write_text(text.replace("kSortThreads", "kSortThreads ", 1).replace("return 0;", "return 1;", 1))
+    assert bench.kernel_sources_digest() != d0
+    assert bench.ncu_traffic("advance") is None and bench.ncu_step_traffic() is None
