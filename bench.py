@@ -509,14 +509,15 @@ def run_native(args, rank, world, local_rank):
     roof = None
     if dom:
         achieved = dom["units"] * dom["bytes_per_unit"] / (dom["total_ms"] / 1e3) / 1e9
-        per_launch_units = dom["units"] / max(dom["launches"], 1)
+        # each timed entry runs once per step (some entries hold several kernels)
+        per_launch_units = dom["units"] / max(args.steps, 1)
         tb = ncu_traffic(dom["name"])
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tb is None else tb * per_launch_units,
                 "issue_slots_busy": ncu_issue(dom["name"]),
                 "algorithmic_bytes_per_launch": dom["bytes_per_unit"] * per_launch_units,
-                "avg_launch_ms": dom["total_ms"] / max(dom["launches"], 1)}
+                "avg_launch_ms": dom["total_ms"] / max(args.steps, 1)}
     # the whole step against the copy bandwidth: measured DRAM bytes per particle-step
     # (one-pass ncu capture of the default run) and the algorithmic 48 B
     default_run = (args.grains, args.n0, tuple(args.plate), args.warmup, args.steps) == \
