@@ -1563,7 +1563,7 @@ inline unsigned persistent(int64_t n_max, int per_cta, int ctas_total) {
 //                    the group's cell-table entries and every record's sorted position
 //   k_group_gather   one thread per record: record, position, key and ACTIVE flag to
 //                    the sorted position; k_act_list then lists the ACTIVE ones
-// On the 4 x 2 x 1 mm weld plate this takes 1.1 + 4.7 ms per step against 5.7 + 2.5 ms
+// On the 4 x 2 x 1 mm weld plate this takes 1.1 + 3.2 ms per step against 5.7 + 2.5 ms
 // for the histogram, four onesweep passes and the build.
 // ---------------------------------------------------------------------------------
 
@@ -1620,24 +1620,33 @@ __global__ void __launch_bounds__(256) k_group_scatter(const uint32_t* __restric
   }
 }
 
+// shared-memory slot of a group's cell: lane l owns cells 32 l .. 32 l + 31 (its two
+// segments); cell 32 l + m sits in row m at column l ^ m, so that the 32 lanes reading
+// their m-th cells, and consecutive cells of one row of the group, fall in different banks
+static_assert(kGroupCells == 1024, "one lane per 32 cells of a group");
+__device__ __forceinline__ uint32_t group_slot(uint32_t key) {
+  const uint32_t ci = key & (kGroupCells - 1), m = ci & 31u;
+  return (m << 5) | ((ci >> 5) ^ m);
+}
+
 // One warp per group of kGroupCells cells (groups strided over the warps of the grid).
 // s_c holds the group's cell counts, then the sorted position of each cell's next
 // record, which the last pass advances to give every grouped record its sorted
-// position (dest).  The offsets are scanned 32 cells (two segments) per round,
-// conflict-free, and each round writes its two cell-table entries.
-__global__ void __launch_bounds__(256) k_group_order(
+// position (dest).  Each lane sums its 32 cells, one warp scan gives the lanes' first
+// positions, and each lane then writes its cells' offsets and its two cell-table entries.
+__global__ void __launch_bounds__(256, 6) k_group_order(
     const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ ofs,
     const uint32_t* __restrict__ bsum, uint32_t ng, int64_t n, uint64_t seg0,
     uint32_t* __restrict__ dest, uint4* __restrict__ tab, uint32_t stamp, DevStats* st) {
-  __shared__ uint32_t s_c[8][kGroupCells];
+  __shared__ uint4 s_c4[8][kGroupCells / 4];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t* c = s_c[w];
+  uint32_t* c = reinterpret_cast<uint32_t*>(s_c4[w]);
   for (int64_t g = (int64_t)blockIdx.x * 8 + w; g < (int64_t)ng; g += (int64_t)gridDim.x * 8) {
     const uint32_t s = tile_start(ofs, bsum, g, ng, n);
     const uint32_t e = tile_start(ofs, bsum, g + 1, ng, n);
     if (s >= e) continue;  // warp-uniform
 #pragma unroll
-    for (int q = 0; q < kGroupCells / 32; ++q) c[q * 32 + lane] = 0;
+    for (int q = 0; q < kGroupCells / 128; ++q) s_c4[w][q * 32 + lane] = make_uint4(0, 0, 0, 0);
     __syncwarp();
     // four keys of the lane in flight at a time
     for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
@@ -1646,44 +1655,48 @@ __global__ void __launch_bounds__(256) k_group_order(
       for (int u = 0; u < 4; ++u) k[u] = i0 + 32 * u < e ? __ldg(gkey + i0 + 32 * u) : 0u;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (i0 + 32 * u < e) atomicAdd(c + (k[u] & (kGroupCells - 1)), 1u);
+        if (i0 + 32 * u < e) atomicAdd(c + group_slot(k[u]), 1u);
     }
     __syncwarp();
-    uint32_t run = s;
-    const uint64_t sg0 = seg0 + ((uint64_t)g << (kGroupShift - kSegShift));
-#pragma unroll 1
-    for (int q = 0; q < kGroupCells / 32; ++q) {
-      const uint32_t v = c[q * 32 + lane];
-      if (!__any_sync(0xffffffffu, v != 0u)) continue;  // no record in these 32 cells
-      uint32_t inc = v;
+    uint32_t tot = 0;
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += y;
-      }
-      c[q * 32 + lane] = run + inc - v;
-      const uint32_t t15 = __shfl_sync(0xffffffffu, inc, 15);
-      const uint32_t t31 = __shfl_sync(0xffffffffu, inc, 31);
-      // 4-bit counts saturated at 15: lanes 0-7 / 8-15 give the z / w word of the
-      // round's first segment, lanes 16-23 / 24-31 those of its second
-      uint32_t nb = (v < 15u ? v : 15u) << (4 * (lane & 7));
-      nb |= __shfl_xor_sync(0xffffffffu, nb, 1);
-      nb |= __shfl_xor_sync(0xffffffffu, nb, 2);
-      nb |= __shfl_xor_sync(0xffffffffu, nb, 4);
-      const uint32_t nbw = __shfl_sync(0xffffffffu, nb, (lane + 8) & 31);
-      const uint32_t sat = __ballot_sync(0xffffffffu, v >= 15u);
-      if (lane == 0 || lane == 16) {
-        const uint32_t cnt = lane == 0 ? t15 : t31 - t15;
+    for (int m = 0; m < 32; ++m) tot += c[(m << 5) | (lane ^ m)];
+    uint32_t inc = tot;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += y;
+    }
+    if (tot) {
+      // cells 0-7 / 8-15 of a segment give its z / w word: 4-bit counts saturated at 15
+      uint32_t run = s + inc - tot;
+      const uint64_t sg = seg0 + ((uint64_t)g << (kGroupShift - kSegShift)) + 2 * lane;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t start = run;
+        uint32_t nb[2];
+        bool sat = false;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          nb[j] = 0u;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int m = 16 * h + 8 * j + t;
+            uint32_t* p = c + ((m << 5) | (lane ^ m));
+            const uint32_t v = *p;
+            *p = run;
+            run += v;
+            nb[j] |= (v < 15u ? v : 15u) << (4 * t);
+            sat |= v >= 15u;
+          }
+        }
+        const uint32_t cnt = run - start;
         if (cnt) {
           if (cnt >= kSegMaxCount) atomicOr(&st->err, ERR_CELL_OVERFLOW);
           const uint32_t cc = cnt < kSegMaxCount ? cnt : kSegMaxCount;
-          const bool sf = lane == 0 ? (sat & 0xffffu) != 0 : (sat >> 16) != 0;
-          tab[sg0 + 2 * q + (lane >> 4)] =
-              make_uint4(run + (lane == 0 ? 0u : t15), (stamp << 16) | (sf ? 0x8000u : 0u) | cc,
-                         nb, nbw);
+          tab[sg + h] = make_uint4(start, (stamp << 16) | (sat ? 0x8000u : 0u) | cc, nb[0], nb[1]);
         }
       }
-      run += t31;
     }
     __syncwarp();
     for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
@@ -1692,7 +1705,7 @@ __global__ void __launch_bounds__(256) k_group_order(
       for (int u = 0; u < 4; ++u) k[u] = i0 + 32 * u < e ? __ldg(gkey + i0 + 32 * u) : 0u;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (i0 + 32 * u < e) dest[i0 + 32 * u] = atomicAdd(c + (k[u] & (kGroupCells - 1)), 1u);
+        if (i0 + 32 * u < e) dest[i0 + 32 * u] = atomicAdd(c + group_slot(k[u]), 1u);
     }
     __syncwarp();
   }
