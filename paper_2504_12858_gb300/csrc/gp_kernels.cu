@@ -1990,7 +1990,8 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
   k_group_scatter<<<g1, 256, 0, st>>>(keys, n, ng, gofs, gbsum, gfill, perm, gkey, &dst->err);
   if (prof) prof->end(K_GROUP, (double)n, 4);
   if (prof) prof->begin(K_BUILD);
-  k_group_order<<<(unsigned)(sms * 8), 256, 0, st>>>(gkey, gofs, gbsum, ng, n, P.geo.seg0, gdest,
+  // one wave: 32 KB of shared memory per CTA leaves room for six CTAs per SM
+  k_group_order<<<(unsigned)(sms * 6), 256, 0, st>>>(gkey, gofs, gbsum, ng, n, P.geo.seg0, gdest,
                                                      tab, stamp, dst);
   k_group_gather<<<blocks(n), 256, 0, st>>>(P, gkey, perm, gdest, n, rin, rout, pos4, skeys, svals,
                                             sact, dst);
