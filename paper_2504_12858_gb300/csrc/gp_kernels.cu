@@ -1621,12 +1621,14 @@ __global__ void __launch_bounds__(256) k_group_scatter(const uint32_t* __restric
 }
 
 // shared-memory slot of a group's cell: lane l owns cells 32 l .. 32 l + 31 (its two
-// segments); cell 32 l + m sits in row m at column l ^ m, so that the 32 lanes reading
-// their m-th cells, and consecutive cells of one row of the group, fall in different banks
+// segments), stored contiguously in a row of kGroupRow words, so that the lane reads and
+// writes them as eight 16-byte vectors; with rows of 36 words the eight lanes of each
+// quarter warp fall in different banks
 static_assert(kGroupCells == 1024, "one lane per 32 cells of a group");
+constexpr int kGroupRow = 36;
 __device__ __forceinline__ uint32_t group_slot(uint32_t key) {
-  const uint32_t ci = key & (kGroupCells - 1), m = ci & 31u;
-  return (m << 5) | ((ci >> 5) ^ m);
+  const uint32_t ci = key & (kGroupCells - 1);
+  return (ci >> 5) * kGroupRow + (ci & 31u);
 }
 
 // One warp per group of kGroupCells cells (groups strided over the warps of the grid).
@@ -1638,15 +1640,16 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ ofs,
     const uint32_t* __restrict__ bsum, uint32_t ng, int64_t n, uint64_t seg0,
     uint32_t* __restrict__ dest, uint4* __restrict__ tab, uint32_t stamp, DevStats* st) {
-  __shared__ uint4 s_c4[8][kGroupCells / 4];
+  __shared__ uint4 s_c4[8][32 * kGroupRow / 4];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* c = reinterpret_cast<uint32_t*>(s_c4[w]);
+  uint4* row = s_c4[w] + lane * (kGroupRow / 4);  // the lane's 32 cells
   for (int64_t g = (int64_t)blockIdx.x * 8 + w; g < (int64_t)ng; g += (int64_t)gridDim.x * 8) {
     const uint32_t s = tile_start(ofs, bsum, g, ng, n);
     const uint32_t e = tile_start(ofs, bsum, g + 1, ng, n);
     if (s >= e) continue;  // warp-uniform
 #pragma unroll
-    for (int q = 0; q < kGroupCells / 128; ++q) s_c4[w][q * 32 + lane] = make_uint4(0, 0, 0, 0);
+    for (int q = 0; q < kGroupRow / 4; ++q) s_c4[w][q * 32 + lane] = make_uint4(0, 0, 0, 0);
     __syncwarp();
     // four keys of the lane in flight at a time
     for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
@@ -1660,7 +1663,10 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     __syncwarp();
     uint32_t tot = 0;
 #pragma unroll
-    for (int m = 0; m < 32; ++m) tot += c[(m << 5) | (lane ^ m)];
+    for (int q = 0; q < 8; ++q) {
+      const uint4 v = row[q];
+      tot += (v.x + v.y) + (v.z + v.w);
+    }
     uint32_t inc = tot;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -1674,22 +1680,31 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
         const uint32_t start = run;
-        uint32_t nb[2];
-        bool sat = false;
+        uint32_t nb[2], vmax = 0u;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           nb[j] = 0u;
 #pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int m = 16 * h + 8 * j + t;
-            uint32_t* p = c + ((m << 5) | (lane ^ m));
-            const uint32_t v = *p;
-            *p = run;
-            run += v;
-            nb[j] |= (v < 15u ? v : 15u) << (4 * t);
-            sat |= v >= 15u;
+          for (int t = 0; t < 2; ++t) {
+            // cells 8 j + 4 t .. 8 j + 4 t + 3 of the segment
+            const int q = 4 * h + 2 * j + t;
+            const uint4 v = row[q];
+            uint4 o;
+            o.x = run;
+            run += v.x;
+            o.y = run;
+            run += v.y;
+            o.z = run;
+            run += v.z;
+            o.w = run;
+            run += v.w;
+            row[q] = o;
+            nb[j] |= (min(v.x, 15u) | (min(v.y, 15u) << 4) | (min(v.z, 15u) << 8) |
+                      (min(v.w, 15u) << 12)) << (16 * t);
+            vmax = max(vmax, max(max(v.x, v.y), max(v.z, v.w)));
           }
         }
+        const bool sat = vmax >= 15u;
         const uint32_t cnt = run - start;
         if (cnt) {
           if (cnt >= kSegMaxCount) atomicOr(&st->err, ERR_CELL_OVERFLOW);
