@@ -72,6 +72,7 @@ def lib():
         "go_set_thermal_grid": (None, [vp, P_F, P_I32, P_D, P_D, P_D]),
         "go_set_solute_grid": (None, [vp, P_F, P_I32, P_D, P_D, P_D, d, d]),
         "go_set_melting": (None, [vp, C.c_int]),
+        "go_set_reach_tol": (None, [vp, d]),
         "go_set_periodic": (None, [vp, C.c_int]),
         "go_add_grains": (i64, [vp, i64, P_D, P_D, C.c_int]),
         "go_seed_shell": (None, [vp, i64, P_I32, i32, d, C.c_int]),
@@ -163,6 +164,10 @@ class Oracle:
     def set_melting(self, on=True):
         """Melting walk-back pass at the start of every step (Sec. 2.1.3)."""
         lib().go_set_melting(self._p, 1 if on else 0)
+
+    def set_reach_tol(self, tol):
+        """Tolerance of the reached-target test (default 2^-20 of a spacing)."""
+        lib().go_set_reach_tol(self._p, float(tol))
 
     def add_grains(self, pos, quat, nucleate=True) -> int:
         pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)

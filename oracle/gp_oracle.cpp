@@ -10,7 +10,7 @@
 // It is written for a reader checking it against the paper: slow, sequential,
 // standard containers, no blocking or fusion.  Each function names the passage
 // it follows.  Where the paper is silent, the reading taken is stated in the
-// comment (readings r1..r14 are listed in the design notes of the repository).
+// comment beside the code that implements it.
 //
 // Notation (paper Sec. 2.1.2): a grain g has a nucleus c_g and a crystal->lab
 // rotation R_g; its six <100> growth directions are d_k = R_g e_k with
@@ -41,8 +41,10 @@ namespace {
 
 enum State : int { ACTIVE = 0, FROZEN = 1, REMOVED = 2 };
 
-// progress tolerance of the reached-target test (reading r6)
-constexpr double kReachTol = 1.0 / 1048576.0;
+// progress tolerance of the reached-target test (reading r6): 2^-20 by default,
+// settable (go_set_reach_tol) so that a pin can show it changes nothing on steps
+// that are not commensurate with h
+constexpr double kReachTolDefault = 1.0 / 1048576.0;
 
 inline int axis_of(int k) { return k >> 1; }
 inline int sign_of(int k) { return (k & 1) ? -1 : +1; }
@@ -134,6 +136,7 @@ struct Sim {
   int gn[3] = {0, 0, 0};
   double gorigin[3] = {0, 0, 0}, gspacing[3] = {1, 1, 1}, gvel[3] = {0, 0, 0};
   int64_t step = 0;
+  double reach_tol = kReachTolDefault;
   bool melting = false;  // melting walk-back (Sec. 2.1.3), reading r17
   std::vector<Grain> grains;
   std::vector<Particle> parts;
@@ -499,7 +502,7 @@ struct Sim {
         ++st.n_clamped;
       }
       double e = p.ell + dl;
-      if (e >= 1.0 - kReachTol) {
+      if (e >= 1.0 - reach_tol) {
         cross[i] = 1;
         carry[i] = e > 1.0 ? e - 1.0 : 0.0;
       } else {
@@ -952,6 +955,10 @@ void go_get_stats(void* s, int64_t* out) {
 // Axes with periodic conditions: bit a set for axis a (reading r18).  A periodic
 // axis needs at least three cells of the contact search along it.
 void go_set_periodic(void* s, int axes) { ((Sim*)s)->periodic = axes & 7; }
+
+// Tolerance of the reached-target test (reading r6): a particle whose progress
+// reaches 1 - tol counts as having reached its target (carry max(0, ell - 1)).
+void go_set_reach_tol(void* s, double tol) { ((Sim*)s)->reach_tol = tol; }
 
 // Enables (1) or disables (0) the melting walk-back pass (reading r17).
 void go_set_melting(void* s, int on) { ((Sim*)s)->melting = on != 0; }

@@ -4,9 +4,11 @@ Each test checks the oracle against something other than itself: closed forms
 (the isotropic octahedron of Sec. 2.1.2 / Fig. 1, lattice counting), an
 independent ODE integration (the single grain in a gradient of Sec. 3.1),
 exhaustive searches (contacts, grain map), exact interpolation of linear fields,
-or invariants (no interpenetration, hash ordering).  A plausible mistake in the
-oracle (dropped term, wrong sign, wrong index, transposed rotation) fails at
-least one of them.
+or invariants (no interpenetration, hash ordering).  The orientation convention
+is pinned separately against rotation matrices written out from their
+definitions and against the quaternion sandwich product.  A plausible mistake in
+the oracle (dropped term, wrong sign, wrong index, transposed or wrong-handed
+rotation) fails at least one of them.
 """
 import math
 
@@ -55,6 +57,163 @@ def test_outer_directions_match_volume_increase():
 def test_outer_counts_by_site_class(site, count):
     # nucleus 6; fewer than six afterwards (Sec. 2.1.2): vertex 5, edge 4, face 3
     assert sum(oracle.is_outer(site, k) for k in range(6)) == count
+
+
+# ----------------------------------------------------------------------------------
+# Orientation convention (reading r10): a unit quaternion q = (w, x, y, z) maps the
+# crystal frame to the lab frame, d_k = R(q) e_k, with the growth directions along the
+# rotated <100> axes (Sec. 2.1.2).  Pinned against the elementary rotation matrices
+# written out from their definitions, the Bunge Z-X-Z product of Sec. 3.1's Euler
+# angles, and the quaternion sandwich product q (0, v) q*.
+# ----------------------------------------------------------------------------------
+def _rx(t):
+    c, s = math.cos(t), math.sin(t)
+    return np.array([[1.0, 0.0, 0.0], [0.0, c, -s], [0.0, s, c]])
+
+
+def _ry(t):
+    c, s = math.cos(t), math.sin(t)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def _rz(t):
+    c, s = math.cos(t), math.sin(t)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def _hamilton(p, q):
+    w1, x1, y1, z1 = p
+    w2, x2, y2, z2 = q
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
+                     w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 + y1 * w2 + z1 * x2 - x1 * z2,
+                     w1 * z2 + z1 * w2 + x1 * y2 - y1 * x2])
+
+
+def _oracle_R(quats):
+    o = Oracle((0, 0, 0), (1e-4,) * 3, 2e-6, 1e-3, (1e-5,), (2.0,), 1000.0)
+    quats = np.asarray(quats, np.float64).reshape(-1, 4)
+    o.add_grains(np.full((len(quats), 3), 5e-5), quats, nucleate=False)
+    return [o.grain(i)[1] for i in range(len(quats))]
+
+
+@pytest.mark.parametrize("deg", [90.0, 30.0, -47.5, 180.0])
+def test_rotation_about_each_axis_is_the_elementary_matrix(deg):
+    t = math.radians(deg)
+    c2, s2 = math.cos(t / 2), math.sin(t / 2)
+    Rx, Ry, Rz = _oracle_R([[c2, s2, 0, 0], [c2, 0, s2, 0], [c2, 0, 0, s2]])
+    assert np.allclose(Rx, _rx(t), atol=1e-15)
+    assert np.allclose(Ry, _ry(t), atol=1e-15)
+    assert np.allclose(Rz, _rz(t), atol=1e-15)
+    # the crystal x axis turned about z lands at (cos t, sin t, 0): counter-clockwise
+    assert np.allclose(Rz @ [1.0, 0.0, 0.0], [math.cos(t), math.sin(t), 0.0], atol=1e-15)
+
+
+def test_rotation_of_bunge_euler_angles_is_the_zxz_product():
+    # Sec. 3.1 gives the grain orientation as Euler angles (20, 20, 20) degrees; under
+    # the Bunge convention crystal -> lab is Rz(psi) Rx(theta) Rz(phi)
+    for ang in [(20.0, 20.0, 20.0), (4.0, 0.0, 0.0), (130.0, 75.0, -20.0)]:
+        (R,) = _oracle_R(inputs.euler_zxz_to_quaternion(*ang))
+        psi, th, phi = (math.radians(a) for a in ang)
+        assert np.allclose(R, _rz(psi) @ _rx(th) @ _rz(phi), atol=1e-14)
+
+
+def test_rotation_equals_quaternion_sandwich_and_is_proper():
+    g = inputs.rng(21)
+    q = inputs.shoemake_quaternions(40, g)
+    scale = g.uniform(0.2, 5.0, size=(40, 1))        # the oracle normalises its input
+    Rs = _oracle_R(q * scale)
+    for qi, R in zip(q, Rs):
+        qc = qi * np.array([1.0, -1.0, -1.0, -1.0])
+        for v in np.eye(3):
+            w = _hamilton(_hamilton(qi, np.concatenate([[0.0], v])), qc)
+            assert abs(w[0]) < 1e-15
+            assert np.allclose(R @ v, w[1:], atol=1e-14)
+        assert np.allclose(R.T @ R, np.eye(3), atol=1e-14)
+        assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-14)
+
+
+def test_grown_tips_follow_the_closed_form_rotation():
+    # 90 degrees about z: the crystal +x arm grows along lab +y and the crystal +y arm
+    # along lab -x; the vertices sit at c + v t R e_a with R written out, not read back
+    dT, h = 5.0, 2e-6
+    v = 1e-5 * dT ** 2
+    dt = 0.2718281828 * h / v
+    c = np.array([60e-6, 60e-6, 60e-6])
+    t = math.radians(90.0)
+    for q, R in [((math.cos(t / 2), 0.0, 0.0, math.sin(t / 2)), _rz(t)),
+                 (inputs.euler_zxz_to_quaternion(20.0, 20.0, 20.0),
+                  _rz(math.radians(20)) @ _rx(math.radians(20)) @ _rz(math.radians(20)))]:
+        T_L = 1000.0
+        o = Oracle((0, 0, 0), (120e-6,) * 3, h, dt, (1e-5,), (2.0,), T_L)
+        o.set_thermal_analytic(T_L - dT, (0, 0, 0), (0, 0, 0), 0.0)
+        o.add_grains(c[None], np.asarray(q)[None])
+        n = 50
+        o.step(n)
+        p = o.particles()
+        for k in range(6):
+            ax, sg = k // 2, (1 if k % 2 == 0 else -1)
+            others = [a for a in range(3) if a != ax]
+            m = ((p["dir"] == k) & (p["site"][:, ax] * sg >= 0)
+                 & (p["site"][:, others] == 0).all(axis=1))
+            assert m.sum() == 1
+            assert np.allclose(p["x"][m][0], c + v * n * dt * sg * R[:, ax], rtol=0, atol=1e-15)
+        if R is not None and np.allclose(R, _rz(t)):
+            tip = p["x"][(p["dir"] == 0) & (p["site"][:, 1:] == 0).all(axis=1)
+                         & (p["site"][:, 0] >= 0)][0]
+            assert tip[1] - c[1] == pytest.approx(v * n * dt, rel=1e-12)
+            assert abs(tip[0] - c[0]) < 1e-15
+
+
+# ----------------------------------------------------------------------------------
+# Reached-target tolerance (reading r6): a target counts as reached at progress
+# 1 - 2^-20, so a step commensurate with h (v dt = h/4) spawns on the same step in
+# binary32 and FP64.  The snap moves a particle by at most 2^-20 h, and only when
+# its progress lands within 2^-20 of a full spacing; on steps that are not
+# commensurate with h the tolerance changes nothing.
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("ratio,field", [(0.2718281828, "uniform"), (0.41421356237, "uniform"),
+                                         (0.0, "gradient")])
+def test_reach_tolerance_changes_nothing_off_commensurate_steps(ratio, field):
+    def run(tol):
+        if field == "uniform":
+            dT, h = 5.0, 2e-6
+            v = 1e-5 * dT ** 2
+            o = _uniform_sim(dT, dt=ratio * h / v, half=60e-6)
+            n = 90
+            prog = np.arange(1, n + 1) * ratio
+            assert np.min(np.abs(prog - np.round(prog))[prog > 0.5]) > 1e-4
+        else:   # the single grain in the Sec. 3.1 gradient: progress varies continuously
+            a, b, dT0, Tdot, G, h, T_L = 1e-4, 2.0, 2.0, -0.1, 250.0, 200e-6, 1000.0
+            c = np.array([4e-3] * 3)
+            o = Oracle((0, 0, 0), (8e-3,) * 3, h, 0.01, (a,), (b,), T_L)
+            o.set_thermal_analytic(T_L - dT0, (0.0, 0.0, G), c, Tdot)
+            o.add_grains(c[None], inputs.euler_zxz_to_quaternion(20.0, 20.0, 20.0)[None])
+            n = 300
+        if tol is not None:
+            o.set_reach_tol(tol)
+        o.step(n)
+        return o.particles(), o.stats(), o.reached()
+    p0, s0, r0 = run(None)
+    p1, s1, r1 = run(0.0)
+    assert s0 == s1
+    for k in p0:
+        assert np.array_equal(p0[k], p1[k]), k
+    assert np.array_equal(r0[0], r1[0]) and np.array_equal(r0[1], r1[1])
+    assert s0["reached"] > 100
+
+
+def test_reach_tolerance_snap_is_bounded_on_commensurate_steps():
+    # v dt = h/4 exactly: with the tolerance the spawns come every fourth step; without
+    # it the FP64 sum of four quarters may stop short of 1 and lose a step.  Either
+    # way the positions of the particles both runs share differ by at most 2^-20 h
+    # per snap taken.
+    dT, h = 5.0, 2e-6
+    v = 1e-5 * dT ** 2
+    o = _uniform_sim(dT, dt=0.25 * h / v, half=60e-6)
+    o.step(40)
+    p = o.particles()
+    assert np.abs(p["ell"] - np.round(p["ell"] * 4) / 4).max() <= 40 * 2.0 ** -20
 
 
 # ----------------------------------------------------------------------------------
