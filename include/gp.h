@@ -407,6 +407,21 @@ gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state
                      int64_t pair_cap, int64_t* n_pairs, void* workspace,
                      size_t workspace_bytes, void* cuda_stream);
 
+/* ---- failure detection --------------------------------------------------------- */
+
+/* Self-test of the library's bounded device waits.  Every wait of the library gives
+ * up after a limit of polls, sets a sticky device error bit and lets the kernel
+ * return, so that a stalled producer shows up as GP_ERR_TIMEOUT on the host instead
+ * of a hung GPU.  which = 0: the decoupled look-back of a radix-sort pass, waiting
+ * for a preceding tile's status word; which = 1: a claim-table insert, waiting for
+ * another warp to publish a block's pool slot.  The call allocates a 2 KB device
+ * buffer, prepares in it a word that nothing ever publishes, runs that wait in one
+ * thread with a limit of spin_limit polls (1 .. 4194304, the limit of the production
+ * waits) and frees the buffer.  It returns GP_ERR_TIMEOUT when the wait gave up, as
+ * it must; the device stays usable.  GP_ERR_ARG for other which or spin_limit.
+ * The paper has no counterpart of this call (it describes no software). */
+gp_status gp_selftest_wait(int32_t which, uint32_t spin_limit, void* cuda_stream);
+
 /* ---- stand-alone hash without allocation ------------------------------------- */
 
 /* Largest point count gp_hash_build_static accepts. */
@@ -419,9 +434,9 @@ gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state
  * budgeted by that code's own allocator, or a caller that must not pay the
  * device synchronisation of cudaMalloc.  The paper has no counterpart of this
  * call; it exists for such callers only.
- * Scratch comes from one static device array of the library (about 6.5 MB),
- * which every GPU that loads the library keeps until the process exits.  The
- * call allocates no device memory.
+ * Scratch comes from one static device array of the library (6,390,784 bytes,
+ * about 6.4 MB), which every GPU that loads the library keeps until the process
+ * exits.  The call allocates no device memory.
  *  - n > GP_STATIC_SCRATCH_MAX_POINTS returns GP_ERR_CAPACITY (nothing runs).
  *  - All calls on a device share the array and find what the previous call left
  *    there; the call clears the counters that must start at zero.  Calls whose

@@ -18,11 +18,6 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// cell edge: contact radius h enlarged by 2^-9 so that binary32 rounding of the
-// cell coordinate can never separate two points closer than h by more than one
-// cell (up to 4096 cells per axis)
-inline double cell_edge(double h) { return h * (1.0 + 1.0 / 512.0); }
-
 // hash geometry of one run and its place in the context-wide key, cell-table and
 // reached-head ranges
 struct RunLayout {
@@ -55,18 +50,7 @@ struct Layout {
 };
 
 bool cells_of(const gp_domain* d, double h, int nc[3], uint64_t* ncells) {
-  const double e = cell_edge(h);
-  uint64_t tot = 1;
-  for (int a = 0; a < 3; ++a) {
-    double ext = d->hi[a] - d->lo[a];
-    if (!(ext >= 0) || !std::isfinite(ext)) return false;
-    double v = std::ceil(ext / e);
-    if (v > 4096.0) return false;
-    nc[a] = v < 1 ? 1 : (int)v;
-    tot *= (uint64_t)nc[a];
-  }
-  *ncells = tot;
-  return tot < (1ull << 32);
+  return hash_cells(d->lo, d->hi, h, nc, ncells);
 }
 
 int64_t pow2_at_least(int64_t v) {
@@ -1035,6 +1019,14 @@ gp_status gp_run_nucleation_sites(gp_ctx* c, int32_t run, int64_t n, const doubl
   if (c->n_nuclei + n > c->L.max_nuclei) return fail(c, GP_ERR_CAPACITY, "nucleus capacity");
   if (c->batch && c->n_grains + n > c->L.max_grains)
     return fail(c, GP_ERR_CAPACITY, "grain capacity");
+  for (int64_t i = 0; i < n; ++i) {
+    const double* q = quat4 + 4 * i;
+    const double nq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (!(nq > 0) || !std::isfinite(nq)) return fail(c, GP_ERR_ARG, "quaternion is zero or not finite");
+    if (!std::isfinite(dTn[i])) return fail(c, GP_ERR_ARG, "nucleation undercooling not finite");
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(pos3[3 * i + a])) return fail(c, GP_ERR_ARG, "site position not finite");
+  }
   if (out_first_grain) *out_first_grain = c->batch ? (int32_t)c->n_grains : -1;
   if (n == 0) return GP_OK;
   std::vector<float4> P(n), G(4 * (size_t)n);
@@ -1675,6 +1667,13 @@ gp_status gp_profile_read(gp_ctx* c, int32_t max, gp_kernel_prof* out, int32_t* 
 // stand-alone hash / contact
 // ---------------------------------------------------------------------------------
 namespace {
+// status of the sticky device error bits of a stand-alone call
+gp_status sa_status(uint32_t err) {
+  if (err & ERR_CELL_OVERFLOW) return GP_ERR_CAPACITY;
+  if (err & ERR_TIMEOUT) return GP_ERR_TIMEOUT;
+  return err ? GP_ERR_STATE : GP_OK;
+}
+
 struct SaLayout {
   size_t keys0, keys1, vals0, vals1, status, hist, tickets, err, flags, ofs, bsum, ncell, pos4,
       sstate, cells, total;
@@ -1807,7 +1806,7 @@ gp_status gp_hash_build(const float* x3, int64_t n, const gp_domain* domain, dou
       cudaMemcpyAsync(&err, sb.err, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st) ||
       cudaGetLastError())
     return GP_ERR_CUDA;
-  if (err) return GP_ERR_TIMEOUT;
+  if (err) return sa_status(err);
   if (n_cells) *n_cells = (int64_t)nc;
   return GP_OK;
 }
@@ -1849,9 +1848,31 @@ gp_status gp_contact(const float* x3, const int32_t* grain, const uint8_t* state
       cudaMemcpyAsync(&err, sb.err, 4, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st) ||
       cudaGetLastError())
     return GP_ERR_CUDA;
-  if (err) return GP_ERR_TIMEOUT;
+  if (err) return sa_status(err);
   if (n_pairs) *n_pairs = (int64_t)np;
   return GP_OK;
+}
+
+gp_status gp_selftest_wait(int32_t which, uint32_t spin_limit, void* cuda_stream) {
+  if (which < 0 || which > 1 || spin_limit < 1 || spin_limit > kSpinLimit) return GP_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  uint32_t* words = nullptr;
+  if (cudaMalloc((void**)&words, 4 * 513) != cudaSuccess) return GP_ERR_CUDA;
+  uint32_t err = 0;
+  cudaError_t e = cudaMemsetAsync(words, 0, 4 * 513, st);
+  if (e == cudaSuccess && which == 1) {  // bucket 0: key set, slot never published
+    const unsigned long long key = 1ull;
+    e = cudaMemcpyAsync(words, &key, sizeof(key), cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) {
+    launch_selftest_wait(which, spin_limit, words, words + 512, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, words + 512, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(words);
+  if (e != cudaSuccess) return GP_ERR_CUDA;
+  return err & ERR_TIMEOUT ? GP_ERR_TIMEOUT : (err ? GP_ERR_STATE : GP_OK);
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 // where a_k = k >> 1 is the axis and sigma_k = +1 for even k, -1 for odd k.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -42,6 +43,31 @@ constexpr int kTileZShift = 3;
 // segments) and orders them by cell inside each group, in place of the radix sort
 constexpr int kGroupShift = 10;
 constexpr int kGroupCells = 1 << kGroupShift;
+
+// ---------------------------------------------------------------------------------
+// hash grid (host side): cells of edge h (1 + 2^-9), the contact radius enlarged so
+// that binary32 rounding of the cell coordinate can never separate two points closer
+// than h by more than one cell (up to 4096 cells per axis).  Cells per axis
+// n_a = max(1, ceil((hi_a - lo_a) / edge)); false if an extent is not finite and
+// non-negative, an axis needs more than 4096 cells or the grid 2^32 cells or more.
+// ---------------------------------------------------------------------------------
+inline double cell_edge(double h) { return h * (1.0 + 1.0 / 512.0); }
+
+inline bool hash_cells(const double lo[3], const double hi[3], double h, int nc[3],
+                       uint64_t* ncells) {
+  const double e = cell_edge(h);
+  uint64_t tot = 1;
+  for (int a = 0; a < 3; ++a) {
+    const double ext = hi[a] - lo[a];
+    if (!(ext >= 0) || !std::isfinite(ext)) return false;
+    const double v = std::ceil(ext / e);
+    if (v > 4096.0) return false;
+    nc[a] = v < 1 ? 1 : (int)v;
+    tot *= (uint64_t)nc[a];
+  }
+  *ncells = tot;
+  return tot < (1ull << 32);
+}
 
 // ---------------------------------------------------------------------------------
 // particle record: 16 bytes, loaded and stored as one int4
@@ -441,15 +467,48 @@ __device__ inline int64_t claim_probe(const Claims& C, unsigned long long key, b
   return -1;
 }
 
-// bounded wait for the slot of bucket b
-__device__ inline int64_t claim_wait(const Claims& C, uint32_t b) {
+// bounded wait for the slot of bucket b: at most `limit` polls, then ERR_TIMEOUT
+__device__ inline int64_t claim_wait(const Claims& C, uint32_t b, uint32_t limit = kSpinLimit) {
   volatile unsigned long long* sv = &C.bucket[b].y;
-  for (uint32_t spins = 0; spins < kSpinLimit; ++spins) {
+  for (uint32_t spins = 0; spins < limit; ++spins) {
     const unsigned long long v = *sv;
     if (v) return slot_of(v);
   }
   atomicOr(C.err, ERR_TIMEOUT);
   return -1;
+}
+
+// ---------------------------------------------------------------------------------
+// decoupled look-back of a onesweep pass: each tile publishes, per digit, a status
+// word {flag, value}: kFlagAgg with its own count, then kFlagInc with the inclusive
+// prefix.  A tile sums the preceding tiles' words from the nearest one backwards until
+// it meets an inclusive prefix.  A predecessor that has not published yet is polled;
+// after `limit` polls in all the wait gives up, sets ERR_TIMEOUT in *err and returns
+// the partial sum (the sort's result is then invalid and the host reports the error).
+// ---------------------------------------------------------------------------------
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+__device__ inline uint32_t lookback_excl(const uint32_t* status, int64_t tile, int d,
+                                         uint32_t limit, uint32_t* err) {
+  uint32_t excl = 0, spins = 0;
+  int64_t pred = tile - 1;
+  while (pred >= 0) {
+    const uint32_t s = *((volatile const uint32_t*)(status + (size_t)pred * 256 + d));
+    const uint32_t flag = s & ~kValMask;
+    if (flag == 0u) {
+      if (++spins > limit) {
+        atomicOr(err, ERR_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    excl += s & kValMask;
+    if (flag == kFlagInc) break;
+    --pred;
+  }
+  return excl;
 }
 
 // The targets of one particle are the neighbours of one site, so they nearly

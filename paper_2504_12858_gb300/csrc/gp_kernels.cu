@@ -1783,11 +1783,31 @@ __global__ void __launch_bounds__(256) k_act_list(const uint8_t* __restrict__ sa
   }
 }
 
+// Runs one bounded wait whose word nothing ever publishes (one thread), with a
+// limit of `limit` polls: which = 0 the onesweep look-back of tile 1 on the
+// never-published status word of tile 0; which = 1 the claim-slot wait on a
+// pending bucket (key set, slot word 0).  The error bits land in *err.
+__global__ void k_selftest_wait(int which, uint32_t limit, uint32_t* words, uint32_t* err) {
+  if (which == 0) {
+    (void)lookback_excl(words, 1, 0, limit, err);
+  } else {
+    Claims C{};
+    C.bucket = reinterpret_cast<ulonglong2*>(words);
+    C.err = err;
+    (void)claim_wait(C, 0, limit);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
+void launch_selftest_wait(int which, uint32_t limit, uint32_t* words, uint32_t* err,
+                          cudaStream_t st) {
+  k_selftest_wait<<<1, 1, 0, st>>>(which, limit, words, err);
+}
+
 // A batch context (batch == true) sorts uint64 keys, a single-run context uint32.
 void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* keys,
                  uint32_t* vals, cudaStream_t st) {

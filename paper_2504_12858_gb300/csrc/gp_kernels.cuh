@@ -93,4 +93,9 @@ void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstat
                        int64_t n, uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
                        unsigned long long* npairs, cudaStream_t st);
 
+// bounded-wait self-test: words holds 512 zeroed uint32 (a status array of two
+// tiles, or one claim bucket), err one zeroed word
+void launch_selftest_wait(int which, uint32_t limit, uint32_t* words, uint32_t* err,
+                          cudaStream_t st);
+
 }  // namespace gp

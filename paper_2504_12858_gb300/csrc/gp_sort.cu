@@ -20,10 +20,6 @@ namespace gp {
 
 namespace {
 
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagInc = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
-
 // Counts every digit of every pass: 32-bit keys, four per 16-byte load.  With
 // n_dev the key count is read on the device.
 __global__ void __launch_bounds__(256) k_hist32(const uint32_t* __restrict__ keys, int64_t n,
@@ -205,22 +201,7 @@ __global__ void __launch_bounds__(kSortThreads, SortTile<K>::ctas) k_onesweep(
       atomicExch(my, kFlagInc | cnt);
     } else {
       atomicExch(my, kFlagAgg | cnt);
-      int64_t pred = (int64_t)tile - 1;
-      uint32_t spins = 0;
-      while (pred >= 0) {
-        uint32_t s = *((volatile uint32_t*)(status + (size_t)pred * 256 + d));
-        uint32_t flag = s & ~kValMask;
-        if (flag == 0u) {
-          if (++spins > kSpinLimit) {
-            atomicOr(err, ERR_TIMEOUT);
-            break;
-          }
-          continue;
-        }
-        excl += s & kValMask;
-        if (flag == kFlagInc) break;
-        --pred;
-      }
+      excl = lookback_excl(status, (int64_t)tile, d, kSpinLimit, err);
       atomicExch(my, kFlagInc | ((excl + cnt) & kValMask));
     }
     s_gofs[d] = dbase + excl - start;  // wraps modulo 2^32; the sum below is exact

@@ -52,6 +52,8 @@ constexpr size_t kBsum = kOfs + up(4 * kMaxPoints);
 constexpr size_t kNcell = kBsum + up(4 * (kMaxPoints / 256 + 1) + 16);
 constexpr size_t kBytes = kNcell + up(64);
 
+// 6,390,784 bytes: the size include/gp.h states
+static_assert(kBytes == 6390784, "scratch size stated in gp.h");
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
 constexpr int kMaxDevices = 64;
@@ -87,22 +89,15 @@ extern "C" gp_status gp_hash_build_static(const float* x3, int64_t n, const gp_d
     if (n_cells) *n_cells = 0;
     return GP_OK;
   }
-  // hash grid: same definition as gp_hash_build (cell edge h (1 + 2^-9))
-  const double e = h * (1.0 + 1.0 / 512.0);
+  // hash grid: the definition gp_hash_build uses (cell edge h (1 + 2^-9))
   Params P{};
   uint64_t ncells = 1;
+  if (!hash_cells(domain->lo, domain->hi, h, P.geo.nc, &ncells)) return GP_ERR_ARG;
   for (int a = 0; a < 3; ++a) {
-    const double ext = domain->hi[a] - domain->lo[a];
-    if (!(ext >= 0) || !std::isfinite(ext)) return GP_ERR_ARG;
-    const double v = std::ceil(ext / e);
-    if (v > 4096.0) return GP_ERR_ARG;
-    P.geo.nc[a] = v < 1 ? 1 : (int)v;
     P.geo.lo[a] = (float)domain->lo[a];
     P.geo.hi[a] = (float)domain->hi[a];
-    ncells *= (uint64_t)P.geo.nc[a];
   }
-  if (ncells >= (1ull << 32)) return GP_ERR_ARG;
-  P.inv_c = (float)(1.0 / e);
+  P.inv_c = (float)(1.0 / cell_edge(h));
   for (int a = 0; a < 3; ++a) P.geo.inv[a] = P.inv_c;
   float hf = (float)h;
   P.rc2 = hf * hf;

@@ -113,6 +113,7 @@ SIGNATURES = {
                              C.c_int64, C.POINTER(C.c_int64), _P, C.c_size_t, _P]),
     "gp_hash_build_static": (C.c_int, [_P, C.c_int64, C.POINTER(gp_domain), C.c_double, _P, _P,
                                        _P, _P, C.POINTER(C.c_int64), _P]),
+    "gp_selftest_wait": (C.c_int, [C.c_int32, C.c_uint32, _P]),
     "gp_tape_begin": (C.c_int, [_P]),
     "gp_adjoint": (C.c_int, [_P, _P, C.c_int64, C.c_int32, C.POINTER(C.c_double)]),
     "gp_batch_arena_bytes": (C.c_int, [C.c_int32, C.POINTER(gp_domain), C.c_double,
@@ -496,6 +497,14 @@ class Batch(Sim):
         active = np.zeros(self.nruns, np.int64)
         self._check(load().gp_run_counts(self._h, self.nruns, _ptr(live), _ptr(active)))
         return live, active
+
+
+def gp_selftest_wait(which, spin_limit, stream=None):
+    """Runs one bounded device wait on a word nothing publishes; returns the status
+    (GP_ERR_TIMEOUT = 6 when the wait gave up, as it must)."""
+    import torch
+    s = stream or torch.cuda.current_stream()
+    return int(load().gp_selftest_wait(int(which), int(spin_limit), C.c_void_p(s.cuda_stream)))
 
 
 def grain_table(sim):

@@ -13,7 +13,13 @@ One step from the state after three warm-up steps:
 - (grain, site, dir) is unique over all live particles;
 - every live particle has ell in [0, 1) and a known grain;
 - the particle steps counted equal the ACTIVE particles at the start of the step,
-  and each crossing records one reached site.
+  and each crossing records one reached site;
+- for 20000 sampled ACTIVE particles the contact predicate of Sec. 2.1.2 (a live
+  particle of another grain closer than h) is evaluated by brute force on the host,
+  over every exported position in a 3 x 3 x 3 block of 2h cells around the particle,
+  with the binary32 arithmetic the kernels use (d2 = ((dx dx + dy dy) + dz dz) < hf hf,
+  every operation rounded); the GPU must have frozen exactly the sampled particles
+  for which it holds.
 """
 import numpy as np
 import pytest
@@ -105,3 +111,38 @@ def test_weld_fixture_full_size_sampled_step():
         checked += 1
     assert checked > 1000, checked
     assert frozen < checked
+
+    # contact decisions of sampled ACTIVE particles against a brute-force predicate
+    x0 = p0["x"]
+    E = 2.0 * w.h                                   # > h: neighbours lie in adjacent cells
+    cell = np.floor((x0.astype(np.float64) - np.array(w.lo)) / E).astype(np.int64)
+    ncell = cell.max(axis=0) + 3
+    ckey = ((cell[:, 2] + 1) * ncell[1] + (cell[:, 1] + 1)) * ncell[0] + (cell[:, 0] + 1)
+    corder = np.argsort(ckey, kind="stable")
+    cks = ckey[corder]
+    smp = np.random.default_rng(8).choice(act, 20000, replace=False)
+    off = np.array([(dz * ncell[1] + dy) * ncell[0] + dx for dz in (-1, 0, 1)
+                    for dy in (-1, 0, 1) for dx in (-1, 0, 1)], np.int64)
+    qk = ckey[smp][:, None] + off[None, :]
+    lo_i = np.searchsorted(cks, qk, side="left")
+    hi_i = np.searchsorted(cks, qk, side="right")
+    hf = np.float32(w.h)
+    rc2 = np.float32(hf * hf)
+    expect = np.zeros(len(smp), bool)
+    for t, i in enumerate(smp):
+        cand = np.concatenate([corder[a:b] for a, b in zip(lo_i[t], hi_i[t])])
+        cand = cand[p0["grain"][cand] != p0["grain"][i]]
+        if cand.size == 0:
+            continue
+        d = x0[i][None, :] - x0[cand]                # binary32, each operation rounded
+        d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        expect[t] = bool((d2 < rc2).any())
+    ksmp = _keys({f: p0[f][smp] for f in ("grain", "site", "dir")})
+    j = np.minimum(np.searchsorted(ks, ksmp), len(ks) - 1)
+    present = ks[j] == ksmp
+    q = order[j]
+    got_frozen = present & (p1["state"][q] == 1)
+    assert np.array_equal(got_frozen, expect), (int((got_frozen & ~expect).sum()),
+                                                int((expect & ~got_frozen).sum()))
+    assert (p1["ell"][q[expect]] == p0["ell"][smp[expect]]).all()
+    assert expect.sum() > 200 and (~expect).sum() > 200, int(expect.sum())

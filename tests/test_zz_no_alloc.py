@@ -5,9 +5,10 @@ must not pay the synchronisation of an allocation) can neither pass a workspace
 nor let the library call cudaMalloc; this entry point draws its scratch from a
 static device array of the library instead.  These tests call it through the C
 ABI and require results identical to those of gp_hash_build (the workspace
-variant) on consecutive calls that reuse the shared array, and a clean refusal
-of inputs above its size limit.  The file sorts last so that a run stopping at
-its first failure has already run every other test.
+variant) on consecutive calls that reuse the shared array, unchanged free device
+memory across further calls, and a clean refusal of inputs above its size limit.
+The file sorts last so that a run stopping at its first failure has already run
+every other test.
 """
 import ctypes as C
 
@@ -66,6 +67,27 @@ def test_static_scratch_hash_equals_workspace_hash_on_consecutive_calls():
         ref = native.gp_hash_build(xd, lo, hi, h)
         for a, b in zip(got, ref):
             assert np.array_equal(a, b)
+
+
+def test_static_scratch_call_allocates_no_device_memory():
+    n, lo, hi, h, seed = CASES[0]
+    g = inputs.rng(seed)
+    x = (np.array(lo) + g.random((n, 3)) * (np.array(hi) - np.array(lo))).astype(np.float32)
+    xd = torch.from_numpy(x).to(DEV)
+    d = native.domain(lo, hi)
+    out = [torch.empty(n, dtype=torch.int32, device=DEV) for _ in range(4)]
+    nc = C.c_int64(-1)
+    stream = torch.cuda.current_stream(DEV)
+    args = [C.c_void_p(xd.data_ptr()), n, C.byref(d), float(h),
+            *[C.c_void_p(t.data_ptr()) for t in out], C.byref(nc), C.c_void_p(stream.cuda_stream)]
+    assert LIB.gp_hash_build_static(*args) == 0          # warm-up: module and address set up
+    torch.cuda.synchronize(DEV)
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    for _ in range(3):
+        assert LIB.gp_hash_build_static(*args) == 0
+    torch.cuda.synchronize(DEV)
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert free1 == free0
 
 
 def test_static_scratch_refuses_inputs_above_its_limit():
