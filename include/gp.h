@@ -229,6 +229,47 @@ gp_status gp_set_periodic(gp_ctx* ctx, int32_t axes);
  * tape records. */
 gp_status gp_set_melting(gp_ctx* ctx, int32_t enable);
 
+/* Obstacle store of a single-run context.  A particle stopped by another grain
+ * (FROZEN) never moves again: the points where two grains meet stop for good and
+ * form the grain boundary (Sec. 2.1.2, impingement).  Instead of carrying FROZEN
+ * particles through the per-step ordering, gather and compaction, the library moves
+ * them, in batches, into an obstacle store: ordered by cell, with their positions and
+ * a cell table of their own, which the contact search reads beside the table of the
+ * moving particles.  Results do not depend on the mode; only the cost does.
+ *   mode 0: off, every particle stays in the per-step store (obstacles already
+ *           moved go back to it);
+ *   mode 1 (default): a batch is moved once carrying the FROZEN particles from step
+ *           to step has cost about as much as merging them into the store;
+ *   mode 2: every step that starts with FROZEN particles in the per-step store.
+ * The store is not used by a batch context, with periodic axes, with melting (which
+ * removes frozen particles) or while the adjoint tape records; turning any of these on
+ * moves the obstacles back.  gp_get_particles lists the per-step store first, then
+ * the obstacle store; gp_stats counts both.  GP_ERR_ARG for another mode. */
+gp_status gp_set_obstacle_store(gp_ctx* ctx, int32_t mode);
+
+/* Inspection of the ordering of the particle step (used by the tests; the paper has
+ * no counterpart).  which = 0: runs on the current state the ordering the next gp_step
+ * starts with (cell key of every particle of the per-step store, the particles grouped
+ * by tile of 1024 cells and ordered by cell inside each tile, the cell table), without
+ * advancing the state, and copies to host arrays (any may be NULL):
+ *   keys_in     the cell key of every particle, in the order of gp_get_particles;
+ *   keys_sorted the keys in the ordered sequence;
+ *   src         the gp_get_particles index of each ordered particle;
+ *   table       4 words per segment of 16 cells (table_cap segments at most): index
+ *               of its first ordered particle, stamp << 16 | saturation flag << 15 |
+ *               count, then the 4-bit counts (saturated at 15) of cells 0-7 and 8-15;
+ *               an entry whose stamp differs from *stamp is an empty segment.
+ * Particles of one cell may come in any order (the ordering places them by atomic
+ * counters); keys, cells and counts are exact.
+ * which = 1: the obstacle store: keys_sorted, src (identity: the obstacles are the
+ * last *n_out particles of gp_get_particles, in order) and its table (*stamp = 1; an
+ * entry with count 0 is empty).  *n_out receives the particle count, *n_seg the
+ * number of segments of the table.  GP_ERR_STATE on a batch context. */
+gp_status gp_inspect_order(gp_ctx* ctx, int32_t which, int64_t cap, uint32_t* keys_in,
+                           uint32_t* keys_sorted, uint32_t* src, int64_t* n_out,
+                           uint32_t* table, int64_t table_cap, int64_t* n_seg,
+                           uint32_t* stamp);
+
 /* Sets (or replaces) the composition field of a single-run context; the grid is
  * copied into the arena (gp_memory.solute_nodes) or, for a library-allocated
  * context, into memory the library allocates.  GP_ERR_STATE on a batch context;

@@ -16,6 +16,9 @@ using namespace gp;
 namespace {
 
 constexpr size_t kAlign = 256;
+// record-steps of carrying a FROZEN record in the dynamic store (ordering, gather,
+// emit) that cost about as much as merging one record into the obstacle store
+constexpr double kObsCarry = 4.0;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // hash geometry of one run and its place in the context-wide key, cell-table and
@@ -45,7 +48,7 @@ struct Layout {
       rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, gflags, gdtn, dstats, grid,
       sgrid, runs,
       rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, gcnt, gofs, gfill,
-      gbsum, gkey, gdest, total;
+      gbsum, gkey, gdest, orec[2], opos[2], okey[2], otab, otcnt, osplit, total;
   uint32_t ngroups = 0;  // one run: cell groups of the record grouping
 };
 
@@ -202,6 +205,17 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->gbsum = take(4 * (((size_t)L->ngroups + 255) / 256) + 16);
   L->gkey = take(batch ? 16 : 4 * cap + 16);   // one run: cell keys in grouped order
   L->gdest = take(batch ? 16 : 4 * cap + 16);  // and the sorted position of each
+  // one run: the obstacle store (FROZEN records ordered by cell key, positions, keys;
+  // two copies, merged from one into the other) and its cell table
+  const size_t ocap = batch ? 1 : cap;
+  for (int b = 0; b < 2; ++b) {
+    L->orec[b] = take(16 * ocap);
+    L->opos[b] = take(16 * ocap);
+    L->okey[b] = take(4 * ocap + 16);
+  }
+  L->otab = take(batch ? 16 : 16 * (size_t)L->nseg);
+  L->otcnt = take(4 * (ocap / 8192 + 16));
+  L->osplit = take(4 * (2 * ocap / 2048 + 16));
   L->total = o;
   return true;
 }
@@ -244,7 +258,7 @@ void grain_entry(const double* pos, const double* q, double h, int run, float4 o
 const char* kKernelNames[K_COUNT] = {"hist",      "onesweep", "keys",     "build",
                                      "advance",   "emit",     "nucleate", "grain_map",
                                      "seed",      "contact",  "cells",    "finalize",
-                                     "group"};
+                                     "group",     "obstacle"};
 // algorithmic DRAM bytes per processed item:
 //   hist      read key (4)
 //   onesweep  read key + value, write key + value (16)
@@ -256,7 +270,9 @@ const char* kKernelNames[K_COUNT] = {"hist",      "onesweep", "keys",     "build
 //             cells (cache)
 //   emit      read record (16), write record (16) + key + value (8) per output
 //   group     read key twice (8), write the grouped identity (4)
-const double kKernelBytes[K_COUNT] = {4, 16, 24, 56, 52, 40, 0, 0, 0, 0, 0, 0, 12};
+//   obstacle  per record of the merged obstacle store: read and write its key,
+//             position and record (72)
+const double kKernelBytes[K_COUNT] = {4, 16, 24, 56, 52, 40, 0, 0, 0, 0, 0, 0, 12, 72};
 
 struct Prof : ProfHook {
   cudaStream_t st = nullptr;
@@ -394,6 +410,12 @@ struct gp_ctx {
   // instantiated graphs by step count
   int graph_steps = 0;
   std::map<int, cudaGraphExec_t> graphs;
+  // obstacle store of a single run: n_obs FROZEN records in copy ocur; obs_carry sums
+  // the FROZEN records the dynamic store carried since the last flush
+  int64_t n_obs = 0;
+  int ocur = 0;
+  double obs_carry = 0;
+  int obs_mode = 1;  // 0 off, 1 flushes when carrying costs as much as merging, 2 every step
 };
 
 namespace {
@@ -517,6 +539,8 @@ gp_status push_counts(gp_ctx* c) {
   c->hst->n_live = (unsigned long long)c->n_live;
   c->hst->n_grains = (unsigned long long)c->n_grains;
   c->hst->step = (unsigned long long)c->step;
+  GP_CUDA(c, cudaMemcpyAsync(&c->dst->n_frozen, &c->hst->n_frozen, sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, c->st));
   GP_CUDA(c, cudaMemcpyAsync(&c->dst->step, &c->hst->step, sizeof(unsigned long long),
                              cudaMemcpyHostToDevice, c->st));
   GP_CUDA(c, cudaMemcpyAsync(&c->dst->n_live, &c->hst->n_live, sizeof(unsigned long long),
@@ -525,6 +549,36 @@ gp_status push_counts(gp_ctx* c) {
                              cudaMemcpyHostToDevice, c->st));
   GP_CUDA(c, cudaStreamSynchronize(c->st));
   return GP_OK;
+}
+
+// The obstacle store serves the plain single-run step.  Periodic axes, melting (which
+// removes frozen particles) and the adjoint tape (which follows every particle through
+// every step) keep all particles in the dynamic store.
+bool obs_usable(const gp_ctx* c) {
+  return c->obs_mode != 0 && !c->batch && !c->periodic && !c->melting && !c->tape_on;
+}
+
+// empties the obstacle store (its table back to all-empty entries)
+gp_status obs_reset(gp_ctx* c) {
+  c->n_obs = 0;
+  c->obs_carry = 0;
+  if (!c->batch) GP_CUDA(c, cudaMemsetAsync(at<uint4>(c, c->L.otab), 0, 16 * c->L.nseg, c->st));
+  return GP_OK;
+}
+
+// moves the obstacle records back to the end of the dynamic store (its keys are then
+// recomputed before the next ordering)
+gp_status obs_return(gp_ctx* c) {
+  if (c->n_obs == 0) return GP_OK;
+  if (c->n_live + c->n_obs > c->L.cap) return fail(c, GP_ERR_CAPACITY, "particle capacity");
+  launch_append(at<int4>(c, c->L.orec[c->ocur]), c->n_obs, c->rec[c->cur], c->n_live, c->st);
+  GP_CUDA(c, cudaGetLastError());
+  c->n_live += c->n_obs;
+  c->hst->n_frozen += (unsigned long long)c->n_obs;
+  c->keys_valid = false;
+  gp_status s = obs_reset(c);
+  if (s) return s;
+  return push_counts(c);
 }
 
 void drop_graphs(gp_ctx* c) {
@@ -656,6 +710,7 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemsetAsync(c->cells, 0, 16 * L.nseg, s);
+  if (!batch) e = e ? e : cudaMemsetAsync(c->base + L.otab, 0, 16 * L.nseg, s);
   e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.nheads, s);
   e = e ? e : cudaMemsetAsync(c->C.bucket, 0, 16 * (size_t)L.buckets, s);
   e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.blocks, s);
@@ -746,7 +801,8 @@ gp_status gp_run_add_grains(gp_ctx* c, int32_t run, int64_t n, const double* pos
   if (run < 0 || run >= c->L.nruns) return fail(c, GP_ERR_ARG, "no such run");
   if (n < 0 || (n > 0 && (!pos3 || !quat4))) return fail(c, GP_ERR_ARG, "bad arguments");
   if (c->n_grains + n > c->L.max_grains) return fail(c, GP_ERR_CAPACITY, "grain capacity");
-  if (nucleate && c->n_live + 6 * n > c->L.cap) return fail(c, GP_ERR_CAPACITY, "particle capacity");
+  if (nucleate && c->n_live + c->n_obs + 6 * n > c->L.cap)
+    return fail(c, GP_ERR_CAPACITY, "particle capacity");
   for (int64_t i = 0; i < n; ++i) {
     const double* q = quat4 + 4 * i;
     double nq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
@@ -832,8 +888,8 @@ gp_status gp_seed_shell(gp_ctx* c, int64_t n, const int32_t* grains, int32_t n0,
   GP_CUDA(c, cudaMemcpyAsync(ds, soff.data(), 8 * soff.size(), cudaMemcpyHostToDevice, c->st));
   s = push_counts(c);
   if (s) return s;
-  launch_seed_shell(c->P, dg, n, dt, (int64_t)toff.size(), (float)ell0, c->rec[c->cur], c->L.cap,
-                    &c->dst->n_live, c->C, &c->dst->err, c->st);
+  launch_seed_shell(c->P, dg, n, dt, (int64_t)toff.size(), (float)ell0, c->rec[c->cur],
+                    c->L.cap - c->n_obs, &c->dst->n_live, c->C, &c->dst->err, c->st);
   launch_seed_shell_sites(c->P, dg, n, ds, (int64_t)soff.size(), c->C, c->R, c->st);
   GP_CUDA(c, cudaGetLastError());
   c->keys_valid = false;
@@ -923,6 +979,10 @@ gp_status gp_set_periodic(gp_ctx* c, int32_t axes) {
     if (((axes >> a) & 1) &&
         std::floor((c->dom[0].hi[a] - c->dom[0].lo[a]) / cell_edge(c->h)) < 3)
       return fail(c, GP_ERR_ARG, "a periodic axis needs at least three contact cells");
+  if (axes) {  // the periodic contact search reads the dynamic store only
+    s = obs_return(c);
+    if (s) return s;
+  }
   // the thermal constants set so far live in P.geo: keep them across the refresh
   const Geo keep = c->P.geo;
   c->periodic = axes;
@@ -956,7 +1016,80 @@ gp_status gp_set_melting(gp_ctx* c, int32_t enable) {
   if (s) return s;
   if (c->batch) return fail(c, GP_ERR_STATE, "melting applies to single-run contexts");
   if (enable && c->tape_on) return fail(c, GP_ERR_STATE, "the adjoint tape is recording");
+  if (enable) {  // the melting pass removes frozen particles too: all in the dynamic store
+    s = obs_return(c);
+    if (s) return s;
+  }
   c->melting = enable != 0;
+  return GP_OK;
+}
+
+gp_status gp_set_obstacle_store(gp_ctx* c, int32_t mode) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (mode < 0 || mode > 2) return fail(c, GP_ERR_ARG, "mode is 0, 1 or 2");
+  if (mode == 0) {
+    s = obs_return(c);
+    if (s) return s;
+  }
+  c->obs_mode = mode;
+  return GP_OK;
+}
+
+gp_status gp_inspect_order(gp_ctx* c, int32_t which, int64_t cap, uint32_t* keys_in,
+                           uint32_t* keys_sorted, uint32_t* src, int64_t* n_out, uint32_t* table,
+                           int64_t table_cap, int64_t* n_seg, uint32_t* stamp) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "the inspection is for single-run contexts");
+  if ((which != 0 && which != 1) || cap < 0 || table_cap < 0)
+    return fail(c, GP_ERR_ARG, "bad arguments");
+  if (n_seg) *n_seg = (int64_t)c->L.nseg;
+  const int64_t n = which == 0 ? c->n_live : c->n_obs;
+  if (n_out) *n_out = n;
+  const int64_t m = std::min(n, cap);
+  const uint4* tab = at<uint4>(c, c->L.otab);
+  if (which == 0) {
+    if (n > 0) {
+      const Params P = step_params(c, c->step);
+      if (!c->keys_valid) {
+        launch_keys(false, P, c->rec[c->cur], n, c->sb.keys[0], c->sb.vals[0], c->st);
+        c->keys_valid = true;
+      }
+      if (++c->stamp > 0xffffu) {
+        GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
+        c->stamp = 1;
+      }
+      GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
+      launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), n, c->L.ngroups,
+                         at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
+                         at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
+                         at<uint32_t>(c, c->L.gkey), at<uint32_t>(c, c->L.gdest), c->rec[c->cur],
+                         c->rec[c->cur ^ 1], c->pos4, static_cast<uint32_t*>(c->sb.keys[1]),
+                         c->sb.vals[0], reinterpret_cast<uint8_t*>(c->site_slot), c->cells,
+                         c->stamp, c->act, c->dst, c->sms, nullptr, c->st);
+      GP_CUDA(c, cudaGetLastError());
+    }
+    if (m > 0 && keys_in)
+      GP_CUDA(c, cudaMemcpyAsync(keys_in, c->sb.keys[0], 4 * m, cudaMemcpyDeviceToHost, c->st));
+    if (m > 0 && keys_sorted)
+      GP_CUDA(c, cudaMemcpyAsync(keys_sorted, c->sb.keys[1], 4 * m, cudaMemcpyDeviceToHost, c->st));
+    if (m > 0 && src)
+      GP_CUDA(c, cudaMemcpyAsync(src, c->sb.vals[0], 4 * m, cudaMemcpyDeviceToHost, c->st));
+    tab = c->cells;
+    if (stamp) *stamp = c->stamp;
+  } else {
+    if (m > 0 && keys_sorted)
+      GP_CUDA(c, cudaMemcpyAsync(keys_sorted, at<uint32_t>(c, c->L.okey[c->ocur]), 4 * m,
+                                 cudaMemcpyDeviceToHost, c->st));
+    if (src)
+      for (int64_t i = 0; i < m; ++i) src[i] = (uint32_t)i;
+    if (stamp) *stamp = 1;
+  }
+  const int64_t ts = std::min<int64_t>(table_cap, (int64_t)c->L.nseg);
+  if (table && ts > 0)
+    GP_CUDA(c, cudaMemcpyAsync(table, tab, 16 * ts, cudaMemcpyDeviceToHost, c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
   return GP_OK;
 }
 
@@ -1191,6 +1324,7 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       if (s) return s;
     }
     const int64_t n = c->n_live;
+    const bool obs = obs_usable(c);
     const bool rec = c->tape_on && c->tape_pos < c->L.tape_steps;
     const size_t tq = (size_t)c->tape_pos, tcap = (size_t)c->L.cap;
     int32_t* tpar = rec ? at<int32_t>(c, c->L.tape_par) + tq * tcap : nullptr;
@@ -1229,17 +1363,56 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
         GP_CUDA(c, cudaMemcpyAsync(at<uint32_t>(c, c->L.tape_vals) + tq * tcap, c->sb.vals[0],
                                    4 * n, cudaMemcpyDeviceToDevice, c->st));
       }
+      // obstacle flush: the FROZEN records of the ordered store (hst->n_frozen of them,
+      // as the last emit counted) join the obstacle store once carrying them from step
+      // to step has cost about as much as merging them, counted as kObsCarry record
+      // steps per merged record; the first FROZEN records are flushed at once
+      if (obs) {
+        const double f = (double)c->hst->n_frozen;
+        c->obs_carry += f;
+        if (f > 0 && (c->obs_mode == 2 || kObsCarry * c->obs_carry >= (double)c->n_obs + f)) {
+          c->prof.begin(K_OBS);
+          uint32_t* flist = at<uint32_t>(c, c->L.gdest);
+          launch_obs_list(reinterpret_cast<const uint8_t*>(c->site_slot), n,
+                          at<uint32_t>(c, c->L.otcnt), sorted, flist, c->dst, c->st);
+          GP_CUDA(c, cudaMemcpyAsync(&c->hst->obs_new, &c->dst->obs_new, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, c->st));
+          GP_CUDA(c, cudaStreamSynchronize(c->st));
+          const int64_t nf = (int64_t)c->hst->obs_new;
+          if (c->n_obs + nf > c->L.cap) {
+            c->broken = true;
+            return fail(c, GP_ERR_CAPACITY, "particle capacity exceeded");
+          }
+          if (nf > 0) {
+            const int o = c->ocur;
+            launch_obs_merge(P, at<uint32_t>(c, c->L.okey[o]), at<float4>(c, c->L.opos[o]),
+                             at<int4>(c, c->L.orec[o]), c->n_obs, skeys, c->pos4, sorted, flist,
+                             nf, at<uint32_t>(c, c->L.osplit), at<uint32_t>(c, c->L.okey[o ^ 1]),
+                             at<float4>(c, c->L.opos[o ^ 1]), at<int4>(c, c->L.orec[o ^ 1]),
+                             at<uint4>(c, c->L.otab), &c->dst->err, c->st);
+            GP_CUDA(c, cudaGetLastError());
+            c->ocur ^= 1;
+            c->n_obs += nf;
+          }
+          c->obs_carry = 0;
+          c->prof.end(K_OBS, (double)c->n_obs, nf > 0 ? 6 : 3);
+        }
+      }
+      const Obs ob{at<uint4>(c, c->L.otab), at<uint32_t>(c, c->L.okey[c->ocur]),
+                   at<float4>(c, c->L.opos[c->ocur]), c->n_obs};
       c->prof.begin(K_ADVANCE);
       launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp, n, c->act,
-                     c->C, c->site_slot, c->dst, c->st);
+                     c->C, c->site_slot, c->dst, c->st, obs ? &ob : nullptr);
       // units: the ACTIVE particles entering the step (live minus frozen after the last step)
       c->prof.end(K_ADVANCE, (double)(n - std::min<int64_t>(n, (int64_t)c->hst->n_frozen)));
       if (rec) launch_tape_state(sorted, n, at<uint8_t>(c, c->L.tape_state) + tq * tcap, c->st);
       c->prof.begin(K_EMIT);
       launch_emit(batch, P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
-                  c->sb.vals[0], c->L.cap, c->C, c->R, tpar, c->dst, c->st);
+                  c->sb.vals[0], c->L.cap - c->n_obs, c->C, c->R, tpar, c->dst, c->st);
       c->prof.end(K_EMIT, (double)n, 2);  // k_emit, k_emit_check
     }
+    // the dynamic store holds what the particle capacity leaves beside the obstacles
+    const int64_t dcap = c->L.cap - c->n_obs;
     // pending sites: registered minus activated (re-nucleations of dormant seeds
     // count as nucleations too, so they are subtracted back)
     const int64_t pending =
@@ -1254,16 +1427,16 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       c->prof.begin(K_NUCLEATE);
       launch_nucleate(P, S1, c->npos, c->ngrain, c->nstate, c->n_nuclei, c->gtab,
                       c->L.max_grains, c->rec[c->cur], static_cast<uint32_t*>(c->sb.keys[0]),
-                      c->sb.vals[0], c->L.cap, c->C, c->R, c->dst, c->gdtn, c->st);
+                      c->sb.vals[0], dcap, c->C, c->R, c->dst, c->gdtn, c->st);
       c->prof.end(K_NUCLEATE, 1.0);
     } else {
       c->prof.begin(K_FINALIZE);
-      launch_finalize(c->dst, c->L.cap, false, c->st);
+      launch_finalize(c->dst, dcap, false, c->st);
       c->prof.end(K_FINALIZE, 1.0);
     }
     if (dormant > 0)
       launch_renucleate(P, c->gflags, (int)c->n_grains, c->rec[c->cur],
-                        static_cast<uint32_t*>(c->sb.keys[0]), c->sb.vals[0], c->L.cap, c->C,
+                        static_cast<uint32_t*>(c->sb.keys[0]), c->sb.vals[0], dcap, c->C,
                         c->R, c->dst, c->st);
     GP_CUDA(c, cudaGetLastError());
     const int64_t stepped = c->step;
@@ -1290,6 +1463,8 @@ gp_status gp_tape_begin(gp_ctx* c) {
   if (c->P.solute) return fail(c, GP_ERR_STATE, "the adjoint takes the nominal liquidus");
   if (c->L.tape_steps <= 0) return fail(c, GP_ERR_STATE, "no tape (gp_memory.tape_steps = 0)");
   if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
+  s = obs_return(c);  // the tape follows every particle through the dynamic store
+  if (s) return s;
   c->tape_on = true;
   c->tape_pos = 0;
   c->tape_n.clear();
@@ -1343,8 +1518,8 @@ gp_status gp_stats(gp_ctx* c, gp_stats_t* o) {
     cudaStreamSynchronize(c->st);
   const DevStats& d = *c->hst;
   o->step = c->step;
-  o->n_live = (int64_t)d.n_live;
-  o->n_frozen = (int64_t)d.n_frozen;
+  o->n_live = (int64_t)d.n_live + c->n_obs;      // dynamic store + obstacle store
+  o->n_frozen = (int64_t)d.n_frozen + c->n_obs;
   o->n_active = o->n_live - o->n_frozen;
   o->n_grains = (int64_t)d.n_grains;
   o->n_reached = (int64_t)std::min<unsigned long long>(d.reached, (unsigned long long)c->L.rcap);
@@ -1367,16 +1542,23 @@ gp_status gp_get_particles(gp_ctx* c, int64_t cap, int32_t* grain, int32_t* site
   gp_status s = check_ctx(c);
   if (s) return s;
   if (cap < 0) return fail(c, GP_ERR_ARG, "cap < 0");
-  const int64_t n = c->n_live;
+  // the dynamic store, then the obstacle store
+  const int64_t nd = c->n_live, n = nd + c->n_obs;
   if (n_out) *n_out = n;
-  const int64_t m = std::min(n, cap);
+  const int64_t m = std::min(n, cap), md = std::min(nd, m), mo = m - md;
   if (m == 0) return GP_OK;
   std::vector<int4> recs(m);
-  GP_CUDA(c, cudaMemcpyAsync(recs.data(), c->rec[c->cur], sizeof(int4) * m,
-                             cudaMemcpyDeviceToHost, c->st));
+  const int4* orec = at<int4>(c, c->L.orec[c->ocur]);
+  if (md)
+    GP_CUDA(c, cudaMemcpyAsync(recs.data(), c->rec[c->cur], sizeof(int4) * md,
+                               cudaMemcpyDeviceToHost, c->st));
+  if (mo)
+    GP_CUDA(c, cudaMemcpyAsync(recs.data() + md, orec, sizeof(int4) * mo, cudaMemcpyDeviceToHost,
+                               c->st));
   if (x3) {
-    float* dx = reinterpret_cast<float*>(c->pos4);
-    launch_positions(c->P, c->rec[c->cur], m, dx, c->st);
+    float* dx = reinterpret_cast<float*>(c->pos4);  // 16 bytes per particle of capacity
+    launch_positions(c->P, c->rec[c->cur], md, dx, c->st);
+    launch_positions(c->P, orec, mo, dx + 3 * md, c->st);
     GP_CUDA(c, cudaMemcpyAsync(x3, dx, sizeof(float) * 3 * m, cudaMemcpyDeviceToHost, c->st));
   }
   GP_CUDA(c, cudaStreamSynchronize(c->st));
@@ -1426,6 +1608,11 @@ gp_status gp_load_particles(gp_ctx* c, int64_t n, const int32_t* grain, const in
   c->n_live = n;
   c->step = step;
   c->keys_valid = false;
+  int64_t nfz = 0;
+  for (int64_t i = 0; i < n; ++i) nfz += state[i] == ST_FROZEN;
+  c->hst->n_frozen = (unsigned long long)nfz;
+  s = obs_reset(c);  // every particle is in the dynamic store now
+  if (s) return s;
   return push_counts(c);
 }
 

@@ -640,6 +640,23 @@ struct DevStats {
   unsigned long long n_mlist;      // sites melted by the last melting pass
   unsigned long long removed;      // particles removed by the last melting pass
   unsigned long long renucleated;  // re-nucleations of dormant seeds (cumulative)
+  unsigned long long obs_new;      // FROZEN records listed by the last obstacle flush
+};
+
+// ---------------------------------------------------------------------------------
+// obstacle store of a single run.  A FROZEN particle never moves again (Sec. 2.1.2:
+// points of two grains that meet stop for good and form the grain boundary), so it
+// need not be reordered, gathered and re-emitted every step.  Flushes move the FROZEN
+// records of the dynamic store into the obstacle store, which keeps them ordered by
+// cell key with their positions and its own cell table (entries in the format of the
+// dynamic table; a count of zero marks an empty segment, no stamp).  The contact
+// search reads both tables.
+// ---------------------------------------------------------------------------------
+struct Obs {
+  const uint4* tab;
+  const uint32_t* keys;
+  const float4* pos;
+  int64_t n;
 };
 
 // warp-aggregated 64-bit counter increment
@@ -662,7 +679,7 @@ __device__ __forceinline__ void warp_add(unsigned long long* ctr, unsigned int v
 // kernel ids for the optional CUDA-event timing
 enum KernelId : int {
   K_HIST = 0, K_ONESWEEP, K_KEYS, K_BUILD, K_ADVANCE, K_EMIT, K_NUCLEATE, K_GRAIN_MAP,
-  K_SEED, K_CONTACT, K_CELLS, K_FINALIZE, K_GROUP, K_COUNT
+  K_SEED, K_CONTACT, K_CELLS, K_FINALIZE, K_GROUP, K_OBS, K_COUNT
 };
 
 struct ProfHook {

@@ -143,6 +143,32 @@ __device__ __forceinline__ uint32_t nib_prefix(uint32_t z, uint32_t w, int p) {
   return nib_sum8(z & low_nibbles(p)) + nib_sum8(w & low_nibbles(max(p - 8, 0)));
 }
 
+// Candidate range [i, end) of the cells c0..c1 of one row of a segment whose table entry
+// is e: from the 4-bit counts (masks mz0/mw0 of the cells before c0, rz/rw of the cells
+// c0..c1), or, when a count is saturated, by scanning the segment's keys for klo..khi.
+// Returns false when the range is empty.
+template <class K>
+__device__ __forceinline__ bool row_range(const uint4 e, uint32_t mz0, uint32_t mw0, uint32_t rz,
+                                          uint32_t rw, K klo, K khi, const K* __restrict__ skeys,
+                                          int64_t n, uint32_t& i, uint32_t& end) {
+  if (!(e.y & 0x8000u)) {
+    const uint32_t cnt = byte_sum(nib_pairs(e.z & rz) + nib_pairs(e.w & rw));
+    if (cnt == 0) return false;  // cells c0..c1 of this row are empty
+    i = e.x + byte_sum(nib_pairs(e.z & mz0) + nib_pairs(e.w & mw0));
+    end = i + cnt;
+  } else {
+    // a cell holds 15 or more particles: locate the cells by their keys
+    i = e.x;
+    end = e.x + (e.y & kSegMaxCount);
+    while (i < end && __ldg(skeys + i) < klo) ++i;
+    uint32_t e2 = i;
+    while (e2 < end && __ldg(skeys + e2) <= khi) ++e2;
+    end = e2;
+  }
+  if ((int64_t)end > n) end = (uint32_t)n;
+  return i < end;
+}
+
 // Finds the sorted particles i of another grain strictly closer than the contact
 // radius to p, among the particles of the 3x3x3 cells around (cx, cy, cz) of run
 // geometry gm.  gw is the pos4.w word of the querying particle (grain and run):
@@ -150,7 +176,9 @@ __device__ __forceinline__ uint32_t nib_prefix(uint32_t z, uint32_t w, int p) {
 // PAIRS == false: returns at the first one.  PAIRS == true: visits all of them and
 // appends the pairs (idj, ids[i]) with idj < ids[i] to pairs (up to pair_cap,
 // counted in *npairs).  Returns whether any was found.
-template <bool PAIRS, class K, bool TILED>
+// OBS == true (one run, first hit only): the rows of the obstacle store's table, at
+// the same segment index, are searched beside those of the dynamic table.
+template <bool PAIRS, class K, bool TILED, bool OBS = false>
 __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                              const uint4* __restrict__ tab, uint32_t stamp,
                                              const K* __restrict__ skeys,
@@ -159,7 +187,9 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                              const uint32_t* __restrict__ ids = nullptr,
                                              uint32_t idj = 0, int32_t* pairs = nullptr,
                                              int64_t pair_cap = 0,
-                                             unsigned long long* npairs = nullptr) {
+                                             unsigned long long* npairs = nullptr,
+                                             const Obs* ob = nullptr) {
+  static_assert(!(OBS && PAIRS), "the obstacle layer is searched for first hits");
   bool hit = false;
   const int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm.nc[0] - 1);
   const int y0 = max(cy - 1, 0), y1 = min(cy + 1, gm.nc[1] - 1);
@@ -177,42 +207,40 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
         const uint32_t sg = TILED ? seg_tiled(gm, sgi, y, z)
                                   : ((uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y) *
                                             (uint32_t)gm.nsx + (uint32_t)sgi;
+        const K klo = (K)gm.key0 +
+                      (K)(TILED ? (sg << kSegShift) + (uint32_t)c0
+                                : ((uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y) *
+                                          (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
+        const K khi = klo + (K)(c1 - c0);
         const uint4 e = __ldg(rtab + sg);
-        if ((e.y >> 16) != stamp) continue;
         uint32_t i, end;
-        if (!(e.y & 0x8000u)) {
-          const uint32_t cnt = byte_sum(nib_pairs(e.z & rz) + nib_pairs(e.w & rw));
-          if (cnt == 0) continue;  // cells c0..c1 of this row are empty
-          i = e.x + byte_sum(nib_pairs(e.z & mz0) + nib_pairs(e.w & mw0));
-          end = i + cnt;
-        } else {
-          // a cell holds 15 or more particles: locate the cells by their keys
-          const K klo = (K)gm.key0 +
-                        (K)(TILED ? (sg << kSegShift) + (uint32_t)c0
-                                  : ((uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y) *
-                                            (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
-          const K khi = klo + (K)(c1 - c0);
-          i = e.x;
-          end = e.x + (e.y & kSegMaxCount);
-          while (i < end && __ldg(skeys + i) < klo) ++i;
-          uint32_t e2 = i;
-          while (e2 < end && __ldg(skeys + e2) <= khi) ++e2;
-          end = e2;
-        }
-        if ((int64_t)end > n) end = (uint32_t)n;
-        for (; i < end; ++i) {
-          const float4 o = __ldg(pos4 + i);
-          if (__float_as_int(o.w) == gw) continue;
-          if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) {
-            if (!PAIRS) return true;
-            hit = true;
-            const uint32_t idi = ids[i];
-            if (idj < idi) {
-              const unsigned long long k = atomicAdd(npairs, 1ull);
-              if ((int64_t)k < pair_cap) {
-                pairs[2 * k] = (int32_t)idj;
-                pairs[2 * k + 1] = (int32_t)idi;
+        if ((e.y >> 16) == stamp && row_range<K>(e, mz0, mw0, rz, rw, klo, khi, skeys, n, i, end)) {
+          for (; i < end; ++i) {
+            const float4 o = __ldg(pos4 + i);
+            if (__float_as_int(o.w) == gw) continue;
+            if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) {
+              if (!PAIRS) return true;
+              hit = true;
+              const uint32_t idi = ids[i];
+              if (idj < idi) {
+                const unsigned long long k = atomicAdd(npairs, 1ull);
+                if ((int64_t)k < pair_cap) {
+                  pairs[2 * k] = (int32_t)idj;
+                  pairs[2 * k + 1] = (int32_t)idi;
+                }
               }
+            }
+          }
+        }
+        if constexpr (OBS) {
+          const uint4 eo = __ldg(ob->tab + sg);
+          if ((eo.y & kSegMaxCount) != 0 &&
+              row_range<uint32_t>(eo, mz0, mw0, rz, rw, (uint32_t)klo, (uint32_t)khi, ob->keys,
+                                  ob->n, i, end)) {
+            for (; i < end; ++i) {
+              const float4 o = __ldg(ob->pos + i);
+              if (__float_as_int(o.w) == gw) continue;
+              if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) return true;
             }
           }
         }
@@ -540,14 +568,15 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
 // ---------------------------------------------------------------------------------
 // k_advance: contact freeze, growth, advance, spawn claims (sorted store, in place)
 // ---------------------------------------------------------------------------------
-template <bool BATCH, class K, bool PER = false>
+template <bool BATCH, class K, bool PER = false, bool OBS = false>
 __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
                                                  const K* __restrict__ skeys,
                                                  const uint4* __restrict__ tab,
                                                  uint32_t stamp, int64_t n,
                                                  const uint32_t* __restrict__ act, Claims C,
-                                                 int32_t* __restrict__ site_slot, DevStats* st) {
+                                                 int32_t* __restrict__ site_slot, DevStats* st,
+                                                 Obs ob) {
   if constexpr (BATCH) {
     n = (int64_t)st->n_live;
     stamp = (uint32_t)st->stamp;
@@ -583,7 +612,8 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
       if constexpr (PER)
         hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
       else
-        hit = contact_scan<false, K, true>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        hit = contact_scan<false, K, true, OBS>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy,
+                                                cz, nullptr, 0, nullptr, 0, nullptr, &ob);
       Rec r = rec_unpack(rs[j]);
       g = r.grain;
       if (hit) {
@@ -1727,7 +1757,7 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
 }
 
 // every grouped record to its sorted position: record, position, key, source index and
-// ACTIVE flag (one thread per record)
+// state byte (1 ACTIVE, 2 FROZEN, 0 otherwise; one thread per record)
 __global__ void __launch_bounds__(256) k_group_gather(
     Params P, const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ dest, int64_t n, const int4* __restrict__ rin,
@@ -1750,7 +1780,7 @@ __global__ void __launch_bounds__(256) k_group_gather(
   pos4[j] = make_float4(pw.x, pw.y, pw.z, __int_as_float(r.grain));
   skeys[j] = __ldg(gkey + i);
   if (svals) svals[j] = o;
-  sact[j] = r.state == ST_ACTIVE ? 1 : 0;
+  sact[j] = r.state == ST_ACTIVE ? 1 : (r.state == ST_FROZEN ? 2 : 0);
 }
 
 // list of the ACTIVE sorted indices (one reservation per 1024 records; each warp's
@@ -1766,7 +1796,7 @@ __global__ void __launch_bounds__(256) k_act_list(const uint8_t* __restrict__ sa
 #pragma unroll
     for (int it = 0; it < kBuildItems; ++it) {
       const int64_t j = j0 + it * 256 + threadIdx.x;
-      if (j < n && __ldg(sact + j)) amask |= 1u << it;
+      if (j < n && __ldg(sact + j) == 1) amask |= 1u << it;
     }
     uint32_t tot;
     const uint32_t ofs = bscan256(__popc(amask), s_warp, tot);
@@ -1781,6 +1811,179 @@ __global__ void __launch_bounds__(256) k_act_list(const uint8_t* __restrict__ sa
       o += __popc(b);
     }
   }
+}
+
+// ---------------------------------------------------------------------------------
+// obstacle flush (one run): the FROZEN records of the ordered dynamic store join the
+// obstacle store.
+//   k_obs_count  FROZEN records per tile of kObsTile ordered records (state bytes of
+//                the gather), summed into DevStats::obs_new
+//   k_scan_sums  exclusive scan of the tile counts
+//   k_obs_list   the ordered indices of the FROZEN records, in key order; each is
+//                marked REMOVED in the ordered store, so that the emit drops it (the
+//                contact search of the step still finds its position in the dynamic
+//                table, and in the obstacle table after the merge)
+//   k_obs_split  merge-path split of every output tile of the merge
+//   k_obs_merge  stable merge by cell key of the obstacle store (first among equal
+//                keys) with the listed records: keys, positions, records (FROZEN)
+//   k_obs_table  the merged store's cell table: one entry per occupied segment
+// The old obstacle store is read and a second one written, so its traffic is about
+// 2 x 36 bytes per obstacle record, in coalesced runs, once per flush.
+// ---------------------------------------------------------------------------------
+constexpr int kObsItems = 32;                // ordered records per thread of the listing
+constexpr int kObsTile = 256 * kObsItems;    // records per tile of the listing
+constexpr int kMergeTile = 2048;             // merged outputs per CTA (8 per thread)
+
+// state bytes of the kObsItems ordered records j0 .. j0 + 31, four per word (0 past n)
+__device__ __forceinline__ void obs_bytes(const uint8_t* __restrict__ sact, int64_t n, int64_t j0,
+                                          uint32_t w[kObsItems / 4]) {
+  if (j0 + kObsItems <= n) {
+    const uint4* p = reinterpret_cast<const uint4*>(sact + j0);  // j0 is a multiple of 32
+    const uint4 a = __ldg(p), b = __ldg(p + 1);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < kObsItems / 4; ++q) {
+      uint32_t v = 0;
+      for (int b = 0; b < 4; ++b) {
+        const int64_t j = j0 + 4 * q + b;
+        if (j < n) v |= (uint32_t)__ldg(sact + j) << (8 * b);
+      }
+      w[q] = v;
+    }
+  }
+}
+
+// FROZEN records among four state bytes (0, 1 or 2): the bytes with bit 1 set
+__device__ __forceinline__ uint32_t frozen4(uint32_t v) { return __popc((v >> 1) & 0x01010101u); }
+
+__global__ void __launch_bounds__(256) k_obs_count(const uint8_t* __restrict__ sact, int64_t n,
+                                                   uint32_t* __restrict__ tcnt, DevStats* st) {
+  __shared__ uint32_t s_warp[8];
+  const int64_t j0 = (int64_t)blockIdx.x * kObsTile + (int64_t)threadIdx.x * kObsItems;
+  uint32_t w[kObsItems / 4], c = 0;
+  obs_bytes(sact, n, j0, w);
+#pragma unroll
+  for (int q = 0; q < kObsItems / 4; ++q) c += frozen4(w[q]);
+  uint32_t tot;
+  bscan256(c, s_warp, tot);
+  if (threadIdx.x == 0) {
+    tcnt[blockIdx.x] = tot;
+    if (tot) atomicAdd(&st->obs_new, (unsigned long long)tot);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_obs_list(const uint8_t* __restrict__ sact, int64_t n,
+                                                  const uint32_t* __restrict__ tofs,
+                                                  int4* __restrict__ rs,
+                                                  uint32_t* __restrict__ flist) {
+  __shared__ uint32_t s_warp[8];
+  const int64_t j0 = (int64_t)blockIdx.x * kObsTile + (int64_t)threadIdx.x * kObsItems;
+  uint32_t w[kObsItems / 4], c = 0;
+  obs_bytes(sact, n, j0, w);
+#pragma unroll
+  for (int q = 0; q < kObsItems / 4; ++q) c += frozen4(w[q]);
+  uint32_t tot;
+  uint32_t o = tofs[blockIdx.x] + bscan256(c, s_warp, tot);
+  if (!c) return;
+#pragma unroll
+  for (int q = 0; q < kObsItems / 4; ++q) {
+    uint32_t v = (w[q] >> 1) & 0x01010101u;
+    while (v) {
+      const int b = (__ffs(v) - 1) >> 3;
+      v &= v - 1;
+      const int64_t j = j0 + 4 * q + b;
+      flist[o++] = (uint32_t)j;
+      int* zp = &rs[j].z;
+      *zp = (int)(((uint32_t)*zp & ~(3u << 20)) | ((uint32_t)ST_REMOVED << 20));
+    }
+  }
+}
+
+// stable merge order of A (obstacle keys, na) and B (keys of the listed records, nb):
+// A[i] comes before B[j] iff A[i] <= B[j].  The split of diagonal d is the number of
+// A elements among the first d outputs.
+__device__ __forceinline__ uint32_t fkey(const uint32_t* __restrict__ skeys,
+                                         const uint32_t* __restrict__ flist, int64_t j) {
+  return __ldg(skeys + __ldg(flist + j));
+}
+
+__global__ void __launch_bounds__(256) k_obs_split(const uint32_t* __restrict__ okey, int64_t na,
+                                                   const uint32_t* __restrict__ skeys,
+                                                   const uint32_t* __restrict__ flist, int64_t nb,
+                                                   uint32_t* __restrict__ split, int64_t ns) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns) return;
+  const int64_t d = min(t * (int64_t)kMergeTile, na + nb);
+  int64_t lo = max((int64_t)0, d - nb), hi = min(d, na);
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(okey + mid) <= fkey(skeys, flist, d - 1 - mid)) lo = mid + 1;
+    else hi = mid;
+  }
+  split[t] = (uint32_t)lo;
+}
+
+__global__ void __launch_bounds__(256) k_obs_merge(
+    const uint32_t* __restrict__ okey, const float4* __restrict__ opos,
+    const int4* __restrict__ orec, int64_t na, const uint32_t* __restrict__ skeys,
+    const float4* __restrict__ pos4, const int4* __restrict__ rs,
+    const uint32_t* __restrict__ flist, int64_t nb, const uint32_t* __restrict__ split,
+    uint32_t* __restrict__ okey2, float4* __restrict__ opos2, int4* __restrict__ orec2) {
+  __shared__ uint32_t s_key[kMergeTile];  // the tile's A keys, then its B keys
+  __shared__ uint32_t s_src[kMergeTile];  // source of each output: A index, or B | 2^31
+  const int64_t t = blockIdx.x;
+  const int64_t d0 = t * kMergeTile, d1 = min(d0 + kMergeTile, na + nb);
+  const int64_t i0 = split[t], i1 = split[t + 1];
+  const int64_t j0 = d0 - i0, j1 = d1 - i1;
+  const int la = (int)(i1 - i0), lb = (int)(j1 - j0);
+  for (int q = threadIdx.x; q < la; q += 256) s_key[q] = __ldg(okey + i0 + q);
+  for (int q = threadIdx.x; q < lb; q += 256) s_key[la + q] = fkey(skeys, flist, j0 + q);
+  __syncthreads();
+  const int dl = threadIdx.x * (kMergeTile / 256);
+  if (dl < la + lb) {
+    int lo = max(0, dl - lb), hi = min(dl, la);
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s_key[mid] <= s_key[la + dl - 1 - mid]) lo = mid + 1;
+      else hi = mid;
+    }
+    int ia = lo, ib = dl - lo;
+#pragma unroll
+    for (int u = 0; u < kMergeTile / 256; ++u) {
+      const int k = dl + u;
+      if (k >= la + lb) break;
+      const bool from_a = ib >= lb || (ia < la && s_key[ia] <= s_key[la + ib]);
+      s_src[k] = from_a ? (uint32_t)ia++ : (0x80000000u | (uint32_t)ib++);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < la + lb; k += 256) {
+    const uint32_t v = s_src[k];
+    const int64_t out = d0 + k;
+    if (!(v & 0x80000000u)) {
+      okey2[out] = s_key[v];
+      opos2[out] = __ldg(opos + i0 + v);
+      orec2[out] = __ldg(orec + i0 + v);
+    } else {
+      const uint32_t b = v & 0x7fffffffu;
+      const uint32_t jj = __ldg(flist + j0 + b);
+      okey2[out] = s_key[la + b];
+      opos2[out] = __ldg(pos4 + jj);
+      int4 r = __ldg(rs + jj);  // marked REMOVED by the listing: restore FROZEN
+      r.z = (int)(((uint32_t)r.z & ~((3u << 20) | (1u << 24))) | ((uint32_t)ST_FROZEN << 20));
+      orec2[out] = r;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_obs_table(Params P, const uint32_t* __restrict__ okey,
+                                                   int64_t n, uint4* __restrict__ otab,
+                                                   uint32_t* err) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  seg_build<uint32_t, true>(P.geo, okey, j, n, __ldg(okey + j), otab, 1u, err);
 }
 
 // Runs one bounded wait whose word nothing ever publishes (one thread), with a
@@ -1803,6 +2006,31 @@ __global__ void k_selftest_wait(int which, uint32_t limit, uint32_t* words, uint
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
+int64_t obs_list_tiles(int64_t n) { return (n + kObsTile - 1) / kObsTile; }
+int64_t obs_merge_tiles(int64_t n) { return (n + kMergeTile - 1) / kMergeTile; }
+
+void launch_obs_list(const uint8_t* sact, int64_t n, uint32_t* tcnt, int4* rs, uint32_t* flist,
+                     DevStats* dst, cudaStream_t st) {
+  const int64_t nt = obs_list_tiles(n);
+  if (nt <= 0) return;
+  cudaMemsetAsync(&dst->obs_new, 0, sizeof(unsigned long long), st);
+  k_obs_count<<<(unsigned)nt, 256, 0, st>>>(sact, n, tcnt, dst);
+  k_scan_sums<<<1, 256, 0, st>>>(tcnt, nt);
+  k_obs_list<<<(unsigned)nt, 256, 0, st>>>(sact, n, tcnt, rs, flist);
+}
+
+void launch_obs_merge(const Params& P, const uint32_t* okey, const float4* opos, const int4* orec,
+                      int64_t na, const uint32_t* skeys, const float4* pos4, const int4* rs,
+                      const uint32_t* flist, int64_t nb, uint32_t* split, uint32_t* okey2,
+                      float4* opos2, int4* orec2, uint4* otab, uint32_t* err, cudaStream_t st) {
+  const int64_t nm = obs_merge_tiles(na + nb);
+  if (nm <= 0) return;
+  k_obs_split<<<blocks(nm + 1), 256, 0, st>>>(okey, na, skeys, flist, nb, split, nm + 1);
+  k_obs_merge<<<(unsigned)nm, 256, 0, st>>>(okey, opos, orec, na, skeys, pos4, rs, flist, nb,
+                                            split, okey2, opos2, orec2);
+  k_obs_table<<<blocks(na + nb), 256, 0, st>>>(P, okey2, na + nb, otab, err);
+}
+
 void launch_selftest_wait(int which, uint32_t limit, uint32_t* words, uint32_t* err,
                           cudaStream_t st) {
   k_selftest_wait<<<1, 1, 0, st>>>(which, limit, words, err);
@@ -1829,17 +2057,21 @@ void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals,
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
                     const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
-                    cudaStream_t st) {
+                    cudaStream_t st, const Obs* ob) {
   if (n <= 0) return;
+  const Obs none{};
   if (batch)
     k_advance<true, uint64_t><<<persistent(n, 256, P.launch.advance_ctas), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst);
+        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst, none);
   else if (P.periodic)
     k_advance<false, uint32_t, true><<<blocks(n), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst);
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, none);
+  else if (ob && ob->n > 0)
+    k_advance<false, uint32_t, false, true><<<blocks(n), 256, 0, st>>>(
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, *ob);
   else
     k_advance<false, uint32_t><<<blocks(n), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst);
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, none);
 }
 
 int64_t emit_tiles(int64_t n) { return (n + 256 * kEmitItems - 1) / (256 * kEmitItems); }

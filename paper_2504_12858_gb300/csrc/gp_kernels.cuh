@@ -24,10 +24,11 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
                         int4* rout, float4* pos4, uint32_t* skeys, uint32_t* svals,
                         uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
                         int sms, ProfHook* prof, cudaStream_t st);
+// ob (one run, optional): the obstacle store, searched beside the dynamic table
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
                     const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
-                    cudaStream_t st);
+                    cudaStream_t st, const Obs* ob = nullptr);
 int64_t emit_tiles(int64_t n);
 void launch_link_reached(bool batch, const Params& P, const Reached& R,
                          unsigned long long* linked, int sms, cudaStream_t st);
@@ -92,6 +93,21 @@ void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstat
                        const uint32_t* ids, const uint32_t* skeys, const uint4* tab,
                        int64_t n, uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
                        unsigned long long* npairs, cudaStream_t st);
+
+// obstacle flush of a single run (see gp_kernels.cu).  launch_obs_list lists, in key
+// order, the FROZEN records of the ordered store rs (n records, state bytes sact) into
+// flist, marks them REMOVED in rs and counts them in dst->obs_new; tcnt holds
+// obs_list_tiles(n) words.  launch_obs_merge merges the obstacle store (okey, opos,
+// orec; na records) with the nb listed records into okey2, opos2, orec2 and writes
+// their cell table otab; split holds obs_merge_tiles(na + nb) + 1 words.
+int64_t obs_list_tiles(int64_t n);
+int64_t obs_merge_tiles(int64_t n);
+void launch_obs_list(const uint8_t* sact, int64_t n, uint32_t* tcnt, int4* rs, uint32_t* flist,
+                     DevStats* dst, cudaStream_t st);
+void launch_obs_merge(const Params& P, const uint32_t* okey, const float4* opos, const int4* orec,
+                      int64_t na, const uint32_t* skeys, const float4* pos4, const int4* rs,
+                      const uint32_t* flist, int64_t nb, uint32_t* split, uint32_t* okey2,
+                      float4* opos2, int4* orec2, uint4* otab, uint32_t* err, cudaStream_t st);
 
 // bounded-wait self-test: words holds 512 zeroed uint32 (a status array of two
 // tiles, or one claim bucket), err one zeroed word

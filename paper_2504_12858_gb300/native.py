@@ -93,6 +93,9 @@ SIGNATURES = {
     "gp_set_solute_grid": (C.c_int, [_P, C.POINTER(gp_solute_grid)]),
     "gp_set_melting": (C.c_int, [_P, C.c_int32]),
     "gp_set_periodic": (C.c_int, [_P, C.c_int32]),
+    "gp_set_obstacle_store": (C.c_int, [_P, C.c_int32]),
+    "gp_inspect_order": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P, _P, C.POINTER(C.c_int64),
+                                   _P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]),
     "gp_nucleation_sites": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "gp_step": (C.c_int, [_P, C.c_int32]),
     "gp_grain_map": (C.c_int, [_P, C.POINTER(gp_voxel_grid), _P, C.c_int32]),
@@ -311,6 +314,27 @@ class Sim:
     def gp_set_periodic(self, axes):
         """Periodic axes, a bit per axis (1 = x, 2 = y, 4 = z)."""
         self._check(load().gp_set_periodic(self._h, int(axes)))
+
+    def gp_set_obstacle_store(self, mode=1):
+        """0 off, 1 automatic (default), 2 a flush every step with FROZEN particles."""
+        self._check(load().gp_set_obstacle_store(self._h, int(mode)))
+
+    def gp_inspect_order(self, which=0):
+        """Ordering of the next step (which = 0) or the obstacle store (1): dict of
+        keys_in, keys_sorted, src (uint32 numpy), table (nseg, 4) uint32 and stamp."""
+        L = load()
+        n, nseg, stamp = C.c_int64(0), C.c_int64(0), C.c_uint32(0)
+        self._check(L.gp_inspect_order(self._h, int(which), 0, None, None, None, C.byref(n),
+                                       None, 0, C.byref(nseg), C.byref(stamp)))
+        m = int(n.value)
+        out = dict(keys_in=np.zeros(m, np.uint32), keys_sorted=np.zeros(m, np.uint32),
+                   src=np.zeros(m, np.uint32), table=np.zeros((int(nseg.value), 4), np.uint32))
+        self._check(L.gp_inspect_order(self._h, int(which), m, _ptr(out["keys_in"]),
+                                       _ptr(out["keys_sorted"]), _ptr(out["src"]), C.byref(n),
+                                       _ptr(out["table"]), int(nseg.value), C.byref(nseg),
+                                       C.byref(stamp)))
+        out["stamp"] = int(stamp.value)
+        return out
 
     def gp_set_melting(self, enable=True):
         self._check(load().gp_set_melting(self._h, 1 if enable else 0))

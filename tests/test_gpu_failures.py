@@ -42,9 +42,9 @@ def _small_sim(**kw):
 
 
 def test_claim_pool_exhausted_is_hash_full():
-    # a growing grain claims a new 8^3-site block every few lattice shells: two
-    # blocks last a few steps only
-    w, s = _small_sim(claim_blocks=2)
+    # the nucleus and its six first targets take four 8^3-site blocks; a grain
+    # growing past eight lattice shells needs more than eight blocks
+    w, s = _small_sim(claim_blocks=8)
     with pytest.raises(native.GPError) as e:
         s.gp_step(200)
     assert e.value.status == GP_ERR_HASH_FULL
