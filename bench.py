@@ -16,7 +16,18 @@ Multi-GPU (torchrun): every rank runs an independent replica of the workload
 barriers and the maximum time over ranks is used.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the first grains of the fixture) on the host cores.
+workload on the host cores: one oracle process per core, each on its own grains
+of the fixture, timed together.
+
+The line also reports, beside the fixture, the two workloads of the method's
+applications at their stated sizes: competitive columnar growth in a slab
+(configuration 2) and growth from the fusion line of the weld plate
+(configuration 3 as the method runs it).
+
+--ncu-digest CSV LOG turns a one-pass ncu capture (dram bytes and durations of
+every launch of `bench.py ... --no-e2e --profile-warmup`) and that command's plain
+JSON line into the per-unit DRAM bytes of every timed entry; the result is written
+to profiles/ncu_traffic.json with the digest of the kernel sources it was taken on.
 """
 from __future__ import annotations
 
@@ -161,46 +172,99 @@ def kernel_sources_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per unit of `kernel` from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+def ncu_record():
+    """The committed per-unit DRAM figures (profiles/ncu_traffic.json), if they were
+    taken on the current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if d.get("sources_digest") != kernel_sources_digest():
-        return None
-    k = d.get("kernels", {}).get(kernel)
-    return None if k is None else float(k["dram_bytes_per_unit"])
+    return d if d.get("sources_digest") == kernel_sources_digest() else None
 
 
-def ncu_issue(kernel: str):
-    """Share of the issue slots busy in `kernel` (ncu smsp__issue_active, small-case
-    capture of the same sources), if recorded for the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
-        d = json.load(open(p))
-    except (OSError, ValueError):
+def step_dram_bytes(prof, psteps):
+    """DRAM bytes per particle-step of a run: every timed entry's per-unit DRAM bytes
+    (from the committed capture) times the units this run processed, summed, divided
+    by the run's particle-steps.  None if the capture does not cover every entry."""
+    d = ncu_record()
+    if d is None or not prof or psteps <= 0:
         return None
-    if d.get("sources_digest") != kernel_sources_digest():
-        return None
-    k = d.get("kernels", {}).get(kernel, {})
-    return None if "issue_slots_busy" not in k else float(k["issue_slots_busy"])
+    per = d.get("entries", {})
+    tot = 0.0
+    for k in prof:
+        if k["total_ms"] <= 0:
+            continue
+        if k["name"] not in per:
+            return None
+        tot += per[k["name"]]["dram_bytes_per_unit"] * k["units"]
+    return tot / psteps
 
 
-def ncu_step_traffic():
-    """DRAM bytes per particle-step of the whole step (every step kernel), from the
-    committed one-pass ncu capture of the default bench's timed steps, if it was taken
-    on the current kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
-        d = json.load(open(p))
-    except (OSError, ValueError):
-        return None
-    if d.get("sources_digest") != kernel_sources_digest() or "step" not in d:
-        return None
-    return float(d["step"]["dram_bytes_per_particle_step"])
+# profile entry -> the kernels it times; k_scan_sums belongs to the entry of the kernel
+# launched before it (group: k_scan_blocks; obstacle: k_obs_count)
+ENTRY_KERNELS = {
+    "group": ("k_group_count", "k_scan_blocks", "k_group_scatter"),
+    "build": ("k_group_order", "k_group_gather", "k_act_list"),
+    "advance": ("k_advance",),
+    "emit": ("k_emit", "k_emit_check"),
+    "obstacle": ("k_obs_count", "k_obs_list", "k_obs_split", "k_obs_merge", "k_obs_table"),
+    "nucleate": ("k_nucleate",),
+    "finalize": ("k_finalize",),
+    "keys": ("k_keys",),
+}
+
+
+def ncu_digest(csv_path, log_path):
+    """Per-unit DRAM bytes of every timed entry from an ncu capture of all launches of
+    `bench.py ... --no-e2e --profile-warmup` and that command's plain JSON line."""
+    import csv
+    import re
+    line = [json.loads(x) for x in open(log_path) if x.startswith('{"metric"')][-1]
+    units = {k: v["units"] for k, v in line["kernels"].items()}
+    launches = {}
+    rows = [r for r in csv.reader(open(csv_path)) if len(r) > 10]
+    head = rows[0]
+    col = {n: head.index(n) for n in ("ID", "Kernel Name", "Metric Name", "Metric Value")}
+    for r in rows[1:]:
+        try:
+            i = int(r[col["ID"]])
+        except ValueError:
+            continue
+        m = re.search(r"\b(k_[a-z0-9_]+)", r[col["Kernel Name"]])
+        rec = launches.setdefault(i, {"kernel": m.group(1) if m else "?", "bytes": 0.0,
+                                      "ns": 0.0})
+        v = float(r[col["Metric Value"]].replace(",", ""))
+        name = r[col["Metric Name"]]
+        if name.startswith("dram__bytes"):
+            rec["bytes"] += v
+        elif name == "gpu__time_duration.sum":
+            rec["ns"] += v
+    owner = {k: e for e, ks in ENTRY_KERNELS.items() for k in ks}
+    per, prev = {}, None
+    for i in sorted(launches):
+        k = launches[i]["kernel"]
+        e = owner.get(k)
+        if k == "k_scan_sums":
+            e = "obstacle" if prev == "k_obs_count" else "group"
+        prev = k
+        if e is None:
+            continue
+        agg = per.setdefault(e, {"bytes": 0.0, "ns": 0.0, "launches": 0})
+        agg["bytes"] += launches[i]["bytes"]
+        agg["ns"] += launches[i]["ns"]
+        agg["launches"] += 1
+    out = {"sources_digest": kernel_sources_digest(), "entries": {},
+           "capture": line["config"], "profiled_particle_steps": line.get("profiled_particle_steps")}
+    for e, agg in per.items():
+        if units.get(e):
+            out["entries"][e] = {"dram_bytes_per_unit": round(agg["bytes"] / units[e], 2),
+                                 "units": units[e], "launches": agg["launches"],
+                                 "ncu_ms": round(agg["ns"] / 1e6, 3)}
+    tot = sum(a["bytes"] for a in per.values())
+    if line.get("profiled_particle_steps"):
+        out["dram_bytes_per_particle_step"] = round(tot / line["profiled_particle_steps"], 1)
+    return out
 
 
 # algorithmic bytes of one particle-step for the whole step: read and write the
@@ -211,13 +275,14 @@ B_ALG_STEP = 48
 # ----------------------------------------------------------------------------------
 # CPU oracle on a bounded sample (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------------
-def oracle_sample(n_grains_sample: int, n0: int):
+def oracle_sample(n_grains_sample: int, n0: int, first: int = 0):
     import oracle
     w = fixture(10000, n0)
     o = oracle.Oracle(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L)
     g = w.grid
     o.set_thermal_grid(g["T"], g["origin"], g["spacing"], g["vel"])
-    o.add_grains(w.seeds[:n_grains_sample], w.quats[:n_grains_sample], nucleate=False)
+    sl = slice(first, first + n_grains_sample)
+    o.add_grains(w.seeds[sl], w.quats[sl], nucleate=False)
     o.seed_shell(np.arange(n_grains_sample), n0)
     return o
 
@@ -230,30 +295,83 @@ def time_oracle(o, steps: int):
     return (o.stats()["particle_steps"] - before) / dt, dt
 
 
-def cpu_baseline(n_grains_sample=100, n0=50, steps=2):
-    o = oracle_sample(n_grains_sample, n0)
-    o.step(1)  # warm the allocator
-    rate, dt = time_oracle(o, steps)
-    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": (f"first {n_grains_sample} of the 1e4 grains of the same workload "
-                       f"(~{o.n_particles:.2e} particles), {steps} steps after 1 untimed step, "
-                       f"{dt:.1f} s of single-threaded FP64 work")}
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(k, n_grains, n0, warm, steps, barrier, q):
+    o = oracle_sample(n_grains, n0, first=k * n_grains)
+    o.step(warm)
+    before = o.stats()["particle_steps"]
+    barrier.wait()
+    t0 = time.perf_counter()
+    o.step(steps)
+    t1 = time.perf_counter()
+    q.put((o.stats()["particle_steps"] - before, t0, t1, o.n_particles))
+
+
+def oracle_all_cores(n_grains=60, n0=50, warm=1, steps=2, procs=None):
+    """One oracle process per host core, each on its own n_grains grains of the
+    fixture (disjoint), stepped together after a barrier: the particle-steps of all
+    processes over the time from the first start to the last finish.  Processes are
+    spawned (never forked from a process that holds a CUDA context)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    procs = min(procs, 10000 // n_grains)
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(k, n_grains, n0, warm, steps, barrier, q))
+          for k in range(procs)]
+    for p in ps:
+        p.start()
+    res = [q.get() for _ in ps]
+    for p in ps:
+        p.join()
+    units = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return units / span, span, procs, sum(r[3] for r in res)
+
+
+def cpu_baseline(n_grains_sample=60, n0=50, steps=2):
+    rate, span, procs, npart = oracle_all_cores(n_grains_sample, n0, 1, steps)
+    return {"value": rate, "unit": METRIC, "cores": procs, "kind": "oracle",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "sample": (f"{procs} oracle processes, one per host core, each on {n_grains_sample} "
+                       f"of the 1e4 grains of the same workload (disjoint, {npart:.2e} particles "
+                       f"in all), {steps} steps after 1 untimed step, {span:.1f} s wall from the "
+                       f"first start to the last finish")}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    o = oracle_sample(args.ref_grains, args.n0)
-    o.step(args.warmup)
-    rate, dt = time_oracle(o, args.steps)
-    cb = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-          "sample": (f"first {args.ref_grains} of the 1e4 grains of the same workload, "
-                     f"{args.steps} timed steps after {args.warmup} warm-up steps")}
+    rate, span, procs, npart = oracle_all_cores(args.ref_grains, args.n0, args.warmup,
+                                                args.steps)
+    cb = {"value": rate, "unit": METRIC, "cores": procs, "kind": "oracle",
+          "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+          "sample": (f"{procs} oracle processes (one per core), each on {args.ref_grains} of "
+                     f"the 1e4 grains of the same workload, {args.steps} timed steps after "
+                     f"{args.warmup} warm-up steps")}
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "ms_per_step": 1e3 * span / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "sample_grains": args.ref_grains},
+            "config": {"workload": WORKLOAD_NAME, "sample_grains_per_process": args.ref_grains,
+                       "processes": procs},
             "cpu_baseline": cb,
             "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -411,6 +529,74 @@ def batch_ensemble(dev, rank=0, world=1, serial_every=8, graph_steps=20):
     return out
 
 
+def _workload_run(w, steps, capacity, dev, **kw):
+    """Steps workload w on the GPU (after its set-up) and measures the timed steps
+    with CUDA events on the library's stream."""
+    import torch
+    from paper_2504_12858_gb300 import native
+    an, g = w.analytic, w.grid
+    s = native.Sim(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L, capacity=capacity,
+                   max_grains=len(w.seeds) + 16, device=dev,
+                   grid_nodes=int(np.prod(g["T"].shape)) if g else 0, **kw)
+    if an:
+        s.gp_set_thermal_analytic(an["T0"], an["G"], an["xref"], an["Tdot"])
+    if g:
+        s.gp_set_thermal_grid(g["T"], g["origin"], g["spacing"], g["vel"])
+    init = w.extra.get("particles")
+    s.gp_add_grains(w.seeds, w.quats, nucleate=init is None)
+    if init is not None:
+        s.gp_load_particles(init["grain"], init["site"], init["dir"], init["ell"], init["state"], 0)
+        gr, sr = w.extra["reached"]
+        s.gp_add_sites(gr, sr, reached=True, claimed=True)
+        s.gp_add_sites(*w.extra["claimed"], reached=False, claimed=True)
+    st0 = s.gp_stats()
+    s.gp_profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(s.stream)
+    s.gp_step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st1 = s.gp_stats()
+    prof = s.gp_profile_read()
+    s.close()
+    psteps = st1["particle_steps"] - st0["particle_steps"]
+    cross = st1["n_reached"] - st0["n_reached"]
+    peak, kind = measured_peak()
+    rate = psteps / (ms / 1e3)
+    return {"steps": steps, "ms_per_step": ms / steps, "particle_steps_per_s": rate,
+            "particles_start": st0["n_live"], "particles_end": st1["n_live"],
+            "frozen_end": st1["n_frozen"], "grains": st1["n_grains"],
+            "crossings_per_particle_step": cross / max(psteps, 1),
+            "algorithmic_frac": rate * B_ALG_STEP / 1e9 / peak, "peak_source": kind,
+            "kernels_ms_per_step": {k["name"]: round(k["total_ms"] / steps, 4) for k in prof}}
+
+
+def application_workloads(dev):
+    """Configurations 2 and 3 at their stated sizes: competitive columnar growth in the
+    1 x 1 x 0.05 mm slab (600 steps) and growth from the fusion line of the weld plate
+    (the base metal cut by the t = 0 liquidus, 2000 steps).  Set-up (input generation,
+    seeding, loading) is outside the timing."""
+    from paper_2504_12858_gb300 import inputs
+    out = {}
+    w = inputs.columnar_slab()
+    out["columnar_slab"] = dict(
+        workload="columnar_slab: 1x1x0.05 mm, 50 bottom seeds, G = 1e4 K/m, Tdot = 10 K/s, "
+                 "v = 1e-5 dT^2, h = 2 um, dt = 1 ms",
+        **_workload_run(w, w.steps, 2000000, dev, reached_capacity=6000000))
+    t0 = time.perf_counter()
+    w = inputs.weld_natural()
+    gen_s = time.perf_counter() - t0
+    out["weld_natural"] = dict(
+        workload="weld_natural: the 4x2x1 mm weld plate, base-metal grains cut by the t = 0 "
+                 "liquidus, particles on the fusion line heading into the melt",
+        input_generation_s=round(gen_s, 1),
+        **_workload_run(w, w.steps, 60000000, dev, reached_capacity=200000000,
+                        claim_blocks=3000000))
+    return out
+
+
 def run_native(args, rank, world, local_rank):
     import torch
     from paper_2504_12858_gb300 import native
@@ -444,11 +630,14 @@ def run_native(args, rank, world, local_rank):
     sim = make_sim()
     n_start = sim.gp_stats()["n_live"]
     stream = sim.stream
-
+    stw = sim.gp_stats()
+    if args.profile_warmup:       # capture mode: the profile covers the warm-up steps too
+        sim.gp_profile(True)
     sim.gp_step(args.warmup)
     torch.cuda.synchronize(dev)
     st0 = sim.gp_stats()
-    sim.gp_profile(True)
+    if not args.profile_warmup:
+        sim.gp_profile(True)
     clocks = ClockSampler(local_rank) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -476,27 +665,31 @@ def run_native(args, rank, world, local_rank):
     # start (the same warm-up steps untimed, then the same steps as the timed region):
     # the thermal table is copied from pinned host memory every step (as a coupled
     # thermal solver would supply it) and the step statistics are read back every step
-    sim = make_sim()
-    sim.gp_step(args.warmup)
     Th = torch.from_numpy(np.ascontiguousarray(g["T"])).pin_memory()
-    Th_np = Th.numpy()
-    torch.cuda.synchronize(dev)
-    barrier(world)
-    t0 = time.perf_counter()
-    sa = sim.gp_stats()
-    for _ in range(e2e_steps):
-        sim.gp_set_thermal_grid(Th_np, g["origin"], g["spacing"], g["vel"])
-        sim.gp_step(1)
-        sim.gp_stats()
-    torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    sb = sim.gp_stats()
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
-    e2e_units = float(sb["particle_steps"] - sa["particle_steps"])
-    e2e_ms, e2e_units = reduce_timing(e2e_s * 1e3, e2e_units, world)
-    e2e_value = e2e_units / (e2e_ms / 1e3)
+    e2e_value = None
+    if args.no_e2e:
+        e2e_steps = 0
+    else:
+        sim = make_sim()
+        sim.gp_step(args.warmup)
+        Th_np = Th.numpy()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        t0 = time.perf_counter()
+        sa = sim.gp_stats()
+        for _ in range(e2e_steps):
+            sim.gp_set_thermal_grid(Th_np, g["origin"], g["spacing"], g["vel"])
+            sim.gp_step(1)
+            sim.gp_stats()
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        sb = sim.gp_stats()
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        e2e_units = float(sb["particle_steps"] - sa["particle_steps"])
+        e2e_ms, e2e_units = reduce_timing(e2e_s * 1e3, e2e_units, world)
+        e2e_value = e2e_units / (e2e_ms / 1e3)
 
     if rank != 0:
         if not args.no_extras:
@@ -506,35 +699,44 @@ def run_native(args, rank, world, local_rank):
     # roofline of the dominant kernel (largest device time in the timed region)
     peak, peak_kind = measured_peak()
     dom = max(prof, key=lambda k: k["total_ms"]) if prof else None
+    rec = ncu_record()
     roof = None
+    nsteps_prof = args.steps + (args.warmup if args.profile_warmup else 0)
     if dom:
         achieved = dom["units"] * dom["bytes_per_unit"] / (dom["total_ms"] / 1e3) / 1e9
         # each timed entry runs once per step (some entries hold several kernels)
-        per_launch_units = dom["units"] / max(args.steps, 1)
-        tb = ncu_traffic(dom["name"])
+        per_launch_units = dom["units"] / max(nsteps_prof, 1)
+        ent = (rec or {}).get("entries", {}).get(dom["name"])
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": None if tb is None else tb * per_launch_units,
-                "issue_slots_busy": ncu_issue(dom["name"]),
+                "traffic": None if ent is None else ent["dram_bytes_per_unit"] * per_launch_units,
+                "traffic_source": None if ent is None else
+                "per-unit DRAM bytes of the 1 mm plate capture, scaled by this run's units",
+                "issue_slots_busy": None if ent is None else ent.get("issue_slots_busy"),
                 "algorithmic_bytes_per_launch": dom["bytes_per_unit"] * per_launch_units,
-                "avg_launch_ms": dom["total_ms"] / max(args.steps, 1)}
-    # the whole step against the copy bandwidth: measured DRAM bytes per particle-step
-    # (one-pass ncu capture of the default run) and the algorithmic 48 B
-    default_run = (args.grains, args.n0, tuple(args.plate), args.warmup, args.steps) == \
-        (10000, 50, (4.0, 2.0, 1.0), 3, 10)
-    sb = ncu_step_traffic() if default_run else None
+                "avg_launch_ms": dom["total_ms"] / max(nsteps_prof, 1)}
+    # the whole step against the copy bandwidth: DRAM bytes per particle-step (per-unit
+    # bytes of every entry from the committed small-plate capture, times this run's
+    # units) and the algorithmic 48 B
+    psteps_prof = float(st1["particle_steps"] - (stw if args.profile_warmup else st0)["particle_steps"])
+    sb = step_dram_bytes(prof, psteps_prof)
     step_roof = {"peak": peak, "unit": "GB/s", "peak_source": peak_kind,
                  "algorithmic_bytes_per_particle_step": B_ALG_STEP,
                  "algorithmic_frac": value * B_ALG_STEP / 1e9 / peak,
                  "dram_bytes_per_particle_step": sb,
-                 "dram_frac": None if sb is None else value * sb / 1e9 / peak}
+                 "dram_frac": None if sb is None else value * sb / 1e9 / peak,
+                 "dram_source": None if sb is None else
+                 "per-unit DRAM bytes of each timed entry from the 1 mm plate capture "
+                 "(profiles/ncu_traffic.json), times this run's units"}
     launches = sum(k["launches"] for k in prof)
     kernels = {k["name"]: {"launches": k["launches"], "ms": round(k["total_ms"], 3),
+                           "units": k["units"],
                            "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in prof),
                                                                1e-9), 4)} for k in prof}
     cb = cpu_baseline(args.cpu_grains, args.n0, 2) if (world == 1 and not args.no_cpu) else None
     adj = adjoint_cost(dev) if not args.no_extras else None
     bat = batch_ensemble(dev, rank, world) if not args.no_extras else None
+    apps = application_workloads(dev) if not args.no_extras else None
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -552,7 +754,9 @@ def run_native(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": METRIC, "steps": e2e_steps,
                     "h2d_bytes_per_step": int(Th.numel() * 4),
                     "d2h_bytes_per_step": 160},
-            "clocks": clk, "gpu_launches": launches, "adjoint": adj, "batch": bat}
+            "clocks": clk, "gpu_launches": launches, "adjoint": adj, "batch": bat,
+            "applications": apps, "obstacles_at_end": st1["n_frozen"],
+            "profiled_particle_steps": psteps_prof}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -573,12 +777,23 @@ def main():
                          "keep the grain density; used for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=0,
                     help="end-to-end steps (default: as many as --steps, on the same states)")
-    ap.add_argument("--cpu-grains", type=int, default=100)
-    ap.add_argument("--ref-grains", type=int, default=40)
+    ap.add_argument("--cpu-grains", type=int, default=60)
+    ap.add_argument("--ref-grains", type=int, default=60)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the adjoint-cost and batched-ensemble measurements")
+                    help="skip the adjoint-cost, batched-ensemble and application measurements")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end context")
+    ap.add_argument("--profile-warmup", action="store_true",
+                    help="capture mode: the per-kernel profile covers the warm-up steps too")
+    ap.add_argument("--ncu-digest", nargs=2, metavar=("CSV", "LOG"),
+                    help="write profiles/ncu_traffic.json from an ncu capture and its plain log")
     args = ap.parse_args()
+    if args.ncu_digest:
+        d = ncu_digest(*args.ncu_digest)
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json"), "w") as f:
+            json.dump(d, f, indent=1)
+        print(json.dumps(d))
+        return 0
     rank, world, local_rank = dist_env()
     if world > 1:
         import torch

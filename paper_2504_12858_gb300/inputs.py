@@ -18,6 +18,11 @@ random draw comes from numpy's PCG64 with the stated seed):
   FP32 grid in the frame of the source, 1e4 Voronoi seeds with random
   orientations, each seeded as an octahedral shell (the laser-welding
   application of Sec. 4.2, with an analytic field standing in for the CFD).
+* ``weld_natural``  - the same plate, field and seeds, with the base-metal grains
+  cut by the fusion line: each grain (Voronoi cell of its seed) starts as the
+  lattice sites of its own lattice lying in the solid within one spacing of the
+  t = 0 liquidus surface, with particles heading into the melt (the weld
+  application of Sec. 4.2, growth from the fusion boundary).
 * ``cet_runs``      - per-run parameters of an ensemble of cubes with columnar
   bottom seeds and bulk nucleation sites (Sec. 3.5 family).
 """
@@ -135,6 +140,19 @@ def columnar_slab(seed: int = 2, n_seeds: int = 50, size_xy: float = 1e-3,
         analytic=dict(T0=T_L, G=(0.0, 0.0, 1e4), xref=(0.0, 0.0, 0.0), Tdot=-10.0))
 
 
+def rosenthal_T(x, y, z, Lz, q=1000.0, k=30.0, alpha=6e-6, V=1.0 / 60.0, T0=300.0,
+                T_cap=3134.0, x_src=3e-3):
+    """Thick-plate moving point source (Rosenthal) in the frame of the source, which
+    sits at (x_src, 0, Lz): T = T0 + q / (2 pi k R) exp(-V (xi + R) / (2 alpha)), with
+    xi = x - x_src along the travel direction and R the distance to the source,
+    capped at T_cap (boiling point of 316L, Table S8)."""
+    X = x - x_src
+    Zd = Lz - z
+    R = np.maximum(np.sqrt(X * X + y * y + Zd * Zd), 1e-9)
+    T = T0 + q / (2.0 * math.pi * k * R) * np.exp(-V * (X + R) / (2.0 * alpha))
+    return np.minimum(T, T_cap)
+
+
 def rosenthal_table(shape=(128, 256, 512), extent=(4e-3, 2e-3, 1e-3), q=1000.0, k=30.0,
                     alpha=6e-6, V=1.0 / 60.0, T0=300.0, T_cap=3134.0, x_src=3e-3):
     """Thick-plate moving point source (Rosenthal) tabulated in the source frame.
@@ -151,13 +169,8 @@ def rosenthal_table(shape=(128, 256, 512), extent=(4e-3, 2e-3, 1e-3), q=1000.0, 
     x = np.arange(nx) * sp[0]
     y = np.arange(ny) * sp[1]
     z = np.arange(nz) * sp[2]
-    X = x[None, None, :] - x_src
-    Y = y[None, :, None]
-    Zd = (Lz - z)[:, None, None]
-    R = np.sqrt(X * X + Y * Y + Zd * Zd)
-    R = np.maximum(R, 1e-9)
-    T = T0 + q / (2.0 * math.pi * k * R) * np.exp(-V * (X + R) / (2.0 * alpha))
-    T = np.minimum(T, T_cap).astype(np.float32)
+    T = rosenthal_T(x[None, None, :], y[None, :, None], z[:, None, None], Lz, q=q, k=k,
+                    alpha=alpha, V=V, T0=T0, T_cap=T_cap, x_src=x_src).astype(np.float32)
     return np.ascontiguousarray(T), (0.0, 0.0, 0.0), sp
 
 
@@ -182,6 +195,143 @@ def weld_fixture(seed: int = 3, n_grains: int = 10000, shell_n0: int = 50,
         name="weld_fixture", lo=(0.0, 0.0, 0.0), hi=ext, h=2e-6, dt=1e-4, a=(3e-6,), b=(3.0,),
         T_L=1780.0, steps=steps, seeds=seeds, quats=q,
         grid=dict(T=T, origin=origin, spacing=sp, vel=(V, 0.0, 0.0)), shell_n0=shell_n0)
+
+
+def quaternion_matrix(q: np.ndarray) -> np.ndarray:
+    """Rotation matrices (n, 3, 3), crystal -> lab, of unit quaternions (w, x, y, z)
+    (normalised here); used to place the lattice sites of an initial state."""
+    q = np.asarray(q, np.float64).reshape(-1, 4)
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    return np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], 1),
+                     np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], 1),
+                     np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1)],
+                    1)
+
+
+def weld_natural(seed: int = 3, n_grains: int = 10000, steps: int = 2000,
+                 grid_shape=(128, 256, 512), extent=(4e-3, 2e-3, 1e-3),
+                 chunk: int = 1 << 18) -> Workload:
+    """The weld plate of ``weld_fixture`` with the base metal cut by the fusion line.
+
+    Same plate, Rosenthal field, growth law, seeds and orientations as the fixture.
+    The base metal is the solid (T <= T_L at t = 0) and each grain owns the points
+    closest to its seed (Voronoi).  The initial particles of a grain sit at the sites
+    s of its lattice (x = c + h R s) that lie in its Voronoi cell, in the solid and
+    inside the plate, for each direction k that is outer at s (it increases |s|_1)
+    and whose target s + e_k lies in the melt (T > T_L): the sites within one spacing
+    of the liquidus surface, heading into the melt.  A target claimed by several such
+    particles goes to the lowest direction index.  Their sites are reached and claimed,
+    their targets claimed.  extra: particles (grain, site, dir, ell, state), reached
+    and claimed (grain, site).  The field is the analytic Rosenthal temperature at
+    t = 0, the one the table samples.
+
+    Candidate sites: the grid cells whose corner temperatures straddle T_L hold the
+    liquidus surface; for each grain that may own part of such a cell, the blocks of
+    4 x 4 x 4 sites of its lattice that the cell touches are listed once, and all their
+    sites are tested.
+    """
+    from scipy.spatial import cKDTree
+    w = weld_fixture(seed=seed, n_grains=n_grains, shell_n0=0, steps=steps,
+                     grid_shape=grid_shape, extent=extent)
+    ext = np.array(w.hi, np.float64)
+    h, T_L = w.h, w.T_L
+    T, origin, sp = w.grid["T"], np.array(w.grid["origin"]), np.array(w.grid["spacing"])
+    x_src = 0.75 * ext[0]
+    B = 4                                           # lattice block edge, in sites
+
+    def temp(p):
+        return rosenthal_T(p[..., 0], p[..., 1], p[..., 2], ext[2], x_src=x_src)
+
+    # grid cells whose eight corner temperatures straddle T_L hold the liquidus surface
+    a = T > T_L
+    corners = [a[dz:a.shape[0] - 1 + dz, dy:a.shape[1] - 1 + dy, dx:a.shape[2] - 1 + dx]
+               for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)]
+    vz, vy, vx = np.nonzero(np.logical_or.reduce(corners) & ~np.logical_and.reduce(corners))
+    vlo = origin + np.stack([vx, vy, vz], 1) * sp   # low corner of each surface cell
+    seeds = w.seeds
+    tree = cKDTree(seeds)
+    kq = min(8, len(seeds))
+    rad = 0.5 * np.linalg.norm(sp) + h
+    dist, cand = tree.query(vlo + 0.5 * sp, k=kq)
+    dist, cand = dist.reshape(len(vlo), kq), cand.reshape(len(vlo), kq)
+    pv, pg = np.nonzero(dist <= dist[:, :1] + 2 * rad)   # (cell, grain) pairs
+    gi = cand[pv, pg]
+    hR = h * quaternion_matrix(w.quats)             # (n, 3, 3), columns h R e_a
+    Rinv = np.transpose(hR, (0, 2, 1)) / (h * h)    # lab -> lattice coordinates
+    cube = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], np.float64)
+    # lattice blocks touched by each pair's cell (its 8 corners give the block range)
+    u = np.einsum("mij,mcj->mci", Rinv[gi], vlo[pv][:, None, :] + cube[None] * sp - seeds[gi][:, None])
+    b0 = np.floor(u.min(1) / B).astype(np.int64)
+    b1 = np.floor(u.max(1) / B).astype(np.int64)
+    span = b1 - b0 + 1                              # blocks per axis, 1..3
+    o = np.array([[i, j, k] for i in range(3) for j in range(3) for k in range(3)])
+    blk = b0[:, None, :] + o[None]                  # (m, 27, 3)
+    valid = np.all(o[None] < span[:, None, :], -1)
+    m_, q_ = np.nonzero(valid)
+    bb = blk[m_, q_] + (1 << 15)                    # block coordinates, made positive
+    packed = (((gi[m_].astype(np.int64) << 16 | bb[:, 0]) << 16 | bb[:, 1]) << 16) | bb[:, 2]
+    packed = np.unique(packed)                      # (grain, block) listed once
+    keys = np.column_stack([packed >> 48, ((packed >> 32) & 0xFFFF) - (1 << 15),
+                            ((packed >> 16) & 0xFFFF) - (1 << 15), (packed & 0xFFFF) - (1 << 15)])
+    # keep the blocks that the liquidus can cross: over the corners of the block grown by
+    # one spacing, T reaches T_L - 5 K and T_L + 5 K (the field is smooth on this scale)
+    corners8 = np.array([[i, j, k] for i in (-1, B) for j in (-1, B) for k in (-1, B)], np.float64)
+    keep = np.zeros(len(keys), bool)
+    cb = 1 << 16
+    for c0 in range(0, len(keys), cb):
+        kb = keys[c0:c0 + cb]
+        Rb = hR[kb[:, 0]]
+        xc = seeds[kb[:, 0]][:, None, :] + np.matmul(Rb[:, None], (kb[:, None, 1:] * B + corners8)[..., None])[..., 0]
+        tc = temp(xc)
+        keep[c0:c0 + cb] = (tc.min(1) <= T_L + 5.0) & (tc.max(1) >= T_L - 5.0)
+    keys = keys[keep]
+    site_off = np.array([[i, j, k] for i in range(B) for j in range(B) for k in range(B)])
+    E = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
+    out_g, out_s, out_k = [], [], []
+    per = max(1, chunk // len(site_off))
+    for c0 in range(0, len(keys), per):
+        kb = keys[c0:c0 + per]
+        gb = kb[:, 0]
+        Rb = hR[gb]                                 # one rotation per block
+        sb = kb[:, None, 1:] * B + site_off[None]   # (nb, 64, 3) sites
+        xs = (seeds[gb] + np.matmul(Rb, (kb[:, 1:] * B)[..., None])[..., 0])[:, None, :] + \
+            np.swapaxes(np.matmul(Rb, site_off.T.astype(np.float64)), 1, 2)
+        bi, si = np.nonzero(np.all((xs >= 0) & (xs <= ext), -1) & (temp(xs) <= T_L))
+        g_, ss, xs = gb[bi], sb[bi, si], xs[bi, si]
+        sel = np.zeros((6, len(g_)), bool)
+        for k in range(6):
+            ax, sg = k // 2, 1 - 2 * (k % 2)
+            outer = (ss[:, ax] == 0) | (np.sign(ss[:, ax]) == sg)
+            sel[k] = outer & (temp(xs + Rb[bi, :, ax] * sg) > T_L)
+        keep = sel.any(0)
+        # Voronoi: the nearest seed owns the site
+        _, near = tree.query(xs[keep])
+        own = np.zeros(len(g_), bool)
+        own[np.flatnonzero(keep)] = near == g_[keep]
+        for k in range(6):
+            ok = sel[k] & own
+            out_g.append(g_[ok])
+            out_s.append(ss[ok])
+            out_k.append(np.full(int(ok.sum()), k))
+    grain = np.concatenate(out_g).astype(np.int32)
+    site = np.concatenate(out_s).astype(np.int64)
+    dirk = np.concatenate(out_k).astype(np.int64)
+    # one particle per target: the lowest direction index among its claimants
+    tgt = site + E[dirk]
+    order = np.lexsort((dirk, tgt[:, 2], tgt[:, 1], tgt[:, 0], grain))
+    grain, site, dirk, tgt = grain[order], site[order], dirk[order], tgt[order]
+    first = np.r_[True, np.any(np.diff(np.column_stack([grain, tgt]), axis=0) != 0, 1)]
+    grain, site, dirk, tgt = grain[first], site[first], dirk[first], tgt[first]
+    reached = np.unique(np.column_stack([grain, site]), axis=0)
+    n = len(grain)
+    w.name = "weld_natural"
+    w.extra = dict(
+        particles=dict(grain=grain, site=site.astype(np.int32), dir=dirk.astype(np.int8),
+                       ell=np.zeros(n, np.float32), state=np.zeros(n, np.uint8)),
+        reached=(reached[:, 0].astype(np.int32), reached[:, 1:].astype(np.int32)),
+        claimed=(grain.copy(), tgt.astype(np.int32)))
+    return w
 
 
 def cet_runs(n_runs: int = 256, base_seed: int = 1000, L_range=(0.5e-3, 2e-3),

@@ -15,10 +15,18 @@ def oracle_from(w: inputs.Workload, nucleate=True):
     if w.solute:
         sd = w.solute
         o.set_solute_grid(sd["w"], sd["origin"], sd["spacing"], sd["Tm"], sd["mL"], sd["vel"])
+    init = w.extra.get("particles") if w.extra else None
     if w.seeds is not None and len(w.seeds):
-        o.add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0)
+        o.add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0 and init is None)
         if w.shell_n0:
             o.seed_shell(np.arange(len(w.seeds)), w.shell_n0)
+    if init is not None:      # an initial state given as particles and lattice sites
+        o.load_particles(init["grain"], init["site"], init["dir"],
+                         init["ell"].astype(np.float64), init["state"])
+        gr, sr = w.extra["reached"]
+        o.add_reached(gr, sr)
+        o.add_claimed(gr, sr)
+        o.add_claimed(*w.extra["claimed"])
     if w.nuclei:
         o.nucleation_sites(w.nuclei["pos"], w.nuclei["dTn"], w.nuclei["quat"])
     return o
@@ -40,10 +48,16 @@ def sim_from(w: inputs.Workload, capacity, nucleate=True, **kw):
     if w.solute:
         sd = w.solute
         s.gp_set_solute_grid(sd["w"], sd["origin"], sd["spacing"], sd["Tm"], sd["mL"], sd["vel"])
+    init = w.extra.get("particles") if w.extra else None
     if w.seeds is not None and len(w.seeds):
-        s.gp_add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0)
+        s.gp_add_grains(w.seeds, w.quats, nucleate=nucleate and not w.shell_n0 and init is None)
         if w.shell_n0:
             s.gp_seed_shell(np.arange(len(w.seeds)), w.shell_n0)
+    if init is not None:      # an initial state given as particles and lattice sites
+        s.gp_load_particles(init["grain"], init["site"], init["dir"], init["ell"], init["state"], 0)
+        gr, sr = w.extra["reached"]
+        s.gp_add_sites(gr, sr, reached=True, claimed=True)
+        s.gp_add_sites(*w.extra["claimed"], reached=False, claimed=True)
     if w.nuclei:
         s.gp_nucleation_sites(w.nuclei["pos"], w.nuclei["dTn"], w.nuclei["quat"])
     return s

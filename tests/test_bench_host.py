@@ -107,10 +107,48 @@ def test_kernel_digest_ignores_comments_and_catches_code(tmp_path, monkeypatch):
     text = f.read_text()
     f.write_text("// a new comment line\n" + text.replace("\n", "\n\n", 3) + "\n/* block */\n")
     assert bench.kernel_sources_digest() == d0
-    json.dump({"sources_digest": d0, "kernels": {"advance": {"dram_bytes_per_unit": 7.0}},
-               "step": {"dram_bytes_per_particle_step": 9.0}},
+    json.dump({"sources_digest": d0, "entries": {"advance": {"dram_bytes_per_unit": 7.0},
+                                                 "emit": {"dram_bytes_per_unit": 3.0}}},
               open(root / "profiles" / "ncu_traffic.json", "w"))
-    assert bench.ncu_traffic("advance") == 7.0 and bench.ncu_step_traffic() == 9.0
+    prof = [{"name": "advance", "units": 10.0, "total_ms": 1.0},
+            {"name": "emit", "units": 20.0, "total_ms": 1.0}]
+    assert bench.step_dram_bytes(prof, 10.0) == (7.0 * 10 + 3.0 * 20) / 10.0
+    assert bench.step_dram_bytes(prof + [{"name": "group", "units": 1.0, "total_ms": 1.0}],
+                                 10.0) is None          # an entry without a figure
     f.write_text(text.replace("kSortThreads", "kSortThreads ", 1).replace("return 0;", "return 1;", 1))
     assert bench.kernel_sources_digest() != d0
-    assert bench.ncu_traffic("advance") is None and bench.ncu_step_traffic() is None
+    assert bench.ncu_record() is None and bench.step_dram_bytes(prof, 10.0) is None
+
+
+def test_ncu_digest_attributes_launches_to_timed_entries(tmp_path):
+    """The digest sums each launch's DRAM bytes into the timed entry of its kernel
+    (k_scan_sums goes to the entry of the kernel launched before it) and divides by
+    the units that entry processed in the plain run."""
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    rows = [["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream",
+             "Block Size", "Grid Size", "Device", "CC", "Metric Name", "Metric Unit",
+             "Metric Value"]]
+    launches = [("k_seed_shell", 5), ("k_group_count", 10), ("k_scan_blocks", 1),
+                ("k_scan_sums", 1), ("k_group_scatter", 20), ("k_obs_count", 2),
+                ("k_scan_sums", 1), ("k_obs_merge", 40), ("k_advance", 100), ("k_emit", 50)]
+    for i, (k, b) in enumerate(launches):
+        name = f"void gp::(anonymous namespace)::{k}<false>(gp::Params, int)"
+        for m, v in (("dram__bytes_read.sum", b / 2), ("dram__bytes_write.sum", b / 2),
+                     ("gpu__time_duration.sum", 1000)):
+            rows.append([str(i), "1", "python", "h", name, "1", "7", "(256,1,1)", "(1,1,1)", "0",
+                         "10.3", m, "byte", str(v)])
+    import csv
+    with open(tmp_path / "c.csv", "w", newline="") as fh:
+        csv.writer(fh).writerows(rows)
+    line = {"metric": "particle-steps/s", "config": {}, "profiled_particle_steps": 10,
+            "kernels": {"group": {"units": 4}, "obstacle": {"units": 2}, "advance": {"units": 10},
+                        "emit": {"units": 5}}}
+    (tmp_path / "p.log").write_text("noise\n" + json.dumps(line) + "\n")
+    d = bench.ncu_digest(str(tmp_path / "c.csv"), str(tmp_path / "p.log"))
+    e = d["entries"]
+    assert e["group"]["dram_bytes_per_unit"] == (10 + 1 + 1 + 20) / 4
+    assert e["obstacle"]["dram_bytes_per_unit"] == (2 + 1 + 40) / 2
+    assert e["advance"]["dram_bytes_per_unit"] == 10.0 and e["emit"]["dram_bytes_per_unit"] == 10.0
+    assert d["dram_bytes_per_particle_step"] == (32 + 43 + 100 + 50) / 10

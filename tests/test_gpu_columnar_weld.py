@@ -1,0 +1,85 @@
+"""The two workloads of the method's applications at their stated sizes (GPU tests).
+
+- Competitive columnar growth (the situation of Sec. 3.3 / 3.4), configuration 2:
+  a 1 mm x 1 mm x 50 um slab, 50 seeds on its bottom face with random orientations,
+  T = T_L + G z - Tdot t with G = 1e4 K/m, Tdot = 10 K/s, v = 1e-5 dT^2, h = 2 um,
+  dt = 1 ms, 600 steps.  The GPU and the FP64 oracle run the whole workload; their
+  grain maps (4 um voxels) agree on >= 99.5 % of all voxels and of the solid ones,
+  and the particle and reached-site counts agree to 1 %.
+- Growth from the fusion line of a weld (Sec. 4.2, Rosenthal stand-in),
+  configuration 3 as the method runs it: the base-metal grains of the 4 x 2 x 1 mm
+  plate cut by the t = 0 liquidus (inputs.weld_natural, about 7e5 particles on 835
+  grains).  After 20 steps the grain maps over the region where the oracle grew
+  agree on >= 99.5 % of the solid voxels, and the counts agree to 1 %.
+"""
+import numpy as np
+import pytest
+
+from paper_2504_12858_gb300 import inputs
+from tests.helpers import oracle_from, sim_from
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2504_12858_gb300 import build, native  # noqa: E402
+
+build.build()
+native.load()
+
+
+def _agree(mo, mg):
+    solid = (mo >= 0) | (mg >= 0)
+    return (mo == mg).mean(), (mo[solid] == mg[solid]).mean(), solid.mean()
+
+
+def test_columnar_slab_at_its_stated_size():
+    w = inputs.columnar_slab()
+    o = oracle_from(w)
+    s = sim_from(w, capacity=2000000, reached_capacity=6000000)
+    for _ in range(w.steps // 50):
+        o.step(50)
+        s.gp_step(50)
+        no, ng = o.n_particles, s.gp_stats()["n_live"]
+        assert abs(ng - no) <= max(5, 0.01 * no), (ng, no)
+    nv, sp = (250, 250, 13), (4e-6,) * 3
+    mo, mg = o.grain_map((0, 0, 0), sp, nv), s.gp_grain_map((0, 0, 0), sp, nv)
+    allv, solid, frac = _agree(mo, mg)
+    assert allv >= 0.995 and solid >= 0.995, (allv, solid)
+    assert frac > 0.5                                   # most of the slab has solidified
+    assert len(np.unique(mo[mo >= 0])) > 10             # many grains compete
+    st, ost = s.gp_stats(), o.stats()
+    assert abs(st["n_reached"] - ost["reached"] - len(w.seeds)) <= 0.01 * ost["reached"]
+    assert st["error_flags"] == 0
+
+
+def test_weld_natural_growth_from_the_fusion_line():
+    w = inputs.weld_natural()
+    n0 = len(w.extra["particles"]["grain"])
+    assert n0 > 5e5
+    o = oracle_from(w)
+    s = sim_from(w, capacity=8000000, reached_capacity=16000000,
+                 claim_blocks=len(w.seeds) * 300)
+    steps = 20
+    o.step(steps)
+    s.gp_step(steps)
+    no, ng = o.n_particles, s.gp_stats()["n_live"]
+    assert abs(ng - no) <= 0.01 * no, (ng, no)
+    assert s.gp_stats()["particle_steps"] > 0 and s.gp_stats()["error_flags"] == 0
+    # the region where the oracle grew: its reached sites beyond the initial ones
+    gr, sr = o.reached()
+    r0 = len(w.extra["reached"][0])
+    assert len(gr) > r0 + 1000, len(gr) - r0
+    c = np.array([o.grain(int(g))[0] for g in gr[r0:]])
+    R = np.array([o.grain(int(g))[1] for g in gr[r0:]])
+    x = c + w.h * np.einsum("nij,nj->ni", R, sr[r0:])
+    lo = np.maximum(x.min(0) - 10e-6, 0.0)
+    hi = np.minimum(x.max(0) + 10e-6, np.array(w.hi))
+    sp = np.maximum((hi - lo) / 120, 2e-6)              # at most about 1.7e6 voxels
+    nv = np.ceil((hi - lo) / sp).astype(int)
+    mo = o.grain_map(lo, sp, nv)
+    mg = s.gp_grain_map(lo, sp, nv)
+    allv, solid, frac = _agree(mo, mg)
+    assert solid >= 0.995, (allv, solid, frac)
