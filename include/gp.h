@@ -120,11 +120,15 @@ typedef struct {
   int32_t max_grains;       /* default 1 << 20                                    */
   int32_t max_nuclei;       /* pending nucleation sites; default 4096             */
   int64_t grid_nodes;       /* thermal-grid nodes reserved in the arena; default 0 */
-  int64_t tape_steps;       /* steps the adjoint tape holds (capacity particles each,
-                               25 bytes per particle and step); default 0 (none)   */
+  int64_t tape_steps;       /* steps the adjoint tape holds; default 0 (none).  Per
+                               particle of capacity: 6 bytes per step, 16 bytes per
+                               checkpoint, 36 bytes of scratch                      */
   void* arena;
   size_t arena_bytes;
   int64_t solute_nodes;     /* composition-grid nodes reserved in the arena; default 0 */
+  int64_t tape_checkpoint_every; /* the tape keeps the particle records of every k-th
+                               step only and rebuilds the others in the reverse sweep
+                               (k replays per taped step at most); default 1        */
 } gp_memory;
 
 typedef struct {
@@ -332,9 +336,13 @@ gp_status gp_profile_read(gp_ctx* ctx, int32_t max, gp_kernel_prof* out, int32_t
 /* ---- adjoint of the advance ---------------------------------------------------- */
 
 /* Starts recording the adjoint tape: the next steps (at most gp_memory.tape_steps)
- * store the particle records before the advance, the permutation that ordered them
- * by cell, the state after the contact search and the parent of every particle of the
- * following step.  Recording restarts at every call.  Needs an analytic field. */
+ * store the state of every particle after the contact search, the parent and the
+ * direction of every particle of the following step, and, every
+ * gp_memory.tape_checkpoint_every steps, the particle records before the step.  The
+ * reverse sweep rebuilds the records of the steps between checkpoints by replaying
+ * these events with the forward's arithmetic.  Recording restarts at every call.
+ * Needs an analytic field; with checkpoints every k > 1 steps, GP_ERR_STATE while
+ * nucleation sites are pending (a nucleation is not replayed). */
 gp_status gp_tape_begin(gp_ctx* ctx);
 
 /* Reverse sweep over the taped steps, with the discrete events of the forward run

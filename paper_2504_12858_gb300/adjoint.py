@@ -43,19 +43,21 @@ def front_outputs(p, h, n_grains):
 
 
 class FrontAdjoint(torch.autograd.Function):
-    """forward(theta, workload, capacity) -> tensor [H, F_0 .. F_{G-1}] (float64).
+    """forward(theta, workload, capacity, every=1) -> tensor [H, F_0 .. F_{G-1}]
+    (float64); every: the tape keeps the records of every every-th step and the reverse
+    sweep rebuilds the others.
 
     The particles of the last forward run are kept in FrontAdjoint.last_particles."""
 
     last_particles = None
 
     @staticmethod
-    def forward(ctx, theta, w, capacity):
+    def forward(ctx, theta, w, capacity, every=1):
         A, n, G, Tdot = (float(v) for v in theta.detach().cpu().numpy())
         an = w.analytic
         sim = native.Sim(w.lo, w.hi, w.h, w.dt, (A,), (n,), w.T_L, capacity=capacity,
                          reached_capacity=4 * capacity, max_grains=len(w.seeds) + 8,
-                         tape_steps=w.steps)
+                         tape_steps=w.steps, tape_checkpoint_every=every)
         sim.gp_set_thermal_analytic(an["T0"], (0.0, 0.0, G), an["xref"], -Tdot)
         sim.gp_add_grains(w.seeds, w.quats)
         sim.gp_tape_begin()
@@ -83,4 +85,4 @@ class FrontAdjoint(torch.autograd.Function):
         d = ctx.sim.gp_adjoint(seed.astype(np.float32))
         # theta = (A, n, G, Tdot); the field's Tdot coefficient is -Tdot
         grad = torch.tensor([d[0], d[1], d[6], -d[7]], dtype=torch.float64)
-        return grad, None, None
+        return grad, None, None, None

@@ -43,12 +43,14 @@ struct Layout {
   int64_t grid_nodes = 0;
   int64_t solute_nodes = 0;
   int64_t tape_steps = 0;
+  int64_t tape_every = 1;  // checkpoint interval of the adjoint tape
   // offsets into the arena
   size_t rec0, rec1, pos4, sslot, act, keys0, keys1, vals0, vals1, sstatus, hist, tickets, cells,
       rkey, rnext, rhead, ckeys, cdata, gtab, npos, ngrain, nstate, nmeta, gflags, gdtn, dstats, grid,
       sgrid, runs,
-      rtherm, rcount, tape_rec, tape_vals, tape_state, tape_par, tape_grad, gcnt, gofs, gfill,
-      gbsum, gkey, gdest, orec[2], opos[2], okey[2], otab, otcnt, osplit, total;
+      rtherm, rcount, tape_post, tape_par, tape_code, tape_ckpt, tape_replay, tape_svals,
+      tape_grad, gcnt, gofs, gfill,
+      gbsum, gkey, gdest, orec[2], opos[2], okey[2], otcnt, osplit, total;
   uint32_t ngroups = 0;  // one run: cell groups of the record grouping
 };
 
@@ -148,6 +150,7 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->grid_nodes = m->grid_nodes > 0 ? m->grid_nodes : 0;
   L->solute_nodes = m->solute_nodes > 0 ? m->solute_nodes : 0;
   L->tape_steps = m->tape_steps > 0 ? m->tape_steps : 0;
+  L->tape_every = m->tape_checkpoint_every > 0 ? m->tape_checkpoint_every : 1;
   if (batch && (L->grid_nodes || L->tape_steps || L->solute_nodes)) {
     *why = "a batch of runs takes analytic fields only and no adjoint tape";
     return false;
@@ -171,7 +174,9 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->sstatus = take(4 * radix_status_words(L->cap, L->key_bytes));
   L->hist = take(4 * 256 * (size_t)((L->nbits + 7) / 8));  // one histogram per digit
   L->tickets = take(4 * 8);
-  L->cells = take(16 * (size_t)L->nseg);
+  // cell table: a batch one entry per segment; a single run two interleaved entries
+  // per segment (its moving particles, then its obstacle store)
+  L->cells = take((batch ? 16 : 32) * (size_t)L->nseg);
   L->rkey = take(8 * (size_t)L->rcap);
   L->rnext = take(4 * (size_t)L->rcap);
   L->rhead = take(4 * (size_t)L->nheads);
@@ -183,11 +188,17 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->nstate = take(4 * (size_t)L->max_nuclei);
   L->dstats = take(sizeof(DevStats));
   L->grid = take(4 * (size_t)L->grid_nodes);
+  // adjoint tape: per step the post-contact states, parents and directions (6 bytes per
+  // particle), the store at every tape_every-th step (16 bytes), two stores for the
+  // replay and the sorted-to-store map of the step being taped
   const size_t ts = (size_t)L->tape_steps;
-  L->tape_rec = take(16 * cap * ts);
-  L->tape_vals = take(4 * cap * ts);
-  L->tape_state = take(cap * ts);
+  const size_t nck = (ts + (size_t)L->tape_every - 1) / (size_t)L->tape_every;
+  L->tape_post = take(cap * ts);
   L->tape_par = take(4 * cap * ts);
+  L->tape_code = take(cap * ts);
+  L->tape_ckpt = take(16 * cap * nck);
+  L->tape_replay = take(ts ? 32 * cap : 16);
+  L->tape_svals = take(ts ? 4 * cap : 16);
   L->tape_grad = take(8 * 8);
   L->act = take(4 * cap);
   L->nmeta = take(8 * (size_t)L->max_nuclei);
@@ -213,7 +224,6 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
     L->opos[b] = take(16 * ocap);
     L->okey[b] = take(4 * ocap + 16);
   }
-  L->otab = take(batch ? 16 : 16 * (size_t)L->nseg);
   L->otcnt = take(4 * (ocap / 8192 + 16));
   L->osplit = take(4 * (2 * ocap / 2048 + 16));
   L->total = o;
@@ -551,6 +561,15 @@ gp_status push_counts(gp_ctx* c) {
   return GP_OK;
 }
 
+// the obstacle store's half of a single run's interleaved cell table (entry 2 sg + 1)
+uint4* obs_tab(gp_ctx* c) { return c->cells + 1; }
+
+// clears one half (0: moving particles, 1: obstacles) of a single run's interleaved table
+gp_status clear_half(gp_ctx* c, int half) {
+  GP_CUDA(c, cudaMemset2DAsync(c->cells + half, 32, 0, 16, c->L.nseg, c->st));
+  return GP_OK;
+}
+
 // The obstacle store serves the plain single-run step.  Periodic axes, melting (which
 // removes frozen particles) and the adjoint tape (which follows every particle through
 // every step) keep all particles in the dynamic store.
@@ -562,8 +581,7 @@ bool obs_usable(const gp_ctx* c) {
 gp_status obs_reset(gp_ctx* c) {
   c->n_obs = 0;
   c->obs_carry = 0;
-  if (!c->batch) GP_CUDA(c, cudaMemsetAsync(at<uint4>(c, c->L.otab), 0, 16 * c->L.nseg, c->st));
-  return GP_OK;
+  return c->batch ? GP_OK : clear_half(c, 1);
 }
 
 // moves the obstacle records back to the end of the dynamic store (its keys are then
@@ -709,8 +727,7 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   if (batch) c->sb.n_dev = &c->dst->n_live;  // device-sized sort
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
-  e = e ? e : cudaMemsetAsync(c->cells, 0, 16 * L.nseg, s);
-  if (!batch) e = e ? e : cudaMemsetAsync(c->base + L.otab, 0, 16 * L.nseg, s);
+  e = e ? e : cudaMemsetAsync(c->cells, 0, (batch ? 16 : 32) * L.nseg, s);
   e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.nheads, s);
   e = e ? e : cudaMemsetAsync(c->C.bucket, 0, 16 * (size_t)L.buckets, s);
   e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.blocks, s);
@@ -1048,7 +1065,7 @@ gp_status gp_inspect_order(gp_ctx* c, int32_t which, int64_t cap, uint32_t* keys
   const int64_t n = which == 0 ? c->n_live : c->n_obs;
   if (n_out) *n_out = n;
   const int64_t m = std::min(n, cap);
-  const uint4* tab = at<uint4>(c, c->L.otab);
+  const uint4* tab = obs_tab(c);
   if (which == 0) {
     if (n > 0) {
       const Params P = step_params(c, c->step);
@@ -1057,7 +1074,8 @@ gp_status gp_inspect_order(gp_ctx* c, int32_t which, int64_t cap, uint32_t* keys
         c->keys_valid = true;
       }
       if (++c->stamp > 0xffffu) {
-        GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
+        s = clear_half(c, 0);  // stamps wrap: every moving-particle entry empty
+        if (s) return s;
         c->stamp = 1;
       }
       GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
@@ -1087,8 +1105,8 @@ gp_status gp_inspect_order(gp_ctx* c, int32_t which, int64_t cap, uint32_t* keys
     if (stamp) *stamp = 1;
   }
   const int64_t ts = std::min<int64_t>(table_cap, (int64_t)c->L.nseg);
-  if (table && ts > 0)
-    GP_CUDA(c, cudaMemcpyAsync(table, tab, 16 * ts, cudaMemcpyDeviceToHost, c->st));
+  if (table && ts > 0)  // one half of the interleaved table
+    GP_CUDA(c, cudaMemcpy2DAsync(table, 16, tab, 32, 16, ts, cudaMemcpyDeviceToHost, c->st));
   GP_CUDA(c, cudaStreamSynchronize(c->st));
   return GP_OK;
 }
@@ -1328,7 +1346,11 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
     const bool rec = c->tape_on && c->tape_pos < c->L.tape_steps;
     const size_t tq = (size_t)c->tape_pos, tcap = (size_t)c->L.cap;
     int32_t* tpar = rec ? at<int32_t>(c, c->L.tape_par) + tq * tcap : nullptr;
+    uint32_t* tsrc = rec ? at<uint32_t>(c, c->L.tape_svals) : nullptr;
     if (rec) GP_CUDA(c, cudaMemsetAsync(tpar, 0xff, 4 * tcap, c->st));
+    if (rec && tq % (size_t)c->L.tape_every == 0 && n > 0)  // checkpoint: the store now
+      GP_CUDA(c, cudaMemcpyAsync(at<int4>(c, c->L.tape_ckpt) + (tq / c->L.tape_every) * tcap,
+                                 c->rec[c->cur], 16 * n, cudaMemcpyDeviceToDevice, c->st));
     GP_CUDA(c, cudaMemsetAsync(&c->dst->n_out, 0, sizeof(unsigned long long), c->st));
     GP_CUDA(c, cudaMemsetAsync(&c->dst->n_frozen, 0, sizeof(unsigned long long), c->st));
     if (n > 0) {
@@ -1339,7 +1361,8 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
         c->keys_valid = true;
       }
       if (++c->stamp > 0xffffu) {
-        GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
+        s = clear_half(c, 0);  // stamps wrap: every moving-particle entry empty
+        if (s) return s;
         c->stamp = 1;
       }
       int4* sorted = c->rec[c->cur ^ 1];
@@ -1353,16 +1376,10 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                          at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
                          at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
                          at<uint32_t>(c, c->L.gkey), at<uint32_t>(c, c->L.gdest), c->rec[c->cur],
-                         sorted, c->pos4, skeys, rec ? c->sb.vals[0] : nullptr,
+                         sorted, c->pos4, skeys, tsrc,
                          reinterpret_cast<uint8_t*>(c->site_slot), c->cells, c->stamp, c->act,
                          c->dst, c->sms, &c->prof, c->st);
       GP_CUDA(c, cudaGetLastError());
-      if (rec) {
-        GP_CUDA(c, cudaMemcpyAsync(at<int4>(c, c->L.tape_rec) + tq * tcap, sorted, 16 * n,
-                                   cudaMemcpyDeviceToDevice, c->st));
-        GP_CUDA(c, cudaMemcpyAsync(at<uint32_t>(c, c->L.tape_vals) + tq * tcap, c->sb.vals[0],
-                                   4 * n, cudaMemcpyDeviceToDevice, c->st));
-      }
       // obstacle flush: the FROZEN records of the ordered store (hst->n_frozen of them,
       // as the last emit counted) join the obstacle store once carrying them from step
       // to step has cost about as much as merging them, counted as kObsCarry record
@@ -1389,7 +1406,7 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                              at<int4>(c, c->L.orec[o]), c->n_obs, skeys, c->pos4, sorted, flist,
                              nf, at<uint32_t>(c, c->L.osplit), at<uint32_t>(c, c->L.okey[o ^ 1]),
                              at<float4>(c, c->L.opos[o ^ 1]), at<int4>(c, c->L.orec[o ^ 1]),
-                             at<uint4>(c, c->L.otab), &c->dst->err, c->st);
+                             obs_tab(c), &c->dst->err, c->st);
             GP_CUDA(c, cudaGetLastError());
             c->ocur ^= 1;
             c->n_obs += nf;
@@ -1398,14 +1415,14 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
           c->prof.end(K_OBS, (double)c->n_obs, nf > 0 ? 6 : 3);
         }
       }
-      const Obs ob{at<uint4>(c, c->L.otab), at<uint32_t>(c, c->L.okey[c->ocur]),
+      const Obs ob{obs_tab(c), at<uint32_t>(c, c->L.okey[c->ocur]),
                    at<float4>(c, c->L.opos[c->ocur]), c->n_obs};
       c->prof.begin(K_ADVANCE);
       launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp, n, c->act,
                      c->C, c->site_slot, c->dst, c->st, obs ? &ob : nullptr);
       // units: the ACTIVE particles entering the step (live minus frozen after the last step)
       c->prof.end(K_ADVANCE, (double)(n - std::min<int64_t>(n, (int64_t)c->hst->n_frozen)));
-      if (rec) launch_tape_state(sorted, n, at<uint8_t>(c, c->L.tape_state) + tq * tcap, c->st);
+      if (rec) launch_tape_state(sorted, tsrc, n, at<uint8_t>(c, c->L.tape_post) + tq * tcap, c->st);
       c->prof.begin(K_EMIT);
       launch_emit(batch, P, S, sorted, c->site_slot, n, c->rec[c->cur], c->sb.keys[0],
                   c->sb.vals[0], c->L.cap - c->n_obs, c->C, c->R, tpar, c->dst, c->st);
@@ -1438,6 +1455,9 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       launch_renucleate(P, c->gflags, (int)c->n_grains, c->rec[c->cur],
                         static_cast<uint32_t*>(c->sb.keys[0]), c->sb.vals[0], dcap, c->C,
                         c->R, c->dst, c->st);
+    if (rec)
+      launch_tape_out(tpar, tsrc, c->rec[c->cur], at<uint8_t>(c, c->L.tape_code) + tq * tcap,
+                      c->L.cap, c->dst, c->sms, c->st);
     GP_CUDA(c, cudaGetLastError());
     const int64_t stepped = c->step;
     ++c->step;
@@ -1463,6 +1483,11 @@ gp_status gp_tape_begin(gp_ctx* c) {
   if (c->P.solute) return fail(c, GP_ERR_STATE, "the adjoint takes the nominal liquidus");
   if (c->L.tape_steps <= 0) return fail(c, GP_ERR_STATE, "no tape (gp_memory.tape_steps = 0)");
   if (c->thermal != 1) return fail(c, GP_ERR_STATE, "the adjoint needs an analytic field");
+  if (c->L.tape_every > 1 &&
+      c->n_nuclei - ((int64_t)c->hst->nucleated - (int64_t)c->hst->renucleated) > 0)
+    return fail(c, GP_ERR_STATE,
+                "a tape with checkpoints replays its steps and cannot replay nucleation: "
+                "no pending nucleation sites (or tape_checkpoint_every = 1)");
   s = obs_return(c);  // the tape follows every particle through the dynamic store
   if (s) return s;
   c->tape_on = true;
@@ -1492,16 +1517,29 @@ gp_status gp_adjoint(gp_ctx* c, const float* seed, int64_t n, int32_t flags, dou
                                                        : cudaMemcpyHostToDevice,
                                c->st));
   GP_CUDA(c, cudaMemsetAsync(gdev, 0, 8 * 8, c->st));
+  const int64_t every = c->L.tape_every;
+  const int4* ckpt = at<int4>(c, c->L.tape_ckpt);
+  int4* replay[2] = {at<int4>(c, c->L.tape_replay), at<int4>(c, c->L.tape_replay) + tcap};
+  auto post = [&](int64_t q) { return at<uint8_t>(c, c->L.tape_post) + q * tcap; };
+  auto par = [&](int64_t q) { return at<int32_t>(c, c->L.tape_par) + q * tcap; };
+  auto code = [&](int64_t q) { return at<uint8_t>(c, c->L.tape_code) + q * tcap; };
   for (int64_t q = c->tape_pos - 1; q >= 0; --q) {
     const int64_t nn = c->tape_n[q], m = c->tape_m[q];
+    // the store at step q: its checkpoint, replayed forward over the steps since
+    const int64_t q0 = (q / every) * every;
+    const int4* R = ckpt + (size_t)(q / every) * tcap;
+    for (int64_t j = q0; j < q; ++j) {
+      int4* out = replay[(j - q0) & 1];
+      launch_adj_replay(step_params(c, c->tape_t[j]), step_args(c, c->tape_t[j]), R, post(j),
+                        par(j), code(j), c->tape_m[j], out, c->st);
+      R = out;
+    }
     if (nn > 0) GP_CUDA(c, cudaMemsetAsync(lam_s, 0, 4 * nn, c->st));
     const StepArgs S = step_args(c, c->tape_t[q]);
     const float t = (float)((double)c->tape_t[q] * c->dt);
-    launch_adj_step(step_params(c, c->tape_t[q]), S, t, at<int4>(c, c->L.tape_rec) + q * tcap,
-                    at<uint8_t>(c, c->L.tape_state) + q * tcap,
-                    at<int32_t>(c, c->L.tape_par) + q * tcap, lam_u, m, lam_s, gdev, c->st);
-    if (q > 0)
-      launch_adj_unsort(lam_s, at<uint32_t>(c, c->L.tape_vals) + q * tcap, nn, lam_u, c->st);
+    launch_adj_step(step_params(c, c->tape_t[q]), S, t, R, post(q), par(q), lam_u, m, lam_s,
+                    gdev, c->st);
+    std::swap(lam_u, lam_s);  // the adjoint of step q, by store index
   }
   GP_CUDA(c, cudaGetLastError());
   GP_CUDA(c, cudaMemcpyAsync(grad, gdev, 8 * 8, cudaMemcpyDeviceToHost, c->st));

@@ -386,6 +386,23 @@ __device__ __forceinline__ float growth_v(const Params& P, float dT) {
   return v;
 }
 
+// Explicit Euler step of a particle's progress (Sec. 2.1.2, Eq. 1/2, reading r2): the
+// undercooling at its position x_n at t_n, the growth law, dl = v dt / h capped at one
+// spacing (capped is set), and e = ell + dl.  The advance and the adjoint's replay of
+// the taped steps both call it, so the two obtain the same binary32 values.
+__device__ __forceinline__ float euler_ell(const Params& P, const Geo& gm, const StepArgs& S,
+                                           float3 x, float ell, bool& capped) {
+  const float dT = undercooling(P, gm, S, x, gm.dT_base);
+  float dl = __fmul_rn(growth_v(P, dT), P.dt_over_h);
+  capped = dl > 1.f;
+  if (capped) dl = 1.f;
+  return __fadd_rn(ell, dl);
+}
+
+// the target counts as reached within 2^-20 of a full spacing (reading r6), so that a
+// step commensurate with h does not lose a step to binary32 rounding
+__device__ __forceinline__ bool reaches_target(float e) { return e >= 1.f - 0x1p-20f; }
+
 // ---------------------------------------------------------------------------------
 // lattice-site claim table: open addressing over 8^3-site blocks of a grain; each
 // block holds one byte per site: bit 7 = claimed, bits 0..2 = claimant axes of an

@@ -38,7 +38,10 @@ constexpr uint32_t kNoEntry = 0xffffffffu;
 //      the segment (low 15 bits)
 //   z, w: particle count of each of the 16 cells, 4 bits each (cell 0 in the low
 //         nibble of z), saturated at 15; the flag is set when any count saturates
-// An entry whose stamp is not the current build's is an empty segment.  A query
+// An entry whose stamp is not the current build's is an empty segment.  A single run
+// interleaves two tables, entry 2 sg for its moving particles and entry 2 sg + 1 for
+// its obstacle store (a 32-byte sector holds both halves of a segment; stride TS = 2).
+// A query
 // turns the 3 cells x-1..x+1 of a neighbour row into a candidate range directly
 // from the nibble counts; when a count is saturated it scans the segment's keys.
 // Two cell orders.  Linear (the stand-alone hash): local = (z ny + y) nx + x, segments
@@ -88,7 +91,7 @@ __device__ __forceinline__ uint32_t local_tiled(const Geo& g, int cx, int cy, in
 
 // Writes the entry of the segment that starts at sorted index j (if one does).
 // The keys of the run are key0 + local; a key outside that range ends the run.
-template <class K, bool TILED>
+template <class K, bool TILED, int TS = 1>
 __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ skeys, int64_t j,
                                           int64_t n, K key, uint4* __restrict__ tab,
                                           uint32_t stamp, uint32_t* err) {
@@ -121,8 +124,8 @@ __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ s
       break;
   }
   const bool sat = ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
-  tab[gm.seg0 + sg] = make_uint4((uint32_t)j, (stamp << 16) | (sat ? 0x8000u : 0u) | c,
-                                 (uint32_t)nib, (uint32_t)(nib >> 32));
+  tab[(gm.seg0 + sg) * TS] = make_uint4((uint32_t)j, (stamp << 16) | (sat ? 0x8000u : 0u) | c,
+                                        (uint32_t)nib, (uint32_t)(nib >> 32));
 }
 
 // the eight 4-bit counts of v summed in pairs, one pair per byte (at most 30 each)
@@ -177,8 +180,9 @@ __device__ __forceinline__ bool row_range(const uint4 e, uint32_t mz0, uint32_t 
 // appends the pairs (idj, ids[i]) with idj < ids[i] to pairs (up to pair_cap,
 // counted in *npairs).  Returns whether any was found.
 // OBS == true (one run, first hit only): the rows of the obstacle store's table, at
-// the same segment index, are searched beside those of the dynamic table.
-template <bool PAIRS, class K, bool TILED, bool OBS = false>
+// the same segment index, are searched beside those of the dynamic table, in one loop
+// over the two candidate ranges of each row.  TS: stride of the table entries.
+template <bool PAIRS, class K, bool TILED, bool OBS = false, int TS = 1>
 __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                              const uint4* __restrict__ tab, uint32_t stamp,
                                              const K* __restrict__ skeys,
@@ -212,9 +216,29 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                 : ((uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y) *
                                           (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
         const K khi = klo + (K)(c1 - c0);
-        const uint4 e = __ldg(rtab + sg);
+        const uint4 e = __ldg(rtab + (size_t)sg * TS);
         uint32_t i, end;
-        if ((e.y >> 16) == stamp && row_range<K>(e, mz0, mw0, rz, rw, klo, khi, skeys, n, i, end)) {
+        if constexpr (OBS) {
+          const uint4 eo = __ldg(ob->tab + (size_t)sg * TS);
+          if ((e.y >> 16) != stamp ||
+              !row_range<K>(e, mz0, mw0, rz, rw, klo, khi, skeys, n, i, end))
+            i = end = 0;
+          uint32_t io, eend;
+          if ((eo.y & kSegMaxCount) == 0 ||
+              !row_range<uint32_t>(eo, mz0, mw0, rz, rw, (uint32_t)klo, (uint32_t)khi, ob->keys,
+                                   ob->n, io, eend))
+            io = eend = 0;
+          // candidates t < nd from the moving particles, the others from the obstacles
+          const uint32_t nd = end - i, tot = nd + (eend - io);
+          const float4* __restrict__ pd = pos4 + i;
+          const float4* __restrict__ po = ob->pos + io - nd;
+          for (uint32_t t = 0; t < tot; ++t) {
+            const float4 o = __ldg((t < nd ? pd : po) + t);
+            if (__float_as_int(o.w) == gw) continue;
+            if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) return true;
+          }
+        } else if ((e.y >> 16) == stamp &&
+                   row_range<K>(e, mz0, mw0, rz, rw, klo, khi, skeys, n, i, end)) {
           for (; i < end; ++i) {
             const float4 o = __ldg(pos4 + i);
             if (__float_as_int(o.w) == gw) continue;
@@ -232,18 +256,6 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
             }
           }
         }
-        if constexpr (OBS) {
-          const uint4 eo = __ldg(ob->tab + sg);
-          if ((eo.y & kSegMaxCount) != 0 &&
-              row_range<uint32_t>(eo, mz0, mw0, rz, rw, (uint32_t)klo, (uint32_t)khi, ob->keys,
-                                  ob->n, i, end)) {
-            for (; i < end; ++i) {
-              const float4 o = __ldg(ob->pos + i);
-              if (__float_as_int(o.w) == gw) continue;
-              if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) return true;
-            }
-          }
-        }
       }
     }
   }
@@ -253,7 +265,7 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
 // contact_scan (first hit only) for a single run with periodic axes: neighbour rows
 // and cells wrap around the periodic faces and distances take the nearest image.
 // With at least three cells per periodic axis the 27 cells are distinct.
-template <class K>
+template <class K, int TS = 1>
 __device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __restrict__ tab,
                                  uint32_t stamp, const K* __restrict__ skeys,
                                  const float4* __restrict__ pos4, int64_t n, float3 p, int gw,
@@ -285,7 +297,7 @@ __device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __
         const int x0 = wx0[wi], x1 = wx1[wi];
         for (int sgi = x0 >> kSegShift; sgi <= (x1 >> kSegShift); ++sgi) {
           const uint32_t sg = seg_tiled(gm, sgi, y, z);
-          const uint4 e = __ldg(rtab + sg);
+          const uint4 e = __ldg(rtab + (size_t)sg * TS);
           if ((e.y >> 16) != stamp) continue;
           const int base = sgi << kSegShift;
           const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
@@ -609,11 +621,13 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
       int cx, cy, cz;
       cell_local(gm, p, cx, cy, cz);
       bool hit;
+      // a single run interleaves its two cell tables (stride 2), a batch has one
+      constexpr int TS = BATCH ? 1 : 2;
       if constexpr (PER)
-        hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        hit = contact_scan_per<K, TS>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
       else
-        hit = contact_scan<false, K, true, OBS>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy,
-                                                cz, nullptr, 0, nullptr, 0, nullptr, &ob);
+        hit = contact_scan<false, K, true, OBS, TS>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx,
+                                                    cy, cz, nullptr, 0, nullptr, 0, nullptr, &ob);
       Rec r = rec_unpack(rs[j]);
       g = r.grain;
       if (hit) {
@@ -621,16 +635,8 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
         r.state = ST_FROZEN;
       } else {
         // thermal sample at (x_n, t_n), growth law, explicit Euler step of ell
-        const float dT = undercooling(P, gm, S, p, gm.dT_base);
-        float dl = __fmul_rn(growth_v(P, dT), P.dt_over_h);
-        if (dl > 1.f) {
-          dl = 1.f;
-          clamped = true;
-        }
-        const float e = __fadd_rn(r.ell, dl);
-        // the target is reached within 2^-20 of a full spacing, so a step
-        // commensurate with h does not lose a step to binary32 rounding
-        if (e >= 1.f - 0x1p-20f) {
+        const float e = euler_ell(P, gm, S, p, r.ell, clamped);
+        if (reaches_target(e)) {
           r.cross = 1;
           r.ell = fmaxf(__fsub_rn(e, 1.f), 0.f);
           crossing = true;
@@ -1662,6 +1668,8 @@ __device__ __forceinline__ uint32_t group_slot(uint32_t key) {
 }
 
 // One warp per group of kGroupCells cells (groups strided over the warps of the grid).
+// It writes the moving particles' half of the single run's interleaved table (entry
+// 2 sg).
 // s_c holds the group's cell counts, then the sorted position of each cell's next
 // record, which the last pass advances to give every grouped record its sorted
 // position (dest).  Each lane sums its 32 cells, one warp scan gives the lanes' first
@@ -1739,7 +1747,8 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
         if (cnt) {
           if (cnt >= kSegMaxCount) atomicOr(&st->err, ERR_CELL_OVERFLOW);
           const uint32_t cc = cnt < kSegMaxCount ? cnt : kSegMaxCount;
-          tab[sg + h] = make_uint4(start, (stamp << 16) | (sat ? 0x8000u : 0u) | cc, nb[0], nb[1]);
+          tab[2 * (sg + h)] = make_uint4(start, (stamp << 16) | (sat ? 0x8000u : 0u) | cc, nb[0],
+                                         nb[1]);
         }
       }
     }
@@ -1815,7 +1824,8 @@ __global__ void __launch_bounds__(256) k_act_list(const uint8_t* __restrict__ sa
 
 // ---------------------------------------------------------------------------------
 // obstacle flush (one run): the FROZEN records of the ordered dynamic store join the
-// obstacle store.
+// obstacle store, whose table is the odd half of the interleaved table (otab points at
+// entry 1, stride 2).
 //   k_obs_count  FROZEN records per tile of kObsTile ordered records (state bytes of
 //                the gather), summed into DevStats::obs_new
 //   k_scan_sums  exclusive scan of the tile counts
@@ -1983,7 +1993,7 @@ __global__ void __launch_bounds__(256) k_obs_table(Params P, const uint32_t* __r
                                                    uint32_t* err) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  seg_build<uint32_t, true>(P.geo, okey, j, n, __ldg(okey + j), otab, 1u, err);
+  seg_build<uint32_t, true, 2>(P.geo, okey, j, n, __ldg(okey + j), otab, 1u, err);
 }
 
 // Runs one bounded wait whose word nothing ever publishes (one thread), with a

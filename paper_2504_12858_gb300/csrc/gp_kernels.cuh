@@ -40,13 +40,21 @@ void launch_nucleate_batch(const Params& P, const StepArgs& S1, const float4* np
                            const int2* nmeta, int* nstate, int m, int4* rout, uint64_t* keys,
                            uint32_t* vals, int64_t cap, const Claims& C, const Reached& R,
                            DevStats* dst, int sms, cudaStream_t st);
-// adjoint tape and reverse sweep (gp_adjoint.cu)
-void launch_tape_state(const int4* rs, int64_t n, uint8_t* out, cudaStream_t st);
+// adjoint tape and reverse sweep (gp_adjoint.cu), in store order.  tape_state: the
+// post-contact state of sorted particle j at its store index src[j]; tape_out (after
+// the step): the emit's sorted parent indices to store indices and the direction of
+// every particle of the new store; adj_replay: the store of step n+1 from that of
+// step n and the taped events; adj_step: one reverse step
+void launch_tape_state(const int4* rs, const uint32_t* src, int64_t n, uint8_t* out,
+                       cudaStream_t st);
+void launch_tape_out(int32_t* par, const uint32_t* src, const int4* rec, uint8_t* code,
+                     int64_t cap, const DevStats* dst, int sms, cudaStream_t st);
+void launch_adj_replay(const Params& P, const StepArgs& S, const int4* rec, const uint8_t* post,
+                       const int32_t* par, const uint8_t* code, int64_t m, int4* out,
+                       cudaStream_t st);
 void launch_adj_step(const Params& P, const StepArgs& S, float t, const int4* rec,
                      const uint8_t* post, const int32_t* par, const float* lam_u, int64_t m,
                      float* lam_s, double* grad, cudaStream_t st);
-void launch_adj_unsort(const float* lam_s, const uint32_t* vals, int64_t n, float* lam_u,
-                       cudaStream_t st);
 void launch_nucleate(const Params& P, const StepArgs& S1, const float4* npos, const float4* ngrain,
                      int* nstate, int m, float4* gtab, int max_grains, int4* rout, uint32_t* keys,
                      uint32_t* vals, int64_t cap, const Claims& C, const Reached& R, DevStats* dst,

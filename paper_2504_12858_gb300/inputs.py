@@ -396,15 +396,18 @@ def thin_sample(lambda0: float = 48e-6, steps: int = 200) -> Workload:
 
 
 def adjoint_cube(seed: int = 5, n_grains: int = 32, steps: int = 200, A: float = 1e-5,
-                 n: float = 2.0, G: float = 1e3, Tdot: float = 10.0) -> Workload:
+                 n: float = 2.0, G: float = 1e3, Tdot: float = 10.0,
+                 height: float = 200e-6) -> Workload:
     """Calibration case of the adjoint: the 200 um single-grain cube with 32 grains
-    (seed 5), T = T_L - 5 + G (z - z_c) - Tdot t, v = A dT^n, h = 2 um, dt = 2 ms."""
+    (seed 5), T = T_L - 5 + G (z - z_c) - Tdot t, v = A dT^n, h = 2 um, dt = 2 ms.
+    With height > 200 um the box is taller than the cube that holds the seeds, so the
+    highest point of the envelope grows freely (the front height stays ACTIVE)."""
     g = rng(seed)
     L = 200e-6
     seeds = g.random((n_grains, 3)) * L
     q = shoemake_quaternions(n_grains, g)
     T_L = 1000.0
     return Workload(
-        name="adjoint_cube", lo=(0.0, 0.0, 0.0), hi=(L, L, L), h=2e-6, dt=2e-3, a=(A,), b=(n,),
-        T_L=T_L, steps=steps, seeds=seeds, quats=q,
+        name="adjoint_cube", lo=(0.0, 0.0, 0.0), hi=(L, L, height), h=2e-6, dt=2e-3, a=(A,),
+        b=(n,), T_L=T_L, steps=steps, seeds=seeds, quats=q,
         analytic=dict(T0=T_L - 5.0, G=(0.0, 0.0, G), xref=(0.0, 0.0, L / 2), Tdot=-Tdot))

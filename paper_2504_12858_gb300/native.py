@@ -54,7 +54,8 @@ class gp_memory(C.Structure):
                 ("claim_blocks", C.c_int64), ("max_grains", C.c_int32),
                 ("max_nuclei", C.c_int32), ("grid_nodes", C.c_int64),
                 ("tape_steps", C.c_int64), ("arena", C.c_void_p),
-                ("arena_bytes", C.c_size_t), ("solute_nodes", C.c_int64)]
+                ("arena_bytes", C.c_size_t), ("solute_nodes", C.c_int64),
+                ("tape_checkpoint_every", C.c_int64)]
 
 
 STATS_FIELDS = ["step", "n_live", "n_active", "n_frozen", "n_grains", "n_reached",
@@ -202,14 +203,15 @@ class Sim:
 
     def __init__(self, lo, hi, h, dt, a, b, T_L, capacity, reached_capacity=0,
                  claim_blocks=0, max_grains=0, max_nuclei=0, grid_nodes=0, tape_steps=0,
-                 stream=None, device="cuda", solute_nodes=0):
+                 stream=None, device="cuda", solute_nodes=0, tape_checkpoint_every=0):
         self.lo, self.hi = tuple(lo), tuple(hi)
         self._open([(lo, hi)], False, h, dt, a, b, T_L, capacity, reached_capacity,
                    claim_blocks, max_grains, max_nuclei, grid_nodes, tape_steps, stream, device,
-                   solute_nodes)
+                   solute_nodes, tape_checkpoint_every)
 
     def _open(self, domains, batch, h, dt, a, b, T_L, capacity, reached_capacity, claim_blocks,
-              max_grains, max_nuclei, grid_nodes, tape_steps, stream, device, solute_nodes=0):
+              max_grains, max_nuclei, grid_nodes, tape_steps, stream, device, solute_nodes=0,
+              tape_checkpoint_every=0):
         import torch
         self._torch = torch
         L = load()
@@ -226,6 +228,7 @@ class Sim:
         mem.grid_nodes = int(grid_nodes)
         mem.tape_steps = int(tape_steps)
         mem.solute_nodes = int(solute_nodes)
+        mem.tape_checkpoint_every = int(tape_checkpoint_every)
         nb = C.c_size_t(0)
         if batch:
             self._check(L.gp_batch_arena_bytes(self.nruns, self._doms, self.h, C.byref(mem),

@@ -88,12 +88,12 @@ def tip_signatures(p, n_grains):
     return [tuple(sorted(x)) for x in sig], top
 
 
-def oracle_front_run(theta):
+def oracle_front_run(job):
     """Oracle front outputs (H, F), tip signatures and highest particle of the adjoint
-    case for theta = (A, n, G, Tdot) (runs in a worker process)."""
+    case for job = (theta, height), theta = (A, n, G, Tdot) (runs in a worker process)."""
     from paper_2504_12858_gb300.adjoint import front_outputs
-    A, n, G, Tdot = theta
-    w = inputs.adjoint_cube(A=A, n=n, G=G, Tdot=Tdot)
+    (A, n, G, Tdot), height = job
+    w = inputs.adjoint_cube(A=A, n=n, G=G, Tdot=Tdot, height=height)
     o = oracle_from(w)
     o.step(w.steps)
     p = o.particles()
