@@ -607,9 +607,10 @@ def application_workloads(dev):
                  "liquidus, particles on the fusion line heading into the melt, 2000 steps "
                  "of 0.1 ms (the source crosses the plate)",
         input_generation_s=round(time.perf_counter() - t0, 1))
-    # the solid left behind the moving pool: up to about 1e9 reached lattice sites
+    # the solid left behind the moving pool: up to about 1e9 reached lattice sites and
+    # 1e8 particles on its grain boundaries
     guarded("weld_natural",
-            lambda: _workload_run(w, w.steps, 40000000, dev, reached_capacity=1500000000,
+            lambda: _workload_run(w, w.steps, 200000000, dev, reached_capacity=1500000000,
                                   claim_blocks=8000000))
     return out
 

@@ -253,22 +253,22 @@ gp_status gp_set_obstacle_store(gp_ctx* ctx, int32_t mode);
 
 /* Inspection of the ordering of the particle step (used by the tests; the paper has
  * no counterpart).  which = 0: runs on the current state the ordering the next gp_step
- * starts with (cell key of every particle of the per-step store, the particles grouped
- * by tile of 1024 cells and ordered by cell inside each tile, the cell table), without
- * advancing the state, and copies to host arrays (any may be NULL):
+ * starts with, without advancing the state: the cell key of every particle, and the
+ * cell-ordered sequence that the contact search reads, which holds the particles of
+ * the per-step store (grouped by tile of 1024 cells, ordered by cell inside each tile)
+ * and those of the obstacle store; it copies to host arrays (any may be NULL):
  *   keys_in     the cell key of every particle, in the order of gp_get_particles;
- *   keys_sorted the keys in the ordered sequence;
- *   src         the gp_get_particles index of each ordered particle;
+ *   keys_sorted the keys of the sequence (*n_out entries, all particles);
+ *   src         the gp_get_particles index of each entry of the sequence;
  *   table       4 words per segment of 16 cells (table_cap segments at most): index
- *               of its first ordered particle, stamp << 16 | saturation flag << 15 |
- *               count, then the 4-bit counts (saturated at 15) of cells 0-7 and 8-15;
- *               an entry whose stamp differs from *stamp is an empty segment.
+ *               of its first entry, stamp << 16 | saturation flag << 15 | count, then the
+ *               4-bit counts (saturated at 15) of cells 0-7 and 8-15; an entry whose
+ *               stamp differs from *stamp is an empty segment.
  * Particles of one cell may come in any order (the ordering places them by atomic
- * counters); keys, cells and counts are exact.
- * which = 1: the obstacle store: keys_sorted, src (identity: the obstacles are the
- * last *n_out particles of gp_get_particles, in order) and its table (*stamp = 1; an
- * entry with count 0 is empty).  *n_out receives the particle count, *n_seg the
- * number of segments of the table.  GP_ERR_STATE on a batch context. */
+ * counters); keys, cells and counts are exact.  which = 1: the obstacle store: its
+ * *n_out keys in its order in keys_sorted, src the gp_get_particles index of each (the
+ * obstacles are the last particles that gp_get_particles lists), no table (*n_seg = 0).
+ * GP_ERR_STATE on a batch context. */
 gp_status gp_inspect_order(gp_ctx* ctx, int32_t which, int64_t cap, uint32_t* keys_in,
                            uint32_t* keys_sorted, uint32_t* src, int64_t* n_out,
                            uint32_t* table, int64_t table_cap, int64_t* n_seg,

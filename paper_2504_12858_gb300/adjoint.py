@@ -56,7 +56,7 @@ class FrontAdjoint(torch.autograd.Function):
         A, n, G, Tdot = (float(v) for v in theta.detach().cpu().numpy())
         an = w.analytic
         sim = native.Sim(w.lo, w.hi, w.h, w.dt, (A,), (n,), w.T_L, capacity=capacity,
-                         reached_capacity=4 * capacity, max_grains=len(w.seeds) + 8,
+                         reached_capacity=10 * capacity, max_grains=len(w.seeds) + 8,
                          tape_steps=w.steps, tape_checkpoint_every=every)
         sim.gp_set_thermal_analytic(an["T0"], (0.0, 0.0, G), an["xref"], -Tdot)
         sim.gp_add_grains(w.seeds, w.quats)

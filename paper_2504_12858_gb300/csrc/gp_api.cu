@@ -50,7 +50,7 @@ struct Layout {
       sgrid, runs,
       rtherm, rcount, tape_post, tape_par, tape_code, tape_ckpt, tape_replay, tape_svals,
       tape_grad, gcnt, gofs, gfill,
-      gbsum, gkey, gdest, orec[2], opos[2], okey[2], otcnt, osplit, total;
+      gbsum, gkey, gdest, orec[2], opos[2], okey[2], otcnt, ogofs[2], msrc, total;
   uint32_t ngroups = 0;  // one run: cell groups of the record grouping
 };
 
@@ -174,9 +174,7 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->sstatus = take(4 * radix_status_words(L->cap, L->key_bytes));
   L->hist = take(4 * 256 * (size_t)((L->nbits + 7) / 8));  // one histogram per digit
   L->tickets = take(4 * 8);
-  // cell table: a batch one entry per segment; a single run two interleaved entries
-  // per segment (its moving particles, then its obstacle store)
-  L->cells = take((batch ? 16 : 32) * (size_t)L->nseg);
+  L->cells = take(16 * (size_t)L->nseg);
   L->rkey = take(8 * (size_t)L->rcap);
   L->rnext = take(4 * (size_t)L->rcap);
   L->rhead = take(4 * (size_t)L->nheads);
@@ -216,16 +214,18 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->gbsum = take(4 * (((size_t)L->ngroups + 255) / 256) + 16);
   L->gkey = take(batch ? 16 : 4 * cap + 16);   // one run: cell keys in grouped order
   L->gdest = take(batch ? 16 : 4 * cap + 16);  // and the sorted position of each
-  // one run: the obstacle store (FROZEN records ordered by cell key, positions, keys;
-  // two copies, merged from one into the other) and its cell table
+  // one run: the obstacle store (FROZEN records ordered by cell key, positions, keys,
+  // the first obstacle of every group; two copies, a flush writes one from the other),
+  // the source of every entry of the cell-ordered sequence and the flush's tile counts
   const size_t ocap = batch ? 1 : cap;
   for (int b = 0; b < 2; ++b) {
     L->orec[b] = take(16 * ocap);
     L->opos[b] = take(16 * ocap);
     L->okey[b] = take(4 * ocap + 16);
+    L->ogofs[b] = take(4 * ((size_t)L->ngroups + 16));
   }
+  L->msrc = take(4 * ocap + 16);
   L->otcnt = take(4 * (ocap / 8192 + 16));
-  L->osplit = take(4 * (2 * ocap / 2048 + 16));
   L->total = o;
   return true;
 }
@@ -561,15 +561,6 @@ gp_status push_counts(gp_ctx* c) {
   return GP_OK;
 }
 
-// the obstacle store's half of a single run's interleaved cell table (entry 2 sg + 1)
-uint4* obs_tab(gp_ctx* c) { return c->cells + 1; }
-
-// clears one half (0: moving particles, 1: obstacles) of a single run's interleaved table
-gp_status clear_half(gp_ctx* c, int half) {
-  GP_CUDA(c, cudaMemset2DAsync(c->cells + half, 32, 0, 16, c->L.nseg, c->st));
-  return GP_OK;
-}
-
 // The obstacle store serves the plain single-run step.  Periodic axes, melting (which
 // removes frozen particles) and the adjoint tape (which follows every particle through
 // every step) keep all particles in the dynamic store.
@@ -581,7 +572,7 @@ bool obs_usable(const gp_ctx* c) {
 gp_status obs_reset(gp_ctx* c) {
   c->n_obs = 0;
   c->obs_carry = 0;
-  return c->batch ? GP_OK : clear_half(c, 1);
+  return GP_OK;
 }
 
 // moves the obstacle records back to the end of the dynamic store (its keys are then
@@ -727,7 +718,7 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   if (batch) c->sb.n_dev = &c->dst->n_live;  // device-sized sort
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
-  e = e ? e : cudaMemsetAsync(c->cells, 0, (batch ? 16 : 32) * L.nseg, s);
+  e = e ? e : cudaMemsetAsync(c->cells, 0, 16 * L.nseg, s);
   e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.nheads, s);
   e = e ? e : cudaMemsetAsync(c->C.bucket, 0, 16 * (size_t)L.buckets, s);
   e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.blocks, s);
@@ -1061,53 +1052,75 @@ gp_status gp_inspect_order(gp_ctx* c, int32_t which, int64_t cap, uint32_t* keys
   if (c->batch) return fail(c, GP_ERR_STATE, "the inspection is for single-run contexts");
   if ((which != 0 && which != 1) || cap < 0 || table_cap < 0)
     return fail(c, GP_ERR_ARG, "bad arguments");
-  if (n_seg) *n_seg = (int64_t)c->L.nseg;
-  const int64_t n = which == 0 ? c->n_live : c->n_obs;
-  if (n_out) *n_out = n;
-  const int64_t m = std::min(n, cap);
-  const uint4* tab = obs_tab(c);
-  if (which == 0) {
-    if (n > 0) {
-      const Params P = step_params(c, c->step);
-      if (!c->keys_valid) {
-        launch_keys(false, P, c->rec[c->cur], n, c->sb.keys[0], c->sb.vals[0], c->st);
-        c->keys_valid = true;
-      }
-      if (++c->stamp > 0xffffu) {
-        s = clear_half(c, 0);  // stamps wrap: every moving-particle entry empty
-        if (s) return s;
-        c->stamp = 1;
-      }
-      GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
-      launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), n, c->L.ngroups,
-                         at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
-                         at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
-                         at<uint32_t>(c, c->L.gkey), at<uint32_t>(c, c->L.gdest), c->rec[c->cur],
-                         c->rec[c->cur ^ 1], c->pos4, static_cast<uint32_t*>(c->sb.keys[1]),
-                         c->sb.vals[0], reinterpret_cast<uint8_t*>(c->site_slot), c->cells,
-                         c->stamp, c->act, c->dst, c->sms, nullptr, c->st);
-      GP_CUDA(c, cudaGetLastError());
-    }
-    if (m > 0 && keys_in)
-      GP_CUDA(c, cudaMemcpyAsync(keys_in, c->sb.keys[0], 4 * m, cudaMemcpyDeviceToHost, c->st));
+  const int64_t nd = c->n_live, no = c->n_obs, o = c->ocur;
+  if (which == 1) {  // the obstacle store: keys in its order, no table
+    if (n_out) *n_out = no;
+    if (n_seg) *n_seg = 0;
+    if (stamp) *stamp = 0;
+    const int64_t m = std::min(no, cap);
     if (m > 0 && keys_sorted)
-      GP_CUDA(c, cudaMemcpyAsync(keys_sorted, c->sb.keys[1], 4 * m, cudaMemcpyDeviceToHost, c->st));
-    if (m > 0 && src)
-      GP_CUDA(c, cudaMemcpyAsync(src, c->sb.vals[0], 4 * m, cudaMemcpyDeviceToHost, c->st));
-    tab = c->cells;
-    if (stamp) *stamp = c->stamp;
-  } else {
-    if (m > 0 && keys_sorted)
-      GP_CUDA(c, cudaMemcpyAsync(keys_sorted, at<uint32_t>(c, c->L.okey[c->ocur]), 4 * m,
+      GP_CUDA(c, cudaMemcpyAsync(keys_sorted, at<uint32_t>(c, c->L.okey[o]), 4 * m,
                                  cudaMemcpyDeviceToHost, c->st));
     if (src)
-      for (int64_t i = 0; i < m; ++i) src[i] = (uint32_t)i;
-    if (stamp) *stamp = 1;
+      for (int64_t i = 0; i < m; ++i) src[i] = (uint32_t)(nd + i);
+    GP_CUDA(c, cudaStreamSynchronize(c->st));
+    return GP_OK;
+  }
+  const int64_t nseq = nd + no;
+  if (n_out) *n_out = nseq;
+  if (n_seg) *n_seg = (int64_t)c->L.nseg;
+  if (nd > 0) {  // the ordering the next step starts with
+    const Params P = step_params(c, c->step);
+    if (!c->keys_valid) {
+      launch_keys(false, P, c->rec[c->cur], nd, c->sb.keys[0], c->sb.vals[0], c->st);
+      c->keys_valid = true;
+    }
+    if (++c->stamp > 0xffffu) {
+      GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
+      c->stamp = 1;
+    }
+    GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
+    launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), nd, c->L.ngroups,
+                       at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
+                       at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
+                       at<uint32_t>(c, c->L.gkey), at<uint32_t>(c, c->L.gdest), c->rec[c->cur],
+                       c->rec[c->cur ^ 1], c->pos4, static_cast<uint32_t*>(c->sb.keys[1]),
+                       nullptr, reinterpret_cast<uint8_t*>(c->site_slot), c->cells, c->stamp,
+                       c->act, c->dst, c->sms, nullptr, c->st, at<uint32_t>(c, c->L.okey[o]),
+                       at<float4>(c, c->L.opos[o]), at<uint32_t>(c, c->L.ogofs[o]), no,
+                       at<uint32_t>(c, c->L.msrc));
+    GP_CUDA(c, cudaGetLastError());
+  }
+  if (stamp) *stamp = c->stamp;
+  const int64_t m = std::min(nseq, cap), md = std::min(nd, m);
+  if (keys_in) {  // the key of every particle in gp_get_particles order: moving, then obstacles
+    if (md > 0)
+      GP_CUDA(c, cudaMemcpyAsync(keys_in, c->sb.keys[0], 4 * md, cudaMemcpyDeviceToHost, c->st));
+    if (m > md)
+      GP_CUDA(c, cudaMemcpyAsync(keys_in + md, at<uint32_t>(c, c->L.okey[o]), 4 * (m - md),
+                                 cudaMemcpyDeviceToHost, c->st));
+  }
+  if (m > 0 && keys_sorted)
+    GP_CUDA(c, cudaMemcpyAsync(keys_sorted, c->sb.keys[1], 4 * m, cudaMemcpyDeviceToHost, c->st));
+  std::vector<uint32_t> ms, perm;
+  if (src && m > 0) {
+    ms.resize(m);
+    perm.resize(nd);
+    GP_CUDA(c, cudaMemcpyAsync(ms.data(), at<uint32_t>(c, c->L.msrc), 4 * m,
+                               cudaMemcpyDeviceToHost, c->st));
+    if (nd > 0)
+      GP_CUDA(c, cudaMemcpyAsync(perm.data(), c->sb.vals[1], 4 * nd, cudaMemcpyDeviceToHost,
+                                 c->st));
   }
   const int64_t ts = std::min<int64_t>(table_cap, (int64_t)c->L.nseg);
-  if (table && ts > 0)  // one half of the interleaved table
-    GP_CUDA(c, cudaMemcpy2DAsync(table, 16, tab, 32, 16, ts, cudaMemcpyDeviceToHost, c->st));
+  if (table && ts > 0)
+    GP_CUDA(c, cudaMemcpyAsync(table, c->cells, 16 * ts, cudaMemcpyDeviceToHost, c->st));
   GP_CUDA(c, cudaStreamSynchronize(c->st));
+  // the gp_get_particles index of every entry of the sequence
+  for (int64_t p = 0; src && p < m; ++p) {
+    const uint32_t w = ms[p], idx = w & 0x3fffffffu;
+    src[p] = (w & 0x80000000u) ? (uint32_t)(nd + idx) : perm[idx];
+  }
   return GP_OK;
 }
 
@@ -1361,65 +1374,57 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
         c->keys_valid = true;
       }
       if (++c->stamp > 0xffffu) {
-        s = clear_half(c, 0);  // stamps wrap: every moving-particle entry empty
-        if (s) return s;
+        GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
         c->stamp = 1;
       }
-      int4* sorted = c->rec[c->cur ^ 1];
+      int4* sorted = c->rec[c->cur ^ 1];  // the records in grouped order
       GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
-      // records grouped by cell (in place of the radix sort): the emit's keys in keys[0],
-      // the grouped identities in vals[1], the sorted keys in keys[1], the source index
-      // of each sorted record in vals[0] (for the tape), the ACTIVE flags in the claim-slot
-      // hand-off (overwritten by the advance before the emit reads it)
+      // records grouped by cell tile (in place of the radix sort): the emit's keys in
+      // keys[0], the grouped identities in vals[1]; the cell-ordered sequence of the moving
+      // records and the obstacles (positions, keys in keys[1], sources, cell table); the
+      // store index of each grouped record for the tape; the state bytes in the
+      // claim-slot hand-off (overwritten by the advance before the emit reads it)
+      const int o = c->ocur;
+      const int64_t nseq = n + (obs ? c->n_obs : 0);
       uint32_t* skeys = static_cast<uint32_t*>(c->sb.keys[1]);
+      uint32_t* msrc = at<uint32_t>(c, c->L.msrc);
       launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), n, c->L.ngroups,
                          at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
                          at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
                          at<uint32_t>(c, c->L.gkey), at<uint32_t>(c, c->L.gdest), c->rec[c->cur],
                          sorted, c->pos4, skeys, tsrc,
                          reinterpret_cast<uint8_t*>(c->site_slot), c->cells, c->stamp, c->act,
-                         c->dst, c->sms, &c->prof, c->st);
+                         c->dst, c->sms, &c->prof, c->st, at<uint32_t>(c, c->L.okey[o]),
+                         at<float4>(c, c->L.opos[o]), at<uint32_t>(c, c->L.ogofs[o]),
+                         obs ? c->n_obs : 0, msrc);
       GP_CUDA(c, cudaGetLastError());
-      // obstacle flush: the FROZEN records of the ordered store (hst->n_frozen of them,
-      // as the last emit counted) join the obstacle store once carrying them from step
-      // to step has cost about as much as merging them, counted as kObsCarry record
-      // steps per merged record; the first FROZEN records are flushed at once
+      // obstacle flush: the obstacles and the FROZEN records (hst->n_frozen of them, as the
+      // last emit counted) of the cell-ordered sequence become the new obstacle store once
+      // carrying the FROZEN records from step to step has cost about as much as rewriting
+      // the store, counted as kObsCarry record-steps per obstacle; the first FROZEN records
+      // are flushed at once
       if (obs) {
         const double f = (double)c->hst->n_frozen;
         c->obs_carry += f;
         if (f > 0 && (c->obs_mode == 2 || kObsCarry * c->obs_carry >= (double)c->n_obs + f)) {
           c->prof.begin(K_OBS);
-          uint32_t* flist = at<uint32_t>(c, c->L.gdest);
-          launch_obs_list(reinterpret_cast<const uint8_t*>(c->site_slot), n,
-                          at<uint32_t>(c, c->L.otcnt), sorted, flist, c->dst, c->st);
+          launch_obs_flush(msrc, skeys, c->pos4, nseq, at<uint32_t>(c, c->L.otcnt),
+                           at<int4>(c, c->L.orec[o]), sorted, at<uint32_t>(c, c->L.okey[o ^ 1]),
+                           at<float4>(c, c->L.opos[o ^ 1]), at<int4>(c, c->L.orec[o ^ 1]),
+                           c->L.ngroups, at<uint32_t>(c, c->L.ogofs[o ^ 1]), c->dst, c->st);
           GP_CUDA(c, cudaMemcpyAsync(&c->hst->obs_new, &c->dst->obs_new, sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, c->st));
           GP_CUDA(c, cudaStreamSynchronize(c->st));
-          const int64_t nf = (int64_t)c->hst->obs_new;
-          if (c->n_obs + nf > c->L.cap) {
-            c->broken = true;
-            return fail(c, GP_ERR_CAPACITY, "particle capacity exceeded");
-          }
-          if (nf > 0) {
-            const int o = c->ocur;
-            launch_obs_merge(P, at<uint32_t>(c, c->L.okey[o]), at<float4>(c, c->L.opos[o]),
-                             at<int4>(c, c->L.orec[o]), c->n_obs, skeys, c->pos4, sorted, flist,
-                             nf, at<uint32_t>(c, c->L.osplit), at<uint32_t>(c, c->L.okey[o ^ 1]),
-                             at<float4>(c, c->L.opos[o ^ 1]), at<int4>(c, c->L.orec[o ^ 1]),
-                             obs_tab(c), &c->dst->err, c->st);
-            GP_CUDA(c, cudaGetLastError());
-            c->ocur ^= 1;
-            c->n_obs += nf;
-          }
+          GP_CUDA(c, cudaGetLastError());
+          c->ocur ^= 1;
+          c->n_obs = (int64_t)c->hst->obs_new;
           c->obs_carry = 0;
-          c->prof.end(K_OBS, (double)c->n_obs, nf > 0 ? 6 : 3);
+          c->prof.end(K_OBS, (double)c->n_obs, 4);
         }
       }
-      const Obs ob{obs_tab(c), at<uint32_t>(c, c->L.okey[c->ocur]),
-                   at<float4>(c, c->L.opos[c->ocur]), c->n_obs};
       c->prof.begin(K_ADVANCE);
-      launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp, n, c->act,
-                     c->C, c->site_slot, c->dst, c->st, obs ? &ob : nullptr);
+      launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp, nseq, c->act,
+                     c->C, c->site_slot, c->dst, c->st, n, at<uint32_t>(c, c->L.gdest));
       // units: the ACTIVE particles entering the step (live minus frozen after the last step)
       c->prof.end(K_ADVANCE, (double)(n - std::min<int64_t>(n, (int64_t)c->hst->n_frozen)));
       if (rec) launch_tape_state(sorted, tsrc, n, at<uint8_t>(c, c->L.tape_post) + tq * tcap, c->st);

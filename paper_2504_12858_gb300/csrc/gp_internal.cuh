@@ -662,19 +662,12 @@ struct DevStats {
 
 // ---------------------------------------------------------------------------------
 // obstacle store of a single run.  A FROZEN particle never moves again (Sec. 2.1.2:
-// points of two grains that meet stop for good and form the grain boundary), so it
-// need not be reordered, gathered and re-emitted every step.  Flushes move the FROZEN
-// records of the dynamic store into the obstacle store, which keeps them ordered by
-// cell key with their positions and its own cell table (entries in the format of the
-// dynamic table; a count of zero marks an empty segment, no stamp).  The contact
-// search reads both tables.
+// points of two grains that meet stop for good and form the grain boundary), so its
+// record need not be regrouped, gathered and re-emitted every step.  Flushes move the
+// FROZEN records into an obstacle store ordered by cell key (records, positions, keys);
+// every step's ordering copies the obstacles' positions and keys into the cell-ordered
+// sequence that the contact search reads, beside the moving records.
 // ---------------------------------------------------------------------------------
-struct Obs {
-  const uint4* tab;
-  const uint32_t* keys;
-  const float4* pos;
-  int64_t n;
-};
 
 // warp-aggregated 64-bit counter increment
 __device__ __forceinline__ void warp_add(unsigned long long* ctr, unsigned int v) {

@@ -38,10 +38,7 @@ constexpr uint32_t kNoEntry = 0xffffffffu;
 //      the segment (low 15 bits)
 //   z, w: particle count of each of the 16 cells, 4 bits each (cell 0 in the low
 //         nibble of z), saturated at 15; the flag is set when any count saturates
-// An entry whose stamp is not the current build's is an empty segment.  A single run
-// interleaves two tables, entry 2 sg for its moving particles and entry 2 sg + 1 for
-// its obstacle store (a 32-byte sector holds both halves of a segment; stride TS = 2).
-// A query
+// An entry whose stamp is not the current build's is an empty segment.  A query
 // turns the 3 cells x-1..x+1 of a neighbour row into a candidate range directly
 // from the nibble counts; when a count is saturated it scans the segment's keys.
 // Two cell orders.  Linear (the stand-alone hash): local = (z ny + y) nx + x, segments
@@ -91,7 +88,7 @@ __device__ __forceinline__ uint32_t local_tiled(const Geo& g, int cx, int cy, in
 
 // Writes the entry of the segment that starts at sorted index j (if one does).
 // The keys of the run are key0 + local; a key outside that range ends the run.
-template <class K, bool TILED, int TS = 1>
+template <class K, bool TILED>
 __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ skeys, int64_t j,
                                           int64_t n, K key, uint4* __restrict__ tab,
                                           uint32_t stamp, uint32_t* err) {
@@ -124,8 +121,8 @@ __device__ __forceinline__ void seg_build(const Geo& gm, const K* __restrict__ s
       break;
   }
   const bool sat = ((nib & (nib >> 1) & (nib >> 2) & (nib >> 3)) & 0x1111111111111111ull) != 0;
-  tab[(gm.seg0 + sg) * TS] = make_uint4((uint32_t)j, (stamp << 16) | (sat ? 0x8000u : 0u) | c,
-                                        (uint32_t)nib, (uint32_t)(nib >> 32));
+  tab[gm.seg0 + sg] = make_uint4((uint32_t)j, (stamp << 16) | (sat ? 0x8000u : 0u) | c,
+                                 (uint32_t)nib, (uint32_t)(nib >> 32));
 }
 
 // the eight 4-bit counts of v summed in pairs, one pair per byte (at most 30 each)
@@ -179,10 +176,7 @@ __device__ __forceinline__ bool row_range(const uint4 e, uint32_t mz0, uint32_t 
 // PAIRS == false: returns at the first one.  PAIRS == true: visits all of them and
 // appends the pairs (idj, ids[i]) with idj < ids[i] to pairs (up to pair_cap,
 // counted in *npairs).  Returns whether any was found.
-// OBS == true (one run, first hit only): the rows of the obstacle store's table, at
-// the same segment index, are searched beside those of the dynamic table, in one loop
-// over the two candidate ranges of each row.  TS: stride of the table entries.
-template <bool PAIRS, class K, bool TILED, bool OBS = false, int TS = 1>
+template <bool PAIRS, class K, bool TILED>
 __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                              const uint4* __restrict__ tab, uint32_t stamp,
                                              const K* __restrict__ skeys,
@@ -191,9 +185,7 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                              const uint32_t* __restrict__ ids = nullptr,
                                              uint32_t idj = 0, int32_t* pairs = nullptr,
                                              int64_t pair_cap = 0,
-                                             unsigned long long* npairs = nullptr,
-                                             const Obs* ob = nullptr) {
-  static_assert(!(OBS && PAIRS), "the obstacle layer is searched for first hits");
+                                             unsigned long long* npairs = nullptr) {
   bool hit = false;
   const int x0 = max(cx - 1, 0), x1 = min(cx + 1, gm.nc[0] - 1);
   const int y0 = max(cy - 1, 0), y1 = min(cy + 1, gm.nc[1] - 1);
@@ -216,29 +208,9 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
                                 : ((uint32_t)z * (uint32_t)gm.nc[1] + (uint32_t)y) *
                                           (uint32_t)gm.nc[0] + (uint32_t)(base + c0));
         const K khi = klo + (K)(c1 - c0);
-        const uint4 e = __ldg(rtab + (size_t)sg * TS);
+        const uint4 e = __ldg(rtab + sg);
         uint32_t i, end;
-        if constexpr (OBS) {
-          const uint4 eo = __ldg(ob->tab + (size_t)sg * TS);
-          if ((e.y >> 16) != stamp ||
-              !row_range<K>(e, mz0, mw0, rz, rw, klo, khi, skeys, n, i, end))
-            i = end = 0;
-          uint32_t io, eend;
-          if ((eo.y & kSegMaxCount) == 0 ||
-              !row_range<uint32_t>(eo, mz0, mw0, rz, rw, (uint32_t)klo, (uint32_t)khi, ob->keys,
-                                   ob->n, io, eend))
-            io = eend = 0;
-          // candidates t < nd from the moving particles, the others from the obstacles
-          const uint32_t nd = end - i, tot = nd + (eend - io);
-          const float4* __restrict__ pd = pos4 + i;
-          const float4* __restrict__ po = ob->pos + io - nd;
-          for (uint32_t t = 0; t < tot; ++t) {
-            const float4 o = __ldg((t < nd ? pd : po) + t);
-            if (__float_as_int(o.w) == gw) continue;
-            if (dist2_rn(p, make_float3(o.x, o.y, o.z)) < P.rc2) return true;
-          }
-        } else if ((e.y >> 16) == stamp &&
-                   row_range<K>(e, mz0, mw0, rz, rw, klo, khi, skeys, n, i, end)) {
+        if ((e.y >> 16) == stamp && row_range<K>(e, mz0, mw0, rz, rw, klo, khi, skeys, n, i, end)) {
           for (; i < end; ++i) {
             const float4 o = __ldg(pos4 + i);
             if (__float_as_int(o.w) == gw) continue;
@@ -265,7 +237,7 @@ __device__ __forceinline__ bool contact_scan(const Params& P, const Geo& gm,
 // contact_scan (first hit only) for a single run with periodic axes: neighbour rows
 // and cells wrap around the periodic faces and distances take the nearest image.
 // With at least three cells per periodic axis the 27 cells are distinct.
-template <class K, int TS = 1>
+template <class K>
 __device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __restrict__ tab,
                                  uint32_t stamp, const K* __restrict__ skeys,
                                  const float4* __restrict__ pos4, int64_t n, float3 p, int gw,
@@ -297,7 +269,7 @@ __device__ bool contact_scan_per(const Params& P, const Geo& gm, const uint4* __
         const int x0 = wx0[wi], x1 = wx1[wi];
         for (int sgi = x0 >> kSegShift; sgi <= (x1 >> kSegShift); ++sgi) {
           const uint32_t sg = seg_tiled(gm, sgi, y, z);
-          const uint4 e = __ldg(rtab + (size_t)sg * TS);
+          const uint4 e = __ldg(rtab + sg);
           if ((e.y >> 16) != stamp) continue;
           const int base = sgi << kSegShift;
           const int c0 = max(x0, base) - base, c1 = min(x1, base + kSegCells - 1) - base;
@@ -580,7 +552,10 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
 // ---------------------------------------------------------------------------------
 // k_advance: contact freeze, growth, advance, spawn claims (sorted store, in place)
 // ---------------------------------------------------------------------------------
-template <bool BATCH, class K, bool PER = false, bool OBS = false>
+// A batch: rs and pos4 share the sorted index.  A single run: rs is in grouped order and
+// mpos[j] is the position of record j in the cell-ordered sequence (pos4, skeys, tab) that
+// also holds the obstacle store; n is that sequence's length.
+template <bool BATCH, class K, bool PER = false>
 __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
                                                  const K* __restrict__ skeys,
@@ -588,7 +563,7 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
                                                  uint32_t stamp, int64_t n,
                                                  const uint32_t* __restrict__ act, Claims C,
                                                  int32_t* __restrict__ site_slot, DevStats* st,
-                                                 Obs ob) {
+                                                 const uint32_t* __restrict__ mpos) {
   if constexpr (BATCH) {
     n = (int64_t)st->n_live;
     stamp = (uint32_t)st->stamp;
@@ -614,20 +589,17 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
     // it, so that it does not occupy registers during the search
     if (j >= 0 && ((((uint32_t)__ldg(&rs[j].z)) >> 20) & 3u) == (uint32_t)ST_ACTIVE) {
       active = true;
-      const float4 q = __ldg(pos4 + j);
+      const float4 q = __ldg(pos4 + (BATCH ? j : (int64_t)__ldg(mpos + j)));
       const float3 p = make_float3(q.x, q.y, q.z);
       const int gw = __float_as_int(q.w);
       const Geo& gm = geo_of<BATCH>(P, (int)((uint32_t)gw >> kRunShift));
       int cx, cy, cz;
       cell_local(gm, p, cx, cy, cz);
       bool hit;
-      // a single run interleaves its two cell tables (stride 2), a batch has one
-      constexpr int TS = BATCH ? 1 : 2;
       if constexpr (PER)
-        hit = contact_scan_per<K, TS>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
+        hit = contact_scan_per<K>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
       else
-        hit = contact_scan<false, K, true, OBS, TS>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx,
-                                                    cy, cz, nullptr, 0, nullptr, 0, nullptr, &ob);
+        hit = contact_scan<false, K, true>(P, gm, tab, stamp, skeys, pos4, n, p, gw, cx, cy, cz);
       Rec r = rec_unpack(rs[j]);
       g = r.grain;
       if (hit) {
@@ -1668,16 +1640,23 @@ __device__ __forceinline__ uint32_t group_slot(uint32_t key) {
 }
 
 // One warp per group of kGroupCells cells (groups strided over the warps of the grid).
-// It writes the moving particles' half of the single run's interleaved table (entry
-// 2 sg).
-// s_c holds the group's cell counts, then the sorted position of each cell's next
-// record, which the last pass advances to give every grouped record its sorted
-// position (dest).  Each lane sums its 32 cells, one warp scan gives the lanes' first
-// positions, and each lane then writes its cells' offsets and its two cell-table entries.
+// The cell-ordered sequence of a single run holds its moving records and its obstacle
+// store (the obstacles of a group, okey/opos[ogofs[g] .. ogofs[g+1]), already ordered by
+// cell, are copied into it).  s_c holds the group's cell counts, moving records in the low
+// 16 bits and obstacles in the high 16 bits of each counter, then the position of each
+// cell's next entry in the sequence, which the last pass advances to place every entry
+// (dest for the moving records).  Each lane sums its 32 cells, one warp scan gives the
+// lanes' first positions, and each lane then writes its cells' offsets and its two
+// cell-table entries (counts of both kinds).  msrc[position] tells the flush what the entry
+// is: an obstacle (bit 31 | obstacle index) or a moving record (grouped index; bit 30 if
+// FROZEN, set by the gather).
 __global__ void __launch_bounds__(256, 6) k_group_order(
     const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ ofs,
     const uint32_t* __restrict__ bsum, uint32_t ng, int64_t n, uint64_t seg0,
-    uint32_t* __restrict__ dest, uint4* __restrict__ tab, uint32_t stamp, DevStats* st) {
+    uint32_t* __restrict__ dest, uint4* __restrict__ tab, uint32_t stamp, DevStats* st,
+    const uint32_t* __restrict__ okey, const float4* __restrict__ opos,
+    const uint32_t* __restrict__ ogofs, int64_t no, float4* __restrict__ pos4,
+    uint32_t* __restrict__ skeys, uint32_t* __restrict__ msrc) {
   __shared__ uint4 s_c4[8][32 * kGroupRow / 4];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* c = reinterpret_cast<uint32_t*>(s_c4[w]);
@@ -1685,7 +1664,8 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
   for (int64_t g = (int64_t)blockIdx.x * 8 + w; g < (int64_t)ng; g += (int64_t)gridDim.x * 8) {
     const uint32_t s = tile_start(ofs, bsum, g, ng, n);
     const uint32_t e = tile_start(ofs, bsum, g + 1, ng, n);
-    if (s >= e) continue;  // warp-uniform
+    const uint32_t os = no ? __ldg(ogofs + g) : 0u, oe = no ? __ldg(ogofs + g + 1) : 0u;
+    if (s >= e && os >= oe) continue;  // warp-uniform
 #pragma unroll
     for (int q = 0; q < kGroupRow / 4; ++q) s_c4[w][q * 32 + lane] = make_uint4(0, 0, 0, 0);
     __syncwarp();
@@ -1698,12 +1678,21 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
       for (int u = 0; u < 4; ++u)
         if (i0 + 32 * u < e) atomicAdd(c + group_slot(k[u]), 1u);
     }
+    for (uint32_t i0 = os + lane; i0 < oe; i0 += 128) {
+      uint32_t k[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) k[u] = i0 + 32 * u < oe ? __ldg(okey + i0 + 32 * u) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + 32 * u < oe) atomicAdd(c + group_slot(k[u]), 1u << 16);
+    }
     __syncwarp();
     uint32_t tot = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const uint4 v = row[q];
-      tot += (v.x + v.y) + (v.z + v.w);
+      tot += ((v.x & 0xffffu) + (v.x >> 16)) + ((v.y & 0xffffu) + (v.y >> 16)) +
+             ((v.z & 0xffffu) + (v.z >> 16)) + ((v.w & 0xffffu) + (v.w >> 16));
     }
     uint32_t inc = tot;
 #pragma unroll
@@ -1713,7 +1702,7 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     }
     if (tot) {
       // cells 0-7 / 8-15 of a segment give its z / w word: 4-bit counts saturated at 15
-      uint32_t run = s + inc - tot;
+      uint32_t run = s + os + inc - tot;
       const uint64_t sg = seg0 + ((uint64_t)g << (kGroupShift - kSegShift)) + 2 * lane;
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
@@ -1726,7 +1715,11 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
           for (int t = 0; t < 2; ++t) {
             // cells 8 j + 4 t .. 8 j + 4 t + 3 of the segment
             const int q = 4 * h + 2 * j + t;
-            const uint4 v = row[q];
+            uint4 v = row[q];
+            v.x = (v.x & 0xffffu) + (v.x >> 16);
+            v.y = (v.y & 0xffffu) + (v.y >> 16);
+            v.z = (v.z & 0xffffu) + (v.z >> 16);
+            v.w = (v.w & 0xffffu) + (v.w >> 16);
             uint4 o;
             o.x = run;
             run += v.x;
@@ -1747,12 +1740,26 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
         if (cnt) {
           if (cnt >= kSegMaxCount) atomicOr(&st->err, ERR_CELL_OVERFLOW);
           const uint32_t cc = cnt < kSegMaxCount ? cnt : kSegMaxCount;
-          tab[2 * (sg + h)] = make_uint4(start, (stamp << 16) | (sat ? 0x8000u : 0u) | cc, nb[0],
-                                         nb[1]);
+          tab[sg + h] = make_uint4(start, (stamp << 16) | (sat ? 0x8000u : 0u) | cc, nb[0], nb[1]);
         }
       }
     }
     __syncwarp();
+    // the obstacles go to their cells' slots, then the moving records (any order inside
+    // a cell)
+    for (uint32_t i0 = os + lane; i0 < oe; i0 += 128) {
+      uint32_t k[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) k[u] = i0 + 32 * u < oe ? __ldg(okey + i0 + 32 * u) : 0u;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + 32 * u < oe) {
+          const uint32_t d = atomicAdd(c + group_slot(k[u]), 1u);
+          pos4[d] = __ldg(opos + i0 + 32 * u);
+          skeys[d] = k[u];
+          msrc[d] = 0x80000000u | (i0 + 32 * u);
+        }
+    }
     for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
       uint32_t k[4];
 #pragma unroll
@@ -1765,22 +1772,24 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
   }
 }
 
-// every grouped record to its sorted position: record, position, key, source index and
-// state byte (1 ACTIVE, 2 FROZEN, 0 otherwise; one thread per record)
+// every grouped record i: the record in grouped order (the store the advance and the emit
+// walk), its position, key and source in the cell-ordered sequence at dest[i], its store
+// index (tape) and its state byte (1 ACTIVE, 2 FROZEN, 0 otherwise); one thread per record
 __global__ void __launch_bounds__(256) k_group_gather(
     Params P, const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ dest, int64_t n, const int4* __restrict__ rin,
     int4* __restrict__ rout, float4* __restrict__ pos4, uint32_t* __restrict__ skeys,
-    uint32_t* __restrict__ svals, uint8_t* __restrict__ sact, DevStats* st) {
+    uint32_t* __restrict__ svals, uint8_t* __restrict__ sact, uint32_t* __restrict__ msrc,
+    int64_t nseq, DevStats* st) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t o = __ldg(perm + i), j = __ldg(dest + i);
-  if ((int64_t)o >= n || (int64_t)j >= n) {  // only after inconsistent keys
+  if ((int64_t)o >= n || (int64_t)j >= nseq) {  // only after inconsistent keys
     atomicOr(&st->err, ERR_TIMEOUT);
     return;
   }
   const int4 rv = __ldg(rin + o);
-  rout[j] = rv;
+  rout[i] = rv;
   const Rec r = rec_unpack(rv);
   float4 gc, r0, r1, r2;
   grain_load(P.gtab, r.grain, gc, r0, r1, r2);
@@ -1788,8 +1797,9 @@ __global__ void __launch_bounds__(256) k_group_gather(
   const float3 pw = P.periodic ? wrap_pos(P, P.geo, p) : p;
   pos4[j] = make_float4(pw.x, pw.y, pw.z, __int_as_float(r.grain));
   skeys[j] = __ldg(gkey + i);
-  if (svals) svals[j] = o;
-  sact[j] = r.state == ST_ACTIVE ? 1 : (r.state == ST_FROZEN ? 2 : 0);
+  msrc[j] = (uint32_t)i | (r.state == ST_FROZEN ? 0x40000000u : 0u);
+  if (svals) svals[i] = o;
+  sact[i] = r.state == ST_ACTIVE ? 1 : (r.state == ST_FROZEN ? 2 : 0);
 }
 
 // list of the ACTIVE sorted indices (one reservation per 1024 records; each warp's
@@ -1823,59 +1833,51 @@ __global__ void __launch_bounds__(256) k_act_list(const uint8_t* __restrict__ sa
 }
 
 // ---------------------------------------------------------------------------------
-// obstacle flush (one run): the FROZEN records of the ordered dynamic store join the
-// obstacle store, whose table is the odd half of the interleaved table (otab points at
-// entry 1, stride 2).
-//   k_obs_count  FROZEN records per tile of kObsTile ordered records (state bytes of
-//                the gather), summed into DevStats::obs_new
-//   k_scan_sums  exclusive scan of the tile counts
-//   k_obs_list   the ordered indices of the FROZEN records, in key order; each is
-//                marked REMOVED in the ordered store, so that the emit drops it (the
-//                contact search of the step still finds its position in the dynamic
-//                table, and in the obstacle table after the merge)
-//   k_obs_split  merge-path split of every output tile of the merge
-//   k_obs_merge  stable merge by cell key of the obstacle store (first among equal
-//                keys) with the listed records: keys, positions, records (FROZEN)
-//   k_obs_table  the merged store's cell table: one entry per occupied segment
-// The old obstacle store is read and a second one written, so its traffic is about
-// 2 x 36 bytes per obstacle record, in coalesced runs, once per flush.
+// obstacle flush (one run).  The cell-ordered sequence of the step holds the obstacle
+// store and the moving records in key order; its entries that are obstacles or FROZEN
+// moving records (msrc bit 31 or bit 30), taken in sequence order, are the new obstacle
+// store, already ordered by key:
+//   k_obs_count    joining entries per tile of kObsTile entries, summed into
+//                  DevStats::obs_new (the new store's size)
+//   k_scan_sums    exclusive scan of the tile counts
+//   k_obs_compact  their keys, positions and records into the other copy of the store;
+//                  a moving record that joins is marked REMOVED in the grouped store, so
+//                  that the emit drops it (the contact search of the step still finds its
+//                  position in the sequence)
+//   k_obs_groups   the first obstacle of every group of kGroupCells cells (binary search
+//                  of the group's first key), which the next steps' ordering reads
+// The step after a flush carries no FROZEN record from before it.
 // ---------------------------------------------------------------------------------
-constexpr int kObsItems = 32;                // ordered records per thread of the listing
-constexpr int kObsTile = 256 * kObsItems;    // records per tile of the listing
-constexpr int kMergeTile = 2048;             // merged outputs per CTA (8 per thread)
+constexpr int kObsItems = 32;                // sequence entries per thread
+constexpr int kObsTile = 256 * kObsItems;    // entries per tile
 
-// state bytes of the kObsItems ordered records j0 .. j0 + 31, four per word (0 past n)
-__device__ __forceinline__ void obs_bytes(const uint8_t* __restrict__ sact, int64_t n, int64_t j0,
-                                          uint32_t w[kObsItems / 4]) {
-  if (j0 + kObsItems <= n) {
-    const uint4* p = reinterpret_cast<const uint4*>(sact + j0);  // j0 is a multiple of 32
-    const uint4 a = __ldg(p), b = __ldg(p + 1);
-    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-  } else {
+// source words of the kObsItems entries j0 .. j0 + 31 (0: not joining, past nseq)
+__device__ __forceinline__ void obs_words(const uint32_t* __restrict__ msrc, int64_t nseq,
+                                          int64_t j0, uint32_t w[kObsItems]) {
+  if (j0 + kObsItems <= nseq) {
+    const uint4* p = reinterpret_cast<const uint4*>(msrc + j0);  // j0 is a multiple of 32
 #pragma unroll
     for (int q = 0; q < kObsItems / 4; ++q) {
-      uint32_t v = 0;
-      for (int b = 0; b < 4; ++b) {
-        const int64_t j = j0 + 4 * q + b;
-        if (j < n) v |= (uint32_t)__ldg(sact + j) << (8 * b);
-      }
-      w[q] = v;
+      const uint4 v = __ldg(p + q);
+      w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
     }
+  } else {
+#pragma unroll
+    for (int q = 0; q < kObsItems; ++q) w[q] = j0 + q < nseq ? __ldg(msrc + j0 + q) : 0u;
   }
 }
 
-// FROZEN records among four state bytes (0, 1 or 2): the bytes with bit 1 set
-__device__ __forceinline__ uint32_t frozen4(uint32_t v) { return __popc((v >> 1) & 0x01010101u); }
+__device__ __forceinline__ bool joins(uint32_t src) { return (src & 0xC0000000u) != 0u; }
 
-__global__ void __launch_bounds__(256) k_obs_count(const uint8_t* __restrict__ sact, int64_t n,
-                                                   uint32_t* __restrict__ tcnt, DevStats* st) {
+__global__ void __launch_bounds__(256) k_obs_count(const uint32_t* __restrict__ msrc,
+                                                   int64_t nseq, uint32_t* __restrict__ tcnt,
+                                                   DevStats* st) {
   __shared__ uint32_t s_warp[8];
   const int64_t j0 = (int64_t)blockIdx.x * kObsTile + (int64_t)threadIdx.x * kObsItems;
-  uint32_t w[kObsItems / 4], c = 0;
-  obs_bytes(sact, n, j0, w);
+  uint32_t w[kObsItems], c = 0;
+  obs_words(msrc, nseq, j0, w);
 #pragma unroll
-  for (int q = 0; q < kObsItems / 4; ++q) c += frozen4(w[q]);
+  for (int q = 0; q < kObsItems; ++q) c += joins(w[q]) ? 1u : 0u;
   uint32_t tot;
   bscan256(c, s_warp, tot);
   if (threadIdx.x == 0) {
@@ -1884,116 +1886,54 @@ __global__ void __launch_bounds__(256) k_obs_count(const uint8_t* __restrict__ s
   }
 }
 
-__global__ void __launch_bounds__(256) k_obs_list(const uint8_t* __restrict__ sact, int64_t n,
-                                                  const uint32_t* __restrict__ tofs,
-                                                  int4* __restrict__ rs,
-                                                  uint32_t* __restrict__ flist) {
+__global__ void __launch_bounds__(256) k_obs_compact(
+    const uint32_t* __restrict__ msrc, const uint32_t* __restrict__ skeys,
+    const float4* __restrict__ pos4, int64_t nseq, const uint32_t* __restrict__ tofs,
+    const int4* __restrict__ orec, int4* __restrict__ rs, uint32_t* __restrict__ okey2,
+    float4* __restrict__ opos2, int4* __restrict__ orec2) {
   __shared__ uint32_t s_warp[8];
   const int64_t j0 = (int64_t)blockIdx.x * kObsTile + (int64_t)threadIdx.x * kObsItems;
-  uint32_t w[kObsItems / 4], c = 0;
-  obs_bytes(sact, n, j0, w);
+  uint32_t w[kObsItems], c = 0;
+  obs_words(msrc, nseq, j0, w);
 #pragma unroll
-  for (int q = 0; q < kObsItems / 4; ++q) c += frozen4(w[q]);
+  for (int q = 0; q < kObsItems; ++q) c += joins(w[q]) ? 1u : 0u;
   uint32_t tot;
   uint32_t o = tofs[blockIdx.x] + bscan256(c, s_warp, tot);
   if (!c) return;
-#pragma unroll
-  for (int q = 0; q < kObsItems / 4; ++q) {
-    uint32_t v = (w[q] >> 1) & 0x01010101u;
-    while (v) {
-      const int b = (__ffs(v) - 1) >> 3;
-      v &= v - 1;
-      const int64_t j = j0 + 4 * q + b;
-      flist[o++] = (uint32_t)j;
-      int* zp = &rs[j].z;
-      *zp = (int)(((uint32_t)*zp & ~(3u << 20)) | ((uint32_t)ST_REMOVED << 20));
+#pragma unroll 1
+  for (int q = 0; q < kObsItems; ++q) {
+    const uint32_t src = w[q];
+    if (!joins(src)) continue;
+    const int64_t j = j0 + q;
+    const uint32_t idx = src & 0x3fffffffu;
+    okey2[o] = __ldg(skeys + j);
+    opos2[o] = __ldg(pos4 + j);
+    if (src & 0x80000000u) {
+      orec2[o] = __ldg(orec + idx);
+    } else {
+      int4 r = rs[idx];  // FROZEN: it moves to the obstacles, the emit drops it
+      orec2[o] = r;
+      r.z = (int)(((uint32_t)r.z & ~(3u << 20)) | ((uint32_t)ST_REMOVED << 20));
+      rs[idx] = r;
     }
+    ++o;
   }
 }
 
-// stable merge order of A (obstacle keys, na) and B (keys of the listed records, nb):
-// A[i] comes before B[j] iff A[i] <= B[j].  The split of diagonal d is the number of
-// A elements among the first d outputs.
-__device__ __forceinline__ uint32_t fkey(const uint32_t* __restrict__ skeys,
-                                         const uint32_t* __restrict__ flist, int64_t j) {
-  return __ldg(skeys + __ldg(flist + j));
-}
-
-__global__ void __launch_bounds__(256) k_obs_split(const uint32_t* __restrict__ okey, int64_t na,
-                                                   const uint32_t* __restrict__ skeys,
-                                                   const uint32_t* __restrict__ flist, int64_t nb,
-                                                   uint32_t* __restrict__ split, int64_t ns) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ns) return;
-  const int64_t d = min(t * (int64_t)kMergeTile, na + nb);
-  int64_t lo = max((int64_t)0, d - nb), hi = min(d, na);
+__global__ void __launch_bounds__(256) k_obs_groups(const uint32_t* __restrict__ okey,
+                                                    const DevStats* st, uint32_t ng,
+                                                    uint32_t* __restrict__ ogofs) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > (int64_t)ng) return;
+  const int64_t n = (int64_t)st->obs_new;
+  const uint64_t key = (uint64_t)g << kGroupShift;
+  int64_t lo = 0, hi = n;
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if (__ldg(okey + mid) <= fkey(skeys, flist, d - 1 - mid)) lo = mid + 1;
+    if ((uint64_t)__ldg(okey + mid) < key) lo = mid + 1;
     else hi = mid;
   }
-  split[t] = (uint32_t)lo;
-}
-
-__global__ void __launch_bounds__(256) k_obs_merge(
-    const uint32_t* __restrict__ okey, const float4* __restrict__ opos,
-    const int4* __restrict__ orec, int64_t na, const uint32_t* __restrict__ skeys,
-    const float4* __restrict__ pos4, const int4* __restrict__ rs,
-    const uint32_t* __restrict__ flist, int64_t nb, const uint32_t* __restrict__ split,
-    uint32_t* __restrict__ okey2, float4* __restrict__ opos2, int4* __restrict__ orec2) {
-  __shared__ uint32_t s_key[kMergeTile];  // the tile's A keys, then its B keys
-  __shared__ uint32_t s_src[kMergeTile];  // source of each output: A index, or B | 2^31
-  const int64_t t = blockIdx.x;
-  const int64_t d0 = t * kMergeTile, d1 = min(d0 + kMergeTile, na + nb);
-  const int64_t i0 = split[t], i1 = split[t + 1];
-  const int64_t j0 = d0 - i0, j1 = d1 - i1;
-  const int la = (int)(i1 - i0), lb = (int)(j1 - j0);
-  for (int q = threadIdx.x; q < la; q += 256) s_key[q] = __ldg(okey + i0 + q);
-  for (int q = threadIdx.x; q < lb; q += 256) s_key[la + q] = fkey(skeys, flist, j0 + q);
-  __syncthreads();
-  const int dl = threadIdx.x * (kMergeTile / 256);
-  if (dl < la + lb) {
-    int lo = max(0, dl - lb), hi = min(dl, la);
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (s_key[mid] <= s_key[la + dl - 1 - mid]) lo = mid + 1;
-      else hi = mid;
-    }
-    int ia = lo, ib = dl - lo;
-#pragma unroll
-    for (int u = 0; u < kMergeTile / 256; ++u) {
-      const int k = dl + u;
-      if (k >= la + lb) break;
-      const bool from_a = ib >= lb || (ia < la && s_key[ia] <= s_key[la + ib]);
-      s_src[k] = from_a ? (uint32_t)ia++ : (0x80000000u | (uint32_t)ib++);
-    }
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < la + lb; k += 256) {
-    const uint32_t v = s_src[k];
-    const int64_t out = d0 + k;
-    if (!(v & 0x80000000u)) {
-      okey2[out] = s_key[v];
-      opos2[out] = __ldg(opos + i0 + v);
-      orec2[out] = __ldg(orec + i0 + v);
-    } else {
-      const uint32_t b = v & 0x7fffffffu;
-      const uint32_t jj = __ldg(flist + j0 + b);
-      okey2[out] = s_key[la + b];
-      opos2[out] = __ldg(pos4 + jj);
-      int4 r = __ldg(rs + jj);  // marked REMOVED by the listing: restore FROZEN
-      r.z = (int)(((uint32_t)r.z & ~((3u << 20) | (1u << 24))) | ((uint32_t)ST_FROZEN << 20));
-      orec2[out] = r;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(256) k_obs_table(Params P, const uint32_t* __restrict__ okey,
-                                                   int64_t n, uint4* __restrict__ otab,
-                                                   uint32_t* err) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  seg_build<uint32_t, true, 2>(P.geo, okey, j, n, __ldg(okey + j), otab, 1u, err);
+  ogofs[g] = (uint32_t)lo;
 }
 
 // Runs one bounded wait whose word nothing ever publishes (one thread), with a
@@ -2016,29 +1956,21 @@ __global__ void k_selftest_wait(int which, uint32_t limit, uint32_t* words, uint
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
-int64_t obs_list_tiles(int64_t n) { return (n + kObsTile - 1) / kObsTile; }
-int64_t obs_merge_tiles(int64_t n) { return (n + kMergeTile - 1) / kMergeTile; }
+int64_t obs_tiles(int64_t nseq) { return (nseq + kObsTile - 1) / kObsTile; }
 
-void launch_obs_list(const uint8_t* sact, int64_t n, uint32_t* tcnt, int4* rs, uint32_t* flist,
-                     DevStats* dst, cudaStream_t st) {
-  const int64_t nt = obs_list_tiles(n);
-  if (nt <= 0) return;
+void launch_obs_flush(const uint32_t* msrc, const uint32_t* skeys, const float4* pos4,
+                      int64_t nseq, uint32_t* tcnt, const int4* orec, int4* rs, uint32_t* okey2,
+                      float4* opos2, int4* orec2, uint32_t ng, uint32_t* ogofs2, DevStats* dst,
+                      cudaStream_t st) {
+  const int64_t nt = obs_tiles(nseq);
   cudaMemsetAsync(&dst->obs_new, 0, sizeof(unsigned long long), st);
-  k_obs_count<<<(unsigned)nt, 256, 0, st>>>(sact, n, tcnt, dst);
-  k_scan_sums<<<1, 256, 0, st>>>(tcnt, nt);
-  k_obs_list<<<(unsigned)nt, 256, 0, st>>>(sact, n, tcnt, rs, flist);
-}
-
-void launch_obs_merge(const Params& P, const uint32_t* okey, const float4* opos, const int4* orec,
-                      int64_t na, const uint32_t* skeys, const float4* pos4, const int4* rs,
-                      const uint32_t* flist, int64_t nb, uint32_t* split, uint32_t* okey2,
-                      float4* opos2, int4* orec2, uint4* otab, uint32_t* err, cudaStream_t st) {
-  const int64_t nm = obs_merge_tiles(na + nb);
-  if (nm <= 0) return;
-  k_obs_split<<<blocks(nm + 1), 256, 0, st>>>(okey, na, skeys, flist, nb, split, nm + 1);
-  k_obs_merge<<<(unsigned)nm, 256, 0, st>>>(okey, opos, orec, na, skeys, pos4, rs, flist, nb,
-                                            split, okey2, opos2, orec2);
-  k_obs_table<<<blocks(na + nb), 256, 0, st>>>(P, okey2, na + nb, otab, err);
+  if (nt > 0) {
+    k_obs_count<<<(unsigned)nt, 256, 0, st>>>(msrc, nseq, tcnt, dst);
+    k_scan_sums<<<1, 256, 0, st>>>(tcnt, nt);
+    k_obs_compact<<<(unsigned)nt, 256, 0, st>>>(msrc, skeys, pos4, nseq, tcnt, orec, rs, okey2,
+                                                opos2, orec2);
+  }
+  k_obs_groups<<<blocks((int64_t)ng + 1), 256, 0, st>>>(okey2, dst, ng, ogofs2);
 }
 
 void launch_selftest_wait(int which, uint32_t limit, uint32_t* words, uint32_t* err,
@@ -2067,21 +1999,17 @@ void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals,
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
                     const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
-                    cudaStream_t st, const Obs* ob) {
+                    cudaStream_t st, int64_t nrec, const uint32_t* mpos) {
   if (n <= 0) return;
-  const Obs none{};
   if (batch)
     k_advance<true, uint64_t><<<persistent(n, 256, P.launch.advance_ctas), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst, none);
+        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst, nullptr);
   else if (P.periodic)
-    k_advance<false, uint32_t, true><<<blocks(n), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, none);
-  else if (ob && ob->n > 0)
-    k_advance<false, uint32_t, false, true><<<blocks(n), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, *ob);
+    k_advance<false, uint32_t, true><<<blocks(nrec), 256, 0, st>>>(
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, mpos);
   else
-    k_advance<false, uint32_t><<<blocks(n), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, none);
+    k_advance<false, uint32_t><<<blocks(nrec), 256, 0, st>>>(
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, mpos);
 }
 
 int64_t emit_tiles(int64_t n) { return (n + 256 * kEmitItems - 1) / (256 * kEmitItems); }
@@ -2254,7 +2182,8 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
                         uint32_t* perm, uint32_t* gkey, uint32_t* gdest, const int4* rin,
                         int4* rout, float4* pos4, uint32_t* skeys, uint32_t* svals,
                         uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
-                        int sms, ProfHook* prof, cudaStream_t st) {
+                        int sms, ProfHook* prof, cudaStream_t st, const uint32_t* okey,
+                        const float4* opos, const uint32_t* ogofs, int64_t no, uint32_t* msrc) {
   if (n <= 0) return;
   if (prof) prof->begin(K_GROUP);
   cudaMemsetAsync(gcnt, 0, 4 * (size_t)ng, st);
@@ -2269,11 +2198,12 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
   if (prof) prof->begin(K_BUILD);
   // one wave: 32 KB of shared memory per CTA leaves room for six CTAs per SM
   k_group_order<<<(unsigned)(sms * 6), 256, 0, st>>>(gkey, gofs, gbsum, ng, n, P.geo.seg0, gdest,
-                                                     tab, stamp, dst);
+                                                     tab, stamp, dst, okey, opos, ogofs, no, pos4,
+                                                     skeys, msrc);
   k_group_gather<<<blocks(n), 256, 0, st>>>(P, gkey, perm, gdest, n, rin, rout, pos4, skeys, svals,
-                                            sact, dst);
+                                            sact, msrc, n + no, dst);
   k_act_list<<<blocks(n, 256 * kBuildItems), 256, 0, st>>>(sact, n, act, dst);
-  if (prof) prof->end(K_BUILD, (double)n, 3);
+  if (prof) prof->end(K_BUILD, (double)(n + no), 3);  // entries of the cell-ordered sequence
 }
 
 }  // namespace gp

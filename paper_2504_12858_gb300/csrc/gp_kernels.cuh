@@ -15,20 +15,27 @@ void launch_keys(bool batch, const Params& P, const int4* rec, int64_t n, void* 
 void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals, const int4* rin,
                   int4* rout, float4* pos4, uint4* tab, int64_t n, uint64_t key_end, uint32_t* act,
                   DevStats* dst, cudaStream_t st);
-// one run: the records grouped by cell in place of the radix sort and build (keys: the
-// emit's cell keys of rin; perm, skeys, sact: sorted-order scratch; svals, if given,
-// receives the source index of each sorted record)
+// one run: the records grouped by cell tile in place of the radix sort and build (keys:
+// the emit's cell keys of the n records of rin).  rout receives the records in grouped
+// order (gdest[i]: the position of grouped record i in the cell-ordered sequence; svals,
+// if given, its store index; sact its state byte; act the ACTIVE ones); the sequence holds
+// the moving records and the no obstacles of (okey, opos, group offsets ogofs): positions
+// pos4, keys skeys, sources msrc, cell table tab
 void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32_t ng,
                         uint32_t* gcnt, uint32_t* gofs, uint32_t* gbsum, uint32_t* gfill,
                         uint32_t* perm, uint32_t* gkey, uint32_t* gdest, const int4* rin,
                         int4* rout, float4* pos4, uint32_t* skeys, uint32_t* svals,
                         uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
-                        int sms, ProfHook* prof, cudaStream_t st);
-// ob (one run, optional): the obstacle store, searched beside the dynamic table
+                        int sms, ProfHook* prof, cudaStream_t st, const uint32_t* okey = nullptr,
+                        const float4* opos = nullptr, const uint32_t* ogofs = nullptr,
+                        int64_t no = 0, uint32_t* msrc = nullptr);
+// a batch: n records, sorted like pos4.  A single run: pos4, skeys and tab hold the n
+// entries of the cell-ordered sequence (moving particles and obstacles), rs the nrec
+// records in grouped order, mpos[j] the position of record j in the sequence.
 void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, const float4* pos4,
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
                     const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
-                    cudaStream_t st, const Obs* ob = nullptr);
+                    cudaStream_t st, int64_t nrec = 0, const uint32_t* mpos = nullptr);
 int64_t emit_tiles(int64_t n);
 void launch_link_reached(bool batch, const Params& P, const Reached& R,
                          unsigned long long* linked, int sms, cudaStream_t st);
@@ -102,20 +109,17 @@ void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstat
                        int64_t n, uint8_t* freeze, int32_t* pairs, int64_t pair_cap,
                        unsigned long long* npairs, cudaStream_t st);
 
-// obstacle flush of a single run (see gp_kernels.cu).  launch_obs_list lists, in key
-// order, the FROZEN records of the ordered store rs (n records, state bytes sact) into
-// flist, marks them REMOVED in rs and counts them in dst->obs_new; tcnt holds
-// obs_list_tiles(n) words.  launch_obs_merge merges the obstacle store (okey, opos,
-// orec; na records) with the nb listed records into okey2, opos2, orec2 and writes
-// their cell table otab; split holds obs_merge_tiles(na + nb) + 1 words.
-int64_t obs_list_tiles(int64_t n);
-int64_t obs_merge_tiles(int64_t n);
-void launch_obs_list(const uint8_t* sact, int64_t n, uint32_t* tcnt, int4* rs, uint32_t* flist,
-                     DevStats* dst, cudaStream_t st);
-void launch_obs_merge(const Params& P, const uint32_t* okey, const float4* opos, const int4* orec,
-                      int64_t na, const uint32_t* skeys, const float4* pos4, const int4* rs,
-                      const uint32_t* flist, int64_t nb, uint32_t* split, uint32_t* okey2,
-                      float4* opos2, int4* orec2, uint4* otab, uint32_t* err, cudaStream_t st);
+// obstacle flush of a single run (see gp_kernels.cu): the entries of the cell-ordered
+// sequence (nseq of them: keys skeys, positions pos4, sources msrc) that are obstacles or
+// FROZEN moving records become the new obstacle store (okey2, opos2, orec2; records from
+// orec and from the grouped store rs, whose joining records are marked REMOVED); its size
+// lands in dst->obs_new and the first obstacle of every group in ogofs2[0 .. ng].  tcnt
+// holds obs_tiles(nseq) words.
+int64_t obs_tiles(int64_t nseq);
+void launch_obs_flush(const uint32_t* msrc, const uint32_t* skeys, const float4* pos4,
+                      int64_t nseq, uint32_t* tcnt, const int4* orec, int4* rs, uint32_t* okey2,
+                      float4* opos2, int4* orec2, uint32_t ng, uint32_t* ogofs2, DevStats* dst,
+                      cudaStream_t st);
 
 // bounded-wait self-test: words holds 512 zeroed uint32 (a status array of two
 // tiles, or one claim bucket), err one zeroed word

@@ -2,18 +2,19 @@
 
 A FROZEN particle never moves again (Sec. 2.1.2: points of two grains that meet
 stop and form the grain boundary); the library moves such particles into an
-obstacle store with its own cell table, which the contact search reads beside the
-table of the moving particles.  These tests check that:
+obstacle store ordered by cell, whose positions every step's ordering places beside
+those of the moving particles for the contact search.  These tests check that:
 - the three modes (off, automatic, a flush every step) give bit-identical results:
   every particle's grain, site, direction, state, progress and position, the step
   counters and the grain map, on a polycrystal in a gradient, on a small weld plate
   and on a state with crowded cells;
 - the ordering the step builds (the per-step store grouped by tile of 1024 cells and
-  ordered by cell inside each tile) equals a stable sort of the same tiled cell keys,
-  up to the order of particles inside one cell; the keys themselves equal the tiled
-  form of the oracle's binary32 cell of each exported position; the cell table of
-  both stores (first index, count, 4-bit cell counts, saturation flag) is recomputed
-  from the sorted keys and compared entry by entry;
+  ordered by cell inside each tile, together with the obstacles) equals a stable sort
+  of the same tiled cell keys, up to the order of particles inside one cell; the keys
+  themselves equal the tiled form of the oracle's binary32 cell of each exported
+  position; the cell table (first index, count, 4-bit cell counts, saturation flag) is
+  recomputed from the sorted keys and compared entry by entry; the obstacle store is
+  ordered by key;
 - melting, periodic axes, the adjoint tape and gp_load_particles bring the
   obstacles back into the per-step store without changing the particle set.
 """
@@ -131,31 +132,35 @@ def _check_table(keys_sorted, table, valid):
 
 
 def _check_ordering(s, w):
+    """The cell-ordered sequence of the next step (moving particles and obstacles) and
+    the obstacle store, against the oracle's cells of the exported positions."""
     p = s.gp_get_particles()
     d, o = s.gp_inspect_order(0), s.gp_inspect_order(1)
-    nd, no = len(d["keys_in"]), len(o["keys_sorted"])
-    assert nd + no == len(p["grain"])
+    n, no = len(p["grain"]), len(o["keys_sorted"])
+    nd = n - no
+    assert len(d["keys_sorted"]) == n
     lo, hi = np.array(w.lo, np.float64), np.array(w.hi, np.float64)
     keys = _tiled_keys(p["x"], lo, hi, w.h)
-    # per-step store: keys, a stable sort of them up to the order inside a cell, table
-    assert np.array_equal(d["keys_in"], keys[:nd])
-    stable = np.argsort(keys[:nd], kind="stable")
-    assert np.array_equal(d["keys_sorted"], keys[:nd][stable])
-    assert np.array_equal(np.sort(d["src"]), np.arange(nd, dtype=np.uint32))
-    assert np.array_equal(keys[:nd][d["src"]], d["keys_sorted"])
+    # every particle's key; the sequence is a stable sort of them up to the order inside
+    # a cell; every entry of the table
+    assert np.array_equal(d["keys_in"], keys)
+    stable = np.argsort(keys, kind="stable")
+    assert np.array_equal(d["keys_sorted"], keys[stable])
+    assert np.array_equal(np.sort(d["src"]), np.arange(n, dtype=np.uint32))
+    assert np.array_equal(keys[d["src"]], d["keys_sorted"])
     _check_table(d["keys_sorted"], d["table"], lambda t: (t[:, 1] >> 16) == d["stamp"])
-    # obstacle store: frozen particles, in key order, with their own table
+    # the obstacle store: frozen particles, the last ones listed, in key order
     assert (p["state"][nd:] == 1).all()
+    assert np.array_equal(o["src"], np.arange(nd, n, dtype=np.uint32))
     assert np.array_equal(o["keys_sorted"], keys[nd:])
     assert np.all(np.diff(o["keys_sorted"].astype(np.int64)) >= 0)
-    _check_table(o["keys_sorted"], o["table"], lambda t: (t[:, 1] & 0x7FFF) != 0)
-    return nd, no
+    return nd, no, d
 
 
 def test_ordering_and_tables_match_the_oracle_cells():
     w = _polycrystal(seed=7, n_grains=16, L=80e-6, dT=8.0)
     s, n_obs = _run(w, 2, 30, 600000)
-    nd, no = _check_ordering(s, w)
+    nd, no, _ = _check_ordering(s, w)
     assert nd > 1000 and no > 1000
     s.gp_step(1)
     _check_ordering(s, w)
@@ -183,8 +188,11 @@ def test_crowded_cells_in_both_stores():
         runs[mode] = s
     o = runs[2].gp_inspect_order(1)
     assert len(o["keys_sorted"]) > 100
-    assert (o["table"][:, 1] & 0x8000).any()          # a saturated cell in the obstacles
-    _check_ordering(runs[2], w)
+    _, _, d = _check_ordering(runs[2], w)
+    sat = np.flatnonzero(((d["table"][:, 1] >> 16) == d["stamp"]) & (d["table"][:, 1] & 0x8000 != 0))
+    assert len(sat) > 0                                # saturated cells hold obstacles
+    crowd_seg = np.unique(o["keys_sorted"] >> 4)
+    assert np.isin(sat, crowd_seg).any()
     _check_ordering(runs[0], w)
     _same(runs[2], runs[0])
 
