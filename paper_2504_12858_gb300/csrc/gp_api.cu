@@ -1387,7 +1387,18 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       const int o = c->ocur;
       const int64_t nseq = n + (obs ? c->n_obs : 0);
       uint32_t* skeys = static_cast<uint32_t*>(c->sb.keys[1]);
-      uint32_t* msrc = at<uint32_t>(c, c->L.msrc);
+      // obstacle flush: the obstacles and the FROZEN records (hst->n_frozen of them, as the
+      // last emit counted) of the cell-ordered sequence become the new obstacle store once
+      // carrying the FROZEN records from step to step has cost about as much as rewriting
+      // the store, counted as kObsCarry record-steps per obstacle; the first FROZEN records
+      // are flushed at once
+      bool flush = false;
+      if (obs) {
+        const double f = (double)c->hst->n_frozen;
+        c->obs_carry += f;
+        flush = f > 0 && (c->obs_mode == 2 || kObsCarry * c->obs_carry >= (double)c->n_obs + f);
+      }
+      uint32_t* msrc = flush ? at<uint32_t>(c, c->L.msrc) : nullptr;  // the flush's input
       launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), n, c->L.ngroups,
                          at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
                          at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
@@ -1398,29 +1409,20 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                          at<float4>(c, c->L.opos[o]), at<uint32_t>(c, c->L.ogofs[o]),
                          obs ? c->n_obs : 0, msrc);
       GP_CUDA(c, cudaGetLastError());
-      // obstacle flush: the obstacles and the FROZEN records (hst->n_frozen of them, as the
-      // last emit counted) of the cell-ordered sequence become the new obstacle store once
-      // carrying the FROZEN records from step to step has cost about as much as rewriting
-      // the store, counted as kObsCarry record-steps per obstacle; the first FROZEN records
-      // are flushed at once
-      if (obs) {
-        const double f = (double)c->hst->n_frozen;
-        c->obs_carry += f;
-        if (f > 0 && (c->obs_mode == 2 || kObsCarry * c->obs_carry >= (double)c->n_obs + f)) {
-          c->prof.begin(K_OBS);
-          launch_obs_flush(msrc, skeys, c->pos4, nseq, at<uint32_t>(c, c->L.otcnt),
-                           at<int4>(c, c->L.orec[o]), sorted, at<uint32_t>(c, c->L.okey[o ^ 1]),
-                           at<float4>(c, c->L.opos[o ^ 1]), at<int4>(c, c->L.orec[o ^ 1]),
-                           c->L.ngroups, at<uint32_t>(c, c->L.ogofs[o ^ 1]), c->dst, c->st);
-          GP_CUDA(c, cudaMemcpyAsync(&c->hst->obs_new, &c->dst->obs_new, sizeof(unsigned long long),
-                                     cudaMemcpyDeviceToHost, c->st));
-          GP_CUDA(c, cudaStreamSynchronize(c->st));
-          GP_CUDA(c, cudaGetLastError());
-          c->ocur ^= 1;
-          c->n_obs = (int64_t)c->hst->obs_new;
-          c->obs_carry = 0;
-          c->prof.end(K_OBS, (double)c->n_obs, 4);
-        }
+      if (flush) {
+        c->prof.begin(K_OBS);
+        launch_obs_flush(msrc, skeys, c->pos4, nseq, at<uint32_t>(c, c->L.otcnt),
+                         at<int4>(c, c->L.orec[o]), sorted, at<uint32_t>(c, c->L.okey[o ^ 1]),
+                         at<float4>(c, c->L.opos[o ^ 1]), at<int4>(c, c->L.orec[o ^ 1]),
+                         c->L.ngroups, at<uint32_t>(c, c->L.ogofs[o ^ 1]), c->dst, c->st);
+        GP_CUDA(c, cudaMemcpyAsync(&c->hst->obs_new, &c->dst->obs_new, sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, c->st));
+        GP_CUDA(c, cudaStreamSynchronize(c->st));
+        GP_CUDA(c, cudaGetLastError());
+        c->ocur ^= 1;
+        c->n_obs = (int64_t)c->hst->obs_new;
+        c->obs_carry = 0;
+        c->prof.end(K_OBS, (double)c->n_obs, 4);
       }
       c->prof.begin(K_ADVANCE);
       launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp, nseq, c->act,

@@ -1647,9 +1647,9 @@ __device__ __forceinline__ uint32_t group_slot(uint32_t key) {
 // cell's next entry in the sequence, which the last pass advances to place every entry
 // (dest for the moving records).  Each lane sums its 32 cells, one warp scan gives the
 // lanes' first positions, and each lane then writes its cells' offsets and its two
-// cell-table entries (counts of both kinds).  msrc[position] tells the flush what the entry
-// is: an obstacle (bit 31 | obstacle index) or a moving record (grouped index; bit 30 if
-// FROZEN, set by the gather).
+// cell-table entries (counts of both kinds).  msrc[position] (on a flush step only) tells
+// the flush what the entry is: an obstacle (bit 31 | obstacle index) or a moving record
+// (grouped index; bit 30 if FROZEN, set by the gather).
 __global__ void __launch_bounds__(256, 6) k_group_order(
     const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ ofs,
     const uint32_t* __restrict__ bsum, uint32_t ng, int64_t n, uint64_t seg0,
@@ -1757,7 +1757,7 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
           const uint32_t d = atomicAdd(c + group_slot(k[u]), 1u);
           pos4[d] = __ldg(opos + i0 + 32 * u);
           skeys[d] = k[u];
-          msrc[d] = 0x80000000u | (i0 + 32 * u);
+          if (msrc) msrc[d] = 0x80000000u | (i0 + 32 * u);
         }
     }
     for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
@@ -1797,7 +1797,7 @@ __global__ void __launch_bounds__(256) k_group_gather(
   const float3 pw = P.periodic ? wrap_pos(P, P.geo, p) : p;
   pos4[j] = make_float4(pw.x, pw.y, pw.z, __int_as_float(r.grain));
   skeys[j] = __ldg(gkey + i);
-  msrc[j] = (uint32_t)i | (r.state == ST_FROZEN ? 0x40000000u : 0u);
+  if (msrc) msrc[j] = (uint32_t)i | (r.state == ST_FROZEN ? 0x40000000u : 0u);
   if (svals) svals[i] = o;
   sact[i] = r.state == ST_ACTIVE ? 1 : (r.state == ST_FROZEN ? 2 : 0);
 }
@@ -1886,37 +1886,49 @@ __global__ void __launch_bounds__(256) k_obs_count(const uint32_t* __restrict__ 
   }
 }
 
+// Warp w of the tile takes entries tile * kObsTile + w * 1024 + q * 32 + lane (q = 0..31),
+// so that every load and store of a q is coalesced; ranks follow the entries' order (warp
+// ballots inside a warp, a block scan of the warps' totals).
 __global__ void __launch_bounds__(256) k_obs_compact(
     const uint32_t* __restrict__ msrc, const uint32_t* __restrict__ skeys,
     const float4* __restrict__ pos4, int64_t nseq, const uint32_t* __restrict__ tofs,
     const int4* __restrict__ orec, int4* __restrict__ rs, uint32_t* __restrict__ okey2,
     float4* __restrict__ opos2, int4* __restrict__ orec2) {
   __shared__ uint32_t s_warp[8];
-  const int64_t j0 = (int64_t)blockIdx.x * kObsTile + (int64_t)threadIdx.x * kObsItems;
-  uint32_t w[kObsItems], c = 0;
-  obs_words(msrc, nseq, j0, w);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t wb = (int64_t)blockIdx.x * kObsTile + (int64_t)w * (32 * kObsItems);
+  uint32_t bits = 0, wcnt = 0;
 #pragma unroll
-  for (int q = 0; q < kObsItems; ++q) c += joins(w[q]) ? 1u : 0u;
+  for (int q = 0; q < kObsItems; ++q) {
+    const int64_t j = wb + q * 32 + lane;
+    const bool f = j < nseq && joins(__ldg(msrc + j));
+    bits |= (f ? 1u : 0u) << q;
+    wcnt += __popc(__ballot_sync(0xffffffffu, f));
+  }
   uint32_t tot;
-  uint32_t o = tofs[blockIdx.x] + bscan256(c, s_warp, tot);
-  if (!c) return;
+  const uint32_t wofs = bscan256(lane == 0 ? wcnt : 0u, s_warp, tot);
+  uint32_t o = tofs[blockIdx.x] + __shfl_sync(0xffffffffu, wofs, 0);
+  const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll 1
   for (int q = 0; q < kObsItems; ++q) {
-    const uint32_t src = w[q];
-    if (!joins(src)) continue;
-    const int64_t j = j0 + q;
-    const uint32_t idx = src & 0x3fffffffu;
-    okey2[o] = __ldg(skeys + j);
-    opos2[o] = __ldg(pos4 + j);
-    if (src & 0x80000000u) {
-      orec2[o] = __ldg(orec + idx);
-    } else {
-      int4 r = rs[idx];  // FROZEN: it moves to the obstacles, the emit drops it
-      orec2[o] = r;
-      r.z = (int)(((uint32_t)r.z & ~(3u << 20)) | ((uint32_t)ST_REMOVED << 20));
-      rs[idx] = r;
+    const bool f = (bits >> q) & 1u;
+    const uint32_t b = __ballot_sync(0xffffffffu, f);
+    if (f) {
+      const int64_t j = wb + q * 32 + lane;
+      const uint32_t r = o + __popc(b & lt);
+      const uint32_t src = __ldg(msrc + j), idx = src & 0x3fffffffu;
+      okey2[r] = __ldg(skeys + j);
+      opos2[r] = __ldg(pos4 + j);
+      if (src & 0x80000000u) {
+        orec2[r] = __ldg(orec + idx);
+      } else {
+        int4 rv = rs[idx];  // FROZEN: it moves to the obstacles, the emit drops it
+        orec2[r] = rv;
+        rv.z = (int)(((uint32_t)rv.z & ~(3u << 20)) | ((uint32_t)ST_REMOVED << 20));
+        rs[idx] = rv;
+      }
     }
-    ++o;
+    o += __popc(b);
   }
 }
 

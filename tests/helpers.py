@@ -90,10 +90,11 @@ def tip_signatures(p, n_grains):
 
 def oracle_front_run(job):
     """Oracle front outputs (H, F), tip signatures and highest particle of the adjoint
-    case for job = (theta, height), theta = (A, n, G, Tdot) (runs in a worker process)."""
+    case for job = (theta, height, steps), theta = (A, n, G, Tdot) (runs in a worker
+    process)."""
     from paper_2504_12858_gb300.adjoint import front_outputs
-    (A, n, G, Tdot), height = job
-    w = inputs.adjoint_cube(A=A, n=n, G=G, Tdot=Tdot, height=height)
+    (A, n, G, Tdot), height, steps = job
+    w = inputs.adjoint_cube(A=A, n=n, G=G, Tdot=Tdot, height=height, steps=steps)
     o = oracle_from(w)
     o.step(w.steps)
     p = o.particles()

@@ -4,7 +4,7 @@ FP64 oracle.
 Case: 200 um cube, 32 grains (seed 5), v = A dT^n, T = T_L - 5 + G (z - z_c) - Tdot t,
 theta = (A, n, G, Tdot) = (1e-5, 2, 1e3 K/m, 10 K/s), h = 2 um, dt = 2 ms, 200 steps;
 and the same grains in a box 400 um tall, where the highest point of the envelope
-grows freely.  Outputs: every grain's mean primary-tip distance F_g, and the front
+grows freely (182 steps).  Outputs: every grain's mean primary-tip distance F_g, and the front
 height H (the largest z).  Each parameter is perturbed by 1e-4 relative.  The adjoint
 holds the discrete events of the run fixed, so an output is compared only when the
 events that shape it are the same in the minus, base and plus oracle runs and in the
@@ -36,30 +36,35 @@ if not torch.cuda.is_available():
 
 THETA0 = np.array([1e-5, 2.0, 1e3, 10.0])
 REL = 1e-4
-HEIGHTS = (200e-6, 400e-6)
+# (box height, steps): the cube, and the tall box stopped at a step where one tip leads
+# the envelope's nearly flat top face by 0.37 h and lies between two sites (progress
+# 0.73).  The front height max z has a kink wherever two particles tie in z or the
+# highest one crosses a site; at most other steps the lead is about 0.02 h and a relative
+# change of 1e-4 of the exponent n moves the maximum to another particle.
+CASES = ((200e-6, 200), (400e-6, 182))
 
 
 @pytest.fixture(scope="module")
 def finite_differences():
     jobs = []
-    for height in HEIGHTS:
-        jobs.append((THETA0.copy(), height))
+    for height, steps in CASES:
+        jobs.append((THETA0.copy(), height, steps))
         for p in range(4):
             for sgn in (1, -1):
                 t = THETA0.copy()
                 t[p] *= 1 + sgn * REL
-                jobs.append((t, height))
+                jobs.append((t, height, steps))
     with mp.get_context("spawn").Pool(min(len(jobs), max(1, mp.cpu_count()))) as pool:
         res = pool.map(oracle_front_run, jobs)
-    return {h: res[9 * i: 9 * (i + 1)] for i, h in enumerate(HEIGHTS)}
+    return {case: res[9 * i: 9 * (i + 1)] for i, case in enumerate(CASES)}
 
 
-def _gpu_jacobian(height, every=1):
+def _gpu_jacobian(height, steps, every=1):
     from paper_2504_12858_gb300 import build, inputs, native
     from paper_2504_12858_gb300.adjoint import FrontAdjoint
     build.build()
     native.load()
-    w = inputs.adjoint_cube(height=height)
+    w = inputs.adjoint_cube(height=height, steps=steps)
     G = len(w.seeds)
     th = torch.tensor(THETA0, dtype=torch.float64, requires_grad=True)
     out = FrontAdjoint.apply(th, w, 400000, every)
@@ -68,12 +73,13 @@ def _gpu_jacobian(height, every=1):
     return w, out.detach().numpy(), jac, FrontAdjoint.last_particles
 
 
-@pytest.mark.parametrize("height", HEIGHTS)
-def test_adjoint_gradients_match_oracle_central_differences(finite_differences, height):
-    w, out, jac, parts = _gpu_jacobian(height)
+@pytest.mark.parametrize("case", CASES)
+def test_adjoint_gradients_match_oracle_central_differences(finite_differences, case):
+    height, steps = case
+    w, out, jac, parts = _gpu_jacobian(height, steps)
     G = len(w.seeds)
     gpu_sig, gpu_top = tip_signatures(parts, G)
-    fd_runs = finite_differences[height]
+    fd_runs = finite_differences[case]
     base = fd_runs[0]
     assert abs(out[0] - base[0]) <= 1e-5 * abs(base[0])
     compared, excluded, h_compared = 0, 0, 0
@@ -109,8 +115,9 @@ def test_adjoint_gradients_match_oracle_central_differences(finite_differences, 
 
 @pytest.mark.parametrize("every", [10, 7])
 def test_checkpointed_tape_gives_the_same_gradients(every):
-    _, out1, jac1, p1 = _gpu_jacobian(400e-6, 1)
-    _, outk, jack, pk = _gpu_jacobian(400e-6, every)
-    assert np.array_equal(out1, outk)
+    _, out1, jac1, p1 = _gpu_jacobian(*CASES[1], 1)
+    _, outk, jack, pk = _gpu_jacobian(*CASES[1], every)
+    # the same forward run (its outputs are float64 sums in store order, which varies)
+    assert np.allclose(out1, outk, rtol=1e-12, atol=0)
     scale = np.maximum(np.abs(jac1), 1e-12 + 1e-6 * np.abs(jac1).max(axis=0, keepdims=True))
     assert (np.abs(jack - jac1) <= 1e-5 * scale).all(), np.abs(jack - jac1).max()
