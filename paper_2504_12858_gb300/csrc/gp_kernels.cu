@@ -1748,16 +1748,25 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     // the obstacles go to their cells' slots, then the moving records (any order inside
     // a cell)
     for (uint32_t i0 = os + lane; i0 < oe; i0 += 128) {
+      // keys and positions of four obstacles in flight before their slots are taken
       uint32_t k[4];
+      float4 q[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) k[u] = i0 + 32 * u < oe ? __ldg(okey + i0 + 32 * u) : 0u;
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = i0 + 32 * u < oe;
+        k[u] = ok ? __ldg(okey + i0 + 32 * u) : 0u;
+        q[u] = ok ? __ldg(opos + i0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      uint32_t d[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        d[u] = i0 + 32 * u < oe ? atomicAdd(c + group_slot(k[u]), 1u) : 0u;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (i0 + 32 * u < oe) {
-          const uint32_t d = atomicAdd(c + group_slot(k[u]), 1u);
-          pos4[d] = __ldg(opos + i0 + 32 * u);
-          skeys[d] = k[u];
-          if (msrc) msrc[d] = 0x80000000u | (i0 + 32 * u);
+          pos4[d[u]] = q[u];
+          skeys[d[u]] = k[u];
+          if (msrc) msrc[d[u]] = 0x80000000u | (i0 + 32 * u);
         }
     }
     for (uint32_t i0 = s + lane; i0 < e; i0 += 128) {
