@@ -1080,6 +1080,7 @@ gp_status gp_inspect_order(gp_ctx* c, int32_t which, int64_t cap, uint32_t* keys
       c->stamp = 1;
     }
     GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
+    GP_CUDA(c, cudaMemsetAsync(&c->dst->n_actx, 0, sizeof(uint32_t), c->st));
     launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), nd, c->L.ngroups,
                        at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
                        at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
@@ -1379,6 +1380,7 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       }
       int4* sorted = c->rec[c->cur ^ 1];  // the records in grouped order
       GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
+      GP_CUDA(c, cudaMemsetAsync(&c->dst->n_actx, 0, sizeof(uint32_t), c->st));
       // records grouped by cell tile (in place of the radix sort): the emit's keys in
       // keys[0], the grouped identities in vals[1]; the cell-ordered sequence of the moving
       // records and the obstacles (positions, keys in keys[1], sources, cell table); the

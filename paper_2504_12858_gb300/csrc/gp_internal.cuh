@@ -646,7 +646,7 @@ struct DevStats {
   unsigned long long claim_used;   // occupied claim buckets
   unsigned long long n_live;       // after nucleation
   uint32_t err;
-  uint32_t pad;
+  uint32_t n_actx;                 // ACTIVE particles listed from the back of the list
   unsigned long long linked;       // reached sites linked into the per-cell lists
   unsigned long long n_act;        // ACTIVE particles listed by the last build
   unsigned long long step;         // batch: index n of the step being computed

@@ -554,7 +554,8 @@ __global__ void __launch_bounds__(256) k_build(Params P, const K* __restrict__ s
 // ---------------------------------------------------------------------------------
 // A batch: rs and pos4 share the sorted index.  A single run: rs is in grouped order and
 // mpos[j] is the position of record j in the cell-ordered sequence (pos4, skeys, tab) that
-// also holds the obstacle store; n is that sequence's length.
+// also holds the obstacle store; n is that sequence's length; the list act of nrec entries
+// holds n_act indices at its front and n_actx at its back (k_act_list).
 template <bool BATCH, class K, bool PER = false>
 __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* __restrict__ rs,
                                                  const float4* __restrict__ pos4,
@@ -563,7 +564,8 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
                                                  uint32_t stamp, int64_t n,
                                                  const uint32_t* __restrict__ act, Claims C,
                                                  int32_t* __restrict__ site_slot, DevStats* st,
-                                                 const uint32_t* __restrict__ mpos) {
+                                                 const uint32_t* __restrict__ mpos,
+                                                 int64_t nrec) {
   if constexpr (BATCH) {
     n = (int64_t)st->n_live;
     stamp = (uint32_t)st->stamp;
@@ -577,11 +579,13 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
   uint32_t c_act = 0, c_froze = 0, c_clamp = 0;
   // thread i advances the i-th listed ACTIVE particle (sorted index j); the loop is
   // uniform over a CTA so that every lane reaches the warp-wide claims
-  const int64_t m = (int64_t)st->n_act;
+  const int64_t ma = (int64_t)st->n_act;
+  const int64_t m = BATCH ? ma : ma + (int64_t)st->n_actx;
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < m;
        i0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = i0 + threadIdx.x;
-    const int64_t j = i < m ? (int64_t)__ldg(act + i) : -1;
+    const int64_t j = i < ma ? (int64_t)__ldg(act + i)
+                             : (i < m ? (int64_t)__ldg(act + (nrec - 1 - (i - ma))) : -1);
     bool active = false, froze = false, clamped = false;
     bool crossing = false;
     int g = 0, sx = 0, sy = 0, sz = 0;
@@ -1783,7 +1787,8 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
 
 // every grouped record i: the record in grouped order (the store the advance and the emit
 // walk), its position, key and source in the cell-ordered sequence at dest[i], its store
-// index (tape) and its state byte (1 ACTIVE, 2 FROZEN, 0 otherwise); one thread per record
+// index (tape) and its state byte (1 ACTIVE, 3 ACTIVE in the first or last cell of its
+// segment, 2 FROZEN, 0 otherwise); one thread per record
 __global__ void __launch_bounds__(256) k_group_gather(
     Params P, const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ perm,
     const uint32_t* __restrict__ dest, int64_t n, const int4* __restrict__ rin,
@@ -1808,35 +1813,54 @@ __global__ void __launch_bounds__(256) k_group_gather(
   skeys[j] = __ldg(gkey + i);
   if (msrc) msrc[j] = (uint32_t)i | (r.state == ST_FROZEN ? 0x40000000u : 0u);
   if (svals) svals[i] = o;
-  sact[i] = r.state == ST_ACTIVE ? 1 : (r.state == ST_FROZEN ? 2 : 0);
+  // the 3-cell window x-1..x+1 of a cell at either end of its segment reaches into the
+  // next segment (tiled keys: x & 15 is the cell's place in its segment)
+  const uint32_t xs = (uint32_t)(__ldg(gkey + i) - (uint32_t)P.geo.key0) & (kSegCells - 1);
+  sact[i] = r.state == ST_ACTIVE ? (xs == 0 || xs == kSegCells - 1 ? 3 : 1)
+                                 : (r.state == ST_FROZEN ? 2 : 0);
 }
 
-// list of the ACTIVE sorted indices (one reservation per 1024 records; each warp's
-// entries contiguous and ascending within each item)
+// List of the ACTIVE grouped indices (one reservation per 1024 records; each warp's
+// entries contiguous within each item).  State byte 1 goes to the front of act (count in
+// n_act), state byte 3 to the back, from act[n - 1] downwards (count in n_actx): the
+// contact search of a particle in the first or last cell of a segment reads two segments
+// per neighbour row, and a warp runs the second one whenever any of its lanes needs it
+// (one lane in eight; nearly every warp of a mixed list).
 __global__ void __launch_bounds__(256) k_act_list(const uint8_t* __restrict__ sact, int64_t n,
                                                   uint32_t* __restrict__ act, DevStats* st) {
   __shared__ uint32_t s_warp[8];
-  __shared__ unsigned long long s_base;
+  __shared__ unsigned long long s_base[2];
   const int lane = threadIdx.x & 31;
+  const uint32_t below = (1u << lane) - 1u;
   for (int64_t j0 = (int64_t)blockIdx.x * (256 * kBuildItems); j0 < n;
        j0 += (int64_t)gridDim.x * (256 * kBuildItems)) {
-    uint32_t amask = 0;
+    uint32_t amask = 0, xmask = 0;
 #pragma unroll
     for (int it = 0; it < kBuildItems; ++it) {
       const int64_t j = j0 + it * 256 + threadIdx.x;
-      if (j < n && __ldg(sact + j) == 1) amask |= 1u << it;
+      const uint8_t v = j < n ? __ldg(sact + j) : (uint8_t)0;
+      if (v == 1) amask |= 1u << it;
+      if (v == 3) xmask |= 1u << it;
     }
-    uint32_t tot;
+    uint32_t tot, totx;
     const uint32_t ofs = bscan256(__popc(amask), s_warp, tot);
-    if (threadIdx.x == 0) s_base = tot ? atomicAdd(&st->n_act, (unsigned long long)tot) : 0ull;
+    const uint32_t ofx = bscan256(__popc(xmask), s_warp, totx);
+    if (threadIdx.x == 0) {
+      s_base[0] = tot ? atomicAdd(&st->n_act, (unsigned long long)tot) : 0ull;
+      s_base[1] = totx ? (unsigned long long)atomicAdd(&st->n_actx, totx) : 0ull;
+    }
     __syncthreads();
-    unsigned long long o = s_base + __shfl_sync(0xffffffffu, ofs, 0);
+    unsigned long long o = s_base[0] + __shfl_sync(0xffffffffu, ofs, 0);
+    unsigned long long ox = s_base[1] + __shfl_sync(0xffffffffu, ofx, 0);
 #pragma unroll 1
     for (int it = 0; it < kBuildItems; ++it) {
-      const bool a = (amask >> it) & 1u;
-      const uint32_t b = __ballot_sync(0xffffffffu, a);
-      if (a) act[o + __popc(b & ((1u << lane) - 1u))] = (uint32_t)(j0 + it * 256 + threadIdx.x);
-      o += __popc(b);
+      const uint32_t j = (uint32_t)(j0 + it * 256 + threadIdx.x);
+      const bool a = (amask >> it) & 1u, x = (xmask >> it) & 1u;
+      const uint32_t b = __ballot_sync(0xffffffffu, a), bx = __ballot_sync(0xffffffffu, x);
+      if (a) act[o + __popc(b & below)] = j;
+      if (x) act[n - 1 - (int64_t)(ox + __popc(bx & below))] = j;
+      o += __popc(b);  // s_base is rewritten only after the next scans
+      ox += __popc(bx);
     }
   }
 }
@@ -2024,13 +2048,16 @@ void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, co
   if (n <= 0) return;
   if (batch)
     k_advance<true, uint64_t><<<persistent(n, 256, P.launch.advance_ctas), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst, nullptr);
+        P, S, rs, pos4, (const uint64_t*)skeys, tab, stamp, n, act, C, site_slot, dst, nullptr,
+        0);
   else if (P.periodic)
     k_advance<false, uint32_t, true><<<blocks(nrec), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, mpos);
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, mpos,
+        nrec);
   else
     k_advance<false, uint32_t><<<blocks(nrec), 256, 0, st>>>(
-        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, mpos);
+        P, S, rs, pos4, (const uint32_t*)skeys, tab, stamp, n, act, C, site_slot, dst, mpos,
+        nrec);
 }
 
 int64_t emit_tiles(int64_t n) { return (n + 256 * kEmitItems - 1) / (256 * kEmitItems); }

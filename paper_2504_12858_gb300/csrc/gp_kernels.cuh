@@ -18,8 +18,9 @@ void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals,
 // one run: the records grouped by cell tile in place of the radix sort and build (keys:
 // the emit's cell keys of the n records of rin).  rout receives the records in grouped
 // order (gdest[i]: the position of grouped record i in the cell-ordered sequence; svals,
-// if given, its store index; sact its state byte; act the ACTIVE ones); the sequence holds
-// the moving records and the no obstacles of (okey, opos, group offsets ogofs): positions
+// if given, its store index; sact its state byte; act the ACTIVE ones, dst->n_act at the
+// front and dst->n_actx at the back, both zero before the build); the sequence holds the
+// moving records and the no obstacles of (okey, opos, group offsets ogofs): positions
 // pos4, keys skeys, sources msrc, cell table tab
 void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32_t ng,
                         uint32_t* gcnt, uint32_t* gofs, uint32_t* gbsum, uint32_t* gfill,
