@@ -454,12 +454,18 @@ __device__ __forceinline__ int64_t slot_of(unsigned long long v) {
 // spatial locality (grain offset + Morton code of the block) clusters the
 // occupied buckets into long runs and multiplies the probe lengths by two orders
 // of magnitude at the loads used here.
+// A bucket only ever goes from empty to {key, 0} to {key, slot + 1}, so a key or a slot
+// that a plain (cacheable) load shows is final; an empty bucket or slot that it shows
+// may be an older copy and is read again from memory before it is acted on.  The plain
+// load serves most probes from L1: the warps of an SM look up the same few blocks.
 __device__ inline int64_t claim_probe(const Claims& C, unsigned long long key, bool insert) {
   uint32_t b = (uint32_t)mix64(key) & C.mask;
   for (int i = 0; i < kClaimProbeLimit; ++i) {
     volatile unsigned long long* kv = &C.bucket[b].x;
     volatile unsigned long long* sv = &C.bucket[b].y;
-    unsigned long long k = *kv;
+    const ulonglong2 seen = C.bucket[b];
+    unsigned long long k = seen.x;
+    if (k == 0ull) k = *kv;
     if (k == 0ull) {
       if (!insert) return -1;
       k = atomicCAS(&C.bucket[b].x, 0ull, key);
@@ -475,7 +481,7 @@ __device__ inline int64_t claim_probe(const Claims& C, unsigned long long key, b
       }
     }
     if (k == key) {
-      const unsigned long long v = *sv;
+      const unsigned long long v = seen.x == key && seen.y ? seen.y : *sv;
       return v ? slot_of(v) : -2 - (int64_t)b;
     }
     b = (b + 1) & C.mask;

@@ -628,23 +628,40 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
     }
     // spawn claims: every outer direction k' at the reached site s' claims the target
     // s' + e_k' for this step (claimant bit of its axis).  All lanes take part.
-    // The pool slot of the block holding s' is kept for the resolution in k_emit
-    // (most targets lie in that block).
+    // The warp looks up the block of every s' once (s' was claimed as a target, so its
+    // block exists); a target inside that block is claimed directly, and the warp looks
+    // up the others (on a face of the block: about one lane in three has one) one per
+    // lane and round.  The slot of the block of s' is kept for the resolution in k_emit.
     if (__any_sync(0xffffffffu, crossing)) {
-      BlockCache bc;
-      int32_t sslot = -1;
+      BlockCache b0;
+      int sh = 0;
+      warp_claim_word(C, crossing && site_in_range(sx, sy, sz), g, sx, sy, sz, false, sh, b0);
+      const int bx = sx >> 3, by = sy >> 3, bz = sz >> 3;
+      uint32_t face = 0;  // outer directions whose target needs a lookup of its own
       for (int k = 0; k < 6; ++k) {
-        const bool have = crossing && is_outer(sx, sy, sz, k);
-        if (!__any_sync(0xffffffffu, have)) continue;  // warp-uniform
+        if (!crossing || !is_outer(sx, sy, sz, k)) continue;
         int tx = sx, ty = sy, tz = sz;
         step_site(tx, ty, tz, k);
-        int sh = 0;
-        uint32_t* w = warp_claim_word(C, have, g, tx, ty, tz, true, sh, bc);
-        if (w) atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << sh);
-        if (have && (tx >> 3) == (sx >> 3) && (ty >> 3) == (sy >> 3) && (tz >> 3) == (sz >> 3))
-          sslot = (int32_t)bc.b;
+        if (b0.b >= 0 && site_in_range(tx, ty, tz) && (tx >> 3) == bx && (ty >> 3) == by &&
+            (tz >> 3) == bz) {
+          int st2;
+          uint32_t* w = block_word(C, b0.b, tx, ty, tz, st2);
+          atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << st2);
+        } else {
+          face |= 1u << k;
+        }
       }
-      if (crossing) site_slot[j] = sslot;
+      BlockCache bf;
+      while (__any_sync(0xffffffffu, face != 0)) {  // warp-uniform
+        const bool have = face != 0;
+        const int k = have ? __ffs(face) - 1 : 0;
+        face &= face - 1u;
+        int tx = sx, ty = sy, tz = sz;
+        step_site(tx, ty, tz, k);
+        uint32_t* w = warp_claim_word(C, have, g, tx, ty, tz, true, sh, bf);
+        if (w) atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << sh);
+      }
+      if (crossing) site_slot[j] = (int32_t)b0.b;
     }
     c_act += active ? 1u : 0u;
     c_froze += froze ? 1u : 0u;
