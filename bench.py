@@ -346,14 +346,39 @@ def oracle_all_cores(n_grains=60, n0=50, warm=1, steps=2, procs=None):
     return units / span, span, procs, sum(r[3] for r in res)
 
 
-def cpu_baseline(n_grains_sample=60, n0=50, steps=2):
+def _oracle_config_worker(job):
+    name, steps = job
+    import oracle
+    from paper_2504_12858_gb300 import inputs
+    w = getattr(inputs, name)()
+    o = oracle.Oracle(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L)
+    an = w.analytic
+    o.set_thermal_analytic(an["T0"], an["G"], an["xref"], an["Tdot"])
+    o.add_grains(w.seeds, w.quats, nucleate=True)
+    rate, dt = time_oracle(o, steps)
+    return name, steps, rate, dt, int(o.stats()["particle_steps"])
+
+
+def oracle_configs():
+    """The oracle on configurations 1 (single grain, 400 steps) and 2 (columnar slab,
+    600 steps) at their stated sizes, one process (one core) each, run side by side."""
+    import multiprocessing as mp
+    jobs = [("single_grain", 400), ("columnar_slab", 600)]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_config_worker, jobs)
+    return {n: {"value": r, "unit": METRIC, "cores": 1, "steps": st, "seconds": round(t, 2),
+                "particle_steps": ps} for n, st, r, t, ps in res}
+
+
+def cpu_baseline(n_grains_sample=60, n0=50, steps=4):
     rate, span, procs, npart = oracle_all_cores(n_grains_sample, n0, 1, steps)
     return {"value": rate, "unit": METRIC, "cores": procs, "kind": "oracle",
             "nproc": os.cpu_count(), "cpu_model": cpu_model(),
             "sample": (f"{procs} oracle processes, one per host core, each on {n_grains_sample} "
                        f"of the 1e4 grains of the same workload (disjoint, {npart:.2e} particles "
                        f"in all), {steps} steps after 1 untimed step, {span:.1f} s wall from the "
-                       f"first start to the last finish")}
+                       f"first start to the last finish"),
+            "configs": oracle_configs()}
 
 
 def run_reference(args, rank, world):
@@ -579,10 +604,10 @@ def _workload_run(w, steps, capacity, dev, **kw):
 
 
 def application_workloads(dev):
-    """Configurations 2 and 3 at their stated sizes: competitive columnar growth in the
-    1 x 1 x 0.05 mm slab (600 steps) and growth from the fusion line of the weld plate
-    (the base metal cut by the t = 0 liquidus, 500 steps).  Set-up (input generation,
-    seeding, loading) is outside the timing."""
+    """Configurations 1 to 3 at their stated sizes: the single grain (400 steps),
+    competitive columnar growth in the 1 x 1 x 0.05 mm slab (600 steps) and growth from
+    the fusion line of the weld plate (the base metal cut by the t = 0 liquidus, 500
+    steps).  Set-up (input generation, seeding, loading) is outside the timing."""
     import torch
     from paper_2504_12858_gb300 import inputs, native
     out = {}
@@ -594,6 +619,11 @@ def application_workloads(dev):
             out[name]["error"] = str(e)
         torch.cuda.empty_cache()
 
+    w = inputs.single_grain()
+    out["single_grain"] = dict(
+        workload="single_grain: 200 um cube, one grain, uniform dT = 5 K, v = 1e-5 dT^2, "
+                 "h = 2 um, dt = 2 ms, 400 steps")
+    guarded("single_grain", lambda: _workload_run(w, w.steps, 200000, dev))
     w = inputs.columnar_slab()
     out["columnar_slab"] = dict(
         workload="columnar_slab: 1x1x0.05 mm, 50 bottom seeds, G = 1e4 K/m, Tdot = 10 K/s, "
@@ -752,7 +782,7 @@ def run_native(args, rank, world, local_rank):
                            "units": k["units"],
                            "share": round(k["total_ms"] / max(sum(x["total_ms"] for x in prof),
                                                                1e-9), 4)} for k in prof}
-    cb = cpu_baseline(args.cpu_grains, args.n0, 2) if (world == 1 and not args.no_cpu) else None
+    cb = cpu_baseline(args.cpu_grains, args.n0, 4) if (world == 1 and not args.no_cpu) else None
     adj = adjoint_cost(dev) if not args.no_extras else None
     bat = batch_ensemble(dev, rank, world) if not args.no_extras else None
     apps = application_workloads(dev) if not args.no_extras else None

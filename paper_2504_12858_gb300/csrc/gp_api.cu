@@ -18,7 +18,7 @@ namespace {
 constexpr size_t kAlign = 256;
 // record-steps of carrying a FROZEN record in the dynamic store (ordering, gather,
 // emit) that cost about as much as merging one record into the obstacle store
-constexpr double kObsCarry = 4.0;
+constexpr double kObsCarry = 3.0;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // hash geometry of one run and its place in the context-wide key, cell-table and
