@@ -636,20 +636,27 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
       BlockCache b0;
       int sh = 0;
       warp_claim_word(C, crossing && site_in_range(sx, sy, sz), g, sx, sy, sz, false, sh, b0);
-      const int bx = sx >> 3, by = sy >> 3, bz = sz >> 3;
-      uint32_t face = 0;  // outer directions whose target needs a lookup of its own
-      for (int k = 0; k < 6; ++k) {
-        if (!crossing || !is_outer(sx, sy, sz, k)) continue;
+      // outer directions at s' (is_outer: +a where s_a >= 0, -a where s_a <= 0); those
+      // whose target leaves the block of s' (s' on that face) or the site range need a
+      // lookup of their own
+      uint32_t face = 0, same = 0;
+      if (crossing) {
+        const uint32_t outer = (sx >= 0 ? 1u : 0u) | (sx <= 0 ? 2u : 0u) | (sy >= 0 ? 4u : 0u) |
+                               (sy <= 0 ? 8u : 0u) | (sz >= 0 ? 16u : 0u) | (sz <= 0 ? 32u : 0u);
+        const uint32_t off = ((sx & 7) == 7 ? 1u : 0u) | ((sx & 7) == 0 || sx <= -kSiteMax ? 2u : 0u) |
+                             ((sy & 7) == 7 ? 4u : 0u) | ((sy & 7) == 0 || sy <= -kSiteMax ? 8u : 0u) |
+                             ((sz & 7) == 7 ? 16u : 0u) | ((sz & 7) == 0 || sz <= -kSiteMax ? 32u : 0u);
+        face = b0.b >= 0 ? (outer & off) : outer;
+        same = outer & ~face;
+      }
+      while (same) {  // per lane: the targets inside the block of s'
+        const int k = __ffs(same) - 1;
+        same &= same - 1u;
         int tx = sx, ty = sy, tz = sz;
         step_site(tx, ty, tz, k);
-        if (b0.b >= 0 && site_in_range(tx, ty, tz) && (tx >> 3) == bx && (ty >> 3) == by &&
-            (tz >> 3) == bz) {
-          int st2;
-          uint32_t* w = block_word(C, b0.b, tx, ty, tz, st2);
-          atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << st2);
-        } else {
-          face |= 1u << k;
-        }
+        int st2;
+        uint32_t* w = block_word(C, b0.b, tx, ty, tz, st2);
+        atomicOr(w, (1u << ((k >> 1) + 3 * S.parity)) << st2);
       }
       BlockCache bf;
       while (__any_sync(0xffffffffu, face != 0)) {  // warp-uniform
