@@ -756,8 +756,12 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
     bc.bz = sz >> 3;
     bc.b = sslot;
   }
-  for (int k = 0; k < 6; ++k) {
-    if (!is_outer(sx, sy, sz, k)) continue;
+  // outer directions at s' (is_outer), in ascending order
+  uint32_t outer = (sx >= 0 ? 1u : 0u) | (sx <= 0 ? 2u : 0u) | (sy >= 0 ? 4u : 0u) |
+                   (sy <= 0 ? 8u : 0u) | (sz >= 0 ? 16u : 0u) | (sz <= 0 ? 32u : 0u);
+  while (outer) {
+    const int k = __ffs(outer) - 1;
+    outer &= outer - 1u;
     int tx = sx, ty = sy, tz = sz;
     step_site(tx, ty, tz, k);
     int sh;
@@ -780,8 +784,8 @@ __device__ __forceinline__ uint32_t emit_decide(const Params& P, const StepArgs&
     grain_load(P.gtab, r.grain, gc, r0, r1, r2);
     const Geo& gm = geo_of<BATCH>(P, run_of<BATCH>(gc));
     const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
-    for (int k = 0; k < 6; ++k) {
-      if (!((wins >> k) & 1u)) continue;
+    for (uint32_t wl = wins; wl; wl &= wl - 1u) {
+      const int k = __ffs(wl) - 1;
       if (k != r.dir) ++n_spawn;
       if (inside_np(P, gm, add_dir(sp, r0, r1, r2, k, r.ell))) mask |= 1u << k;
       else ++n_clip;
@@ -815,8 +819,8 @@ __device__ __forceinline__ void emit_write(const Params& P, const Rec& r, uint32
   int sx = r.sx, sy = r.sy, sz = r.sz;
   step_site(sx, sy, sz, r.dir);
   const float3 sp = site_pos_g(gc, r0, r1, r2, sx, sy, sz);
-  for (int k = 0; k < 6; ++k) {
-    if (!(mask & (1u << k))) continue;
+  for (uint32_t ml = mask & 63u; ml; ml &= ml - 1u) {  // the children, in ascending k
+    const int k = __ffs(ml) - 1;
     if (o < (unsigned long long)cap) {
       Rec w;
       w.grain = r.grain;
