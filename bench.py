@@ -623,7 +623,9 @@ def application_workloads(dev):
     out["single_grain"] = dict(
         workload="single_grain: 200 um cube, one grain, uniform dT = 5 K, v = 1e-5 dT^2, "
                  "h = 2 um, dt = 2 ms, 400 steps")
-    guarded("single_grain", lambda: _workload_run(w, w.steps, 200000, dev))
+    # the envelope reaches about 100 sites along each axis: 1.4e6 reached sites inside it
+    guarded("single_grain", lambda: _workload_run(w, w.steps, 200000, dev,
+                                                  reached_capacity=4000000))
     w = inputs.columnar_slab()
     out["columnar_slab"] = dict(
         workload="columnar_slab: 1x1x0.05 mm, 50 bottom seeds, G = 1e4 K/m, Tdot = 10 K/s, "

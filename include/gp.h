@@ -237,9 +237,11 @@ gp_status gp_set_melting(gp_ctx* ctx, int32_t enable);
  * (FROZEN) never moves again: the points where two grains meet stop for good and
  * form the grain boundary (Sec. 2.1.2, impingement).  Instead of carrying FROZEN
  * particles through the per-step ordering, gather and compaction, the library moves
- * them, in batches, into an obstacle store: ordered by cell, with their positions and
- * a cell table of their own, which the contact search reads beside the table of the
- * moving particles.  Results do not depend on the mode; only the cost does.
+ * them, in batches, into an obstacle store ordered by cell, with their positions.  Each
+ * step's ordering lays out the moving particles and the obstacles in one cell-ordered
+ * sequence with one cell table, which the contact search reads; a tile of 16 x 8 x 8
+ * cells that holds no moving particle is read in place from the store instead of being
+ * copied.  Results do not depend on the mode; only the cost does.
  *   mode 0: off, every particle stays in the per-step store (obstacles already
  *           moved go back to it);
  *   mode 1 (default): a batch is moved once carrying the FROZEN particles from step
@@ -265,7 +267,9 @@ gp_status gp_set_obstacle_store(gp_ctx* ctx, int32_t mode);
  *               4-bit counts (saturated at 15) of cells 0-7 and 8-15; an entry whose
  *               stamp differs from *stamp is an empty segment.
  * Particles of one cell may come in any order (the ordering places them by atomic
- * counters); keys, cells and counts are exact.  which = 1: the obstacle store: its
+ * counters); keys, cells and counts are exact.  The inspection copies every obstacle
+ * into the sequence; the step reads those of tiles without moving particles in place.
+ * which = 1: the obstacle store: its
  * *n_out keys in its order in keys_sorted, src the gp_get_particles index of each (the
  * obstacles are the last particles that gp_get_particles lists), no table (*n_seg = 0).
  * GP_ERR_STATE on a batch context. */

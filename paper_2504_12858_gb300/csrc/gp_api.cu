@@ -163,12 +163,16 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   };
   const size_t cap = (size_t)L->cap;
   const size_t kb = (size_t)L->key_bytes;
+  // one run: the obstacle store's positions and keys (two copies) follow the cell-ordered
+  // sequence's own in pos4 and keys1, so that the contact search reads both through one
+  // index (entries cap + b * ocap + i of copy b)
+  const size_t ocap = batch ? 1 : cap;
   L->rec0 = take(16 * cap);
   L->rec1 = take(16 * cap);
-  L->pos4 = take(16 * cap);
+  L->pos4 = take(16 * (cap + 2 * ocap));
   L->sslot = take(4 * cap);
   L->keys0 = take(kb * cap + 16);
-  L->keys1 = take(kb * cap + 16);
+  L->keys1 = take(kb * (cap + 2 * ocap) + 16);
   L->vals0 = take(4 * cap + 16);
   L->vals1 = take(4 * cap + 16);
   L->sstatus = take(4 * radix_status_words(L->cap, L->key_bytes));
@@ -217,11 +221,10 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   // one run: the obstacle store (FROZEN records ordered by cell key, positions, keys,
   // the first obstacle of every group; two copies, a flush writes one from the other),
   // the source of every entry of the cell-ordered sequence and the flush's tile counts
-  const size_t ocap = batch ? 1 : cap;
   for (int b = 0; b < 2; ++b) {
     L->orec[b] = take(16 * ocap);
-    L->opos[b] = take(16 * ocap);
-    L->okey[b] = take(4 * ocap + 16);
+    L->opos[b] = L->pos4 + 16 * (cap + b * ocap);
+    L->okey[b] = L->keys1 + 4 * (cap + b * ocap);
     L->ogofs[b] = take(4 * ((size_t)L->ngroups + 16));
   }
   L->msrc = take(4 * ocap + 16);
@@ -1401,6 +1404,12 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
         flush = f > 0 && (c->obs_mode == 2 || kObsCarry * c->obs_carry >= (double)c->n_obs + f);
       }
       uint32_t* msrc = flush ? at<uint32_t>(c, c->L.msrc) : nullptr;  // the flush's input
+      // index of the current obstacle store in pos4 and skeys (they hold the sequence, then
+      // the two copies of the store); groups without moving records are read there in place
+      // (0: copy every obstacle, when the three parts exceed 32-bit indices)
+      const uint64_t span = 3 * (uint64_t)c->L.cap;
+      const uint32_t obase =
+          obs && span < (1ull << 32) ? (uint32_t)((uint64_t)c->L.cap * (1 + o)) : 0u;
       launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), n, c->L.ngroups,
                          at<uint32_t>(c, c->L.gcnt), at<uint32_t>(c, c->L.gofs),
                          at<uint32_t>(c, c->L.gbsum), at<uint32_t>(c, c->L.gfill), c->sb.vals[1],
@@ -1409,14 +1418,15 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                          reinterpret_cast<uint8_t*>(c->site_slot), c->cells, c->stamp, c->act,
                          c->dst, c->sms, &c->prof, c->st, at<uint32_t>(c, c->L.okey[o]),
                          at<float4>(c, c->L.opos[o]), at<uint32_t>(c, c->L.ogofs[o]),
-                         obs ? c->n_obs : 0, msrc);
+                         obs ? c->n_obs : 0, msrc, obase);
       GP_CUDA(c, cudaGetLastError());
       if (flush) {
         c->prof.begin(K_OBS);
         launch_obs_flush(msrc, skeys, c->pos4, nseq, at<uint32_t>(c, c->L.otcnt),
                          at<int4>(c, c->L.orec[o]), sorted, at<uint32_t>(c, c->L.okey[o ^ 1]),
                          at<float4>(c, c->L.opos[o ^ 1]), at<int4>(c, c->L.orec[o ^ 1]),
-                         c->L.ngroups, at<uint32_t>(c, c->L.ogofs[o ^ 1]), c->dst, c->st);
+                         c->L.ngroups, at<uint32_t>(c, c->L.ogofs[o ^ 1]), c->dst, c->st,
+                         (int64_t)c->L.cap * (1 + o));
         GP_CUDA(c, cudaMemcpyAsync(&c->hst->obs_new, &c->dst->obs_new, sizeof(unsigned long long),
                                    cudaMemcpyDeviceToHost, c->st));
         GP_CUDA(c, cudaStreamSynchronize(c->st));
@@ -1427,8 +1437,10 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
         c->prof.end(K_OBS, (double)c->n_obs, 4);
       }
       c->prof.begin(K_ADVANCE);
-      launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp, nseq, c->act,
-                     c->C, c->site_slot, c->dst, c->st, n, at<uint32_t>(c, c->L.gdest));
+      // the table's ranges lie in the sequence or, read in place, in the obstacle store
+      launch_advance(batch, P, S, sorted, c->pos4, skeys, c->cells, c->stamp,
+                     obase ? (int64_t)span : nseq, c->act, c->C, c->site_slot, c->dst, c->st, n,
+                     at<uint32_t>(c, c->L.gdest));
       // units: the ACTIVE particles entering the step (live minus frozen after the last step)
       c->prof.end(K_ADVANCE, (double)(n - std::min<int64_t>(n, (int64_t)c->hst->n_frozen)));
       if (rec) launch_tape_state(sorted, tsrc, n, at<uint8_t>(c, c->L.tape_post) + tq * tcap, c->st);

@@ -1682,13 +1682,17 @@ __device__ __forceinline__ uint32_t group_slot(uint32_t key) {
 // cell-table entries (counts of both kinds).  msrc[position] (on a flush step only) tells
 // the flush what the entry is: an obstacle (bit 31 | obstacle index) or a moving record
 // (grouped index; bit 30 if FROZEN, set by the gather).
+// With obase != 0 (the index of the obstacle store's first entry in pos4 and skeys, which
+// hold the store after the sequence), a group without moving records keeps its obstacles
+// where they are: its table entries point into the store, nothing is copied, and on a
+// flush step its places in the sequence only carry their msrc, in store order.
 __global__ void __launch_bounds__(256, 6) k_group_order(
     const uint32_t* __restrict__ gkey, const uint32_t* __restrict__ ofs,
     const uint32_t* __restrict__ bsum, uint32_t ng, int64_t n, uint64_t seg0,
     uint32_t* __restrict__ dest, uint4* __restrict__ tab, uint32_t stamp, DevStats* st,
     const uint32_t* __restrict__ okey, const float4* __restrict__ opos,
     const uint32_t* __restrict__ ogofs, int64_t no, float4* __restrict__ pos4,
-    uint32_t* __restrict__ skeys, uint32_t* __restrict__ msrc) {
+    uint32_t* __restrict__ skeys, uint32_t* __restrict__ msrc, uint32_t obase) {
   __shared__ uint4 s_c4[8][32 * kGroupRow / 4];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* c = reinterpret_cast<uint32_t*>(s_c4[w]);
@@ -1698,6 +1702,7 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     const uint32_t e = tile_start(ofs, bsum, g + 1, ng, n);
     const uint32_t os = no ? __ldg(ogofs + g) : 0u, oe = no ? __ldg(ogofs + g + 1) : 0u;
     if (s >= e && os >= oe) continue;  // warp-uniform
+    const bool resident = obase != 0u && s >= e;  // obstacles only: read in place
 #pragma unroll
     for (int q = 0; q < kGroupRow / 4; ++q) s_c4[w][q * 32 + lane] = make_uint4(0, 0, 0, 0);
     __syncwarp();
@@ -1734,7 +1739,7 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     }
     if (tot) {
       // cells 0-7 / 8-15 of a segment give its z / w word: 4-bit counts saturated at 15
-      uint32_t run = s + os + inc - tot;
+      uint32_t run = (resident ? obase + os : s + os) + inc - tot;
       const uint64_t sg = seg0 + ((uint64_t)g << (kGroupShift - kSegShift)) + 2 * lane;
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
@@ -1777,6 +1782,13 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
       }
     }
     __syncwarp();
+    if (resident) {
+      // the group's places in the sequence stand for its obstacles, in store order
+      if (msrc)
+        for (uint32_t i = os + lane; i < oe; i += 32) msrc[s + i] = 0x80000000u | i;
+      __syncwarp();
+      continue;
+    }
     // the obstacles go to their cells' slots, then the moving records (any order inside
     // a cell)
     for (uint32_t i0 = os + lane; i0 < oe; i0 += 128) {
@@ -1954,7 +1966,7 @@ __global__ void __launch_bounds__(256) k_obs_compact(
     const uint32_t* __restrict__ msrc, const uint32_t* __restrict__ skeys,
     const float4* __restrict__ pos4, int64_t nseq, const uint32_t* __restrict__ tofs,
     const int4* __restrict__ orec, int4* __restrict__ rs, uint32_t* __restrict__ okey2,
-    float4* __restrict__ opos2, int4* __restrict__ orec2) {
+    float4* __restrict__ opos2, int4* __restrict__ orec2, int64_t obase) {
   __shared__ uint32_t s_warp[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t wb = (int64_t)blockIdx.x * kObsTile + (int64_t)w * (32 * kObsItems);
@@ -1978,8 +1990,12 @@ __global__ void __launch_bounds__(256) k_obs_compact(
       const int64_t j = wb + q * 32 + lane;
       const uint32_t r = o + __popc(b & lt);
       const uint32_t src = __ldg(msrc + j), idx = src & 0x3fffffffu;
-      okey2[r] = __ldg(skeys + j);
-      opos2[r] = __ldg(pos4 + j);
+      // an obstacle's key and position from the store (entry obase + idx of skeys and
+      // pos4: a group read in place has no copy in the sequence), a FROZEN record's from
+      // the sequence
+      const int64_t from = (src & 0x80000000u) ? obase + idx : j;
+      okey2[r] = __ldg(skeys + from);
+      opos2[r] = __ldg(pos4 + from);
       if (src & 0x80000000u) {
         orec2[r] = __ldg(orec + idx);
       } else {
@@ -2034,14 +2050,14 @@ int64_t obs_tiles(int64_t nseq) { return (nseq + kObsTile - 1) / kObsTile; }
 void launch_obs_flush(const uint32_t* msrc, const uint32_t* skeys, const float4* pos4,
                       int64_t nseq, uint32_t* tcnt, const int4* orec, int4* rs, uint32_t* okey2,
                       float4* opos2, int4* orec2, uint32_t ng, uint32_t* ogofs2, DevStats* dst,
-                      cudaStream_t st) {
+                      cudaStream_t st, int64_t obase) {
   const int64_t nt = obs_tiles(nseq);
   cudaMemsetAsync(&dst->obs_new, 0, sizeof(unsigned long long), st);
   if (nt > 0) {
     k_obs_count<<<(unsigned)nt, 256, 0, st>>>(msrc, nseq, tcnt, dst);
     k_scan_sums<<<1, 256, 0, st>>>(tcnt, nt);
     k_obs_compact<<<(unsigned)nt, 256, 0, st>>>(msrc, skeys, pos4, nseq, tcnt, orec, rs, okey2,
-                                                opos2, orec2);
+                                                opos2, orec2, obase);
   }
   k_obs_groups<<<blocks((int64_t)ng + 1), 256, 0, st>>>(okey2, dst, ng, ogofs2);
 }
@@ -2259,7 +2275,8 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
                         int4* rout, float4* pos4, uint32_t* skeys, uint32_t* svals,
                         uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
                         int sms, ProfHook* prof, cudaStream_t st, const uint32_t* okey,
-                        const float4* opos, const uint32_t* ogofs, int64_t no, uint32_t* msrc) {
+                        const float4* opos, const uint32_t* ogofs, int64_t no, uint32_t* msrc,
+                        uint32_t obase) {
   if (n <= 0) return;
   if (prof) prof->begin(K_GROUP);
   cudaMemsetAsync(gcnt, 0, 4 * (size_t)ng, st);
@@ -2275,7 +2292,7 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
   // one wave: 32 KB of shared memory per CTA leaves room for six CTAs per SM
   k_group_order<<<(unsigned)(sms * 6), 256, 0, st>>>(gkey, gofs, gbsum, ng, n, P.geo.seg0, gdest,
                                                      tab, stamp, dst, okey, opos, ogofs, no, pos4,
-                                                     skeys, msrc);
+                                                     skeys, msrc, no ? obase : 0u);
   k_group_gather<<<blocks(n), 256, 0, st>>>(P, gkey, perm, gdest, n, rin, rout, pos4, skeys, svals,
                                             sact, msrc, n + no, dst);
   k_act_list<<<blocks(n, 256 * kBuildItems), 256, 0, st>>>(sact, n, act, dst);

@@ -21,7 +21,9 @@ void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals,
 // if given, its store index; sact its state byte; act the ACTIVE ones, dst->n_act at the
 // front and dst->n_actx at the back, both zero before the build); the sequence holds the
 // moving records and the no obstacles of (okey, opos, group offsets ogofs): positions
-// pos4, keys skeys, sources msrc, cell table tab
+// pos4, keys skeys, sources msrc, cell table tab.  obase != 0: okey and opos are entries
+// obase.. of skeys and pos4, and a group without moving records is read there in place
+// (its table entries point into the store; its places in the sequence hold no copy)
 void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32_t ng,
                         uint32_t* gcnt, uint32_t* gofs, uint32_t* gbsum, uint32_t* gfill,
                         uint32_t* perm, uint32_t* gkey, uint32_t* gdest, const int4* rin,
@@ -29,7 +31,7 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
                         uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
                         int sms, ProfHook* prof, cudaStream_t st, const uint32_t* okey = nullptr,
                         const float4* opos = nullptr, const uint32_t* ogofs = nullptr,
-                        int64_t no = 0, uint32_t* msrc = nullptr);
+                        int64_t no = 0, uint32_t* msrc = nullptr, uint32_t obase = 0);
 // a batch: n records, sorted like pos4.  A single run: pos4, skeys and tab hold the n
 // entries of the cell-ordered sequence (moving particles and obstacles), rs the nrec
 // records in grouped order, mpos[j] the position of record j in the sequence.
@@ -113,14 +115,15 @@ void launch_contact_sa(const Params& P, const float4* pos4, const uint8_t* sstat
 // obstacle flush of a single run (see gp_kernels.cu): the entries of the cell-ordered
 // sequence (nseq of them: keys skeys, positions pos4, sources msrc) that are obstacles or
 // FROZEN moving records become the new obstacle store (okey2, opos2, orec2; records from
-// orec and from the grouped store rs, whose joining records are marked REMOVED); its size
-// lands in dst->obs_new and the first obstacle of every group in ogofs2[0 .. ng].  tcnt
-// holds obs_tiles(nseq) words.
+// orec and from the grouped store rs, whose joining records are marked REMOVED); an
+// obstacle's key and position come from the current store, entries obase.. of skeys and
+// pos4; its size lands in dst->obs_new and the first obstacle of every group in
+// ogofs2[0 .. ng].  tcnt holds obs_tiles(nseq) words.
 int64_t obs_tiles(int64_t nseq);
 void launch_obs_flush(const uint32_t* msrc, const uint32_t* skeys, const float4* pos4,
                       int64_t nseq, uint32_t* tcnt, const int4* orec, int4* rs, uint32_t* okey2,
                       float4* opos2, int4* orec2, uint32_t ng, uint32_t* ogofs2, DevStats* dst,
-                      cudaStream_t st);
+                      cudaStream_t st, int64_t obase);
 
 // bounded-wait self-test: words holds 512 zeroed uint32 (a status array of two
 // tiles, or one claim bucket), err one zeroed word

@@ -16,7 +16,9 @@ those of the moving particles for the contact search.  These tests check that:
   recomputed from the sorted keys and compared entry by entry; the obstacle store is
   ordered by key;
 - melting, periodic axes, the adjoint tape and gp_load_particles bring the
-  obstacles back into the per-step store without changing the particle set.
+  obstacles back into the per-step store without changing the particle set;
+- behind a moving weld pool, where the ordering reads the obstacles of tiles without
+  moving particles in place from the store, the run equals the one without the store.
 """
 import numpy as np
 import pytest
@@ -235,3 +237,21 @@ def test_obstacle_run_matches_the_oracle_grain_map():
     nv, sp = (50, 50, 50), (1e-6,) * 3
     assert (o.grain_map((0, 0, 0), sp, nv) == s.gp_grain_map((0, 0, 0), sp, nv)).mean() >= 0.995
     assert len(s.gp_inspect_order(1)["src"]) > 0
+
+
+def test_modes_identical_behind_a_moving_weld_pool():
+    # growth from the t = 0 fusion line of the weld plate (inputs.weld_natural): after 150
+    # steps much of the solid lies in tiles of 16 x 8 x 8 cells without moving particles,
+    # whose obstacles the ordering reads in place from the store instead of copying them;
+    # the state equals that of the run without the store, bit for bit
+    w = inputs.weld_natural(steps=150)
+    runs = {}
+    for mode in (0, 1):
+        s = sim_from(w, capacity=30000000, reached_capacity=250000000, claim_blocks=1500000)
+        s.gp_set_obstacle_store(mode)
+        s.gp_step(150)
+        runs[mode] = s
+    assert len(runs[1].gp_inspect_order(1)["keys_sorted"]) > 1000000
+    _same(runs[1], runs[0])
+    for s in runs.values():
+        s.close()
