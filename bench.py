@@ -346,28 +346,67 @@ def oracle_all_cores(n_grains=60, n0=50, warm=1, steps=2, procs=None):
     return units / span, span, procs, sum(r[3] for r in res)
 
 
-def _oracle_config_worker(job):
-    name, steps = job
+def _oracle_from(w, nucleate=True):
+    """The oracle set up on workload w (thermal field, grains, nucleation sites, or the
+    initial particles and lattice sites of a given state)."""
     import oracle
-    from paper_2504_12858_gb300 import inputs
-    w = getattr(inputs, name)()
     o = oracle.Oracle(w.lo, w.hi, w.h, w.dt, w.a, w.b, w.T_L)
-    an = w.analytic
-    o.set_thermal_analytic(an["T0"], an["G"], an["xref"], an["Tdot"])
-    o.add_grains(w.seeds, w.quats, nucleate=True)
+    if w.analytic:
+        an = w.analytic
+        o.set_thermal_analytic(an["T0"], an["G"], an["xref"], an["Tdot"])
+    if w.grid:
+        g = w.grid
+        o.set_thermal_grid(g["T"], g["origin"], g["spacing"], g["vel"])
+    init = w.extra.get("particles") if w.extra else None
+    o.add_grains(w.seeds, w.quats, nucleate=nucleate and init is None)
+    if init is not None:
+        o.load_particles(init["grain"], init["site"], init["dir"],
+                         init["ell"].astype(np.float64), init["state"])
+        gr, sr = w.extra["reached"]
+        o.add_reached(gr, sr)
+        o.add_claimed(gr, sr)
+        o.add_claimed(*w.extra["claimed"])
+    if w.nuclei:
+        o.nucleation_sites(w.nuclei["pos"], w.nuclei["dTn"], w.nuclei["quat"])
+    return o
+
+
+def _oracle_config_worker(name):
+    from paper_2504_12858_gb300 import inputs
+    if name == "cet_runs":
+        # the eight smallest cubes of the ensemble (0.50-0.55 mm), all 400 steps of each
+        runs = inputs.cet_runs()
+        pick = sorted(range(len(runs)), key=lambda r: runs[r].hi[0])[:8]
+        ps, t = 0, 0.0
+        for r in pick:
+            o = _oracle_from(runs[r])
+            rate, dt = time_oracle(o, runs[r].steps)
+            ps += int(o.stats()["particle_steps"])
+            t += dt
+        return name, {"steps": 400, "runs": [int(r) for r in pick]}, ps / t, t, ps
+    if name == "weld_natural":
+        w = inputs.weld_natural()
+        o = _oracle_from(w)
+        steps = 5    # its first 5 of 500 steps (7e5 ACTIVE particles)
+    else:
+        w = getattr(inputs, name)()
+        o = _oracle_from(w)
+        steps = w.steps
     rate, dt = time_oracle(o, steps)
-    return name, steps, rate, dt, int(o.stats()["particle_steps"])
+    return name, {"steps": steps}, rate, dt, int(o.stats()["particle_steps"])
 
 
 def oracle_configs():
-    """The oracle on configurations 1 (single grain, 400 steps) and 2 (columnar slab,
-    600 steps) at their stated sizes, one process (one core) each, run side by side."""
+    """The oracle, one process (one core) per configuration, run side by side: the single
+    grain (400 steps) and the columnar slab (600 steps) at their stated sizes, the first
+    5 steps of growth from the fusion line of the weld plate, and the eight smallest runs
+    of the ensemble (400 steps each)."""
     import multiprocessing as mp
-    jobs = [("single_grain", 400), ("columnar_slab", 600)]
+    jobs = ["single_grain", "columnar_slab", "weld_natural", "cet_runs"]
     with mp.get_context("spawn").Pool(len(jobs)) as pool:
         res = pool.map(_oracle_config_worker, jobs)
-    return {n: {"value": r, "unit": METRIC, "cores": 1, "steps": st, "seconds": round(t, 2),
-                "particle_steps": ps} for n, st, r, t, ps in res}
+    return {n: dict(extra, value=r, unit=METRIC, cores=1, seconds=round(t, 2), particle_steps=ps)
+            for n, extra, r, t, ps in res}
 
 
 def cpu_baseline(n_grains_sample=60, n0=50, steps=4):
