@@ -598,6 +598,29 @@ def batch_ensemble(dev, rank=0, world=1, serial_every=8, graph_steps=20):
     return out
 
 
+def _batch_of_one(w, steps, capacity, dev, graph_steps=20, **kw):
+    """The same workload as a batch context of one run: its steps sized on the device
+    and replayed from CUDA graphs of graph_steps steps (set-up outside the timing)."""
+    import torch
+    from paper_2504_12858_gb300 import ensemble
+    b = ensemble.batch_from([w], capacity, device=dev, **kw)
+    b.gp_set_launch_config(graph_steps=graph_steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    st0 = b.gp_stats()
+    e0.record(b.stream)
+    b.gp_step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st1 = b.gp_stats()
+    b.close()
+    torch.cuda.empty_cache()
+    return {"ms_per_step": ms / steps,
+            "particle_steps_per_s": (st1["particle_steps"] - st0["particle_steps"]) / (ms / 1e3),
+            "particles_end": st1["n_live"], "graph_steps": graph_steps}
+
+
 def _workload_run(w, steps, capacity, dev, **kw):
     """Steps workload w on the GPU (after its set-up) and measures the timed steps
     with CUDA events on the library's stream."""
@@ -665,12 +688,18 @@ def application_workloads(dev):
     # the envelope reaches about 100 sites along each axis: 1.4e6 reached sites inside it
     guarded("single_grain", lambda: _workload_run(w, w.steps, 200000, dev,
                                                   reached_capacity=4000000))
+    # a problem this small is bound by the launches and host round trip of each step: the
+    # same run as a batch context of one replays its steps from CUDA graphs
+    guarded("single_grain", lambda: {"as_batch_of_one": _batch_of_one(
+        w, w.steps, 200000, dev, reached_capacity=4000000)})
     w = inputs.columnar_slab()
     out["columnar_slab"] = dict(
         workload="columnar_slab: 1x1x0.05 mm, 50 bottom seeds, G = 1e4 K/m, Tdot = 10 K/s, "
                  "v = 1e-5 dT^2, h = 2 um, dt = 1 ms, 600 steps")
     guarded("columnar_slab",
             lambda: _workload_run(w, w.steps, 2000000, dev, reached_capacity=6000000))
+    guarded("columnar_slab", lambda: {"as_batch_of_one": _batch_of_one(
+        w, w.steps, 2000000, dev, reached_capacity=6000000)})
     t0 = time.perf_counter()
     w = inputs.weld_natural()
     out["weld_natural"] = dict(
