@@ -152,3 +152,28 @@ def test_ncu_digest_attributes_launches_to_timed_entries(tmp_path):
     assert e["obstacle"]["dram_bytes_per_unit"] == (2 + 1 + 40) / 2
     assert e["advance"]["dram_bytes_per_unit"] == 10.0 and e["emit"]["dram_bytes_per_unit"] == 10.0
     assert d["dram_bytes_per_particle_step"] == (32 + 43 + 100 + 50) / 10
+
+
+def test_bench_oracle_setup_matches_the_tests():
+    """The oracle that the cpu_baseline leg times is set up on a workload as the parity
+    tests set it up (analytic field, grains, nucleation sites, or a given state of
+    particles and reached and claimed sites): five steps give the same particles and
+    counters."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_2504_12858_gb300 import inputs
+    from tests.helpers import oracle_from
+    base = inputs.single_grain()
+    o = oracle_from(base)
+    o.step(20)
+    state = inputs.Workload(**{**base.__dict__, "name": "state", "extra": dict(
+        particles=o.particles(), reached=o.reached(), claimed=o.claimed())})
+    for w in (base, inputs.cet_runs(n_runs=1)[0], state):
+        a, b = bench._oracle_from(w), oracle_from(w)
+        a.step(5)
+        b.step(5)
+        assert a.stats() == b.stats(), w.name
+        pa, pb = a.particles(), b.particles()
+        for f in pa:
+            assert np.array_equal(pa[f], pb[f]), (w.name, f)
