@@ -82,7 +82,7 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   }
   L->batch = batch;
   L->nruns = nruns;
-  L->hshift = batch ? 1 : 0;
+  L->hshift = batch ? 2 : 0;
   L->run.assign(nruns, RunLayout{});
   uint64_t key = 0, seg = 0, head = 0;
   for (int r = 0; r < nruns; ++r) {

@@ -47,9 +47,9 @@ def run_particles(sim, run: int) -> dict:
 
 def cells_bytes(runs: list[Workload]) -> float:
     """Approximate arena bytes of the dense per-run hash tables (cell table and
-    reached-site heads: 1 + 0.5 bytes per hash cell)."""
+    reached-site heads: 1 + 1/16 bytes per hash cell)."""
     tot = 0.0
     for w in runs:
         e = w.h * (1 + 1 / 512)
         tot += float(np.prod([np.ceil((hi - lo) / e) for lo, hi in zip(w.lo, w.hi)]))
-    return 1.5 * tot
+    return (1.0 + 1.0 / 16.0) * tot
