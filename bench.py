@@ -831,7 +831,6 @@ def run_native(args, rank, world, local_rank):
                 "traffic": None if ent is None else ent["dram_bytes_per_unit"] * per_launch_units,
                 "traffic_source": None if ent is None else
                 "per-unit DRAM bytes of the 1 mm plate capture, scaled by this run's units",
-                "issue_slots_busy": None if ent is None else ent.get("issue_slots_busy"),
                 "algorithmic_bytes_per_launch": dom["bytes_per_unit"] * per_launch_units,
                 "avg_launch_ms": dom["total_ms"] / max(nsteps_prof, 1)}
     # the whole step against the copy bandwidth: DRAM bytes per particle-step (per-unit
