@@ -893,10 +893,13 @@ __global__ void __launch_bounds__(256, 6) k_emit(Params P, StepArgs S, const int
     if (tid == 0) s_base = tot ? atomicAdd(&st->n_out, (unsigned long long)tot) : 0ull;
     __syncthreads();
     // the warp's outputs start at its lane 0's offset; inside the warp they go in
-    // item-major order, so each store instruction writes consecutive slots
-    unsigned long long o = s_base + __shfl_sync(0xffffffffu, ofs, 0);
+    // item-major order, so each store instruction writes consecutive slots.  The items
+    // are written last to first, from the end of the warp's range: the records the
+    // decisions read last are read again first, while L2 still holds more of them.
+    unsigned long long o = s_base + __shfl_sync(0xffffffffu, ofs, 0) +
+                           __reduce_add_sync(0xffffffffu, cnt);
 #pragma unroll 1
-    for (int it = 0; it < ITEMS; ++it) {
+    for (int it = ITEMS - 1; it >= 0; --it) {
       const uint32_t m = s_mask[it][tid];
       const uint32_t c = __popc(m);
       uint32_t inc = c;
@@ -905,12 +908,12 @@ __global__ void __launch_bounds__(256, 6) k_emit(Params P, StepArgs S, const int
         const uint32_t t = __shfl_up_sync(0xffffffffu, inc, d);
         if (lane >= d) inc += t;
       }
+      o -= __shfl_sync(0xffffffffu, inc, 31);  // s_base is rewritten only after the next scan
       if (m) {
         const int64_t j = base + it * 256 + tid;
         const Rec r = rec_unpack(__ldg(rs + j));
         emit_write<BATCH, K>(P, r, m, o + inc - c, rout, keys, vals, cap, parent, j);
       }
-      o += __shfl_sync(0xffffffffu, inc, 31);  // s_base is rewritten only after the next scan
     }
   }
   warp_add(&st->n_frozen, n_frozen);
