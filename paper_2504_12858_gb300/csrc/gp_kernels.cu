@@ -714,12 +714,16 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
 // A CTA handles a tile of 256 x ITEMS records (ITEMS per thread, strided by 256).  Its
 // outputs are placed by a block scan and one atomic reservation per CTA on the
 // output counter, so the store order varies from run to run; every result of the
-// method is independent of that order.  A single run takes large tiles (8192 records)
-// because the reservation on the one shared counter and the scan barrier are paid per
-// tile: on the 4 x 2 x 1 mm weld plate, 32 records per thread ran 1.6x faster than 4.
-// A batch step holds few records per run and takes small tiles, to fill the GPU.
+// method is independent of that order.  A large single run takes large tiles (8192
+// records) because the reservation on the one shared counter and the scan barrier are
+// paid per tile: on the 4 x 2 x 1 mm weld plate, 32 records per thread ran 1.6x faster
+// than 4.  A smaller run takes the largest tiles that still fill one wave of CTAs, as a
+// thread walks its records one after another.  A batch step holds few records per run
+// and takes small tiles, to fill the GPU.
 // ---------------------------------------------------------------------------------
-constexpr int kEmitItems = 32;      // records per thread, one run
+constexpr int kEmitItems = 32;      // records per thread, large single run
+constexpr int kEmitItemsMid = 8;    // records per thread, single run of one wave at 8
+constexpr int kEmitItemsSmall = 2;  // records per thread, smaller single run
 constexpr int kEmitItemsBatch = 4;  // records per thread, batch of runs
 
 // decides what record j emits: bit 6 = the record itself, bits 0..5 = children in
@@ -2120,7 +2124,7 @@ void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, co
         nrec);
 }
 
-int64_t emit_tiles(int64_t n) { return (n + 256 * kEmitItems - 1) / (256 * kEmitItems); }
+int64_t emit_tiles(int64_t n, int items) { return (n + 256 * items - 1) / (256 * items); }
 
 void launch_link_reached(bool batch, const Params& P, const Reached& R,
                          unsigned long long* linked, int sms, cudaStream_t st) {
@@ -2133,15 +2137,24 @@ void launch_emit(bool batch, const Params& P, const StepArgs& S, const int4* rs,
                  const int32_t* site_slot, int64_t n, int4* rout, void* keys, uint32_t* vals,
                  int64_t cap, const Claims& C, const Reached& R, int32_t* parent, DevStats* dst,
                  cudaStream_t st) {
-  const int64_t nt = emit_tiles(n);
-  if (nt == 0) return;
+  if (n <= 0) return;
+  // one wave of emit CTAs (P.launch.emit_ctas) sets the tile size of a single run
+  const int64_t wave = P.launch.emit_ctas;
   if (batch)
     k_emit<true, uint64_t, kEmitItemsBatch>
         <<<persistent(n, 256 * kEmitItemsBatch, P.launch.emit_ctas), 256, 0, st>>>(
             P, S, rs, site_slot, n, rout, (uint64_t*)keys, vals, cap, C, R, parent, dst);
-  else
-    k_emit<false, uint32_t, kEmitItems><<<(unsigned)nt, 256, 0, st>>>(
+  else if (emit_tiles(n, kEmitItems) >= wave)
+    k_emit<false, uint32_t, kEmitItems><<<(unsigned)emit_tiles(n, kEmitItems), 256, 0, st>>>(
         P, S, rs, site_slot, n, rout, (uint32_t*)keys, vals, cap, C, R, parent, dst);
+  else if (emit_tiles(n, kEmitItemsMid) >= wave)
+    k_emit<false, uint32_t, kEmitItemsMid>
+        <<<(unsigned)emit_tiles(n, kEmitItemsMid), 256, 0, st>>>(
+            P, S, rs, site_slot, n, rout, (uint32_t*)keys, vals, cap, C, R, parent, dst);
+  else
+    k_emit<false, uint32_t, kEmitItemsSmall>
+        <<<(unsigned)emit_tiles(n, kEmitItemsSmall), 256, 0, st>>>(
+            P, S, rs, site_slot, n, rout, (uint32_t*)keys, vals, cap, C, R, parent, dst);
   k_emit_check<<<1, 1, 0, st>>>(dst, cap);
 }
 

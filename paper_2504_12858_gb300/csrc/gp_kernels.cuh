@@ -39,7 +39,7 @@ void launch_advance(bool batch, const Params& P, const StepArgs& S, int4* rs, co
                     const void* skeys, const uint4* tab, uint32_t stamp, int64_t n,
                     const uint32_t* act, const Claims& C, int32_t* site_slot, DevStats* dst,
                     cudaStream_t st, int64_t nrec = 0, const uint32_t* mpos = nullptr);
-int64_t emit_tiles(int64_t n);
+int64_t emit_tiles(int64_t n, int items);
 void launch_link_reached(bool batch, const Params& P, const Reached& R,
                          unsigned long long* linked, int sms, cudaStream_t st);
 void launch_emit(bool batch, const Params& P, const StepArgs& S, const int4* rs,
