@@ -332,6 +332,38 @@ gp_status gp_add_sites(gp_ctx* ctx, int64_t n, const int32_t* grain, const int32
 gp_status gp_get_reached(gp_ctx* ctx, int64_t cap, int32_t* grain, int32_t* site3,
                          int64_t* n_out);
 
+/* ---- checkpoints (not in the paper, which keeps no run state on disk) --------- */
+
+/* Checkpoint of a single-run context between steps, written to the caller's host
+ * buffer buf of cap bytes; *bytes receives its size (buf == NULL: the size only, nothing
+ * written).  It holds every particle record (dynamic and obstacle store), the grain
+ * frames and melted-grain flags, the nucleation sites and their activation state, the
+ * reached-site list, the claim blocks (key and claim bytes of each), the step counter,
+ * the device counters, the periodic axes, the melting and obstacle-store settings and an
+ * analytic thermal field.  A thermal grid or a solute grid is an input of the caller and
+ * is not saved.  A 64-bit FNV-1a checksum covers the whole buffer.  The buffer stays the
+ * caller's.  GP_ERR_STATE for a batch context or while the adjoint tape records;
+ * GP_ERR_CAPACITY if cap is smaller than the checkpoint (nothing written). */
+gp_status gp_save(gp_ctx* ctx, void* buf, size_t cap, size_t* bytes);
+
+/* Loads a checkpoint of gp_save (host buffer of bytes bytes, read during the call) into
+ * a new single-run context: no grains, particles, nucleation sites, reached sites or
+ * steps yet, created with the same domain, h, dt and growth law; its capacities may
+ * differ as long as the saved state fits.  Every particle starts in the dynamic store.
+ * Stepping on gives the particles, reached sites, grain maps and counters that the
+ * saved run gives.  A thermal grid or a solute grid is set again by the caller (before
+ * or after the load).  GP_ERR_ARG for a buffer that is not an intact checkpoint (magic,
+ * format version, size, checksum), holds an invalid particle, or is of another domain,
+ * h, dt or growth law; GP_ERR_CAPACITY if the saved state does not fit; GP_ERR_STATE for
+ * a batch context, a context that is not new, or while the adjoint tape records. */
+gp_status gp_load(gp_ctx* ctx, const void* buf, size_t bytes);
+
+/* Host-only check of a checkpoint buffer (no context, no device call): GP_OK if buf
+ * holds an intact checkpoint of this format, with its step counter and particle count
+ * in *step and *n_particles (each optional); GP_ERR_ARG otherwise. */
+gp_status gp_checkpoint_check(const void* buf, size_t bytes, int64_t* step,
+                              int64_t* n_particles);
+
 /* Enables (1) / disables (0) per-kernel CUDA-event timing and resets it. */
 gp_status gp_profile(gp_ctx* ctx, int32_t enable);
 /* Copies up to max entries of per-kernel timing; *n_out = number of kernels. */

@@ -2,6 +2,7 @@
 // The declarations and the contract of every entry point are in include/gp.h.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -1721,6 +1722,323 @@ gp_status gp_get_reached(gp_ctx* c, int64_t cap, int32_t* grain, int32_t* site3,
     }
   }
   return GP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// checkpoints of a single-run context
+// ---------------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'G', 'P', 'C', 'K', 'P', 'T', '\0', '\1'};
+constexpr uint32_t kCkptVersion = 1;
+
+// The fixed part of a checkpoint.  The sections follow it, each on a 16-byte boundary
+// (CkptSections); multi-byte values are in the byte order of the machine that wrote it.
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  uint64_t total_bytes;
+  uint64_t checksum;  // 64-bit FNV-1a of the whole checkpoint with this field zero
+  gp_domain dom;
+  double h, dt;
+  gp_growth_law law;
+  int64_t step, n_rec, n_grains, n_nuclei, n_reached, n_blocks;
+  int32_t thermal, periodic, melting, obs_mode;
+  double T0, Tdot;          // analytic field (thermal == 1) as the context holds it
+  float G[3], xref[3];
+  DevStats stats;           // device counters between steps
+};
+
+struct CkptSections {
+  size_t rec, gtab, gflags, gdtn, npos, ngrain, nstate, rkey, bkey, bdata, total;
+};
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// byte offsets of the sections for the counts in h; false for a count out of range
+bool ckpt_sections(const CkptHeader& h, CkptSections* o) {
+  const int64_t lim = (int64_t)1 << 40;
+  const int64_t cnt[5] = {h.n_rec, h.n_grains, h.n_nuclei, h.n_reached, h.n_blocks};
+  for (int64_t v : cnt)
+    if (v < 0 || v > lim) return false;
+  size_t p = align16(sizeof(CkptHeader));
+  auto take = [&](size_t bytes) {
+    const size_t q = p;
+    p = align16(p + bytes);
+    return q;
+  };
+  o->rec = take(16 * (size_t)h.n_rec);            // particle records (int4)
+  o->gtab = take(64 * (size_t)h.n_grains);        // grain frames (4 float4)
+  o->gflags = take(4 * (size_t)h.n_grains);       // melting flags (four bytes per grain)
+  o->gdtn = take(4 * (size_t)h.n_grains);         // nucleation undercooling of each seed
+  o->npos = take(16 * (size_t)h.n_nuclei);        // nucleation sites (position, dTn)
+  o->ngrain = take(64 * (size_t)h.n_nuclei);      // frames of the grains they nucleate
+  o->nstate = take(4 * (size_t)h.n_nuclei);       // their activation state
+  o->rkey = take(8 * (size_t)h.n_reached);        // reached-site list (melted entries too)
+  o->bkey = take(8 * (size_t)h.n_blocks);         // claim block keys, by pool slot
+  o->bdata = take(4 * (size_t)kBrickWords * (size_t)h.n_blocks);  // their claim bytes
+  o->total = p;
+  return true;
+}
+
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t h) {
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// 64-bit FNV-1a of the checkpoint with eight zero bytes in place of the checksum field
+uint64_t ckpt_checksum(const unsigned char* b, size_t bytes) {
+  const size_t off = offsetof(CkptHeader, checksum);
+  const unsigned char zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uint64_t h = fnv1a(b, off, 14695981039346656037ull);
+  h = fnv1a(zero, 8, h);
+  return fnv1a(b + off + 8, bytes - off - 8, h);
+}
+
+// why buf is not a checkpoint of this format (nullptr if it is one)
+const char* ckpt_invalid(const void* buf, size_t bytes, CkptHeader* h, CkptSections* sec) {
+  if (!buf) return "null checkpoint";
+  if (bytes < sizeof(CkptHeader)) return "checkpoint truncated";
+  std::memcpy(h, buf, sizeof(CkptHeader));
+  if (std::memcmp(h->magic, kCkptMagic, sizeof kCkptMagic) != 0) return "not a checkpoint";
+  if (h->version != kCkptVersion || h->header_bytes != (uint32_t)sizeof(CkptHeader))
+    return "checkpoint of another format version";
+  if (h->total_bytes != (uint64_t)bytes) return "checkpoint truncated or padded";
+  if (!ckpt_sections(*h, sec) || sec->total != bytes) return "checkpoint sections do not add up";
+  if (ckpt_checksum(static_cast<const unsigned char*>(buf), bytes) != h->checksum)
+    return "checkpoint checksum mismatch (corrupt)";
+  return nullptr;
+}
+
+bool same_law(const gp_growth_law& a, const gp_growth_law& b) {
+  if (a.nterms != b.nterms || a.T_liquidus != b.T_liquidus) return false;
+  for (int i = 0; i < a.nterms && i < 2; ++i)
+    if (a.a[i] != b.a[i] || a.b[i] != b.b[i]) return false;
+  return true;
+}
+
+}  // namespace
+
+gp_status gp_checkpoint_check(const void* buf, size_t bytes, int64_t* step,
+                              int64_t* n_particles) {
+  CkptHeader h;
+  CkptSections sec;
+  if (ckpt_invalid(buf, bytes, &h, &sec)) return GP_ERR_ARG;
+  if (step) *step = h.step;
+  if (n_particles) *n_particles = h.n_rec;
+  return GP_OK;
+}
+
+gp_status gp_save(gp_ctx* c, void* buf, size_t cap, size_t* bytes) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "checkpoints are of single-run contexts");
+  if (c->tape_on) return fail(c, GP_ERR_STATE, "the adjoint tape is recording");
+  if (!bytes) return fail(c, GP_ERR_ARG, "null size");
+  s = sync_stats(c);
+  if (s) return s;
+  const DevStats d = *c->hst;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof h);
+  std::memcpy(h.magic, kCkptMagic, sizeof kCkptMagic);
+  h.version = kCkptVersion;
+  h.header_bytes = (uint32_t)sizeof(CkptHeader);
+  h.dom = c->dom[0];
+  h.h = c->h;
+  h.dt = c->dt;
+  h.law = c->law;
+  h.step = c->step;
+  h.n_rec = c->n_live + c->n_obs;
+  h.n_grains = c->n_grains;
+  h.n_nuclei = c->n_nuclei;
+  h.n_reached = (int64_t)std::min<unsigned long long>(d.reached, (unsigned long long)c->L.rcap);
+  h.n_blocks = (int64_t)d.claim_used;
+  if (h.n_blocks > c->L.blocks) return fail(c, GP_ERR_STATE, "claim pool overflowed");
+  h.thermal = c->thermal;
+  h.periodic = c->periodic;
+  h.melting = c->melting ? 1 : 0;
+  h.obs_mode = c->obs_mode;
+  if (c->thermal == 1) {
+    h.T0 = c->T0[0];
+    h.Tdot = c->Tdot[0];
+    for (int a = 0; a < 3; ++a) {
+      h.G[a] = c->P.geo.G[a];
+      h.xref[a] = c->P.geo.xref[a];
+    }
+  }
+  h.stats = d;
+  CkptSections sec;
+  ckpt_sections(h, &sec);
+  h.total_bytes = sec.total;
+  *bytes = sec.total;
+  if (!buf) return GP_OK;
+  if (cap < sec.total) return fail(c, GP_ERR_CAPACITY, "checkpoint buffer too small");
+  unsigned char* b = static_cast<unsigned char*>(buf);
+  std::memset(b, 0, sec.total);  // the padding between sections
+  auto d2h = [&](size_t off, const void* src, size_t n) -> gp_status {
+    if (n) GP_CUDA(c, cudaMemcpyAsync(b + off, src, n, cudaMemcpyDeviceToHost, c->st));
+    return GP_OK;
+  };
+  const int64_t nd = c->n_live;
+  gp_status e = GP_OK;
+  // the dynamic store, then the obstacle store
+  e = e ? e : d2h(sec.rec, c->rec[c->cur], 16 * (size_t)nd);
+  e = e ? e : d2h(sec.rec + 16 * (size_t)nd, at<int4>(c, c->L.orec[c->ocur]), 16 * (size_t)c->n_obs);
+  e = e ? e : d2h(sec.gtab, c->gtab, 64 * (size_t)h.n_grains);
+  e = e ? e : d2h(sec.gflags, c->gflags, 4 * (size_t)h.n_grains);
+  e = e ? e : d2h(sec.gdtn, c->gdtn, 4 * (size_t)h.n_grains);
+  e = e ? e : d2h(sec.npos, c->npos, 16 * (size_t)h.n_nuclei);
+  e = e ? e : d2h(sec.ngrain, c->ngrain, 64 * (size_t)h.n_nuclei);
+  e = e ? e : d2h(sec.nstate, c->nstate, 4 * (size_t)h.n_nuclei);
+  e = e ? e : d2h(sec.rkey, c->R.key, 8 * (size_t)h.n_reached);
+  // pool slots 0 .. n_blocks - 1 are the handed-out blocks
+  e = e ? e : d2h(sec.bdata, c->C.data, 4 * (size_t)kBrickWords * (size_t)h.n_blocks);
+  if (e) return e;
+  std::vector<ulonglong2> bk((size_t)c->L.buckets);
+  GP_CUDA(c, cudaMemcpyAsync(bk.data(), c->C.bucket, 16 * bk.size(), cudaMemcpyDeviceToHost,
+                             c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  // the key of every pool slot, from the buckets {key, slot + 1}
+  std::vector<unsigned long long> keys((size_t)h.n_blocks, 0ull);
+  int64_t found = 0;
+  for (const ulonglong2& q : bk) {
+    if (q.x == 0ull) continue;
+    if (q.y == 0ull || q.y == kSlotFull || q.y - 1 >= (unsigned long long)h.n_blocks ||
+        keys[q.y - 1] != 0ull)
+      return fail(c, GP_ERR_STATE, "claim table inconsistent");
+    keys[q.y - 1] = q.x;
+    ++found;
+  }
+  if (found != h.n_blocks) return fail(c, GP_ERR_STATE, "claim table inconsistent");
+  if (h.n_blocks) std::memcpy(b + sec.bkey, keys.data(), 8 * keys.size());
+  std::memcpy(b, &h, sizeof h);
+  h.checksum = ckpt_checksum(b, sec.total);
+  std::memcpy(b + offsetof(CkptHeader, checksum), &h.checksum, sizeof h.checksum);
+  return GP_OK;
+}
+
+gp_status gp_load(gp_ctx* c, const void* buf, size_t bytes) {
+  gp_status s = check_ctx(c);
+  if (s) return s;
+  if (c->batch) return fail(c, GP_ERR_STATE, "checkpoints are of single-run contexts");
+  if (c->tape_on) return fail(c, GP_ERR_STATE, "the adjoint tape is recording");
+  s = sync_stats(c);
+  if (s) return s;
+  if (c->n_grains || c->n_live || c->n_obs || c->n_nuclei || c->step || c->hst->reached ||
+      c->hst->claim_used)
+    return fail(c, GP_ERR_STATE, "a checkpoint loads into a new context (no grains, "
+                                 "particles, sites or steps yet)");
+  CkptHeader h;
+  CkptSections sec;
+  if (const char* why = ckpt_invalid(buf, bytes, &h, &sec)) return fail(c, GP_ERR_ARG, why);
+  if (std::memcmp(&h.dom, &c->dom[0], sizeof(gp_domain)) != 0 || h.h != c->h || h.dt != c->dt ||
+      !same_law(h.law, c->law))
+    return fail(c, GP_ERR_ARG, "checkpoint of another domain, h, dt or growth law");
+  if (h.n_rec > c->L.cap) return fail(c, GP_ERR_CAPACITY, "particle capacity");
+  if (h.n_grains > c->L.max_grains) return fail(c, GP_ERR_CAPACITY, "grain capacity");
+  if (h.n_nuclei > c->L.max_nuclei) return fail(c, GP_ERR_CAPACITY, "nucleus capacity");
+  if (h.n_reached > c->L.rcap) return fail(c, GP_ERR_CAPACITY, "reached-site capacity");
+  if (h.n_blocks > c->L.blocks) return fail(c, GP_ERR_CAPACITY, "claim block capacity");
+  if (h.thermal < 0 || h.thermal > 2 || h.periodic < 0 || h.periodic > 7 || h.obs_mode < 0 ||
+      h.obs_mode > 2 || h.melting < 0 || h.melting > 1 || h.step < 0)
+    return fail(c, GP_ERR_ARG, "checkpoint settings out of range");
+  const unsigned char* b = static_cast<const unsigned char*>(buf);
+  // the claim blocks are staged through the position buffer (16 bytes per particle of
+  // capacity, idle between steps), a chunk at a time
+  const int64_t per = (16 * c->L.cap - 16) / (8 + 4 * kBrickWords);
+  if (h.n_blocks > 0 && per < 1)
+    return fail(c, GP_ERR_CAPACITY, "particle capacity too small to stage the claim blocks");
+  int64_t nfz = 0;
+  for (int64_t i = 0; i < h.n_rec; ++i) {
+    int4 v;
+    std::memcpy(&v, b + sec.rec + 16 * (size_t)i, sizeof v);
+    const Rec r = rec_unpack(v);
+    bool ok = r.grain >= 0 && r.grain < h.n_grains && r.dir >= 0 && r.dir <= 5 &&
+              (r.state == ST_ACTIVE || r.state == ST_FROZEN) && r.ell >= 0.f && r.ell < 1.f;
+    for (int a = 0; a < 3; ++a) {
+      const int sa = a == 0 ? r.sx : (a == 1 ? r.sy : r.sz);
+      ok = ok && sa >= -kSiteMax && sa <= kSiteMax;
+    }
+    if (!ok) return fail(c, GP_ERR_ARG, "invalid particle in the checkpoint");
+    nfz += r.state == ST_FROZEN;
+  }
+  // settings first: periodic axes refresh the cell geometry
+  if (h.periodic) {
+    s = gp_set_periodic(c, h.periodic);
+    if (s) return s;
+  }
+  if (h.melting) {
+    s = gp_set_melting(c, 1);
+    if (s) return s;
+  }
+  c->obs_mode = h.obs_mode;
+  if (h.thermal == 1) {  // a thermal grid is an input: the caller sets it again
+    c->thermal = 1;
+    c->P.thermal = 1;
+    c->T0[0] = h.T0;
+    c->Tdot[0] = h.Tdot;
+    c->thermal_set[0] = 1;
+    for (int a = 0; a < 3; ++a) {
+      c->geo[0].G[a] = c->P.geo.G[a] = h.G[a];
+      c->geo[0].xref[a] = c->P.geo.xref[a] = h.xref[a];
+    }
+  }
+  auto h2d = [&](void* dst, size_t off, size_t n) -> gp_status {
+    if (n) GP_CUDA(c, cudaMemcpyAsync(dst, b + off, n, cudaMemcpyHostToDevice, c->st));
+    return GP_OK;
+  };
+  gp_status e = GP_OK;
+  e = e ? e : h2d(c->rec[c->cur], sec.rec, 16 * (size_t)h.n_rec);
+  e = e ? e : h2d(c->gtab, sec.gtab, 64 * (size_t)h.n_grains);
+  e = e ? e : h2d(c->gflags, sec.gflags, 4 * (size_t)h.n_grains);
+  e = e ? e : h2d(c->gdtn, sec.gdtn, 4 * (size_t)h.n_grains);
+  e = e ? e : h2d(c->npos, sec.npos, 16 * (size_t)h.n_nuclei);
+  e = e ? e : h2d(c->ngrain, sec.ngrain, 64 * (size_t)h.n_nuclei);
+  e = e ? e : h2d(c->nstate, sec.nstate, 4 * (size_t)h.n_nuclei);
+  e = e ? e : h2d(c->R.key, sec.rkey, 8 * (size_t)h.n_reached);
+  if (e) return e;
+  char* stg = reinterpret_cast<char*>(c->pos4);
+  for (int64_t b0 = 0; b0 < h.n_blocks; b0 += per) {
+    const int64_t m = std::min(per, h.n_blocks - b0);
+    unsigned long long* dk = reinterpret_cast<unsigned long long*>(stg);
+    uint32_t* dw = reinterpret_cast<uint32_t*>(stg + align16(8 * (size_t)m));
+    e = e ? e : h2d(dk, sec.bkey + 8 * (size_t)b0, 8 * (size_t)m);
+    e = e ? e : h2d(dw, sec.bdata + 4 * (size_t)kBrickWords * (size_t)b0,
+                    4 * (size_t)kBrickWords * (size_t)m);
+    if (e) return e;
+    launch_claim_restore(c->C, dk, dw, m, c->st);
+    GP_CUDA(c, cudaGetLastError());
+    GP_CUDA(c, cudaStreamSynchronize(c->st));  // before the staging buffer is reused
+  }
+  // the counters as saved, but for what the load itself sets: every particle is in the
+  // dynamic store, the reached sites are linked again before their next query, and the
+  // claim pool holds the blocks just inserted
+  GP_CUDA(c, cudaMemcpyAsync(c->hst, c->dst, sizeof(DevStats), cudaMemcpyDeviceToHost, c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  DevStats nd = h.stats;
+  nd.claim_used = c->hst->claim_used;
+  nd.err = c->hst->err;
+  nd.n_live = (unsigned long long)h.n_rec;
+  nd.n_frozen = (unsigned long long)nfz;
+  nd.n_grains = (unsigned long long)h.n_grains;
+  nd.reached = (unsigned long long)h.n_reached;
+  nd.linked = 0ull;
+  nd.step = (unsigned long long)h.step;
+  nd.stamp = c->hst->stamp;
+  *c->hst = nd;
+  GP_CUDA(c, cudaMemcpyAsync(c->dst, c->hst, sizeof(DevStats), cudaMemcpyHostToDevice, c->st));
+  GP_CUDA(c, cudaStreamSynchronize(c->st));
+  c->n_live = h.n_rec;
+  c->n_grains = h.n_grains;
+  c->n_nuclei = (int)h.n_nuclei;
+  c->step = h.step;
+  c->keys_valid = false;
+  s = obs_reset(c);
+  if (s) return s;
+  return sync_stats(c);
 }
 
 gp_status gp_grain_map(gp_ctx* c, const gp_voxel_grid* g, int32_t* out, int32_t flags) {

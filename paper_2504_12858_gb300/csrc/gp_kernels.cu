@@ -1418,6 +1418,31 @@ __global__ void k_mark_sites(Params P, const int4* __restrict__ sites, int64_t m
 
 // shell seeding: for every (grain, target offset t with |t|_1 = n0 + 1) one ACTIVE
 // particle at the site reached from the lowest axis with t_a != 0.
+// re-inserts m claim blocks of a checkpoint into an empty claim table: block key i
+// (grain g + 1, block coordinates + 512, 10 bits each) gets a pool slot through the
+// same warp-wide insert as every claim, and its kBrickWords words are copied there
+__global__ void k_claim_restore(Claims C, const unsigned long long* __restrict__ keys,
+                                const uint32_t* __restrict__ words, int64_t m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = i < m;
+  int g = 0, tx = 0, ty = 0, tz = 0;
+  if (ok) {
+    const unsigned long long k = keys[i];
+    g = (int)(k >> 30) - 1;
+    // a site inside the block (its last corner: every block of a site in range has one)
+    tx = ((int)((k >> 20) & 1023u) - 512) * 8 + 7;
+    ty = ((int)((k >> 10) & 1023u) - 512) * 8 + 7;
+    tz = ((int)(k & 1023u) - 512) * 8 + 7;
+  }
+  BlockCache bc;
+  int sh = 0;
+  const uint32_t* w = warp_claim_word(C, ok, g, tx, ty, tz, true, sh, bc);
+  if (!w) return;
+  uint32_t* d = C.data + (size_t)bc.b * kBrickWords;
+  const uint32_t* src = words + (size_t)i * kBrickWords;
+  for (int q = 0; q < kBrickWords; ++q) d[q] = src[q];
+}
+
 __global__ void k_seed_shell(Params P, const int32_t* __restrict__ grains, int64_t ng,
                              const short4* __restrict__ toff, int64_t nt, float ell0,
                              int4* __restrict__ rout, int64_t cap, unsigned long long* counter,
@@ -2229,6 +2254,11 @@ void launch_append(const int4* src, int64_t m, int4* rout, int64_t base, cudaStr
 void launch_mark_sites(const Params& P, const int4* sites, int64_t m, int reached, int claimed,
                        const Claims& C, const Reached& R, cudaStream_t st) {
   if (m > 0) k_mark_sites<<<blocks(m), 256, 0, st>>>(P, sites, m, reached, claimed, C, R);
+}
+
+void launch_claim_restore(const Claims& C, const unsigned long long* keys, const uint32_t* words,
+                          int64_t m, cudaStream_t st) {
+  if (m > 0) k_claim_restore<<<blocks(m), 256, 0, st>>>(C, keys, words, m);
 }
 
 void launch_seed_shell(const Params& P, const int32_t* grains, int64_t ng, const short4* toff,

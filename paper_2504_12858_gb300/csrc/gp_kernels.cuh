@@ -88,6 +88,9 @@ void launch_run_counts(const Params& P, const int4* rec, int64_t n, int nruns,
 void launch_append(const int4* src, int64_t m, int4* rout, int64_t base, cudaStream_t st);
 void launch_mark_sites(const Params& P, const int4* sites, int64_t m, int reached, int claimed,
                        const Claims& C, const Reached& R, cudaStream_t st);
+// inserts m claim blocks (keys, kBrickWords words each) into an empty claim table
+void launch_claim_restore(const Claims& C, const unsigned long long* keys, const uint32_t* words,
+                          int64_t m, cudaStream_t st);
 void launch_seed_shell(const Params& P, const int32_t* grains, int64_t ng, const short4* toff,
                        int64_t nt, float ell0, int4* rout, int64_t cap,
                        unsigned long long* counter, const Claims& C, uint32_t* err,

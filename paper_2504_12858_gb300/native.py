@@ -106,6 +106,10 @@ SIGNATURES = {
     "gp_load_particles": (C.c_int, [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_int64]),
     "gp_add_sites": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int32, C.c_int32]),
     "gp_get_reached": (C.c_int, [_P, C.c_int64, _P, _P, C.POINTER(C.c_int64)]),
+    "gp_save": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "gp_load": (C.c_int, [_P, _P, C.c_size_t]),
+    "gp_checkpoint_check": (C.c_int, [_P, C.c_size_t, C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64)]),
     "gp_profile": (C.c_int, [_P, C.c_int32]),
     "gp_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(gp_kernel_prof),
                                   C.POINTER(C.c_int32)]),
@@ -174,6 +178,17 @@ def _ptr(a):
 
 def _dptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def checkpoint_check(data: bytes) -> dict:
+    """Host-only check of a checkpoint (``gp_checkpoint_check``): its step counter and
+    particle count; raises GPError (GP_ERR_ARG) if it is not an intact checkpoint."""
+    data = bytes(data)
+    step, n = C.c_int64(0), C.c_int64(0)
+    st = load().gp_checkpoint_check(data, len(data), C.byref(step), C.byref(n))
+    if st != 0:
+        raise GPError(st, "not an intact checkpoint")
+    return {"step": int(step.value), "n_particles": int(n.value)}
 
 
 def domain(lo, hi):
@@ -416,6 +431,20 @@ class Sim:
         s = np.zeros((m, 3), np.int32)
         self._check(L.gp_get_reached(self._h, m, _ptr(g), _ptr(s), C.byref(n)))
         return g, s
+
+    def gp_save(self) -> bytes:
+        """Checkpoint of the context between steps (``gp_save``), as bytes."""
+        L = load()
+        n = C.c_size_t(0)
+        self._check(L.gp_save(self._h, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(max(int(n.value), 1))
+        self._check(L.gp_save(self._h, buf, int(n.value), C.byref(n)))
+        return buf.raw[:int(n.value)]
+
+    def gp_load(self, data: bytes):
+        """Loads a checkpoint of ``gp_save`` into this new context (``gp_load``)."""
+        data = bytes(data)
+        self._check(load().gp_load(self._h, data, len(data)))
 
     def gp_grain_map(self, origin, spacing, n, out=None):
         """Host numpy result, or into a torch CUDA int32 tensor ``out``."""

@@ -57,3 +57,22 @@ def test_product_path_has_no_oracle_import():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "gp_oracle" not in txt, f
+
+
+def test_checkpoint_check_needs_no_gpu():
+    # the host-only check of gp_checkpoint_check refuses what is not an intact checkpoint
+    # (the round trip through gp_save / gp_load is a GPU test)
+    import ctypes as C
+
+    import numpy as np
+    from paper_2504_12858_gb300 import native
+    L = native.load()
+    step, n = C.c_int64(-1), C.c_int64(-1)
+    assert L.gp_checkpoint_check(None, 0, C.byref(step), C.byref(n)) == 1
+    magic = b"GPCKPT\x00\x01"
+    g = np.random.default_rng(3)
+    for data in (b"", magic, magic + bytes(4096), bytes(g.integers(0, 256, 4096, np.uint8))):
+        assert L.gp_checkpoint_check(data, len(data), C.byref(step), C.byref(n)) == 1
+        with pytest.raises(native.GPError):
+            native.checkpoint_check(data)
+    assert (step.value, n.value) == (-1, -1)        # outputs untouched on a refusal
