@@ -13,7 +13,8 @@ from .inputs import Workload
 
 
 def batch_from(runs: list[Workload], capacity: int, reached_capacity: int = 0,
-               claim_blocks: int = 0, stream=None, device="cuda") -> native.Batch:
+               claim_blocks: int = 0, stream=None, device="cuda",
+               arena_fill=None) -> native.Batch:
     w0 = runs[0]
     for w in runs:
         if (w.h, w.dt, tuple(w.a), tuple(w.b), w.T_L) != (w0.h, w0.dt, tuple(w0.a), tuple(w0.b),
@@ -26,7 +27,8 @@ def batch_from(runs: list[Workload], capacity: int, reached_capacity: int = 0,
     b = native.Batch([(w.lo, w.hi) for w in runs], w0.h, w0.dt, w0.a, w0.b, w0.T_L,
                      capacity=capacity, reached_capacity=reached_capacity,
                      claim_blocks=claim_blocks, max_grains=n_seed + n_nuc + 16,
-                     max_nuclei=n_nuc + 16, stream=stream, device=device)
+                     max_nuclei=n_nuc + 16, stream=stream, device=device,
+                     arena_fill=arena_fill)
     for r, w in enumerate(runs):
         a = w.analytic
         b.gp_run_set_thermal_analytic(r, a["T0"], a["G"], a["xref"], a["Tdot"])

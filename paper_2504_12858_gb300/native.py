@@ -218,15 +218,16 @@ class Sim:
 
     def __init__(self, lo, hi, h, dt, a, b, T_L, capacity, reached_capacity=0,
                  claim_blocks=0, max_grains=0, max_nuclei=0, grid_nodes=0, tape_steps=0,
-                 stream=None, device="cuda", solute_nodes=0, tape_checkpoint_every=0):
+                 stream=None, device="cuda", solute_nodes=0, tape_checkpoint_every=0,
+                 arena_fill=None):
         self.lo, self.hi = tuple(lo), tuple(hi)
         self._open([(lo, hi)], False, h, dt, a, b, T_L, capacity, reached_capacity,
                    claim_blocks, max_grains, max_nuclei, grid_nodes, tape_steps, stream, device,
-                   solute_nodes, tape_checkpoint_every)
+                   solute_nodes, tape_checkpoint_every, arena_fill)
 
     def _open(self, domains, batch, h, dt, a, b, T_L, capacity, reached_capacity, claim_blocks,
               max_grains, max_nuclei, grid_nodes, tape_steps, stream, device, solute_nodes=0,
-              tape_checkpoint_every=0):
+              tape_checkpoint_every=0, arena_fill=None):
         import torch
         self._torch = torch
         L = load()
@@ -253,6 +254,9 @@ class Sim:
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         self.arena = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        if arena_fill is not None:  # tests: a known byte where the library must write first
+            self.arena.fill_(int(arena_fill))
+            torch.cuda.synchronize(self.device)
         mem.arena = self.arena.data_ptr()
         mem.arena_bytes = nb.value
         self.arena_bytes = int(nb.value)
@@ -491,10 +495,12 @@ class Batch(Sim):
     run; the run-level calls take the run index first."""
 
     def __init__(self, domains, h, dt, a, b, T_L, capacity, reached_capacity=0,
-                 claim_blocks=0, max_grains=0, max_nuclei=0, stream=None, device="cuda"):
+                 claim_blocks=0, max_grains=0, max_nuclei=0, stream=None, device="cuda",
+                 arena_fill=None):
         self.domains = [(tuple(lo), tuple(hi)) for lo, hi in domains]
         self._open(self.domains, True, h, dt, a, b, T_L, capacity, reached_capacity,
-                   claim_blocks, max_grains, max_nuclei, 0, 0, stream, device)
+                   claim_blocks, max_grains, max_nuclei, 0, 0, stream, device,
+                   arena_fill=arena_fill)
 
     def gp_run_set_thermal_analytic(self, run, T0, G, xref, Tdot):
         th = gp_thermal_analytic()

@@ -11,7 +11,12 @@ provoke each case on purpose, in forms that fault, trap or hang nothing:
   poll limit, and the device stays usable;
 - zero or non-finite quaternions, non-finite nucleation data and degenerate
   thermal grids: GP_ERR_ARG, with the context still usable;
-- a particle store too small: GP_ERR_CAPACITY.
+- a particle store too small: GP_ERR_CAPACITY;
+- results that do not depend on what the device memory held before the library
+  initialised it: the arena filled with 0x00, 0xFF or 0xA5 bytes gives bit-identical
+  particles, reached sites, counters and grain maps, in a single run and in a batch
+  (the stand-in for the poison-filled buffers of a memory checker, which is closed on
+  this pool).
 """
 import math
 import time
@@ -19,8 +24,8 @@ import time
 import numpy as np
 import pytest
 
-from paper_2504_12858_gb300 import inputs
-from tests.helpers import sim_from
+from paper_2504_12858_gb300 import ensemble, inputs
+from tests.helpers import canon, sim_from
 
 pytestmark = pytest.mark.gpu
 
@@ -117,3 +122,66 @@ def test_particle_store_too_small_is_capacity():
     with pytest.raises(native.GPError) as e:
         s.gp_step(200)
     assert e.value.status == GP_ERR_CAPACITY
+
+
+def _poly(seed, L=60e-6, n_nuclei=30):
+    g = inputs.rng(seed)
+    T_L = 1000.0
+    return inputs.Workload(name="poly", lo=(0, 0, 0), hi=(L,) * 3, h=2e-6, dt=1.3e-3, a=(1e-5,),
+                           b=(2.0,), T_L=T_L, steps=40, seeds=g.random((12, 3)) * L,
+                           quats=inputs.shoemake_quaternions(12, g),
+                           analytic=dict(T0=T_L - 4.0, G=(3e4, -2e4, 1e4), xref=(L / 2,) * 3,
+                                         Tdot=-20.0),
+                           nuclei=dict(pos=g.random((n_nuclei, 3)) * L,
+                                       dTn=4.0 + 1.5 * g.random(n_nuclei),
+                                       quat=inputs.shoemake_quaternions(n_nuclei, g)))
+
+
+def _bits(p):
+    p = canon(p)
+    return {k: (v.view(np.uint32) if v.dtype == np.float32 else v) for k, v in p.items()}
+
+
+def _equal_particles(pa, pb):
+    assert pa.keys() == pb.keys()
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+
+
+MEM = dict(capacity=400000, reached_capacity=2000000, claim_blocks=60000)
+
+
+@pytest.mark.parametrize("fill", [0xFF, 0xA5])
+def test_results_do_not_depend_on_the_arena_contents(fill):
+    w = _poly(5)
+    out = []
+    for f in (0x00, fill):
+        s = sim_from(w, arena_fill=f, **MEM)
+        s.gp_step(40)
+        g, x = s.gp_get_reached()
+        out.append((_bits(s.gp_get_particles()), s.gp_stats(),
+                    s.gp_grain_map((0, 0, 0), (2e-6,) * 3, (30, 30, 30)),
+                    sorted(zip(g.tolist(), map(tuple, x.tolist())))))
+        s.close()
+    (pa, sa, ma, ra), (pb, sb, mb, rb) = out
+    assert sa["n_nucleated"] > 0 and sa["n_frozen"] > 0
+    _equal_particles(pa, pb)
+    assert sa == sb
+    assert np.array_equal(ma, mb)
+    assert ra == rb
+
+
+def test_batch_results_do_not_depend_on_the_arena_contents():
+    runs = [_poly(6), _poly(7)]
+    out = []
+    for f in (0x00, 0xFF):
+        b = ensemble.batch_from(runs, arena_fill=f, **MEM)
+        b.gp_step(40)
+        out.append(([_bits(ensemble.run_particles(b, r)) for r in range(len(runs))],
+                    b.gp_stats()))
+        b.close()
+    (pa, sa), (pb, sb) = out
+    assert sa["n_nucleated"] > 0
+    for a, c in zip(pa, pb):
+        _equal_particles(a, c)
+    assert sa == sb
