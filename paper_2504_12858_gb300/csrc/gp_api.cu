@@ -53,7 +53,7 @@ struct Layout {
       sgrid, runs,
       rtherm, rcount, tape_post, tape_par, tape_code, tape_ckpt, tape_replay, tape_svals,
       tape_grad, gcnt, gofs, gfill,
-      gbsum, gkey, gdest, orec[2], opos[2], okey[2], otcnt, ogofs[2], msrc, total;
+      gbsum, gkey, gdest, orec[2], opos[2], okey[2], otcnt, ogofs[2], msrc, rbuild, total;
   uint32_t ngroups = 0;  // one run: cell groups of the record grouping
 };
 
@@ -219,6 +219,7 @@ bool make_layout(const gp_domain* d, int nruns, bool batch, double h, const gp_m
   L->gofs = take(4 * (size_t)L->ngroups + 16);
   L->gfill = take(4 * (size_t)L->ngroups + 16);
   L->gbsum = take(4 * (((size_t)L->ngroups + 255) / 256) + 16);
+  L->rbuild = take(4 * (size_t)L->ngroups + 16);  // build that last wrote a group resident
   L->gkey = take(batch ? 16 : 4 * cap + 16);   // one run: cell keys in grouped order
   L->gdest = take(batch ? 16 : 4 * cap + 16);  // and the sorted position of each
   // one run: the obstacle store (FROZEN records ordered by cell key, positions, keys,
@@ -435,6 +436,11 @@ struct gp_ctx {
   int ocur = 0;
   double obs_carry = 0;
   int obs_mode = 1;  // 0 off, 1 flushes when carrying costs as much as merging, 2 every step
+  // builds of the single-run ordering (tags in L.rbuild) and whether the next build may keep
+  // the table entries of groups that hold only obstacles: not after a flush, a change of
+  // the store, a wrap of the table stamp or a build by the inspection
+  uint32_t nbuild = 1;
+  bool table_reuse = false;
 };
 
 namespace {
@@ -581,6 +587,7 @@ bool obs_usable(const gp_ctx* c) {
 gp_status obs_reset(gp_ctx* c) {
   c->n_obs = 0;
   c->obs_carry = 0;
+  c->table_reuse = false;
   return GP_OK;
 }
 
@@ -728,6 +735,7 @@ gp_status create_ctx(const gp_domain* domains, int nruns, bool batch, double h, 
   cudaStream_t s = c->st;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMemsetAsync(c->cells, 0, 16 * L.nseg, s);
+  if (L.ngroups) e = e ? e : cudaMemsetAsync(c->base + L.rbuild, 0, 4 * (size_t)L.ngroups, s);
   e = e ? e : cudaMemsetAsync(c->R.head, 0xff, 4 * L.nheads, s);
   e = e ? e : cudaMemsetAsync(c->C.bucket, 0, 16 * (size_t)L.buckets, s);
   e = e ? e : cudaMemsetAsync(c->C.data, 0, 4 * kBrickWords * (size_t)L.blocks, s);
@@ -1022,6 +1030,7 @@ gp_status gp_set_periodic(gp_ctx* c, int32_t axes) {
   c->P.launch = old.launch;
   // cell geometry changed: keys are recomputed and the reached sites relinked
   c->keys_valid = false;
+  c->table_reuse = false;
   GP_CUDA(c, cudaMemsetAsync(c->R.head, 0xff, 4 * c->L.nheads, c->st));
   GP_CUDA(c, cudaMemsetAsync(&c->dst->linked, 0, sizeof(unsigned long long), c->st));
   GP_CUDA(c, cudaStreamSynchronize(c->st));
@@ -1088,6 +1097,7 @@ gp_status gp_inspect_order(gp_ctx* c, int32_t which, int64_t cap, uint32_t* keys
       GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
       c->stamp = 1;
     }
+    c->table_reuse = false;  // this build copies every obstacle into the sequence
     GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
     GP_CUDA(c, cudaMemsetAsync(&c->dst->n_actx, 0, sizeof(uint32_t), c->st));
     launch_group_build(P, static_cast<const uint32_t*>(c->sb.keys[0]), nd, c->L.ngroups,
@@ -1386,6 +1396,13 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
       if (++c->stamp > 0xffffu) {
         GP_CUDA(c, cudaMemsetAsync(c->cells, 0, 16 * c->L.nseg, c->st));
         c->stamp = 1;
+        c->table_reuse = false;
+      }
+      if (++c->nbuild == 0xffffffffu) {  // build tags start again
+        GP_CUDA(c, cudaMemsetAsync(at<uint32_t>(c, c->L.rbuild), 0, 4 * (size_t)c->L.ngroups,
+                                   c->st));
+        c->nbuild = 2;
+        c->table_reuse = false;
       }
       int4* sorted = c->rec[c->cur ^ 1];  // the records in grouped order
       GP_CUDA(c, cudaMemsetAsync(&c->dst->n_act, 0, sizeof(unsigned long long), c->st));
@@ -1424,8 +1441,11 @@ gp_status gp_step(gp_ctx* c, int32_t nsteps) {
                          reinterpret_cast<uint8_t*>(c->site_slot), c->cells, c->stamp, c->act,
                          c->dst, c->sms, &c->prof, c->st, at<uint32_t>(c, c->L.okey[o]),
                          at<float4>(c, c->L.opos[o]), at<uint32_t>(c, c->L.ogofs[o]),
-                         obs ? c->n_obs : 0, msrc, obase);
+                         obs ? c->n_obs : 0, msrc, obase, at<uint32_t>(c, c->L.rbuild),
+                         c->nbuild, c->table_reuse && obase != 0u ? 1 : 0);
       GP_CUDA(c, cudaGetLastError());
+      // a flush replaces the store that the entries of resident groups point into
+      c->table_reuse = obase != 0u && !flush;
       if (flush) {
         c->prof.begin(K_OBS);
         launch_obs_flush(msrc, skeys, c->pos4, nseq, at<uint32_t>(c, c->L.otcnt),

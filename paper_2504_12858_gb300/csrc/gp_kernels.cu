@@ -1740,7 +1740,8 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     uint32_t* __restrict__ dest, uint4* __restrict__ tab, uint32_t stamp, DevStats* st,
     const uint32_t* __restrict__ okey, const float4* __restrict__ opos,
     const uint32_t* __restrict__ ogofs, int64_t no, float4* __restrict__ pos4,
-    uint32_t* __restrict__ skeys, uint32_t* __restrict__ msrc, uint32_t obase) {
+    uint32_t* __restrict__ skeys, uint32_t* __restrict__ msrc, uint32_t obase,
+    uint32_t* __restrict__ rbuild, uint32_t build, int reuse) {
   __shared__ uint4 s_c4[8][32 * kGroupRow / 4];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t* c = reinterpret_cast<uint32_t*>(s_c4[w]);
@@ -1751,6 +1752,28 @@ __global__ void __launch_bounds__(256, 6) k_group_order(
     const uint32_t os = no ? __ldg(ogofs + g) : 0u, oe = no ? __ldg(ogofs + g + 1) : 0u;
     if (s >= e && os >= oe) continue;  // warp-uniform
     const bool resident = obase != 0u && s >= e;  // obstacles only: read in place
+    if (resident && rbuild) {
+      // written as resident by the previous build, with the same store (reuse): its
+      // entries are the previous build's, given this build's stamp
+      if (reuse && rbuild[g] == build - 1u) {  // warp-uniform
+        const uint64_t sg = seg0 + ((uint64_t)g << (kGroupShift - kSegShift)) + 2 * lane;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint4 t = tab[sg + h];
+          if ((t.y >> 16) == stamp - 1u) {
+            t.y = (stamp << 16) | (t.y & 0xffffu);
+            tab[sg + h] = t;
+          }
+        }
+        if (msrc)
+          for (uint32_t i = os + lane; i < oe; i += 32) msrc[s + i] = 0x80000000u | i;
+        __syncwarp();
+        if (lane == 0) rbuild[g] = build;
+        continue;
+      }
+      __syncwarp();
+      if (lane == 0) rbuild[g] = build;  // written below as resident
+    }
 #pragma unroll
     for (int q = 0; q < kGroupRow / 4; ++q) s_c4[w][q * 32 + lane] = make_uint4(0, 0, 0, 0);
     __syncwarp();
@@ -2335,7 +2358,7 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
                         uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
                         int sms, ProfHook* prof, cudaStream_t st, const uint32_t* okey,
                         const float4* opos, const uint32_t* ogofs, int64_t no, uint32_t* msrc,
-                        uint32_t obase) {
+                        uint32_t obase, uint32_t* rbuild, uint32_t build, int reuse) {
   if (n <= 0) return;
   if (prof) prof->begin(K_GROUP);
   cudaMemsetAsync(gcnt, 0, 4 * (size_t)ng, st);
@@ -2351,7 +2374,8 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
   // one wave: 32 KB of shared memory per CTA leaves room for six CTAs per SM
   k_group_order<<<(unsigned)(sms * 6), 256, 0, st>>>(gkey, gofs, gbsum, ng, n, P.geo.seg0, gdest,
                                                      tab, stamp, dst, okey, opos, ogofs, no, pos4,
-                                                     skeys, msrc, no ? obase : 0u);
+                                                     skeys, msrc, no ? obase : 0u, rbuild,
+                                                     build, reuse);
   k_group_gather<<<blocks(n), 256, 0, st>>>(P, gkey, perm, gdest, n, rin, rout, pos4, skeys, svals,
                                             sact, msrc, n + no, dst);
   k_act_list<<<blocks(n, 256 * kActItems), 256, 0, st>>>(sact, n, act, dst);

@@ -23,7 +23,10 @@ void launch_build(const Params& P, const uint64_t* skeys, const uint32_t* svals,
 // moving records and the no obstacles of (okey, opos, group offsets ogofs): positions
 // pos4, keys skeys, sources msrc, cell table tab.  obase != 0: okey and opos are entries
 // obase.. of skeys and pos4, and a group without moving records is read there in place
-// (its table entries point into the store; its places in the sequence hold no copy)
+// (its table entries point into the store; its places in the sequence hold no copy).
+// rbuild (one tag per group), build and reuse: such a group that the previous build (tag
+// build - 1) also wrote as resident keeps its table entries, restamped, when reuse says
+// that the store and the table are those of the previous build
 void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32_t ng,
                         uint32_t* gcnt, uint32_t* gofs, uint32_t* gbsum, uint32_t* gfill,
                         uint32_t* perm, uint32_t* gkey, uint32_t* gdest, const int4* rin,
@@ -31,7 +34,8 @@ void launch_group_build(const Params& P, const uint32_t* keys, int64_t n, uint32
                         uint8_t* sact, uint4* tab, uint32_t stamp, uint32_t* act, DevStats* dst,
                         int sms, ProfHook* prof, cudaStream_t st, const uint32_t* okey = nullptr,
                         const float4* opos = nullptr, const uint32_t* ogofs = nullptr,
-                        int64_t no = 0, uint32_t* msrc = nullptr, uint32_t obase = 0);
+                        int64_t no = 0, uint32_t* msrc = nullptr, uint32_t obase = 0,
+                        uint32_t* rbuild = nullptr, uint32_t build = 0, int reuse = 0);
 // a batch: n records, sorted like pos4.  A single run: pos4, skeys and tab hold the n
 // entries of the cell-ordered sequence (moving particles and obstacles), rs the nrec
 // records in grouped order, mpos[j] the position of record j in the sequence.
