@@ -669,13 +669,17 @@ def _workload_run(w, steps, capacity, dev, **kw):
             "kernels_ms_per_step": {k["name"]: round(k["total_ms"] / steps, 4) for k in prof}}
 
 
-def application_workloads(dev):
+APPLICATIONS = ("single_grain", "columnar_slab", "weld_natural")
+
+
+def application_workloads(dev, only=None):
     """Configurations 1 to 3 at their stated sizes: the single grain (400 steps),
     competitive columnar growth in the 1 x 1 x 0.05 mm slab (600 steps) and growth from
     the fusion line of the weld plate (the base metal cut by the t = 0 liquidus, 500
-    steps).  Set-up (input generation, seeding, loading) is outside the timing."""
+    steps); only: one of APPLICATIONS.  Set-up (input generation, seeding, loading) is
+    outside the timing."""
     import torch
-    from paper_2504_12858_gb300 import inputs, native
+    from paper_2504_12858_gb300 import native
     out = {}
 
     def guarded(name, fn):
@@ -685,6 +689,17 @@ def application_workloads(dev):
             out[name]["error"] = str(e)
         torch.cuda.empty_cache()
 
+    if only in (None, "single_grain"):
+        _single_grain(out, guarded, dev)
+    if only in (None, "columnar_slab"):
+        _columnar_slab(out, guarded, dev)
+    if only in (None, "weld_natural"):
+        _weld_natural(out, guarded, dev)
+    return out
+
+
+def _single_grain(out, guarded, dev):
+    from paper_2504_12858_gb300 import inputs
     w = inputs.single_grain()
     out["single_grain"] = dict(
         workload="single_grain: 200 um cube, one grain, uniform dT = 5 K, v = 1e-5 dT^2, "
@@ -696,6 +711,10 @@ def application_workloads(dev):
     # same run as a batch context of one replays its steps from CUDA graphs
     guarded("single_grain", lambda: {"as_batch_of_one": _batch_of_one(
         w, w.steps, 200000, dev, reached_capacity=4000000)})
+
+
+def _columnar_slab(out, guarded, dev):
+    from paper_2504_12858_gb300 import inputs
     w = inputs.columnar_slab()
     out["columnar_slab"] = dict(
         workload="columnar_slab: 1x1x0.05 mm, 50 bottom seeds, G = 1e4 K/m, Tdot = 10 K/s, "
@@ -704,6 +723,10 @@ def application_workloads(dev):
             lambda: _workload_run(w, w.steps, 2000000, dev, reached_capacity=6000000))
     guarded("columnar_slab", lambda: {"as_batch_of_one": _batch_of_one(
         w, w.steps, 2000000, dev, reached_capacity=6000000)})
+
+
+def _weld_natural(out, guarded, dev):
+    from paper_2504_12858_gb300 import inputs
     t0 = time.perf_counter()
     w = inputs.weld_natural()
     out["weld_natural"] = dict(
@@ -717,7 +740,6 @@ def application_workloads(dev):
     guarded("weld_natural",
             lambda: _workload_run(w, w.steps, 160000000, dev, reached_capacity=1200000000,
                                   claim_blocks=5000000))
-    return out
 
 
 def run_native(args, rank, world, local_rank):
@@ -907,9 +929,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end context")
     ap.add_argument("--profile-warmup", action="store_true",
                     help="capture mode: the per-kernel profile covers the warm-up steps too")
+    ap.add_argument("--application", choices=APPLICATIONS,
+                    help="time one of configurations 1 to 3 alone and print its line")
     ap.add_argument("--ncu-digest", nargs=2, metavar=("CSV", "LOG"),
                     help="write profiles/ncu_traffic.json from an ncu capture and its plain log")
     args = ap.parse_args()
+    if args.application:         # one of configurations 1 to 3 alone, on cuda:0
+        import torch
+        r = application_workloads(torch.device("cuda:0"), only=args.application)
+        print(json.dumps({"application": args.application, **r[args.application]}))
+        return 0 if "error" not in r[args.application] else 1
     if args.ncu_digest:
         d = ncu_digest(*args.ncu_digest)
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json"), "w") as f:
