@@ -177,3 +177,16 @@ def test_bench_oracle_setup_matches_the_tests():
         pa, pb = a.particles(), b.particles()
         for f in pa:
             assert np.array_equal(pa[f], pb[f]), (w.name, f)
+
+
+def test_application_option_names_every_timed_application():
+    # `bench.py --application NAME` runs one of the applications the full bench times;
+    # the option's choices and the timed sections name the same three configurations
+    import inspect
+
+    import bench
+    assert bench.APPLICATIONS == ("single_grain", "columnar_slab", "weld_natural")
+    src = inspect.getsource(bench.application_workloads)
+    for name in bench.APPLICATIONS:
+        assert f'only in (None, "{name}")' in src
+        assert callable(getattr(bench, "_" + name))
