@@ -605,9 +605,10 @@ __global__ void __launch_bounds__(256, 8) k_advance(Params P, StepArgs S, int4* 
     bool active = false, froze = false, clamped = false;
     bool crossing = false;
     int g = 0, sx = 0, sy = 0, sz = 0;
-    // only the state word is read before the contact search; the record is read after
-    // it, so that it does not occupy registers during the search
-    if (j >= 0 && ((((uint32_t)__ldg(&rs[j].z)) >> 20) & 3u) == (uint32_t)ST_ACTIVE) {
+    // a single run lists ACTIVE records only (the build's state bytes); a batch checks the
+    // state word.  The record is read after the contact search, so that it does not occupy
+    // registers during the search
+    if (j >= 0 && (!BATCH || ((((uint32_t)__ldg(&rs[j].z)) >> 20) & 3u) == (uint32_t)ST_ACTIVE)) {
       active = true;
       const float4 q = __ldg(pos4 + (BATCH ? j : (int64_t)__ldg(mpos + j)));
       const float3 p = make_float3(q.x, q.y, q.z);
